@@ -1,0 +1,102 @@
+"""Chebyshev machinery of the fiber discretisation (oracle; test infrastructure).
+
+Sec. 3.1.3 (Eq. cheb-basis): a centreline is X(alpha) = sum_k Xhat_k T_k(alpha)
+on alpha in [-1, 1] with collocation points alpha_k = cos(k pi / p),
+k = 0..p (N = p + 1 points, endpoints included).  Derivatives are exact
+operations on the coefficient series (Sec. 3.1.3) and smooth integrals use
+Clenshaw-Curtis weights (Sec. 3.1.4).
+
+Everything here is built from numpy.polynomial.chebyshev (evaluation,
+differentiation, integration) and dense linear solves: slow and plain.
+"""
+from __future__ import annotations
+
+import numpy as np
+from numpy.polynomial import chebyshev as C
+
+
+def nodes(N: int) -> np.ndarray:
+    """alpha_k = cos(k pi/(N-1)), k = 0..N-1 (Sec. 3.1.3)."""
+    return np.cos(np.pi * np.arange(N) / (N - 1))
+
+
+def first_kind(M: int) -> np.ndarray:
+    """M Chebyshev points of the first kind, cos((2j+1) pi / (2M)); the
+    rectangular-collocation row points (velocity rows: M = N-4, tension rows:
+    M = N-2)."""
+    return np.cos(np.pi * (2.0 * np.arange(M) + 1.0) / (2.0 * M))
+
+
+def vander(x: np.ndarray, n: int) -> np.ndarray:
+    """V[i, j] = T_j(x_i), j < n."""
+    return C.chebvander(np.asarray(x, float), n - 1)
+
+
+def values_to_coeffs(values: np.ndarray) -> np.ndarray:
+    """Chebyshev coefficients of the degree N-1 interpolant of nodal values
+    (rows = nodes), by solving the Chebyshev-Vandermonde system exactly."""
+    N = values.shape[0]
+    return np.linalg.solve(vander(nodes(N), N), values)
+
+
+def cc_weights(N: int) -> np.ndarray:
+    """Clenshaw-Curtis weights on the N nodes (Sec. 3.1.4): w = integral over
+    [-1,1] of each Lagrange cardinal function, i.e. V^T w = moments with
+    moment_j = int T_j = 2/(1-j^2) for even j, 0 for odd j."""
+    mom = np.zeros(N)
+    j = np.arange(0, N, 2).astype(float)
+    mom[0::2] = 2.0 / (1.0 - j * j)
+    return np.linalg.solve(vander(nodes(N), N).T, mom)
+
+
+def series_at(coef: np.ndarray, x, m: int = 0) -> np.ndarray:
+    """m-th alpha-derivative of the series `coef` [n, 3] at the points x -> [len(x), 3]."""
+    x = np.atleast_1d(np.asarray(x, float))
+    c = C.chebder(coef, m, axis=0) if m > 0 else coef
+    if c.shape[0] == 0:
+        return np.zeros((x.shape[0], coef.shape[1]))
+    return C.chebval(x, c, tensor=True).T
+
+
+def nodal_deriv_matrix(N: int, x: np.ndarray, m: int) -> np.ndarray:
+    """Matrix mapping nodal values at the N nodes to the m-th derivative of
+    their interpolant at the points x."""
+    cols = []
+    Vinv = np.linalg.inv(vander(nodes(N), N))
+    for j in range(N):
+        e = np.zeros(N)
+        e[j] = 1.0
+        cj = C.chebder(e, m) if m > 0 else e
+        cols.append(C.chebval(np.asarray(x, float), cj) if cj.size else np.zeros(len(x)))
+    Tm = np.stack(cols, axis=1)          # [len(x), N]: T_j^{(m)}(x)
+    return Tm @ Vinv
+
+
+def integrated_T(j: int, m: int) -> np.ndarray:
+    """Coefficients of I^m T_j: m-fold integral of T_j from alpha = -1 (each
+    antiderivative vanishes at -1)."""
+    e = np.zeros(j + 1)
+    e[j] = 1.0
+    return C.chebint(e, m, lbnd=-1.0)
+
+
+def basis_V(N: int):
+    """Unknown basis for one velocity component (Sec. 3.1.3 representation,
+    integrated form): columns are I^4 T_0 .. I^4 T_{N-5}, then T_0..T_3, so
+    V = I^4 sigma + cubic lies in P_{N-1}."""
+    return [integrated_T(j, 4) for j in range(N - 4)] + [integrated_T(k, 0) for k in range(4)]
+
+
+def basis_T(N: int):
+    """Unknown basis for the tension: I^2 T_0 .. I^2 T_{N-3}, then T_0, T_1."""
+    return [integrated_T(j, 2) for j in range(N - 2)] + [integrated_T(k, 0) for k in range(2)]
+
+
+def basis_matrix(basis, x: np.ndarray, m: int = 0) -> np.ndarray:
+    """[len(x), len(basis)]: m-th derivative of each basis function at x."""
+    x = np.atleast_1d(np.asarray(x, float))
+    out = np.zeros((x.shape[0], len(basis)))
+    for j, c in enumerate(basis):
+        cm = C.chebder(c, m) if m > 0 else c
+        out[:, j] = C.chebval(x, cm) if cm.size else 0.0
+    return out

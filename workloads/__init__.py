@@ -1,0 +1,207 @@
+"""Seeded synthetic inputs for fiber-suspension steps.
+
+This module is shared by the CPU oracle, the tests and the benchmark.  It
+holds no arithmetic of the numerical method (no Chebyshev transforms, no
+quadrature rules of the method, no kernels): it only places fibers in space,
+draws external forces and lays out the spherical boundary's quadrature nodes,
+which the paper treats as precomputed inputs (Sec. 3.1.1, Eq. patch-gl-quad:
+"Jacobian and normal ... are inputs").
+
+Every generator takes a seed and returns plain numpy float64/int32 arrays.
+
+Workloads (shapes follow the paper's experiments: confined arrays of 32-2048
+fibers with 31 points (Table 2), a sedimenting cloud of 1024 free fibers
+(Sec. 4.3)):
+
+* ``free_space``: M fibers, N Chebyshev points each, centres uniform in a
+  cube, orientations uniform on the sphere, lengths uniform in [1, 3],
+  optional smooth initial curvature, i.i.d. N(0,1) external force per node.
+* ``confined``: the same inside a sphere of radius R, centres uniform in a
+  ball of radius R_c, with the sphere's 4x4 Gauss-Legendre patch nodes.
+* ``batched``: independent free-space systems with log-uniform fiber counts
+  and mixed points per fiber.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Boundary:
+    """Quadrature description of a sphere of radius R centred at the origin."""
+    R: float
+    nodes: np.ndarray     # [n, 3]
+    normals: np.ndarray   # [n, 3] outward unit normals
+    weights: np.ndarray   # [n]   Gauss-Legendre weight x surface Jacobian
+
+
+@dataclasses.dataclass
+class Suspension:
+    """One fiber suspension: all arrays fiber-major, nodes of fiber m at
+    rows ptr[m]:ptr[m+1]."""
+    n_per_fiber: np.ndarray   # [M] int32, points per fiber
+    X: np.ndarray             # [N_tot, 3] node positions
+    L: np.ndarray             # [M] fiber lengths
+    f_ext: np.ndarray         # [N_tot, 3] external force per unit length
+    mu: float = 1.0
+    eps: float = 1e-3
+    E: float = 1.0
+    dt: float = 1e-3
+    boundary: Optional[Boundary] = None
+
+    @property
+    def ptr(self) -> np.ndarray:
+        return np.concatenate([[0], np.cumsum(self.n_per_fiber)]).astype(np.int64)
+
+    @property
+    def n_fibers(self) -> int:
+        return int(self.n_per_fiber.shape[0])
+
+    @property
+    def n_points(self) -> int:
+        return int(self.X.shape[0])
+
+    def fiber_id(self) -> np.ndarray:
+        return np.repeat(np.arange(self.n_fibers, dtype=np.int32), self.n_per_fiber)
+
+
+def collocation_alpha(n: int) -> np.ndarray:
+    """Positions of the n collocation points in the fiber parameter,
+    alpha_k = cos(k pi / (n-1)), k = 0..n-1 (Sec. 3.1.3); k = 0 is alpha = +1."""
+    return np.cos(np.pi * np.arange(n) / (n - 1))
+
+
+def _unit_vectors(rng: np.random.Generator, m: int) -> np.ndarray:
+    d = rng.normal(size=(m, 3))
+    return d / np.linalg.norm(d, axis=1, keepdims=True)
+
+
+def _curved_fiber(rng, centre, direction, length, alpha, amp, n_modes=4, n_gl=96):
+    """Centreline whose unit tangent is normalise(t0 + sum_k g_k cos(k acos a)),
+    g_k ~ N(0, amp^2) per component, integrated from the midpoint with
+    Gauss-Legendre quadrature so that |dX/ds| = 1 and the arclength is L."""
+    g = rng.normal(scale=amp, size=(n_modes, 3))
+    xg, wg = np.polynomial.legendre.leggauss(n_gl)
+
+    def tangent(a):
+        a = np.clip(a, -1.0, 1.0)
+        th = np.arccos(a)
+        t = direction[None, :] + sum(np.cos((k + 1) * th)[:, None] * g[k][None, :]
+                                     for k in range(n_modes))
+        return t / np.linalg.norm(t, axis=1, keepdims=True)
+
+    pts = np.empty((alpha.shape[0], 3))
+    for i, a in enumerate(alpha):
+        # integrate tangent over [0, a] in the parameter; ds = (L/2) d alpha
+        half = 0.5 * a
+        nodes = half * (xg + 1.0)
+        pts[i] = centre + (length / 2.0) * half * (wg[:, None] * tangent(nodes)).sum(0)
+    return pts
+
+
+def free_space(M: int, N, side: float, seed: int = 0, curved_amp: float = 0.0,
+               L_range=(1.0, 3.0), mu=1.0, eps=1e-3, E=1.0, dt=1e-3,
+               centre_offset=None) -> Suspension:
+    """M fibers in the cube [0, side]^3 (N may be an int or a per-fiber array)."""
+    rng = np.random.default_rng(seed)
+    n_per = np.full(M, N, dtype=np.int32) if np.isscalar(N) else np.asarray(N, np.int32)
+    centres = rng.uniform(0.0, side, size=(M, 3))
+    if centre_offset is not None:
+        centres = centres + np.asarray(centre_offset)[None, :]
+    dirs = _unit_vectors(rng, M)
+    L = rng.uniform(L_range[0], L_range[1], size=M)
+    return _assemble(rng, n_per, centres, dirs, L, curved_amp, mu, eps, E, dt, None)
+
+
+def _assemble(rng, n_per, centres, dirs, L, curved_amp, mu, eps, E, dt, boundary):
+    Xs = []
+    for m in range(n_per.shape[0]):
+        a = collocation_alpha(int(n_per[m]))
+        if curved_amp > 0.0:
+            Xs.append(_curved_fiber(rng, centres[m], dirs[m], L[m], a, curved_amp))
+        else:
+            Xs.append(centres[m][None, :] + (a[:, None] * L[m] / 2.0) * dirs[m][None, :])
+    X = np.concatenate(Xs, axis=0)
+    f_ext = rng.normal(size=X.shape)
+    return Suspension(n_per_fiber=n_per, X=X, L=L, f_ext=f_ext, mu=mu, eps=eps, E=E,
+                      dt=dt, boundary=boundary)
+
+
+def sphere_quadrature(R: float, n_theta: int, n_phi: int, q: int = 4) -> Boundary:
+    """Uniform (theta, phi) patches on a sphere with a q x q Gauss-Legendre grid
+    on each (Sec. 3.1.1, Eq. patch-gl-quad): weight = nu_i nu_j J, with
+    J = R^2 sin(theta) times the patch's parameter-box half-widths."""
+    x, w = np.polynomial.legendre.leggauss(q)
+    dth = math.pi / n_theta
+    dph = 2.0 * math.pi / n_phi
+    nodes, normals, weights = [], [], []
+    for it in range(n_theta):
+        th = (it + 0.5 + 0.5 * x) * dth
+        for ip in range(n_phi):
+            ph = (ip + 0.5 + 0.5 * x) * dph
+            TH, PH = np.meshgrid(th, ph, indexing="ij")
+            WW = np.outer(w, w) * (0.5 * dth) * (0.5 * dph) * R * R * np.sin(TH)
+            n = np.stack([np.sin(TH) * np.cos(PH), np.sin(TH) * np.sin(PH), np.cos(TH)], -1)
+            nodes.append((R * n).reshape(-1, 3))
+            normals.append(n.reshape(-1, 3))
+            weights.append(WW.reshape(-1))
+    return Boundary(R=R, nodes=np.concatenate(nodes), normals=np.concatenate(normals),
+                    weights=np.concatenate(weights))
+
+
+def confined(M: int, N: int, R: float = 20.0, R_centres: float = 18.0,
+             n_theta: int = 16, n_phi: int = 48, seed: int = 0, L_range=(1.0, 3.0),
+             mu=1.0, eps=1e-3, E=1.0, dt=1e-3) -> Suspension:
+    """M straight fibers with centres uniform in a ball of radius R_centres,
+    inside a no-slip sphere of radius R (16 x 48 patches x 16 = 12,288 nodes
+    by default)."""
+    rng = np.random.default_rng(seed)
+    n_per = np.full(M, N, dtype=np.int32)
+    d = _unit_vectors(rng, M)
+    rad = R_centres * rng.uniform(0.0, 1.0, size=M) ** (1.0 / 3.0)
+    centres = d * rad[:, None]
+    dirs = _unit_vectors(rng, M)
+    L = rng.uniform(L_range[0], L_range[1], size=M)
+    b = sphere_quadrature(R, n_theta, n_phi)
+    return _assemble(rng, n_per, centres, dirs, L, 0.0, mu, eps, E, dt, b)
+
+
+def batched(n_systems: int, seed: int = 0, fibers_range=(8, 512),
+            points_choices=(16, 32, 64), density_ref=(16, 10.0)) -> List[Suspension]:
+    """Independent free-space systems: fiber count log-uniform in fibers_range,
+    one points-per-fiber value per system, cube side scaled to keep the fiber
+    density of `density_ref` = (fibers, side)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    lo, hi = math.log(fibers_range[0]), math.log(fibers_range[1])
+    for s in range(n_systems):
+        M = int(round(math.exp(rng.uniform(lo, hi))))
+        N = int(rng.choice(points_choices))
+        side = density_ref[1] * (M / density_ref[0]) ** (1.0 / 3.0)
+        out.append(free_space(M, N, side, seed=int(rng.integers(1 << 31))))
+    return out
+
+
+# Named workloads (sizes of the paper-shaped benchmark cases).
+def cfg_small_fp64(seed: int = 0) -> Suspension:
+    """16 straight fibers x 32 points in [0,10]^3 (512 points)."""
+    return free_space(16, 32, 10.0, seed=seed)
+
+
+def cfg_cloud_mixed(seed: int = 0) -> Suspension:
+    """1,024 curved fibers x 64 points in [0,40]^3 (65,536 points)."""
+    return free_space(1024, 64, 40.0, seed=seed, curved_amp=0.05)
+
+
+def cfg_confined(seed: int = 0) -> Suspension:
+    """2,000 fibers x 32 points inside a radius-20 sphere with 12,288 nodes."""
+    return confined(2000, 32, seed=seed)
+
+
+def cfg_large_matvec(seed: int = 0) -> Suspension:
+    """8,192 fibers x 128 points in [0,80]^3 (1,048,576 points)."""
+    return free_space(8192, 128, 80.0, seed=seed)
