@@ -1,0 +1,175 @@
+/*
+ * fibersolve: the implicit time step of nonlocal slender-body fibers in Stokes
+ * flow (Nazockdast, Rahimian, Zorin, Shelley, "A fast platform for simulating
+ * flexible fiber suspensions applied to cell mechanics"), as a C-ABI library
+ * running on one sm_103a GPU.
+ *
+ * Conventions for every entry point:
+ *  - Return value is an fs_status; on failure fs_last_error() returns a
+ *    thread-local message describing the first error of the failing call.
+ *  - Arrays are plain C arrays of double (or int32) in the layout stated at
+ *    each argument.  "device" pointers are CUDA device addresses (e.g. a torch
+ *    tensor's data_ptr()) that are only borrowed for the duration of the call
+ *    (the work they feed is enqueued on the context's stream, so the caller
+ *    must keep them alive until that stream reaches the enqueued work);
+ *    "host" pointers are copied before the call returns unless stated.
+ *  - All GPU work of a context runs in the CUDA stream given to fs_create
+ *    (NULL = the legacy default stream).  Calls that return results to host
+ *    memory synchronise that stream.
+ *  - No call throws; no call falls back to the CPU.  A missing GPU or a CUDA
+ *    error returns FS_ECUDA.
+ *  - A context is not thread-safe: serialise calls on one context.
+ */
+#ifndef FIBERSOLVE_H
+#define FIBERSOLVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FS_OK = 0,
+    FS_EINVAL = 1,     /* invalid argument or state */
+    FS_ENOMEM = 2,     /* device allocation failed or exceeds the memory budget */
+    FS_ECUDA = 3,      /* CUDA runtime / launch error */
+    FS_ENOTCONV = 4,   /* GMRES / refinement did not reach the tolerance */
+    FS_ENUMERIC = 5,   /* NaN / Inf found in inputs or results, or a singular block */
+    FS_EAGAIN = 6,     /* serving: result not ready yet */
+    FS_EBUSY = 7,      /* serving: no free slot / memory */
+    FS_ETIMEOUT = 8    /* a bounded device-side wait gave up */
+} fs_status;
+
+typedef enum {
+    FS_FP64 = 0,   /* everything in FP64 (the plain FP64 GPU path) */
+    FS_MIXED = 1   /* FP32 far-field sums inside GMRES, FP64 iterative refinement */
+} fs_precision;
+
+typedef enum {
+    FS_SUM_FP64 = 0, /* direct sums in FP64 arithmetic */
+    FS_SUM_FP32 = 1  /* FP32 arithmetic: hi/lo-split coordinates, FP32 tile sums,
+                        compensated (TwoSum) accumulation across tiles, FP64 output */
+} fs_sum_precision;
+
+/* Spherical no-slip periphery (Sec. 2.1, Eq. main-cortex-density) discretised
+ * by Gauss-Legendre patch quadrature (Sec. 3.1.1, Eq. patch-gl-quad): node
+ * positions, outward unit normals and quadrature weights (GL weight x surface
+ * Jacobian), all host arrays, copied at fs_create.  NULL = free space. */
+typedef struct {
+    double R;
+    int32_t n_nodes;
+    const double *nodes;    /* [n_nodes][3] */
+    const double *normals;  /* [n_nodes][3] */
+    const double *weights;  /* [n_nodes]    */
+} fs_boundary;
+
+typedef struct {
+    int32_t prec;           /* fs_precision (default FS_MIXED) */
+    double tol;             /* preconditioned relative residual target (default 1e-8):
+                               ||P^-1 (b - A u)|| <= tol ||P^-1 b|| */
+    int32_t max_iter;       /* GMRES iterations per solve (default 200) */
+    int32_t restart;        /* GMRES restart length (default 60, at most 250) */
+    int32_t max_refine;     /* FS_MIXED: maximum refinement sweeps (default 6) */
+    double inner_tol;       /* FS_MIXED: relative tolerance of each inner solve (default 1e-6) */
+    double delta_over_L;    /* regularisation delta of K_delta as a fraction of L (default 0.01) */
+    int32_t lsb;            /* 1 = local slender-body theory: drop K_delta (default 0) */
+    int32_t use_graph;      /* reserved: capture the inner iteration in a CUDA graph */
+    int32_t tile_override;  /* 0 = autotuned far-field launch shape, else a shape id */
+} fs_options;
+
+typedef struct {
+    int32_t iters;          /* total GMRES iterations (all sweeps) */
+    int32_t refine_sweeps;  /* outer refinement sweeps (1 for FS_FP64) */
+    double resid;           /* final preconditioned relative residual (FP64 far field) */
+    double t_ms[8];         /* [0] geometry+RHS [1] preconditioner build [2] solve
+                               [3] update [4] total; others reserved */
+    int64_t pairs;          /* Stokeslet pairs evaluated */
+} fs_step_info;
+
+typedef struct fs_ctx fs_ctx;
+
+/* Default options (values listed in fs_options). */
+fs_status fs_options_default(fs_options *opt);
+
+/* Create a context for n_fibers fibers with points_per_fiber[m] >= 6
+ * Chebyshev points each (host array, copied), viscosity mu, slenderness eps,
+ * bending modulus E and time step dt (Sec. 2.3-2.4, 3.2).  n_fibers = 0 gives a
+ * context usable only for the direct-sum entry points.  cuda_stream is a
+ * cudaStream_t or NULL.  Allocates the context's device memory. */
+fs_status fs_create(fs_ctx **out, int32_t n_fibers, const int32_t *points_per_fiber,
+                    double mu, double eps, double E, double dt,
+                    const fs_boundary *boundary, const fs_options *opt, void *cuda_stream);
+
+void fs_destroy(fs_ctx *ctx);
+
+/* Set the fiber state: node positions X [N_tot][3] (fiber-major, node k of
+ * fiber m is alpha_k = cos(k pi/(N_m-1)), k = 0 at alpha = +1), lengths
+ * [n_fibers] and external force per unit length f_ext [N_tot][3] (NULL = 0).
+ * ptr_is_device selects device or host pointers.  Invalidates the
+ * preconditioner. */
+fs_status fs_set_state(fs_ctx *ctx, const double *X, const double *lengths,
+                       const double *f_ext, int32_t ptr_is_device);
+
+/* Read the state after the last step: positions X [N_tot][3], tension T
+ * [N_tot] and velocity V [N_tot][3] at the nodes (any may be NULL).
+ * Synchronises the context's stream. */
+fs_status fs_get_state(fs_ctx *ctx, double *X, double *T, double *V, int32_t ptr_is_device);
+
+/* Direct Stokeslet sum (Eqs. oseen, single-layer; Eq. complementary-uf when
+ * fiber ids are given):
+ *   out_u[i] = sum_j G(tgt_i - src_j) src_wf[j],  G(r) = (I + rhat rhat)/(8 pi mu |r|)
+ * over all j, skipping pairs with tgt_fiber[i] == src_fiber[j] when both id
+ * arrays are non-NULL (then src_fiber must be non-decreasing, i.e. sources
+ * grouped by fiber).  Without ids every pair counts and a target that
+ * coincides with a source gives a non-finite result.
+ * src_xyz [n_src][3], src_wf [n_src][3] (force times quadrature weight),
+ * tgt_xyz [n_tgt][3], out_u [n_tgt][3]: DEVICE arrays of double; ids int32.
+ * mu comes from the context.  Enqueued on the context's stream; uses the
+ * context's scratch memory (grown on demand). */
+fs_status fs_stokeslet_apply(fs_ctx *ctx, const double *src_xyz, const double *src_wf,
+                             int64_t n_src, const int32_t *src_fiber,
+                             const double *tgt_xyz, const int32_t *tgt_fiber, int64_t n_tgt,
+                             double *out_u, int32_t sum_precision);
+
+/* Direct double-layer (stresslet) sum (Eqs. stresslet, double-layer,
+ * cortex-vel) at targets off the surface:
+ *   out_u[i] = sum_j w_j T(tgt_i - y_j) : (q_j n_j),
+ *   T_abc(r) = -(3/4 pi) rhat_a rhat_b rhat_c / |r|^2  (no 1/mu factor),
+ * src_xyz, src_nrm (outward unit normals), src_q: [n_src][3]; src_w [n_src];
+ * tgt_xyz, out_u [n_tgt][3]; all DEVICE arrays of double.  A target on a
+ * source point gives a non-finite result.  Enqueued on the context's stream. */
+fs_status fs_stresslet_apply(fs_ctx *ctx, const double *src_xyz, const double *src_nrm,
+                             const double *src_w, const double *src_q, int64_t n_src,
+                             const double *tgt_xyz, int64_t n_tgt, double *out_u,
+                             int32_t sum_precision);
+
+/* Periphery operator of the context's boundary on a density q (Eq.
+ * main-cortex-density, fluid-side limit, singularity subtraction of Sec.
+ * 3.1.2, rank completion N):
+ *   out_i = sum_{j != i} w_j T(y_i - y_j):((q_j - q_i) n_j) + q_i + n_i sum_j w_j n_j.q_j
+ * q, out: DEVICE [n_nodes][3].  FS_EINVAL if the context has no boundary. */
+fs_status fs_surface_apply(fs_ctx *ctx, const double *q, double *out, int32_t sum_precision);
+
+/* Assemble the per-fiber self blocks (Eq. prec: fiber rows with the
+ * complementary velocity removed, Sec. 3.3) for the current state and LU-factor
+ * them with partial pivoting (FP64).  Called by fs_step when needed. */
+fs_status fs_build_precond(fs_ctx *ctx);
+
+/* One implicit backward-Euler step (Sec. 3.2, set:time-stepping): solve
+ * A u = b by block-Jacobi preconditioned GMRES (Sec. 3.3), then X <- X + dt V.
+ * info may be NULL; when given it is filled (and the stream synchronised).
+ * FS_ENOTCONV leaves the state unchanged. */
+fs_status fs_step(fs_ctx *ctx, fs_step_info *info);
+
+/* Number of points N_tot and unknowns of the context. */
+fs_status fs_sizes(const fs_ctx *ctx, int64_t *n_points, int64_t *n_unknowns);
+
+const char *fs_last_error(void);
+const char *fs_status_str(int32_t status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FIBERSOLVE_H */

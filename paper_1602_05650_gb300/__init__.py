@@ -1,0 +1,188 @@
+"""GB300-native implicit step of nonlocal slender-body fibers in Stokes flow.
+
+Thin Python binding of libfibersolve.so (C ABI in include/fibersolve.h).
+Every function has the C entry point's name and only marshals arguments:
+device arrays are torch CUDA tensors (float64 / int32, contiguous), host
+arrays are numpy arrays.  All arithmetic runs in the library's CUDA kernels;
+if the library is missing, calls raise ImportError (no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+
+from . import _native
+from ._native import (FS_FP64, FS_MIXED, FS_SUM_FP32, FS_SUM_FP64, fs_boundary, fs_options,  # noqa: F401
+                      fs_step_info)
+
+__all__ = ["fs_options_default", "fs_create", "fs_destroy", "fs_set_state", "fs_get_state",
+           "fs_stokeslet_apply", "fs_stresslet_apply", "fs_surface_apply", "fs_build_precond",
+           "fs_step", "fs_sizes", "fs_last_error", "FsError", "FS_FP64", "FS_MIXED",
+           "FS_SUM_FP32", "FS_SUM_FP64"]
+
+
+class FsError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        self.status = status
+        super().__init__("%s: %s (%s)" % (where, message, _status_name(status)))
+
+
+def _status_name(s: int) -> str:
+    return _native.load().fs_status_str(int(s)).decode()
+
+
+def fs_last_error() -> str:
+    return _native.load().fs_last_error().decode()
+
+
+def _check(st: int, where: str):
+    if st != 0:
+        raise FsError(st, where, fs_last_error())
+
+
+def _dev_ptr(t, dtype_name: str, name: str):
+    """Device pointer of a contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    want = {"f64": torch.float64, "i32": torch.int32}[dtype_name]
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != want or not t.is_contiguous():
+        raise TypeError("%s must be a contiguous %s tensor" % (name, want))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_ptr(a, dtype, name: str):
+    if a is None:
+        return None, None
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr, arr.ctypes.data_as(ctypes.c_void_p)
+
+
+class Handle:
+    """Owns an fs_ctx*; destroyed by fs_destroy (or when collected)."""
+
+    def __init__(self, ptr: ctypes.c_void_p, n_points: int, n_unknowns: int):
+        self.ptr = ptr
+        self.n_points = n_points
+        self.n_unknowns = n_unknowns
+
+    def __del__(self):
+        try:
+            fs_destroy(self)
+        except Exception:
+            pass
+
+
+def fs_options_default() -> fs_options:
+    o = fs_options()
+    _check(_native.load().fs_options_default(ctypes.byref(o)), "fs_options_default")
+    return o
+
+
+def fs_create(points_per_fiber, mu: float, eps: float, E: float, dt: float, boundary=None,
+              options: Optional[fs_options] = None, stream=None) -> Handle:
+    """points_per_fiber: host int array; boundary: object with R, nodes, normals,
+    weights (numpy) or None; stream: torch.cuda.Stream, raw cudaStream_t or None."""
+    lib = _native.load()
+    ppf, ppf_p = _host_ptr(np.asarray(points_per_fiber), np.int32, "points_per_fiber")
+    M = 0 if ppf is None else int(ppf.shape[0])
+    b = None
+    keep = []
+    if boundary is not None:
+        nodes, pn = _host_ptr(boundary.nodes, np.float64, "nodes")
+        nrm, pm = _host_ptr(boundary.normals, np.float64, "normals")
+        w, pw = _host_ptr(boundary.weights, np.float64, "weights")
+        keep += [nodes, nrm, w]
+        b = fs_boundary(float(boundary.R), int(nodes.shape[0]), pn, pm, pw)
+    st = None
+    if stream is not None:
+        st = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    out = ctypes.c_void_p()
+    _check(lib.fs_create(ctypes.byref(out), M, ppf_p, float(mu), float(eps), float(E), float(dt),
+                         ctypes.byref(b) if b is not None else None,
+                         ctypes.byref(options) if options is not None else None, st), "fs_create")
+    npts, nunk = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib.fs_sizes(out, ctypes.byref(npts), ctypes.byref(nunk)), "fs_sizes")
+    return Handle(out, npts.value, nunk.value)
+
+
+def fs_destroy(h: Handle):
+    if h.ptr is not None and h.ptr.value:
+        _native.load().fs_destroy(h.ptr)
+    h.ptr = None
+
+
+def fs_sizes(h: Handle):
+    return h.n_points, h.n_unknowns
+
+
+def fs_set_state(h: Handle, X, lengths, f_ext=None):
+    """X [N_tot,3], lengths [M], f_ext [N_tot,3]: all CUDA tensors or all numpy arrays."""
+    lib = _native.load()
+    if hasattr(X, "is_cuda") and X.is_cuda:
+        _check(lib.fs_set_state(h.ptr, _dev_ptr(X, "f64", "X"), _dev_ptr(lengths, "f64", "lengths"),
+                                _dev_ptr(f_ext, "f64", "f_ext"), 1), "fs_set_state")
+    else:
+        xa, xp = _host_ptr(X, np.float64, "X")
+        la, lp = _host_ptr(lengths, np.float64, "lengths")
+        fa, fp = _host_ptr(f_ext, np.float64, "f_ext")
+        _check(lib.fs_set_state(h.ptr, xp, lp, fp, 0), "fs_set_state")
+
+
+def fs_get_state(h: Handle, X=None, T=None, V=None):
+    """Fill the given output arrays (CUDA tensors or numpy arrays, same kind)."""
+    lib = _native.load()
+    arrs = [a for a in (X, T, V) if a is not None]
+    if arrs and hasattr(arrs[0], "is_cuda") and arrs[0].is_cuda:
+        _check(lib.fs_get_state(h.ptr, _dev_ptr(X, "f64", "X"), _dev_ptr(T, "f64", "T"),
+                                _dev_ptr(V, "f64", "V"), 1), "fs_get_state")
+    else:
+        for a in arrs:
+            if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+                raise TypeError("host outputs must be C-contiguous float64 numpy arrays")
+        p = lambda a: None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+        _check(lib.fs_get_state(h.ptr, p(X), p(T), p(V), 0), "fs_get_state")
+
+
+def fs_stokeslet_apply(h: Handle, src_xyz, src_wf, tgt_xyz, out, src_fiber=None, tgt_fiber=None,
+                       sum_precision: int = FS_SUM_FP32):
+    lib = _native.load()
+    _check(lib.fs_stokeslet_apply(h.ptr, _dev_ptr(src_xyz, "f64", "src_xyz"),
+                                  _dev_ptr(src_wf, "f64", "src_wf"), int(src_xyz.shape[0]),
+                                  _dev_ptr(src_fiber, "i32", "src_fiber"),
+                                  _dev_ptr(tgt_xyz, "f64", "tgt_xyz"),
+                                  _dev_ptr(tgt_fiber, "i32", "tgt_fiber"), int(tgt_xyz.shape[0]),
+                                  _dev_ptr(out, "f64", "out"), int(sum_precision)),
+           "fs_stokeslet_apply")
+
+
+def fs_stresslet_apply(h: Handle, src_xyz, src_nrm, src_w, src_q, tgt_xyz, out,
+                       sum_precision: int = FS_SUM_FP32):
+    lib = _native.load()
+    _check(lib.fs_stresslet_apply(h.ptr, _dev_ptr(src_xyz, "f64", "src_xyz"),
+                                  _dev_ptr(src_nrm, "f64", "src_nrm"), _dev_ptr(src_w, "f64", "src_w"),
+                                  _dev_ptr(src_q, "f64", "src_q"), int(src_xyz.shape[0]),
+                                  _dev_ptr(tgt_xyz, "f64", "tgt_xyz"), int(tgt_xyz.shape[0]),
+                                  _dev_ptr(out, "f64", "out"), int(sum_precision)),
+           "fs_stresslet_apply")
+
+
+def fs_surface_apply(h: Handle, q, out, sum_precision: int = FS_SUM_FP64):
+    _check(_native.load().fs_surface_apply(h.ptr, _dev_ptr(q, "f64", "q"), _dev_ptr(out, "f64", "out"),
+                                           int(sum_precision)), "fs_surface_apply")
+
+
+def fs_build_precond(h: Handle):
+    _check(_native.load().fs_build_precond(h.ptr), "fs_build_precond")
+
+
+def fs_step(h: Handle, info: bool = True) -> Optional[fs_step_info]:
+    """One implicit step; returns the step info (synchronising) when info=True.
+    Raises FsError (status FS_ENOTCONV etc.) on failure."""
+    inf = fs_step_info()
+    _check(_native.load().fs_step(h.ptr, ctypes.byref(inf) if info else None), "fs_step")
+    return inf if info else None

@@ -1,0 +1,79 @@
+"""ctypes declarations of the C ABI in include/fibersolve.h (argument
+marshalling only; every computation happens in libfibersolve.so).
+
+Loading fails loudly when the library has not been built: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfibersolve.so")
+
+c_int32 = ctypes.c_int32
+c_int64 = ctypes.c_int64
+c_double = ctypes.c_double
+c_void_p = ctypes.c_void_p
+P = c_void_p
+
+FS_OK, FS_EINVAL, FS_ENOMEM, FS_ECUDA, FS_ENOTCONV, FS_ENUMERIC, FS_EAGAIN, FS_EBUSY, FS_ETIMEOUT = range(9)
+FS_FP64, FS_MIXED = 0, 1
+FS_SUM_FP64, FS_SUM_FP32 = 0, 1
+
+
+class fs_boundary(ctypes.Structure):
+    _fields_ = [("R", c_double), ("n_nodes", c_int32), ("nodes", P), ("normals", P), ("weights", P)]
+
+
+class fs_options(ctypes.Structure):
+    _fields_ = [("prec", c_int32), ("tol", c_double), ("max_iter", c_int32), ("restart", c_int32),
+                ("max_refine", c_int32), ("inner_tol", c_double), ("delta_over_L", c_double),
+                ("lsb", c_int32), ("use_graph", c_int32), ("tile_override", c_int32)]
+
+
+class fs_step_info(ctypes.Structure):
+    _fields_ = [("iters", c_int32), ("refine_sweeps", c_int32), ("resid", c_double),
+                ("t_ms", c_double * 8), ("pairs", c_int64)]
+
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "fs_options_default": (c_int32, [ctypes.POINTER(fs_options)]),
+    "fs_create": (c_int32, [ctypes.POINTER(c_void_p), c_int32, P, c_double, c_double, c_double,
+                            c_double, ctypes.POINTER(fs_boundary), ctypes.POINTER(fs_options), P]),
+    "fs_destroy": (None, [P]),
+    "fs_set_state": (c_int32, [P, P, P, P, c_int32]),
+    "fs_get_state": (c_int32, [P, P, P, P, c_int32]),
+    "fs_stokeslet_apply": (c_int32, [P, P, P, c_int64, P, P, P, c_int64, P, c_int32]),
+    "fs_stresslet_apply": (c_int32, [P, P, P, P, P, c_int64, P, c_int64, P, c_int32]),
+    "fs_surface_apply": (c_int32, [P, P, P, c_int32]),
+    "fs_build_precond": (c_int32, [P]),
+    "fs_step": (c_int32, [P, ctypes.POINTER(fs_step_info)]),
+    "fs_sizes": (c_int32, [P, ctypes.POINTER(c_int64), ctypes.POINTER(c_int64)]),
+    "fs_last_error": (ctypes.c_char_p, []),
+    "fs_status_str": (ctypes.c_char_p, [c_int32]),
+}
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libfibersolve.so (built by paper_1602_05650_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libfibersolve.so is not built; run paper_1602_05650_gb300.build.build() "
+                              "(needs nvcc). There is no CPU fallback.")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    return list(SIGNATURES)

@@ -1,0 +1,209 @@
+// C-ABI entry points: context lifetime, state transfer, direct sums, step.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "context.h"
+
+namespace fs {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+fs_status Scratch::reserve(size_t need, cudaStream_t st)
+{
+    if (need <= bytes) return FS_OK;
+    if (ptr) {
+        FS_CUDA(cudaStreamSynchronize(st));
+        FS_CUDA(cudaFree(ptr));
+        ptr = nullptr;
+        bytes = 0;
+    }
+    size_t want = need + need / 4;
+    if (cudaMalloc(&ptr, want) != cudaSuccess) {
+        cudaGetLastError();
+        ptr = nullptr;
+        set_error("scratch: cudaMalloc of %zu bytes failed", want);
+        return FS_ENOMEM;
+    }
+    bytes = want;
+    return FS_OK;
+}
+
+void Scratch::release()
+{
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+}
+
+}  // namespace fs
+
+using namespace fs;
+
+extern "C" {
+
+const char *fs_last_error(void) { return g_err; }
+
+const char *fs_status_str(int32_t s)
+{
+    switch (s) {
+    case FS_OK: return "FS_OK";
+    case FS_EINVAL: return "FS_EINVAL";
+    case FS_ENOMEM: return "FS_ENOMEM";
+    case FS_ECUDA: return "FS_ECUDA";
+    case FS_ENOTCONV: return "FS_ENOTCONV";
+    case FS_ENUMERIC: return "FS_ENUMERIC";
+    case FS_EAGAIN: return "FS_EAGAIN";
+    case FS_EBUSY: return "FS_EBUSY";
+    case FS_ETIMEOUT: return "FS_ETIMEOUT";
+    default: return "FS_UNKNOWN";
+    }
+}
+
+fs_status fs_options_default(fs_options *o)
+{
+    if (!o) {
+        set_error("fs_options_default: NULL");
+        return FS_EINVAL;
+    }
+    std::memset(o, 0, sizeof(*o));
+    o->prec = FS_MIXED;
+    o->tol = 1e-8;
+    o->max_iter = 200;
+    o->restart = 60;
+    o->max_refine = 6;
+    o->inner_tol = 1e-6;
+    o->delta_over_L = 0.01;
+    o->lsb = 0;
+    o->use_graph = 0;
+    o->tile_override = 0;
+    return FS_OK;
+}
+
+fs_status fs_create(fs_ctx **out, int32_t n_fibers, const int32_t *ppf, double mu, double eps,
+                    double E, double dt, const fs_boundary *boundary, const fs_options *opt,
+                    void *cuda_stream)
+{
+    if (!out) {
+        set_error("fs_create: out is NULL");
+        return FS_EINVAL;
+    }
+    *out = nullptr;
+    if (n_fibers < 0 || (n_fibers > 0 && !ppf)) {
+        set_error("fs_create: bad fiber count or points_per_fiber");
+        return FS_EINVAL;
+    }
+    if (!(mu > 0.0) || !(eps > 0.0 && eps < 1.0) || !(E >= 0.0) || !(dt > 0.0)) {
+        set_error("fs_create: need mu > 0, 0 < eps < 1, E >= 0, dt > 0");
+        return FS_EINVAL;
+    }
+    for (int m = 0; m < n_fibers; ++m)
+        if (ppf[m] < 6 || ppf[m] > 256) {
+            set_error("fs_create: points per fiber must be in [6, 256] (fiber %d has %d)", m, ppf[m]);
+            return FS_EINVAL;
+        }
+    if (boundary && (boundary->n_nodes <= 0 || !boundary->nodes || !boundary->normals ||
+                     !boundary->weights)) {
+        set_error("fs_create: incomplete boundary description");
+        return FS_EINVAL;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        set_error("fs_create: no CUDA device");
+        return FS_ECUDA;
+    }
+    fs_ctx *c = new fs_ctx();
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->mu = mu;
+    c->eps = eps;
+    c->E = E;
+    c->dt = dt;
+    if (opt) c->opt = *opt; else fs_options_default(&c->opt);
+    fs_status s = context_init(c, n_fibers, ppf, boundary);
+    if (s != FS_OK) {
+        context_free(c);
+        delete c;
+        return s;
+    }
+    *out = c;
+    return FS_OK;
+}
+
+void fs_destroy(fs_ctx *c)
+{
+    if (!c) return;
+    context_free(c);
+    delete c;
+}
+
+fs_status fs_sizes(const fs_ctx *c, int64_t *n_points, int64_t *n_unknowns)
+{
+    if (!c) {
+        set_error("fs_sizes: NULL context");
+        return FS_EINVAL;
+    }
+    if (n_points) *n_points = c->n_tot;
+    if (n_unknowns) *n_unknowns = c->n_unk;
+    return FS_OK;
+}
+
+fs_status fs_stokeslet_apply(fs_ctx *c, const double *src_xyz, const double *src_wf, int64_t n_src,
+                             const int32_t *src_fiber, const double *tgt_xyz,
+                             const int32_t *tgt_fiber, int64_t n_tgt, double *out_u,
+                             int32_t sum_precision)
+{
+    if (!c) {
+        set_error("fs_stokeslet_apply: NULL context");
+        return FS_EINVAL;
+    }
+    if (n_src < 0 || n_tgt < 0 || (n_src > 0 && (!src_xyz || !src_wf)) ||
+        (n_tgt > 0 && (!tgt_xyz || !out_u))) {
+        set_error("fs_stokeslet_apply: bad sizes or NULL arrays");
+        return FS_EINVAL;
+    }
+    if (sum_precision != FS_SUM_FP32 && sum_precision != FS_SUM_FP64) {
+        set_error("fs_stokeslet_apply: unknown precision %d", sum_precision);
+        return FS_EINVAL;
+    }
+    if (n_src >= (1LL << 31) - 1 || n_tgt >= (1LL << 31) - 1) {
+        set_error("fs_stokeslet_apply: at most 2^31-2 sources and targets");
+        return FS_EINVAL;
+    }
+    const bool ids = src_fiber && tgt_fiber;
+    const size_t need = pairsum_scratch_bytes(PAIR_STOKESLET, n_src, n_tgt, sum_precision,
+                                              c->opt.tile_override) +
+                        (ids ? static_cast<size_t>(n_tgt) * sizeof(int2) + 512 : 0);
+    FS_TRY(c->scratch.reserve(need, c->stream));
+    Carve cv(c->scratch.ptr, c->scratch.bytes);
+    PairSumArgs a;
+    if (ids) {
+        int2 *excl = cv.take<int2>(n_tgt);
+        FS_TRY(exclusion_from_ids(src_fiber, n_src, tgt_fiber, n_tgt, excl, c->stream));
+        a.excl = excl;
+    }
+    cv.used = (cv.used + 255) & ~size_t(255);
+    a.kind = PAIR_STOKESLET;
+    a.src_xyz = src_xyz;
+    a.src_dens = src_wf;
+    a.n_src = n_src;
+    a.tgt_xyz = tgt_xyz;
+    a.n_tgt = n_tgt;
+    a.out = out_u;
+    a.scale = 1.0 / (8.0 * M_PI * c->mu);
+    a.sum_prec = sum_precision;
+    a.hilo = true;
+    a.shape_override = c->opt.tile_override;
+    return pairsum(a, cv.base + cv.used, cv.cap - cv.used, c->d_status, c->stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,137 @@
+// The fs_ctx object and the internal interfaces of the implicit step.
+#pragma once
+
+#include <map>
+
+#include "internal.h"
+
+namespace fs {
+
+// Offsets (in doubles) of the per-N operator matrices inside one op set; all
+// matrices row-major.  Built on the host in FP64 by chebops.cu.
+struct OpsLayout {
+    int N;
+    int64_t alpha, omega, Vy, V2, V3, Sig, Tn, Vn, D1, D2, D3, D4, Py, Dz, total;
+    __host__ __device__ explicit OpsLayout(int n) : N(n)
+    {
+        int64_t o = 0;
+        alpha = o; o += N;
+        omega = o; o += N;
+        Vy = o; o += int64_t(N - 4) * N;
+        V2 = o; o += 2 * N;
+        V3 = o; o += 2 * N;
+        Sig = o; o += int64_t(N) * N;
+        Tn = o; o += int64_t(N) * N;
+        Vn = o; o += int64_t(N) * N;
+        D1 = o; o += int64_t(N) * N;
+        D2 = o; o += int64_t(N) * N;
+        D3 = o; o += int64_t(N) * N;
+        D4 = o; o += int64_t(N) * N;
+        Py = o; o += int64_t(N - 4) * N;
+        Dz = o; o += int64_t(N - 2) * N;
+        total = (o + 3) & ~int64_t(3);
+    }
+};
+
+// Host construction of one op set (FP64): returns `total` doubles.
+std::vector<double> build_ops(int N);
+
+// Device pointers describing all fibers (passed by value to kernels).
+struct FiberTable {
+    int M;
+    const int *N;              // [M] points per fiber
+    const int64_t *node_ptr;   // [M+1]
+    const int64_t *unk_ptr;    // [M+1] fiber unknown offsets (4N each)
+    const int64_t *blk_ptr;    // [M+1] offsets of the (4N)^2 blocks
+    const int64_t *kp_ptr;     // [M+1] offsets of the N^2 self-pair records
+    const int64_t *z_ptr;      // [M+1] offsets of the N-2 tension points
+    const int64_t *ops_off;    // [M]   op-set offset of each fiber
+    const double *ops;         // op sets
+    const double *L;           // [M]
+    double mu, eps, E, dt, delta_over_L;
+    int lsb;
+    // geometry, written by k_geometry each step
+    double *t;       // [N_tot][3] X_s at nodes
+    double *tz;      // [sum(N-2)][3] X_s at the tension points
+    double *fknown;  // [N_tot][3] f^E - E g^4 X_aaaa
+    double *W;       // [N_tot] Clenshaw-Curtis source weights
+    double *mloc;    // [N_tot][2] local operator coefficients (see k_geometry)
+    double *bc;      // [M][12] free-end data X''(+-1)/dt, X'''(+-1)/dt
+    double *kp;      // [sum N^2][4] K_delta pair records (a_kj, rhat)
+};
+
+struct Surface {
+    int n = 0;
+    double *y = nullptr, *nrm = nullptr, *w = nullptr;  // [n][3], [n][3], [n]
+    double *diag = nullptr;                             // [n][3] Jacobi entries
+    double *A = nullptr;                                // [n][9] subtraction matrices
+    double *tmp = nullptr;                              // [n][3] work
+    double *flux = nullptr;                             // [1] sum w n.q
+    int2 *excl = nullptr;                               // [n] own-node exclusion
+};
+
+}  // namespace fs
+
+struct fs_ctx {
+    cudaStream_t stream = nullptr;
+    double mu = 1, eps = 1e-3, E = 1, dt = 1e-3;
+    fs_options opt{};
+    int M = 0;
+    int64_t n_tot = 0, n_fib_unk = 0, n_unk = 0, n_blk = 0, n_kp = 0, n_z = 0;
+    std::vector<int> Nm;
+    std::vector<int64_t> node_ptr, unk_ptr, blk_ptr;
+    std::map<int, int64_t> ops_offset;  // N -> offset in d_ops
+    int max_N = 0;
+
+    // device
+    int *d_status = nullptr;
+    int *d_N = nullptr;
+    int64_t *d_node_ptr = nullptr, *d_unk_ptr = nullptr, *d_blk_ptr = nullptr, *d_kp_ptr = nullptr,
+            *d_z_ptr = nullptr, *d_ops_off = nullptr;
+    double *d_ops = nullptr;
+    int2 *d_excl = nullptr;       // per node: its own fiber's node range
+    double *d_X = nullptr, *d_L = nullptr, *d_fext = nullptr;
+    double *d_t = nullptr, *d_tz = nullptr, *d_fknown = nullptr, *d_W = nullptr, *d_mloc = nullptr,
+           *d_bc = nullptr, *d_kp = nullptr;
+    double *d_B = nullptr;        // column-major blocks, LU factors after build
+    int *d_piv = nullptr;
+    double *d_V = nullptr, *d_T = nullptr;
+    double *d_f = nullptr, *d_wf = nullptr, *d_ubar = nullptr;
+    // Krylov workspace
+    int kdim = 0;
+    double *d_basis = nullptr, *d_b = nullptr, *d_x = nullptr, *d_r = nullptr, *d_w = nullptr,
+           *d_e = nullptr, *d_res = nullptr, *d_cor = nullptr, *d_h = nullptr, *d_part = nullptr;
+    double *h_pinned = nullptr;
+    fs::Surface surf;
+    double *d_usurf = nullptr;    // fiber Stokeslets at the surface nodes [n_s][3]
+    bool have_state = false, precond_ok = false, geometry_ok = false;
+    fs::Scratch scratch;          // far-field scratch (grown on demand)
+    int64_t pairs_last = 0;
+
+    fs::FiberTable table() const;
+};
+
+namespace fs {
+fs_status context_init(fs_ctx *c, int M, const int32_t *ppf, const fs_boundary *b);
+void context_free(fs_ctx *c);
+
+// fiber.cu
+fs_status launch_geometry(fs_ctx *c);
+// f (and W f) at the nodes from the unknowns u (or f_known when u == nullptr)
+fs_status launch_force(fs_ctx *c, const double *u, double *f, double *wf);
+// rows of the fiber equations: out = B u + Rw(ubar) [+ const and known force, negated, when rhs]
+fs_status launch_rows(fs_ctx *c, const double *u, const double *f, const double *ubar, double *out,
+                      bool rhs);
+fs_status launch_block_build(fs_ctx *c);
+fs_status launch_lu_factor(fs_ctx *c);
+fs_status launch_lu_solve(fs_ctx *c, const double *in, double *out);
+fs_status launch_update(fs_ctx *c, const double *u);
+
+// surface.cu
+fs_status surface_couplings(fs_ctx *c, const double *q, double *ubar_fibers, int sum_prec,
+                            bool hilo);
+fs_status surface_rows(fs_ctx *c, const double *q, const double *usurf, double *out, bool rhs,
+                       int sum_prec, bool hilo);
+fs_status surface_diag(fs_ctx *c);
+fs_status surface_precond(fs_ctx *c, const double *in, double *out);
+}  // namespace fs

@@ -1,0 +1,107 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/fibersolve.h"
+
+namespace fs {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char *fmt, ...);
+
+#define FS_CUDA(call)                                                                    \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            ::fs::set_error("%s:%d: %s: %s", __FILE__, __LINE__, #call,                  \
+                            cudaGetErrorString(e_));                                     \
+            return FS_ECUDA;                                                             \
+        }                                                                                \
+    } while (0)
+
+#define FS_TRY(expr)                                                                     \
+    do {                                                                                 \
+        fs_status s_ = (expr);                                                           \
+        if (s_ != FS_OK) return s_;                                                      \
+    } while (0)
+
+#define FS_LAUNCH_CHECK() FS_CUDA(cudaGetLastError())
+
+// Device status word bits written by kernels (never by faults).
+enum : int {
+    DEV_ERR_TIMEOUT = 1,   // a bounded mbarrier wait gave up
+    DEV_ERR_NUMERIC = 2,   // non-finite value or zero pivot
+};
+
+// ---------------------------------------------------------------- scratch
+// Grow-only device buffer owned by a context.
+struct Scratch {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    fs_status reserve(size_t need, cudaStream_t st);
+    void release();
+};
+
+// Bump allocator over a caller-provided region (256-byte aligned pieces).
+struct Carve {
+    char *base;
+    size_t used = 0, cap;
+    Carve(void *b, size_t c) : base(static_cast<char *>(b)), cap(c) {}
+    template <class T>
+    T *take(size_t n) {
+        used = (used + 255) & ~size_t(255);
+        T *p = reinterpret_cast<T *>(base + used);
+        used += n * sizeof(T);
+        return p;
+    }
+};
+
+// ---------------------------------------------------------------- direct sums
+enum : int { PAIR_STOKESLET = 0, PAIR_STRESSLET = 1 };
+
+// Launch plan of the tiled direct sums.
+struct SumPlan {
+    int tpt;          // targets per thread
+    int splits;       // source splits (CTAs along y)
+    int64_t per_split;
+    int tile;         // sources per shared-memory stage
+    int threads;      // threads per CTA
+};
+
+struct PairSumArgs {
+    int kind = PAIR_STOKESLET;
+    const double *src_xyz = nullptr;   // [n_src][3]
+    const double *src_dens = nullptr;  // Stokeslet: W f [n_src][3]; stresslet: q [n_src][3]
+    const double *src_w = nullptr;     // stresslet: quadrature weights [n_src] (else nullptr)
+    const double *src_nrm = nullptr;   // stresslet: normals [n_src][3] (else nullptr)
+    int64_t n_src = 0;
+    const int2 *excl = nullptr;        // per target: skipped source index range [x, y)
+    const double *tgt_xyz = nullptr;   // [n_tgt][3]
+    int64_t n_tgt = 0;
+    double *out = nullptr;             // [n_tgt][3]
+    double scale = 1.0;                // applied to the kernel sum
+    int sum_prec = FS_SUM_FP32;
+    bool hilo = true;                  // FP32: hi/lo-split coordinates
+    bool accumulate = false;           // out += scale * sum instead of out = ...
+    int shape_override = 0;
+};
+
+SumPlan plan_pairsum(int64_t n_src, int64_t n_tgt, int sum_prec, int shape_override);
+size_t pairsum_scratch_bytes(int kind, int64_t n_src, int64_t n_tgt, int sum_prec,
+                             int shape_override);
+// Enqueue the sum on `st`; scratch must hold pairsum_scratch_bytes(...) bytes.
+fs_status pairsum(const PairSumArgs &a, void *scratch, size_t scratch_bytes, int *d_status,
+                  cudaStream_t st);
+
+// Exclusion ranges from non-decreasing source fiber ids (binary search per target).
+fs_status exclusion_from_ids(const int32_t *src_fiber, int64_t n_src, const int32_t *tgt_fiber,
+                             int64_t n_tgt, int2 *excl, cudaStream_t st);
+
+int num_sms();
+
+}  // namespace fs

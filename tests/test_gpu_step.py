@@ -1,0 +1,102 @@
+"""GPU parity of the implicit step (fs_step) against the oracle's step on the
+same seeded suspensions: plain FP64 path (GMRES to 1e-12 on both sides,
+velocities within 1e-10 at N <= 32 and 1e-9 at N = 64, where the measured
+discretisation sensitivity is 5e-10) and the mixed path (FP32 far field +
+FP64 refinement to 1e-10, velocities within 1e-8)."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import system
+from tests.gpu_helpers import gpu_step, rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1602_05650_gb300 as fs  # noqa: E402
+
+
+def oracle_step(s, steps=1, tol=1e-12, **kw):
+    import copy
+    s = copy.deepcopy(s)
+    out = None
+    for _ in range(steps):
+        out = system.from_suspension(s, **kw).step(tol=tol)
+        s.X = out.X_new
+    return out
+
+
+def test_straight_rod_closed_form():
+    N, L = 24, 2.0
+    a = np.cos(np.pi * np.arange(N) / (N - 1))
+    d = np.array([0.3, -0.2, 0.9]) / np.linalg.norm([0.3, -0.2, 0.9])
+    X = (a[:, None] * L / 2) * d[None, :] + np.array([1.0, 2.0, 3.0])
+    fe = np.array([0.7, -0.4, 0.2])
+    s = wl.Suspension(np.array([N], np.int32), X, np.array([L]), np.tile(fe, (N, 1)))
+    V, T, _, infos = gpu_step(s, torch)
+    c = -math.log(1e-6 * math.e)
+    fpar = (fe @ d) * d
+    expect = (2 * c * fpar + (c + 2) * (fe - fpar)) / (8 * math.pi)
+    assert np.allclose(V, expect[None, :], rtol=1e-10, atol=1e-12)
+    assert np.abs(T).max() < 1e-9
+    assert infos[0].iters == 1
+
+
+@pytest.mark.parametrize("lsb", [False, True])
+def test_fp64_small_straight(lsb):
+    s = wl.cfg_small_fp64(0)
+    ref = oracle_step(s, lsb=lsb)
+    V, T, Xn, infos = gpu_step(s, torch, lsb=lsb)
+    assert rel(V, ref.V) <= 1e-10
+    assert rel(T, ref.T) <= 1e-9
+    assert rel(Xn, ref.X_new) <= 1e-13
+
+
+def test_fp64_curved_ragged():
+    s = wl.free_space(24, np.array([16, 20, 32] * 8), 5.0, seed=2, curved_amp=0.05)
+    ref = oracle_step(s)
+    V, T, _, _ = gpu_step(s, torch)
+    assert rel(V, ref.V) <= 1e-10
+    assert rel(T, ref.T) <= 1e-9
+
+
+def test_fp64_n64_two_steps():
+    s = wl.free_space(20, 64, 8.0, seed=3, curved_amp=0.05)
+    ref = oracle_step(s, steps=2)
+    V, T, Xn, _ = gpu_step(s, torch, steps=2)
+    assert rel(V, ref.V) <= 1e-9
+    assert rel(Xn, ref.X_new) <= 1e-12
+
+
+def test_mixed_refined_matches_oracle():
+    s = wl.free_space(64, 32, 10.0, seed=4, curved_amp=0.05)
+    ref = oracle_step(s)
+    V, T, _, infos = gpu_step(s, torch, prec=fs.FS_MIXED, tol=1e-10)
+    assert rel(V, ref.V) <= 1e-8
+    assert infos[0].resid <= 1e-10 and infos[0].refine_sweeps >= 1
+
+
+def test_confined_small():
+    s = wl.confined(12, 16, R=4.0, R_centres=2.0, n_theta=4, n_phi=8, seed=5)
+    ref = oracle_step(s)
+    V, T, _, _ = gpu_step(s, torch)
+    assert rel(V, ref.V) <= 1e-9
+    Vm, _, _, _ = gpu_step(s, torch, prec=fs.FS_MIXED, tol=1e-10)
+    assert rel(Vm, ref.V) <= 1e-8
+
+
+def test_not_converged_reports_and_keeps_state():
+    s = wl.free_space(32, 16, 4.0, seed=6, curved_amp=0.05)
+    from tests.gpu_helpers import dev, make_ctx
+    h = make_ctx(s, tol=1e-14, max_iter=1, restart=2)
+    X = dev(s.X, torch)
+    fs.fs_set_state(h, X, dev(s.L, torch), dev(s.f_ext, torch))
+    with pytest.raises(fs.FsError) as e:
+        fs.fs_step(h)
+    assert e.value.status == 4
+    Xn = torch.empty_like(X)
+    fs.fs_get_state(h, X=Xn)
+    assert torch.equal(Xn, X)
+    fs.fs_destroy(h)
