@@ -80,6 +80,57 @@ def integrated_T(j: int, m: int) -> np.ndarray:
     return C.chebint(e, m, lbnd=-1.0)
 
 
+# ---------------------------------------------------------- extended precision
+LD = np.longdouble
+PI_LD = LD("3.141592653589793238462643383279502884197")
+
+
+def nodes_ld(N: int) -> np.ndarray:
+    return np.cos(PI_LD * np.arange(N, dtype=LD) / LD(N - 1))
+
+
+def first_kind_ld(M: int) -> np.ndarray:
+    return np.cos(PI_LD * (LD(2) * np.arange(M, dtype=LD) + LD(1)) / LD(2 * M))
+
+
+def solve_ld(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """Gaussian elimination with partial pivoting in numpy.longdouble."""
+    A = np.array(A, dtype=LD)
+    B = np.array(B, dtype=LD)
+    n = A.shape[0]
+    for k in range(n):
+        p = k + int(np.argmax(np.abs(A[k:, k])))
+        if p != k:
+            A[[k, p]] = A[[p, k]]
+            B[[k, p]] = B[[p, k]]
+        f = A[k + 1:, k] / A[k, k]
+        A[k + 1:, k:] -= f[:, None] * A[k, k:][None, :]
+        B[k + 1:] -= f[:, None] * B[k][None, :]
+    X = np.zeros_like(B)
+    for k in range(n - 1, -1, -1):
+        X[k] = (B[k] - A[k, k + 1:] @ X[k + 1:]) / A[k, k]
+    return X
+
+
+def interp_derivs_ext(values: np.ndarray, pts: np.ndarray, m: int) -> np.ndarray:
+    """m-th derivative at pts of the degree N-1 interpolant of nodal values
+    [N, 3], computed in extended precision (numpy.longdouble): values are taken
+    relative to the first node, the Chebyshev-Vandermonde system is solved by
+    Gaussian elimination, then differentiated and evaluated with
+    numpy.polynomial.chebyshev.  Returns float64 [len(pts), 3]."""
+    N = values.shape[0]
+    v = np.asarray(values, dtype=LD)
+    v = v - v[0][None, :]
+    V = C.chebvander(nodes_ld(N), N - 1)
+    coef = solve_ld(V, v)
+    c = C.chebder(coef, m, axis=0) if m > 0 else coef
+    pts = np.atleast_1d(np.asarray(pts, dtype=LD))
+    out = C.chebval(pts, c, tensor=True).T
+    if m == 0:
+        out = out + np.asarray(values, dtype=LD)[0][None, :]
+    return out.astype(np.float64)
+
+
 def basis_V(N: int):
     """Unknown basis for one velocity component (Sec. 3.1.3 representation,
     integrated form): columns are I^4 T_0 .. I^4 T_{N-5}, then T_0..T_3, so

@@ -96,12 +96,17 @@ class Fiber:
         self.N, self.op, self.L = N, op, L
         self.mu, self.E, self.dt = mu, E, dt
         g = 2.0 / L
-        coef = cheb.values_to_coeffs(X)
-        self.t = g * cheb.series_at(coef, op.alpha, 1)        # X_s at nodes
-        self.tz = g * cheb.series_at(coef, op.z, 1)           # X_s at z points
-        X2 = cheb.series_at(coef, [1.0, -1.0], 2)             # X_aa at alpha = +1, -1
-        X3 = cheb.series_at(coef, [1.0, -1.0], 3)
-        Xaaaa = cheb.series_at(coef, op.alpha, 4)
+        # geometry: derivatives of the interpolant of X, in extended precision
+        # (they amplify rounding by up to ~N^8, and the fiber block is
+        # ill-conditioned, so double-precision evaluation would leave O(1e-8)
+        # rounding noise in the step's velocities)
+        Nld = cheb.nodes_ld(N)
+        pm = np.array([1.0, -1.0], dtype=cheb.LD)
+        self.t = g * cheb.interp_derivs_ext(X, Nld, 1)        # X_s at nodes
+        self.tz = g * cheb.interp_derivs_ext(X, cheb.first_kind_ld(N - 2), 1)   # X_s at z
+        X2 = cheb.interp_derivs_ext(X, pm, 2)                 # X_aa at alpha = +1, -1
+        X3 = cheb.interp_derivs_ext(X, pm, 3)
+        Xaaaa = cheb.interp_derivs_ext(X, Nld, 4)
         self.f_known = f_ext - E * g ** 4 * Xaaaa              # [N, 3]
         self.W = op.w * L / 2.0                                # source weights
         s = (op.alpha + 1.0) * L / 2.0

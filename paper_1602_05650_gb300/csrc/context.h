@@ -8,10 +8,15 @@
 namespace fs {
 
 // Offsets (in doubles) of the per-N operator matrices inside one op set; all
-// matrices row-major.  Built on the host in FP64 by chebops.cu.
+// matrices row-major.  Built on the host in long double by chebops.cu and
+// rounded to double (geometry matrices kept as double-double pairs).
 struct OpsLayout {
     int N;
     int64_t alpha, omega, Vy, V2, V3, Sig, Tn, Vn, D1, D2, D3, D4, Py, Dz, total;
+    // geometry matrices as double-double (hi, lo) pairs: first derivative at
+    // the nodes (G1) and at the tension points (Gz), 2nd / 3rd derivative at
+    // alpha = +1, -1 (G2, G3), 4th derivative at the nodes (G4)
+    int64_t G1h, G1l, Gzh, Gzl, G2h, G2l, G3h, G3l, G4h, G4l;
     __host__ __device__ explicit OpsLayout(int n) : N(n)
     {
         int64_t o = 0;
@@ -29,6 +34,16 @@ struct OpsLayout {
         D4 = o; o += int64_t(N) * N;
         Py = o; o += int64_t(N - 4) * N;
         Dz = o; o += int64_t(N - 2) * N;
+        G1h = o; o += int64_t(N) * N;
+        G1l = o; o += int64_t(N) * N;
+        Gzh = o; o += int64_t(N - 2) * N;
+        Gzl = o; o += int64_t(N - 2) * N;
+        G2h = o; o += 2 * N;
+        G2l = o; o += 2 * N;
+        G3h = o; o += 2 * N;
+        G3l = o; o += 2 * N;
+        G4h = o; o += int64_t(N) * N;
+        G4l = o; o += int64_t(N) * N;
         total = (o + 3) & ~int64_t(3);
     }
 };

@@ -47,49 +47,75 @@ struct Fib {
 };
 
 // ---------------------------------------------------------------- geometry
+// Double-double accumulation (Knuth's TwoSum, FMA-based TwoProduct; the
+// compensated dot product of Ogita, Rump and Oishi, SIAM J. Sci. Comput. 2005):
+// derivatives of the node positions multiply O(N^2m) matrix entries by
+// positions, so they are summed with ~2^-104 relative rounding and rounded to
+// double once.
+__device__ __forceinline__ void two_sum_d(double a, double b, double &s, double &e)
+{
+    s = a + b;
+    const double bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// (sh, sl) += (dh + dl) * (xh + xl)
+__device__ __forceinline__ void dd_acc(double &sh, double &sl, double dh, double dl, double xh,
+                                       double xl)
+{
+    const double p = dh * xh;
+    const double pe = fma(dh, xh, -p) + (dh * xl + dl * xh);
+    double s, e;
+    two_sum_d(sh, p, s, e);
+    e += sl + pe;
+    sh = s + e;
+    sl = e - (sh - s);
+}
+
+// sum_j G[row][j] (X_j - X_0)_a with G = Gh + Gl and X_j - X_0 = Xh + Xl
+__device__ __forceinline__ double dd_row(const double *__restrict__ Gh, const double *__restrict__ Gl,
+                                         const double *Xh, const double *Xl, int N, int row, int a)
+{
+    double sh = 0.0, sl = 0.0;
+    for (int j = 0; j < N; ++j)
+        dd_acc(sh, sl, Gh[row * N + j], Gl[row * N + j], Xh[3 * j + a], Xl[3 * j + a]);
+    return sh + sl;
+}
+
 __global__ void __launch_bounds__(128) k_geometry(FiberTable F, const double *__restrict__ X,
                                                   const double *__restrict__ fext)
 {
     extern __shared__ double gsm[];
     const Fib fb(F, blockIdx.x);
     const int N = fb.N;
-    double *Xl = gsm;           // [N][3] local coordinates (relative to node 0)
-    double *ts = gsm + 3 * N;   // [N][3] X_s
+    double *Xh = gsm;           // [N][3] X_j - X_0, high part
+    double *Xlo = gsm + 3 * N;  // [N][3] X_j - X_0, low part (exact difference)
     double *Ws = gsm + 6 * N;   // [N]
     const double *x0 = X + 3 * fb.n0;
-    for (int i = threadIdx.x; i < 3 * N; i += blockDim.x) Xl[i] = x0[i] - x0[i % 3];
+    for (int i = threadIdx.x; i < 3 * N; i += blockDim.x) two_sum_d(x0[i], -x0[i % 3], Xh[i], Xlo[i]);
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
         Ws[k] = fb.op[fb.lay.omega + k] * fb.L * 0.5;
         F.W[fb.n0 + k] = Ws[k];
     }
     __syncthreads();
     const double g = fb.g, g4 = g * g * g * g;
-    const double *D1 = fb.M_(fb.lay.D1), *D4 = fb.M_(fb.lay.D4);
+    const double *G1h = fb.M_(fb.lay.G1h), *G1l = fb.M_(fb.lay.G1l);
+    const double *G4h = fb.M_(fb.lay.G4h), *G4l = fb.M_(fb.lay.G4l);
     for (int i = threadIdx.x; i < 3 * N; i += blockDim.x) {
         const int k = i / 3, a = i % 3;
-        double s1 = 0.0, s4 = 0.0;
-        for (int j = 0; j < N; ++j) {
-            s1 += D1[k * N + j] * Xl[3 * j + a];
-            s4 += D4[k * N + j] * Xl[3 * j + a];
-        }
-        ts[i] = g * s1;
-        F.t[3 * fb.n0 + i] = g * s1;
-        F.fknown[3 * fb.n0 + i] = (fext ? fext[3 * fb.n0 + i] : 0.0) - F.E * g4 * s4;
+        F.t[3 * fb.n0 + i] = g * dd_row(G1h, G1l, Xh, Xlo, N, k, a);
+        const double x4 = dd_row(G4h, G4l, Xh, Xlo, N, k, a);
+        F.fknown[3 * fb.n0 + i] = (fext ? fext[3 * fb.n0 + i] : 0.0) - F.E * g4 * x4;
     }
-    const double *Dz = fb.M_(fb.lay.Dz);
-    for (int i = threadIdx.x; i < 3 * (N - 2); i += blockDim.x) {
-        const int k = i / 3, a = i % 3;
-        double s = 0.0;
-        for (int j = 0; j < N; ++j) s += Dz[k * N + j] * Xl[3 * j + a];
-        F.tz[3 * fb.z0 + i] = g * s;
-    }
+    const double *Gzh = fb.M_(fb.lay.Gzh), *Gzl = fb.M_(fb.lay.Gzl);
+    for (int i = threadIdx.x; i < 3 * (N - 2); i += blockDim.x)
+        F.tz[3 * fb.z0 + i] = g * dd_row(Gzh, Gzl, Xh, Xlo, N, i / 3, i % 3);
     if (threadIdx.x < 12) {
+        // which: 0 = X''(+1), 1 = X''(-1), 2 = X'''(+1), 3 = X'''(-1)
         const int which = threadIdx.x / 3, a = threadIdx.x % 3;
-        const double *D = fb.M_(which < 2 ? fb.lay.D2 : fb.lay.D3);
-        const int row = (which & 1) ? N - 1 : 0;   // node 0 is alpha = +1
-        double s = 0.0;
-        for (int j = 0; j < N; ++j) s += D[row * N + j] * Xl[3 * j + a];
-        F.bc[12 * fb.m + threadIdx.x] = s / F.dt;
+        const double *Gh = fb.M_(which < 2 ? fb.lay.G2h : fb.lay.G3h);
+        const double *Gl = fb.M_(which < 2 ? fb.lay.G2l : fb.lay.G3l);
+        F.bc[12 * fb.m + threadIdx.x] = dd_row(Gh, Gl, Xh, Xlo, N, which & 1, a) / F.dt;
     }
     __syncthreads();
     const double c8 = 1.0 / (8.0 * kPi * F.mu);
@@ -116,8 +142,8 @@ __global__ void __launch_bounds__(128) k_geometry(FiberTable F, const double *__
             const int k = i / N, j = i % N;
             double4_32a rec = make_double4_32a(0.0, 0.0, 0.0, 0.0);
             if (j != k) {
-                const double rx = Xl[3 * k] - Xl[3 * j], ry = Xl[3 * k + 1] - Xl[3 * j + 1],
-                             rz = Xl[3 * k + 2] - Xl[3 * j + 2];
+                const double rx = Xh[3 * k] - Xh[3 * j], ry = Xh[3 * k + 1] - Xh[3 * j + 1],
+                             rz = Xh[3 * k + 2] - Xh[3 * j + 2];
                 const double r2 = rx * rx + ry * ry + rz * rz;
                 const double rn = sqrt(r2);
                 rec.x = Ws[j] * c8 / sqrt(r2 + delta * delta);

@@ -86,3 +86,47 @@ def test_integrated_basis_properties():
     d2 = cheb.basis_matrix(BT, pts, 2)
     for j in range(N - 2):
         assert np.allclose(d2[:, j], np.cos(j * np.arccos(pts)), atol=1e-11)
+
+
+@pytest.mark.parametrize("N", [16, 32, 64])
+def test_extended_precision_derivatives_on_polynomials(N):
+    """Derivatives of the interpolant in extended precision are exact on
+    polynomials up to the rounding of the double data amplified by N^(2m)."""
+    ld_eps = 2.0 * float(np.finfo(np.float64).eps)
+    x = cheb.nodes(N)
+    X = np.stack([2.0 + 3.0 * x, 1.0 - x ** 3, 0.25 * x ** 5], axis=1)
+    pts = np.array([1.0, 0.3, -0.77, -1.0])
+    d1 = cheb.interp_derivs_ext(X, pts, 1)
+    exact1 = np.stack([3.0 + 0 * pts, -3 * pts ** 2, 1.25 * pts ** 4], 1)
+    assert np.abs(d1 - exact1).max() <= max(100 * ld_eps * N ** 2 * 3.0, 1e-15)
+    d3 = cheb.interp_derivs_ext(X, pts, 3)
+    exact3 = np.stack([0 * pts, -6.0 + 0 * pts, 15 * pts ** 2], 1)
+    assert np.abs(d3 - exact3).max() <= max(100 * ld_eps * float(N) ** 6 * 3.0, 1e-14)
+
+
+@pytest.mark.parametrize("N", [12, 24])
+def test_extended_precision_matches_high_precision(N):
+    """Against a 40-digit evaluation (mpmath) of the same interpolant on the
+    same double data: the extended-precision route adds only its own rounding."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    rng = np.random.default_rng(N)
+    x = cheb.nodes(N)
+    X = 30.0 + np.stack([np.sin(1.3 * x + 0.2), np.cos(0.7 * x), x ** 2], 1) + 1e-3 * rng.normal(size=(N, 3))
+    pts = [1.0, 0.41, -1.0]
+    ld_eps = float(np.finfo(np.longdouble).eps)
+    xs = [mpmath.cos(mpmath.pi * k / (N - 1)) for k in range(N)]
+    V = mpmath.matrix([[mpmath.chebyt(j, xk) for j in range(N)] for xk in xs])
+    for m in (1, 2, 3):
+        got = cheb.interp_derivs_ext(X, pts, m)
+        for a in range(3):
+            coef = mpmath.lu_solve(V, mpmath.matrix([mpmath.mpf(float(v)) for v in X[:, a]]))
+            # m-th derivative of sum c_j T_j via the polynomial in monomials
+            poly = [mpmath.mpf(0)] * N
+            for j in range(N):
+                tj = mpmath.taylor(lambda t: mpmath.chebyt(j, t), 0, N - 1)
+                for i in range(N):
+                    poly[i] += coef[j] * tj[i]
+            for ip, p in enumerate(pts):
+                val = sum(poly[i] * mpmath.ff(i, m) * mpmath.mpf(p) ** (i - m) for i in range(m, N))
+                assert abs(got[ip, a] - float(val)) <= 1e-13 + 100 * ld_eps * float(N) ** (2 * m) * 30.0
