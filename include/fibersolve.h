@@ -83,8 +83,9 @@ typedef struct {
     int32_t iters;          /* total GMRES iterations (all sweeps) */
     int32_t refine_sweeps;  /* outer refinement sweeps (1 for FS_FP64) */
     double resid;           /* final preconditioned relative residual (FP64 far field) */
-    double t_ms[8];         /* [0] geometry+RHS [1] preconditioner build [2] solve
-                               [3] update [4] total; others reserved */
+    double t_ms[8];         /* host wall-clock ms: [0] right-hand side [1] geometry and
+                               preconditioner build [2] solve [3] update [4] total;
+                               others reserved (filled when info is requested) */
     int64_t pairs;          /* Stokeslet pairs evaluated */
 } fs_step_info;
 
@@ -158,7 +159,9 @@ fs_status fs_surface_apply(fs_ctx *ctx, const double *q, double *out, int32_t su
 fs_status fs_build_precond(fs_ctx *ctx);
 
 /* One implicit backward-Euler step (Sec. 3.2, set:time-stepping): solve
- * A u = b by block-Jacobi preconditioned GMRES (Sec. 3.3), then X <- X + dt V.
+ * P^-1 A u = P^-1 b by GMRES with the block-Jacobi preconditioner P of Eq. prec
+ * (Sec. 3.3), then X <- X + dt V.  The preconditioned operator is applied as
+ * v + P^-1 (A - P) v on the fiber unknowns (P is their exact self block).
  * info may be NULL; when given it is filled (and the stream synchronised).
  * FS_ENOTCONV leaves the state unchanged. */
 fs_status fs_step(fs_ctx *ctx, fs_step_info *info);

@@ -115,7 +115,8 @@ struct fs_ctx {
     // Krylov workspace
     int kdim = 0;
     double *d_basis = nullptr, *d_b = nullptr, *d_x = nullptr, *d_r = nullptr, *d_w = nullptr,
-           *d_e = nullptr, *d_res = nullptr, *d_cor = nullptr, *d_h = nullptr, *d_part = nullptr;
+           *d_e = nullptr, *d_res = nullptr, *d_cor = nullptr, *d_pb = nullptr, *d_h = nullptr,
+           *d_part = nullptr;
     double *h_pinned = nullptr;
     fs::Surface surf;
     double *d_usurf = nullptr;    // fiber Stokeslets at the surface nodes [n_s][3]
@@ -134,9 +135,11 @@ void context_free(fs_ctx *c);
 fs_status launch_geometry(fs_ctx *c);
 // f (and W f) at the nodes from the unknowns u (or f_known when u == nullptr)
 fs_status launch_force(fs_ctx *c, const double *u, double *f, double *wf);
-// rows of the fiber equations: out = B u + Rw(ubar) [+ const and known force, negated, when rhs]
+// rows of the fiber equations; mode 0: out = B u + Rw(ubar); 1: right-hand side
+// b = -(rows of the known force and free-end data + Rw(ubar)); 2: out = Rw(ubar)
+enum : int { ROWS_FULL = 0, ROWS_RHS = 1, ROWS_COUPLING = 2 };
 fs_status launch_rows(fs_ctx *c, const double *u, const double *f, const double *ubar, double *out,
-                      bool rhs);
+                      int mode);
 fs_status launch_block_build(fs_ctx *c);
 fs_status launch_lu_factor(fs_ctx *c);
 fs_status launch_lu_solve(fs_ctx *c, const double *in, double *out);

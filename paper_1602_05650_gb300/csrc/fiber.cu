@@ -319,21 +319,28 @@ __global__ void __launch_bounds__(128) k_force(FiberTable F, const double *__res
     }
 }
 
+// mode 0: rows of A u (self + coupling); 1: right-hand side (known force,
+// free-end data, negated; u unused); 2: coupling rows only, Rw(ubar) (the
+// off-diagonal part A - P of Eq. prec for the fiber blocks).
 __global__ void __launch_bounds__(128) k_rows(FiberTable F, const double *__restrict__ u,
                                               const double *__restrict__ f,
                                               const double *__restrict__ ubar,
-                                              double *__restrict__ out, int rhs)
+                                              double *__restrict__ out, int mode)
 {
     extern __shared__ double rsm[];
     const Fib fb(F, blockIdx.x);
     const int N = fb.N;
     double *us = rsm, *fs_ = us + 4 * N, *w = fs_ + 3 * N;
-    for (int i = threadIdx.x; i < 4 * N; i += blockDim.x) us[i] = u ? u[fb.u0 + i] : 0.0;
-    for (int i = threadIdx.x; i < 3 * N; i += blockDim.x) fs_[i] = f[3 * fb.n0 + i];
+    for (int i = threadIdx.x; i < 4 * N; i += blockDim.x) us[i] = (u && mode == 0) ? u[fb.u0 + i] : 0.0;
+    if (mode == 2) {
+        for (int i = threadIdx.x; i < 3 * N; i += blockDim.x) w[i] = ubar[3 * fb.n0 + i];
+    } else {
+        for (int i = threadIdx.x; i < 3 * N; i += blockDim.x) fs_[i] = f[3 * fb.n0 + i];
+        __syncthreads();
+        dev_selfvel(F, fb, fs_, 1, ubar, w);
+    }
     __syncthreads();
-    dev_selfvel(F, fb, fs_, 1, ubar, w);
-    __syncthreads();
-    dev_rows(F, fb, us, w, 1, rhs != 0, out + fb.u0, 0);
+    dev_rows(F, fb, us, w, 1, mode == 1, out + fb.u0, 0);
 }
 
 // One CTA per (fiber, chunk of nb columns): B[:, col] = rows(e_col) with ubar = 0.
@@ -532,11 +539,11 @@ fs_status launch_force(fs_ctx *c, const double *u, double *f, double *wf)
 }
 
 fs_status launch_rows(fs_ctx *c, const double *u, const double *f, const double *ubar, double *out,
-                      bool rhs)
+                      int mode)
 {
     if (c->M == 0) return FS_OK;
     const size_t sm = static_cast<size_t>(10 * c->max_N) * sizeof(double);
-    k_rows<<<c->M, 128, sm, c->stream>>>(c->table(), u, f, ubar, out, rhs ? 1 : 0);
+    k_rows<<<c->M, 128, sm, c->stream>>>(c->table(), u, f, ubar, out, mode);
     FS_LAUNCH_CHECK();
     return FS_OK;
 }

@@ -158,32 +158,39 @@ fs_status far_field(fs_ctx *c, int sum_prec, bool hilo)
     return FS_OK;
 }
 
-// out = A v (sum_prec selects the far-field arithmetic)
-fs_status matvec(fs_ctx *c, const double *v, double *out, int sum_prec)
+// Preconditioned operator of Eq. prec, out = P^-1 A v, evaluated as
+//   fibers : v + P^-1 (A - P) v  -- P is exactly the self block, so only the
+//            coupling rows Rw(ubar) pass through the block solves (the block's
+//            own rounding is never amplified by its inverse, cond ~1e9);
+//   surface: D^-1 (S q + fiber Stokeslets)  -- D the Jacobi diagonal.
+// sum_prec selects the far-field arithmetic.
+fs_status apply_pa(fs_ctx *c, const double *v, double *out, int sum_prec)
 {
     FS_TRY(launch_force(c, v, c->d_f, c->d_wf));
     FS_TRY(far_field(c, sum_prec, false));
     const double *q = c->surf.n ? v + c->n_fib_unk : nullptr;
     if (c->surf.n) FS_TRY(surface_couplings(c, q, c->d_ubar, sum_prec, false));
-    FS_TRY(launch_rows(c, v, c->d_f, c->d_ubar, out, false));
-    if (c->surf.n) FS_TRY(surface_rows(c, q, c->d_usurf, out + c->n_fib_unk, false, sum_prec, false));
+    FS_TRY(launch_rows(c, nullptr, c->d_f, c->d_ubar, c->d_e, ROWS_COUPLING));
+    FS_TRY(launch_lu_solve(c, c->d_e, out));
+    k_add<<<blocks_for(c->n_fib_unk), 256, 0, c->stream>>>(out, v, c->n_fib_unk);
+    FS_LAUNCH_CHECK();
+    if (c->surf.n) {
+        FS_TRY(surface_rows(c, q, c->d_usurf, c->d_e + c->n_fib_unk, false, sum_prec, false));
+        FS_TRY(surface_precond(c, c->d_e + c->n_fib_unk, out + c->n_fib_unk));
+    }
     return FS_OK;
 }
 
-fs_status rhs(fs_ctx *c, double *b)
+// b (Eq. sche-linear-eq right-hand side) with the FP64 far field, then pb = P^-1 b
+fs_status rhs(fs_ctx *c, double *b, double *pb)
 {
     FS_TRY(launch_force(c, nullptr, c->d_f, c->d_wf));
     FS_TRY(far_field(c, FS_SUM_FP64, false));
     if (c->surf.n) FS_TRY(surface_couplings(c, nullptr, c->d_ubar, FS_SUM_FP64, false));
-    FS_TRY(launch_rows(c, nullptr, c->d_f, c->d_ubar, b, true));
+    FS_TRY(launch_rows(c, nullptr, c->d_f, c->d_ubar, b, ROWS_RHS));
     if (c->surf.n) FS_TRY(surface_rows(c, nullptr, c->d_usurf, b + c->n_fib_unk, true, FS_SUM_FP64, false));
-    return FS_OK;
-}
-
-fs_status precond(fs_ctx *c, const double *in, double *out)
-{
-    FS_TRY(launch_lu_solve(c, in, out));
-    if (c->surf.n) FS_TRY(surface_precond(c, in + c->n_fib_unk, out + c->n_fib_unk));
+    FS_TRY(launch_lu_solve(c, b, pb));
+    if (c->surf.n) FS_TRY(surface_precond(c, b + c->n_fib_unk, pb + c->n_fib_unk));
     return FS_OK;
 }
 
@@ -193,9 +200,9 @@ struct GmresResult {
     bool converged = false;
 };
 
-// Left-preconditioned restarted GMRES for A x = b (x0 = 0); x overwritten.
-// Tolerance relative to ||P^-1 b||.
-fs_status gmres(fs_ctx *c, const double *b, double *x, double tol, int max_iter, int sum_prec,
+// Restarted GMRES for (P^-1 A) x = pb, x0 = 0 (x overwritten); tolerance
+// relative to ||pb|| = ||P^-1 b||.
+fs_status gmres(fs_ctx *c, const double *pb, double *x, double tol, int max_iter, int sum_prec,
                 GmresResult *res)
 {
     const int64_t n = c->n_unk;
@@ -203,7 +210,7 @@ fs_status gmres(fs_ctx *c, const double *b, double *x, double tol, int max_iter,
     double *V = c->d_basis;
     *res = GmresResult();
     FS_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), c->stream));
-    FS_TRY(precond(c, b, c->d_r));
+    FS_CUDA(cudaMemcpyAsync(c->d_r, pb, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     double *d_beta = c->d_h + 2 * c->kdim + 2;
     FS_TRY(dev_norm(c, c->d_r, n, d_beta));
     double beta0;
@@ -224,21 +231,20 @@ fs_status gmres(fs_ctx *c, const double *b, double *x, double tol, int max_iter,
         FS_LAUNCH_CHECK();
         std::fill(g.begin(), g.end(), 0.0);
         g[0] = beta;
-        int j = 0, kcols = 0;
+        int kcols = 0;
         bool done = false;
-        for (j = 0; j < R; ++j) {
+        for (int j = 0; j < R; ++j) {
             double *Vj = V + j * n, *Vn = V + (j + 1) * n;
-            FS_TRY(matvec(c, Vj, c->d_e, sum_prec));
-            FS_TRY(precond(c, c->d_e, c->d_w));
+            FS_TRY(apply_pa(c, Vj, c->d_w, sum_prec));
             double *h = c->d_h;
             for (int pass = 0; pass < 2; ++pass) {   // CGS2
+                double *hp = h + (pass ? c->kdim : 0);
                 k_multidot<<<dim3(kDotBlocks, j + 1), 256, 0, c->stream>>>(V, n, j + 1, c->d_w, n,
                                                                           c->d_part);
                 FS_LAUNCH_CHECK();
-                k_finish_dots<<<1, 256, 0, c->stream>>>(c->d_part, j + 1, h + (pass ? c->kdim : 0), 0, 0);
+                k_finish_dots<<<1, 256, 0, c->stream>>>(c->d_part, j + 1, hp, 0, 0);
                 FS_LAUNCH_CHECK();
-                k_axpy_multi<<<blocks_for(n), 256, 0, c->stream>>>(c->d_w, V, n, h + (pass ? c->kdim : 0),
-                                                                   j + 1, n);
+                k_axpy_multi<<<blocks_for(n), 256, 0, c->stream>>>(c->d_w, V, n, hp, j + 1, n);
                 FS_LAUNCH_CHECK();
             }
             FS_TRY(dev_norm(c, c->d_w, n, h + 2 * c->kdim));
@@ -295,11 +301,10 @@ fs_status gmres(fs_ctx *c, const double *b, double *x, double tol, int max_iter,
         FS_LAUNCH_CHECK();
         FS_CUDA(cudaStreamSynchronize(c->stream));   // h_pinned is reused below
         if (done) break;
-        // restart: r = P^-1 (b - A x)
-        FS_TRY(matvec(c, x, c->d_e, sum_prec));
-        k_sub<<<blocks_for(n), 256, 0, c->stream>>>(b, c->d_e, c->d_w, n);
+        // restart: r = pb - P^-1 A x
+        FS_TRY(apply_pa(c, x, c->d_w, sum_prec));
+        k_sub<<<blocks_for(n), 256, 0, c->stream>>>(pb, c->d_w, c->d_r, n);
         FS_LAUNCH_CHECK();
-        FS_TRY(precond(c, c->d_w, c->d_r));
         FS_TRY(dev_norm(c, c->d_r, n, d_beta));
         FS_TRY(read_scalar(c, d_beta, &beta));
         res->rel = beta / beta0;
@@ -312,20 +317,19 @@ fs_status gmres(fs_ctx *c, const double *b, double *x, double tol, int max_iter,
     return FS_OK;
 }
 
-// ||P^-1 (b - A x)|| / ||P^-1 b|| with the FP64 far field; r_out = b - A x.
-fs_status true_residual(fs_ctx *c, const double *b, const double *x, double bnorm, double *r_out,
+// r_out = pb - P^-1 A x with the FP64 far field; *rel = ||r_out|| / pbnorm.
+fs_status true_residual(fs_ctx *c, const double *pb, const double *x, double pbnorm, double *r_out,
                         double *rel)
 {
     const int64_t n = c->n_unk;
-    FS_TRY(matvec(c, x, c->d_e, FS_SUM_FP64));
-    k_sub<<<blocks_for(n), 256, 0, c->stream>>>(b, c->d_e, r_out, n);
+    FS_TRY(apply_pa(c, x, c->d_w, FS_SUM_FP64));
+    k_sub<<<blocks_for(n), 256, 0, c->stream>>>(pb, c->d_w, r_out, n);
     FS_LAUNCH_CHECK();
-    FS_TRY(precond(c, r_out, c->d_w));
     double *d_tmp = c->d_h + 2 * c->kdim + 3;
-    FS_TRY(dev_norm(c, c->d_w, n, d_tmp));
+    FS_TRY(dev_norm(c, r_out, n, d_tmp));
     double rn;
     FS_TRY(read_scalar(c, d_tmp, &rn));
-    *rel = bnorm > 0.0 ? rn / bnorm : 0.0;
+    *rel = pbnorm > 0.0 ? rn / pbnorm : 0.0;
     return FS_OK;
 }
 
@@ -455,6 +459,7 @@ fs_status context_init(fs_ctx *c, int M, const int32_t *ppf, const fs_boundary *
     FS_TRY(dalloc(&c->d_e, n));
     FS_TRY(dalloc(&c->d_res, n));
     FS_TRY(dalloc(&c->d_cor, n));
+    FS_TRY(dalloc(&c->d_pb, n));
     FS_TRY(dalloc(&c->d_h, 4 * c->kdim + 8));
     FS_TRY(dalloc(&c->d_part, static_cast<size_t>(c->kdim) * kDotBlocks));
     if (c->surf.n) {
@@ -484,7 +489,7 @@ void context_free(fs_ctx *c)
                     c->d_z_ptr, c->d_ops_off, c->d_ops, c->d_excl, c->d_X, c->d_L, c->d_fext,
                     c->d_t, c->d_tz, c->d_fknown, c->d_W, c->d_mloc, c->d_bc, c->d_kp, c->d_B,
                     c->d_piv, c->d_V, c->d_T, c->d_f, c->d_wf, c->d_ubar, c->d_basis, c->d_b,
-                    c->d_x, c->d_r, c->d_w, c->d_e, c->d_res, c->d_cor, c->d_h, c->d_part, c->surf.y, c->surf.nrm,
+                    c->d_x, c->d_r, c->d_w, c->d_e, c->d_res, c->d_cor, c->d_pb, c->d_h, c->d_part, c->surf.y, c->surf.nrm,
                     c->surf.w, c->surf.diag, c->d_usurf, c->surf.A, c->surf.tmp, c->surf.flux, c->surf.excl};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -601,40 +606,38 @@ fs_status fs_step(fs_ctx *c, fs_step_info *info)
         FS_TRY(launch_geometry(c));
         c->geometry_ok = true;
     }
-    FS_TRY(rhs(c, c->d_b));
+    if (!c->precond_ok) FS_TRY(fs_build_precond(c));
     if (info) {
         FS_CUDA(cudaStreamSynchronize(c->stream));
-        tms[0] = ms_since(t0);
+        tms[1] = ms_since(t0);
     }
-    if (!c->precond_ok) FS_TRY(fs_build_precond(c));
+    FS_TRY(rhs(c, c->d_b, c->d_pb));
     FS_TRY(check_status(c));
-    tms[1] = ms_since(t0) - tms[0];
+    if (info) tms[0] = ms_since(t0) - tms[1];
     const int64_t n = c->n_unk;
     int iters = 0, sweeps = 0;
     double rel = 0.0;
     bool converged = false;
     if (c->opt.prec == FS_FP64) {
         GmresResult gr;
-        FS_TRY(gmres(c, c->d_b, c->d_x, c->opt.tol, c->opt.max_iter, FS_SUM_FP64, &gr));
+        FS_TRY(gmres(c, c->d_pb, c->d_x, c->opt.tol, c->opt.max_iter, FS_SUM_FP64, &gr));
         iters = gr.iters;
         rel = gr.rel;
         sweeps = 1;
         converged = gr.converged;
     } else {
-        // ||P^-1 b|| for the refinement test
-        FS_TRY(precond(c, c->d_b, c->d_w));
         double *d_tmp = c->d_h + 2 * c->kdim + 3;
-        FS_TRY(dev_norm(c, c->d_w, n, d_tmp));
-        double bnorm;
-        FS_TRY(read_scalar(c, d_tmp, &bnorm));
+        FS_TRY(dev_norm(c, c->d_pb, n, d_tmp));
+        double pbnorm;
+        FS_TRY(read_scalar(c, d_tmp, &pbnorm));
         double *u = c->d_x, *d_res = c->d_res, *d_cor = c->d_cor;
         FS_CUDA(cudaMemsetAsync(u, 0, n * sizeof(double), c->stream));
-        FS_CUDA(cudaMemcpyAsync(d_res, c->d_b, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+        FS_CUDA(cudaMemcpyAsync(d_res, c->d_pb, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
         fs_status st = FS_OK;
         rel = 1.0;
         for (sweeps = 0; sweeps < std::max(1, c->opt.max_refine);) {
             GmresResult gr;
-            // inner solve only needs to shrink this sweep's residual to (about) the target
+            // the inner solve only needs to shrink this sweep's residual to (about) the target
             const double inner = std::max(c->opt.inner_tol, 0.1 * c->opt.tol / std::max(rel, 1e-300));
             st = gmres(c, d_res, d_cor, std::min(inner, 0.5), c->opt.max_iter, FS_SUM_FP32, &gr);
             if (st != FS_OK) break;
@@ -646,7 +649,7 @@ fs_status fs_step(fs_ctx *c, fs_step_info *info)
                 set_error("fs_step: refinement update launch");
                 break;
             }
-            st = true_residual(c, c->d_b, u, bnorm, d_res, &rel);
+            st = true_residual(c, c->d_pb, u, pbnorm, d_res, &rel);
             if (st != FS_OK) break;
             if (rel <= c->opt.tol) {
                 converged = true;
