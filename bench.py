@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Benchmark: implicit steps/s of the 1,024-fiber x 64-point curved-fiber cloud
+(65,536 points in [0,40]^3, N(0,1) external force per node), mixed precision
+(FP32 far field inside GMRES, FP64 refinement to 1e-8), one GPU per rank.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Each rank solves an independent replica (seed = rank): weak scaling, no
+collective on the data path; the barrier and the max-over-ranks timing use
+torch.distributed.  Prints ONE JSON line on rank 0.
+
+--impl reference times the CPU oracle (the plain FP64 implementation in
+oracle/) on a bounded sample of the same workload on this host's cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+FLOPS_PER_PAIR = {"stokeslet": 27.0, "stresslet": 31.0}
+KS_NAMES = ["stokeslet_fp32", "stokeslet_fp64", "stresslet_fp32", "stresslet_fp64"]
+WORKLOAD = "cloud-1024x64: 1,024 curved fibers x 64 Chebyshev points (65,536 points), [0,40]^3"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows if len(r) >= 9 for k in range(4)
+                          if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(sm)}
+
+
+def oracle_baseline(s, gpu_fp64_iters: int, budget_fibers: int = 24, budget_targets: int = 1024):
+    """Time the CPU oracle on a bounded sample of the workload and scale to one
+    step: per-fiber setup (geometry, self block, LU) for `budget_fibers` fibers
+    scaled to all fibers, plus (1 + iters) far-field sums, each timed on
+    `budget_targets` targets x all sources and scaled to all targets."""
+    from oracle import kernels as ok
+    from oracle import system
+    ok.build()
+    M, N = s.n_fibers, int(s.n_per_fiber[0])
+    sub = wl.Suspension(s.n_per_fiber[:budget_fibers], s.X[:budget_fibers * N], s.L[:budget_fibers],
+                        s.f_ext[:budget_fibers * N], s.mu, s.eps, s.E, s.dt)
+    t0 = time.perf_counter()
+    system.from_suspension(sub)
+    t_setup = (time.perf_counter() - t0) * M / budget_fibers
+    fid = s.fiber_id()
+    W = np.repeat(s.L / 2.0, N)[:, None] * 0.02 * s.f_ext
+    idx = np.linspace(0, s.n_points - 1, budget_targets).astype(np.int64)
+    t0 = time.perf_counter()
+    ok.stokeslet(s.X[idx], s.X, W, s.mu, fid[idx], fid)
+    t_ff = (time.perf_counter() - t0) * s.n_points / budget_targets
+    n_ff = 1 + gpu_fp64_iters
+    t_step = t_setup + n_ff * t_ff
+    sample = ("oracle setup of %d of %d fibers (x%.0f) + far-field sum on %d of %d targets "
+              "(x%.0f), times %d far fields (right-hand side + %d GMRES iterations of the FP64 "
+              "path on the same step); %.1f s measured" % (
+                  budget_fibers, M, M / budget_fibers, budget_targets, s.n_points,
+                  s.n_points / budget_targets, n_ff, gpu_fp64_iters,
+                  t_setup * budget_fibers / M + t_ff * budget_targets / s.n_points))
+    return {"value": 1.0 / t_step, "unit": "steps/s", "cores": ok.threads(), "kind": "oracle",
+            "sample": sample, "seconds_per_step_extrapolated": t_step}
+
+
+def traffic_for(kernel_class: str):
+    """DRAM bytes per launch from a committed ncu capture, if it was taken on
+    the current source of the kernel (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        import hashlib
+        rec = json.load(open(p)).get(kernel_class)
+        src = open(os.path.join(ROOT, "paper_1602_05650_gb300", "csrc", "pairsum.cu"), "rb").read()
+        if rec and rec.get("pairsum_sha1") == hashlib.sha1(src).hexdigest():
+            return rec.get("dram_bytes_per_launch")
+    except Exception:
+        return None
+    return None
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    s = wl.cfg_cloud_mixed(0)
+    vals = []
+    base = None
+    for k in range(args.warmup + args.steps):
+        base = oracle_baseline(s, gpu_fp64_iters=args.ref_iters, budget_fibers=8, budget_targets=256)
+        if k >= args.warmup:
+            vals.append(base["seconds_per_step_extrapolated"])
+    t = float(np.mean(vals))
+    line = {"metric": "implicit steps/s (%s; mixed FP32/FP64, GMRES 1e-8)" % WORKLOAD,
+            "value": 1.0 / t, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "fibers": s.n_fibers, "points_per_fiber": 64},
+            "cpu_baseline": {"kind": "oracle", "cores": base["cores"], "sample": base["sample"],
+                             "value": 1.0 / t, "unit": "steps/s"},
+            "e2e": {"value": 1.0 / t, "unit": "steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_kernel(args, ws, rank, local, fs, torch, dist):
+    """Direct-sum kernel alone: the cloud's far field with same-fiber exclusion."""
+    dev = torch.device("cuda", local)
+    s = wl.cfg_cloud_mixed(seed=rank)
+    P = args.points or s.n_points
+    prec = fs.FS_SUM_FP32 if args.kernel == "stokeslet_fp32" else fs.FS_SUM_FP64
+    opt = fs.fs_options_default()
+    opt.profile = 1
+    stream = torch.cuda.Stream(device=dev)
+    h = fs.fs_create([], s.mu, s.eps, s.E, s.dt, options=opt, stream=stream)
+    X = torch.tensor(s.X[:P], dtype=torch.float64, device=dev)
+    Wf = torch.tensor(s.f_ext[:P] * 0.02, dtype=torch.float64, device=dev)
+    fid = torch.tensor(s.fiber_id()[:P], dtype=torch.int32, device=dev)
+    out = torch.empty_like(X)
+    for _ in range(args.warmup):
+        fs.fs_stokeslet_apply(h, X, Wf, X, out, fid, fid, prec)
+    torch.cuda.synchronize()
+    fs.fs_kernel_stats(h, reset=True)
+    for _ in range(args.steps):
+        fs.fs_stokeslet_apply(h, X, Wf, X, out, fid, fid, prec)
+    st = fs.fs_kernel_stats(h, reset=True)[0 if prec == fs.FS_SUM_FP32 else 1]
+    fs.fs_destroy(h)
+    if rank == 0:
+        pairs_s = st[2] / (st[1] * 1e-3)
+        print(json.dumps({"kernel": args.kernel, "points": P, "launches": st[0],
+                          "ms_per_launch": st[1] / st[0], "pairs_per_s": pairs_s,
+                          "tflops": 27.0 * pairs_s / 1e12}), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--ref-iters", type=int, default=10,
+                    help="GMRES iterations assumed for the reference arm's extrapolation")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--kernel", choices=["stokeslet_fp32", "stokeslet_fp64"], default=None,
+                    help="time only the direct-sum kernel on the cloud (fs_stokeslet_apply)")
+    ap.add_argument("--points", type=int, default=0,
+                    help="--kernel: use the first P points of the cloud (0 = all)")
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+
+    import torch
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "native" else "gloo")
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    torch.cuda.set_device(local)
+    from paper_1602_05650_gb300 import build as fsbuild
+    fsbuild.build()
+    import paper_1602_05650_gb300 as fs
+    if args.kernel:
+        return run_kernel(args, ws, rank, local, fs, torch, dist)
+
+    dev = torch.device("cuda", local)
+    s = wl.cfg_cloud_mixed(seed=rank)
+    stream = torch.cuda.Stream(device=dev)
+    opt = fs.fs_options_default()
+    opt.prec = fs.FS_MIXED
+    opt.tol = 1e-8
+    opt.profile = 1
+    h = fs.fs_create(s.n_per_fiber, s.mu, s.eps, s.E, s.dt, options=opt, stream=stream)
+    X = torch.tensor(s.X, dtype=torch.float64, device=dev)
+    L = torch.tensor(s.L, dtype=torch.float64, device=dev)
+    F = torch.tensor(s.f_ext, dtype=torch.float64, device=dev)
+    fs.fs_set_state(h, X, L, F)
+    infos = []
+    for _ in range(args.warmup):
+        fs.fs_step(h, info=False)
+    torch.cuda.synchronize()
+    fs.fs_kernel_stats(h, reset=True)
+
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    n0 = fs.fs_kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        infos.append(fs.fs_step(h, info=True))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = fs.fs_kernel_launches() - n0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    stats = fs.fs_kernel_stats(h, reset=True)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    pinned = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    Xh, Lh, Fh = pinned(s.X), pinned(s.L), pinned(s.f_ext)
+    Vh = torch.empty(Xh.shape, dtype=torch.float64).pin_memory().numpy()
+    e2e_steps = max(2, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        fs.fs_set_state(h, Xh, Lh, Fh)
+        fs.fs_step(h, info=False)
+        fs.fs_get_state(h, V=Vh)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = Xh.nbytes + Lh.nbytes + Fh.nbytes
+    d2h = Vh.nbytes
+    fs.fs_destroy(h)
+
+    # plain FP64 GPU path on the same workload (one step after one warm-up)
+    fp64 = None
+    if not args.no_fp64:
+        o64 = fs.fs_options_default()
+        o64.prec = fs.FS_FP64
+        o64.tol = 1e-8
+        h64 = fs.fs_create(s.n_per_fiber, s.mu, s.eps, s.E, s.dt, options=o64, stream=stream)
+        fs.fs_set_state(h64, X.new_tensor(s.X), L, F)
+        fs.fs_step(h64, info=False)
+        fs.fs_set_state(h64, X.new_tensor(s.X), L, F)
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        inf64 = fs.fs_step(h64, info=True)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        fp64 = {"ms_per_step": a0.elapsed_time(a1), "iters": inf64.iters, "resid": inf64.resid}
+        fs.fs_destroy(h64)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant direct-sum kernel (CUDA events on the context's stream)
+    fp32_peak = fs.fs_probe_fma(1)
+    fp64_peak = fs.fs_probe_fma(0)
+    per_class = {KS_NAMES[k]: {"launches": stats[k][0], "ms": stats[k][1], "pairs": stats[k][2]}
+                 for k in range(4)}
+    dom = max(range(4), key=lambda k: stats[k][1])
+    launches_d, total_ms, pairs = stats[dom]
+    kind = "stresslet" if dom >= 2 else "stokeslet"
+    is64 = dom in (1, 3)
+    ach = FLOPS_PER_PAIR[kind] * pairs / (total_ms * 1e-3) / 1e12 if total_ms > 0 else 0.0
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    derived_fp32 = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    peak = (fp64_peak / 1e12) if is64 else derived_fp32
+    roofline = {"bound": "alu", "kernel": "k_pairsum " + KS_NAMES[dom],
+                "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak if peak else None,
+                "traffic": traffic_for(KS_NAMES[dom]),
+                "flops_per_pair": FLOPS_PER_PAIR[kind],
+                "peak_source": ("measured FP64 FMA loop (fs_probe_fma)" if is64 else
+                                "152 SMs x 128 FP32 lanes x 2 x max SM clock"),
+                "launch_ms_avg": total_ms / launches_d if launches_d else None,
+                "measured_fp32_fma_tflops": fp32_peak / 1e12,
+                "measured_fp64_fma_tflops": fp64_peak / 1e12}
+    st32 = per_class["stokeslet_fp32"]
+    pairs_per_s = st32["pairs"] / (st32["ms"] * 1e-3) if st32["ms"] > 0 else None
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        cpu = oracle_baseline(s, fp64["iters"] if fp64 else args.ref_iters)
+    value = ws * 1e3 / ms
+    line = {
+        "metric": "implicit steps/s (%s; mixed FP32/FP64, GMRES 1e-8)" % WORKLOAD,
+        "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 far field + f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "fibers": s.n_fibers, "points_per_fiber": 64,
+                   "precision": "mixed", "tol": 1e-8, "eps": s.eps, "mu": s.mu, "E": s.E, "dt": s.dt,
+                   "l2": "inputs larger than L2 (per-step fiber blocks 537 MB, Krylov basis 128 MB)",
+                   "parallelism": "replicas" if ws > 1 else "1 GPU"},
+        "roofline": roofline,
+        "cpu_baseline": ({"value": cpu["value"], "unit": "steps/s", "cores": cpu["cores"],
+                          "kind": "oracle", "sample": cpu["sample"]} if cpu else None),
+        "e2e": {"value": ws / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
+        "clocks": clk,
+        "stokeslet_pairs_per_s_fp32": pairs_per_s,
+        "kernels": per_class,
+        "step": {"gmres_iters": [i.iters for i in infos], "sweeps": [i.refine_sweeps for i in infos],
+                 "resid": [i.resid for i in infos],
+                 "t_ms_rhs_build_solve": [[round(i.t_ms[0], 2), round(i.t_ms[1], 2), round(i.t_ms[2], 2)]
+                                          for i in infos]},
+        "fp64_path": fp64,
+        "mixed_speedup_vs_fp64": (fp64["ms_per_step"] / ms) if fp64 else None,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

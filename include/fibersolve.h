@@ -77,7 +77,24 @@ typedef struct {
     int32_t lsb;            /* 1 = local slender-body theory: drop K_delta (default 0) */
     int32_t use_graph;      /* reserved: capture the inner iteration in a CUDA graph */
     int32_t tile_override;  /* 0 = autotuned far-field launch shape, else a shape id */
+    int32_t profile;        /* 1 = bracket every direct-sum kernel with CUDA events on the
+                               context's stream (read with fs_kernel_stats) (default 0) */
 } fs_options;
+
+/* Direct-sum kernel classes reported by fs_kernel_stats. */
+typedef enum {
+    FS_KS_STOKESLET_FP32 = 0,
+    FS_KS_STOKESLET_FP64 = 1,
+    FS_KS_STRESSLET_FP32 = 2,
+    FS_KS_STRESSLET_FP64 = 3,
+    FS_KS_COUNT = 6
+} fs_kernel_class;
+
+typedef struct {
+    int64_t launches;   /* kernel launches recorded */
+    double total_ms;    /* summed CUDA-event durations of those launches */
+    double pairs;       /* pair interactions they evaluated */
+} fs_kernel_stat;
 
 typedef struct {
     int32_t iters;          /* total GMRES iterations (all sweeps) */
@@ -165,6 +182,20 @@ fs_status fs_build_precond(fs_ctx *ctx);
  * info may be NULL; when given it is filled (and the stream synchronised).
  * FS_ENOTCONV leaves the state unchanged. */
 fs_status fs_step(fs_ctx *ctx, fs_step_info *info);
+
+/* Per-class totals of the direct-sum kernels recorded since the last reset
+ * (requires opt.profile = 1; otherwise all zero).  out: [FS_KS_COUNT].
+ * Synchronises the context's stream.  reset != 0 clears the records. */
+fs_status fs_kernel_stats(fs_ctx *ctx, fs_kernel_stat *out, int32_t reset);
+
+/* Number of CUDA kernels this library has launched in this process. */
+uint64_t fs_kernel_launches(void);
+
+/* Measured arithmetic throughput of the current device's CUDA cores: a
+ * register-resident FMA loop over all SMs (precision 0 = FP64, 1 = FP32),
+ * timed with CUDA events; *flops_per_s receives 2 x FMAs / s.  Used as the
+ * roofline peak of the pipe-bound direct sums.  Synchronises the device. */
+fs_status fs_probe_fma(int32_t precision, double *flops_per_s);
 
 /* Number of points N_tot and unknowns of the context. */
 fs_status fs_sizes(const fs_ctx *ctx, int64_t *n_points, int64_t *n_unknowns);

@@ -19,7 +19,8 @@ from ._native import (FS_FP64, FS_MIXED, FS_SUM_FP32, FS_SUM_FP64, fs_boundary, 
 
 __all__ = ["fs_options_default", "fs_create", "fs_destroy", "fs_set_state", "fs_get_state",
            "fs_stokeslet_apply", "fs_stresslet_apply", "fs_surface_apply", "fs_build_precond",
-           "fs_step", "fs_sizes", "fs_last_error", "FsError", "FS_FP64", "FS_MIXED",
+           "fs_step", "fs_sizes", "fs_last_error", "fs_kernel_stats", "fs_kernel_launches",
+           "fs_probe_fma", "FsError", "FS_FP64", "FS_MIXED",
            "FS_SUM_FP32", "FS_SUM_FP64"]
 
 
@@ -186,3 +187,21 @@ def fs_step(h: Handle, info: bool = True) -> Optional[fs_step_info]:
     inf = fs_step_info()
     _check(_native.load().fs_step(h.ptr, ctypes.byref(inf) if info else None), "fs_step")
     return inf if info else None
+
+
+def fs_kernel_stats(h: Handle, reset: bool = False):
+    """[(launches, total_ms, pairs)] per direct-sum kernel class (see fs_kernel_class)."""
+    arr = (_native.fs_kernel_stat * _native.FS_KS_COUNT)()
+    _check(_native.load().fs_kernel_stats(h.ptr, arr, 1 if reset else 0), "fs_kernel_stats")
+    return [(a.launches, a.total_ms, a.pairs) for a in arr]
+
+
+def fs_kernel_launches() -> int:
+    return int(_native.load().fs_kernel_launches())
+
+
+def fs_probe_fma(precision: int) -> float:
+    """Measured FMA throughput (flop/s) of the FP64 (0) or FP32 (1) pipe."""
+    v = ctypes.c_double()
+    _check(_native.load().fs_probe_fma(int(precision), ctypes.byref(v)), "fs_probe_fma")
+    return v.value

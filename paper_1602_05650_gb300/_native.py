@@ -30,7 +30,15 @@ class fs_boundary(ctypes.Structure):
 class fs_options(ctypes.Structure):
     _fields_ = [("prec", c_int32), ("tol", c_double), ("max_iter", c_int32), ("restart", c_int32),
                 ("max_refine", c_int32), ("inner_tol", c_double), ("delta_over_L", c_double),
-                ("lsb", c_int32), ("use_graph", c_int32), ("tile_override", c_int32)]
+                ("lsb", c_int32), ("use_graph", c_int32), ("tile_override", c_int32),
+                ("profile", c_int32)]
+
+
+class fs_kernel_stat(ctypes.Structure):
+    _fields_ = [("launches", c_int64), ("total_ms", c_double), ("pairs", c_double)]
+
+
+FS_KS_COUNT = 6
 
 
 class fs_step_info(ctypes.Structure):
@@ -52,6 +60,9 @@ SIGNATURES = {
     "fs_build_precond": (c_int32, [P]),
     "fs_step": (c_int32, [P, ctypes.POINTER(fs_step_info)]),
     "fs_sizes": (c_int32, [P, ctypes.POINTER(c_int64), ctypes.POINTER(c_int64)]),
+    "fs_kernel_stats": (c_int32, [P, ctypes.POINTER(fs_kernel_stat), c_int32]),
+    "fs_kernel_launches": (ctypes.c_uint64, []),
+    "fs_probe_fma": (c_int32, [c_int32, ctypes.POINTER(c_double)]),
     "fs_last_error": (ctypes.c_char_p, []),
     "fs_status_str": (ctypes.c_char_p, [c_int32]),
 }

@@ -86,6 +86,7 @@ fs_status fs_options_default(fs_options *o)
     o->lsb = 0;
     o->use_graph = 0;
     o->tile_override = 0;
+    o->profile = 0;
     return FS_OK;
 }
 
@@ -203,6 +204,8 @@ fs_status fs_stokeslet_apply(fs_ctx *c, const double *src_xyz, const double *src
     a.sum_prec = sum_precision;
     a.hilo = true;
     a.shape_override = c->opt.tile_override;
+    a.pairs = double(n_src) * double(n_tgt);
+    a.prof = c->opt.profile ? &c->prof : nullptr;
     return pairsum(a, cv.base + cv.used, cv.cap - cv.used, c->d_status, c->stream);
 }
 

@@ -30,7 +30,12 @@ void set_error(const char *fmt, ...);
         if (s_ != FS_OK) return s_;                                                      \
     } while (0)
 
-#define FS_LAUNCH_CHECK() FS_CUDA(cudaGetLastError())
+extern unsigned long long g_launches;  // kernels launched by this library
+#define FS_LAUNCH_CHECK()                                                                \
+    do {                                                                                 \
+        __atomic_add_fetch(&::fs::g_launches, 1ULL, __ATOMIC_RELAXED);                   \
+        FS_CUDA(cudaGetLastError());                                                     \
+    } while (0)
 
 // Device status word bits written by kernels (never by faults).
 enum : int {
@@ -73,6 +78,19 @@ struct SumPlan {
     int threads;      // threads per CTA
 };
 
+// CUDA-event records of direct-sum kernel launches (opt.profile).
+struct Profiler {
+    struct Rec {
+        int cls;
+        cudaEvent_t a, b;
+        double pairs;
+    };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t get();
+    void release_all();
+};
+
 struct PairSumArgs {
     int kind = PAIR_STOKESLET;
     const double *src_xyz = nullptr;   // [n_src][3]
@@ -89,6 +107,8 @@ struct PairSumArgs {
     bool hilo = true;                  // FP32: hi/lo-split coordinates
     bool accumulate = false;           // out += scale * sum instead of out = ...
     int shape_override = 0;
+    Profiler *prof = nullptr;          // record the main kernel with CUDA events
+    double pairs = 0.0;                // pairs evaluated (for the profiler)
 };
 
 SumPlan plan_pairsum(int64_t n_src, int64_t n_tgt, int sum_prec, int shape_override);

@@ -529,6 +529,16 @@ fs_status pairsum(const PairSumArgs &a, void *scratch, size_t scratch_bytes, int
     const size_t sm = static_cast<size_t>(n_arr) * 2 * p.tile * v4;
     double *dst = direct ? a.out : part;
     const int acc = a.accumulate ? 1 : 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (a.prof) {
+        ev0 = a.prof->get();
+        ev1 = a.prof->get();
+        if (!ev0 || !ev1) {
+            set_error("pairsum: could not create profiling events");
+            return FS_ECUDA;
+        }
+        FS_CUDA(cudaEventRecord(ev0, st));
+    }
 #define FS_LAUNCH(R, TT, K, HL)                                                                   \
     k_pairsum<R, TT, K, HL><<<grid, kThreads, sm, st>>>(                                         \
         static_cast<const Vec4Of<R>::type *>(packed), a.n_src, p.per_split, a.tgt_xyz, a.excl,   \
@@ -559,6 +569,11 @@ fs_status pairsum(const PairSumArgs &a, void *scratch, size_t scratch_bytes, int
 #undef FS_BY_T
 #undef FS_LAUNCH
     FS_LAUNCH_CHECK();
+    if (a.prof) {
+        FS_CUDA(cudaEventRecord(ev1, st));
+        const int cls = (a.kind == PAIR_STOKESLET ? 0 : 2) + (f32 ? 0 : 1);
+        a.prof->recs.push_back(Profiler::Rec{cls, ev0, ev1, a.pairs});
+    }
     if (!direct) {
         const int64_t n3 = a.n_tgt * 3;
         k_reduce_splits<<<static_cast<unsigned>((n3 + 255) / 256), 256, 0, st>>>(part, p.splits, n3,

@@ -149,11 +149,13 @@ fs_status far_field(fs_ctx *c, int sum_prec, bool hilo)
     a.sum_prec = sum_prec;
     a.hilo = hilo;
     a.shape_override = c->opt.tile_override;
+    int64_t self = 0;
+    for (int m = 0; m < c->M; ++m) self += int64_t(c->Nm[m]) * c->Nm[m];
+    a.pairs = double(c->n_tot) * double(c->n_tot) - double(self);
+    a.prof = c->opt.profile ? &c->prof : nullptr;
     FS_TRY(c->scratch.reserve(pairsum_scratch_bytes(a.kind, a.n_src, a.n_tgt, sum_prec, a.shape_override),
                               c->stream));
     FS_TRY(pairsum(a, c->scratch.ptr, c->scratch.bytes, c->d_status, c->stream));
-    int64_t self = 0;
-    for (int m = 0; m < c->M; ++m) self += int64_t(c->Nm[m]) * c->Nm[m];
     c->pairs_last += c->n_tot * c->n_tot - self;
     return FS_OK;
 }
@@ -494,6 +496,9 @@ void context_free(fs_ctx *c)
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    c->prof.release_all();
+    for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
+    c->prof.pool.clear();
     c->h_pinned = nullptr;
     c->scratch.release();
 }

@@ -93,6 +93,8 @@ __global__ void k_div(const double *__restrict__ in, const double *__restrict__ 
 
 fs_status run_sum(fs_ctx *c, PairSumArgs &a)
 {
+    a.pairs = double(a.n_src) * double(a.n_tgt);
+    a.prof = c->opt.profile ? &c->prof : nullptr;
     FS_TRY(c->scratch.reserve(pairsum_scratch_bytes(a.kind, a.n_src, a.n_tgt, a.sum_prec,
                                                     a.shape_override),
                               c->stream));
