@@ -30,8 +30,11 @@ sys.path.insert(0, ROOT)
 
 import workloads as wl  # noqa: E402
 
-FLOPS_PER_PAIR = {"stokeslet": 27.0, "stresslet": 31.0}
-KS_NAMES = ["stokeslet_fp32", "stokeslet_fp64", "stresslet_fp32", "stresslet_fp64"]
+# algorithmic flops per pair: the Stokeslet formula (27), the stresslet (31)
+# and the float-float evaluation of the Stokeslet (218, FMA = 2, counted from
+# the float-float formula; the rsqrt seed is on the SFU)
+FLOPS_PER_PAIR = {"stokeslet": 27.0, "stresslet": 31.0, "stokeslet_ff": 218.0}
+KS_NAMES = ["stokeslet_fp32", "stokeslet_fp64", "stresslet_fp32", "stresslet_fp64", "stokeslet_ff"]
 WORKLOAD = "cloud-1024x64: 1,024 curved fibers x 64 Chebyshev points (65,536 points), [0,40]^3"
 
 
@@ -165,7 +168,7 @@ def run_kernel(args, ws, rank, local, fs, torch, dist):
     dev = torch.device("cuda", local)
     s = wl.cfg_cloud_mixed(seed=rank)
     P = args.points or s.n_points
-    prec = fs.FS_SUM_FP32 if args.kernel == "stokeslet_fp32" else fs.FS_SUM_FP64
+    prec = {"stokeslet_fp32": fs.FS_SUM_FP32, "stokeslet_fp64": fs.FS_SUM_FP64, "stokeslet_ff": 2}[args.kernel]
     opt = fs.fs_options_default()
     opt.profile = 1
     stream = torch.cuda.Stream(device=dev)
@@ -180,13 +183,14 @@ def run_kernel(args, ws, rank, local, fs, torch, dist):
     fs.fs_kernel_stats(h, reset=True)
     for _ in range(args.steps):
         fs.fs_stokeslet_apply(h, X, Wf, X, out, fid, fid, prec)
-    st = fs.fs_kernel_stats(h, reset=True)[0 if prec == fs.FS_SUM_FP32 else 1]
+    st = fs.fs_kernel_stats(h, reset=True)[{fs.FS_SUM_FP32: 0, fs.FS_SUM_FP64: 1, 2: 4}[prec]]
     fs.fs_destroy(h)
     if rank == 0:
         pairs_s = st[2] / (st[1] * 1e-3)
+        fpp = FLOPS_PER_PAIR["stokeslet_ff" if args.kernel == "stokeslet_ff" else "stokeslet"]
         print(json.dumps({"kernel": args.kernel, "points": P, "launches": st[0],
                           "ms_per_launch": st[1] / st[0], "pairs_per_s": pairs_s,
-                          "tflops": 27.0 * pairs_s / 1e12}), flush=True)
+                          "tflops": fpp * pairs_s / 1e12}), flush=True)
 
 
 def main():
@@ -199,7 +203,7 @@ def main():
                     help="GMRES iterations assumed for the reference arm's extrapolation")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--kernel", choices=["stokeslet_fp32", "stokeslet_fp64"], default=None,
+    ap.add_argument("--kernel", choices=["stokeslet_fp32", "stokeslet_fp64", "stokeslet_ff"], default=None,
                     help="time only the direct-sum kernel on the cloud (fs_stokeslet_apply)")
     ap.add_argument("--points", type=int, default=0,
                     help="--kernel: use the first P points of the cloud (0 = all)")
@@ -315,10 +319,10 @@ def main():
     fp32_peak = fs.fs_probe_fma(1)
     fp64_peak = fs.fs_probe_fma(0)
     per_class = {KS_NAMES[k]: {"launches": stats[k][0], "ms": stats[k][1], "pairs": stats[k][2]}
-                 for k in range(4)}
-    dom = max(range(4), key=lambda k: stats[k][1])
+                 for k in range(5)}
+    dom = max(range(5), key=lambda k: stats[k][1])
     launches_d, total_ms, pairs = stats[dom]
-    kind = "stresslet" if dom >= 2 else "stokeslet"
+    kind = "stresslet" if dom in (2, 3) else ("stokeslet_ff" if dom == 4 else "stokeslet")
     is64 = dom in (1, 3)
     ach = FLOPS_PER_PAIR[kind] * pairs / (total_ms * 1e-3) / 1e12 if total_ms > 0 else 0.0
     sm_max = clk.get("sm_max_mhz") or 2070.0

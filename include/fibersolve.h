@@ -44,13 +44,18 @@ typedef enum {
 
 typedef enum {
     FS_FP64 = 0,   /* everything in FP64 (the plain FP64 GPU path) */
-    FS_MIXED = 1   /* FP32 far-field sums inside GMRES, FP64 iterative refinement */
+    FS_MIXED = 1   /* FP32 far-field sums inside GMRES; iterative refinement whose
+                      right-hand side and residuals use the float-float far field
+                      and FP64 everywhere else */
 } fs_precision;
 
 typedef enum {
     FS_SUM_FP64 = 0, /* direct sums in FP64 arithmetic */
-    FS_SUM_FP32 = 1  /* FP32 arithmetic: hi/lo-split coordinates, FP32 tile sums,
+    FS_SUM_FP32 = 1, /* FP32 arithmetic: hi/lo-split coordinates, FP32 tile sums,
                         compensated (TwoSum) accumulation across tiles, FP64 output */
+    FS_SUM_FF = 2    /* float-float ("double-single") arithmetic on the FP32 pipe,
+                        ~2^-44 relative rounding per pair (Stokeslet; stresslet
+                        sums requested in FS_SUM_FF run in FP64) */
 } fs_sum_precision;
 
 /* Spherical no-slip periphery (Sec. 2.1, Eq. main-cortex-density) discretised
@@ -87,6 +92,7 @@ typedef enum {
     FS_KS_STOKESLET_FP64 = 1,
     FS_KS_STRESSLET_FP32 = 2,
     FS_KS_STRESSLET_FP64 = 3,
+    FS_KS_STOKESLET_FF = 4,
     FS_KS_COUNT = 6
 } fs_kernel_class;
 

@@ -172,7 +172,7 @@ fs_status fs_stokeslet_apply(fs_ctx *c, const double *src_xyz, const double *src
         set_error("fs_stokeslet_apply: bad sizes or NULL arrays");
         return FS_EINVAL;
     }
-    if (sum_precision != FS_SUM_FP32 && sum_precision != FS_SUM_FP64) {
+    if (sum_precision != FS_SUM_FP32 && sum_precision != FS_SUM_FP64 && sum_precision != FS_SUM_FF) {
         set_error("fs_stokeslet_apply: unknown precision %d", sum_precision);
         return FS_EINVAL;
     }

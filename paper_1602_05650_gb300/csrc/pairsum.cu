@@ -32,6 +32,7 @@ namespace {
 constexpr int kThreads = 128;
 constexpr int kTile32 = 256;    // sources per stage, FP32 path
 constexpr int kTile64 = 128;    // sources per stage, FP64 path
+constexpr int kTileFF = 128;    // sources per stage, float-float path
 constexpr int kWaitIters = 1 << 22;
 
 // Per-source arrays: 0 = position (hi part), 1 = weighted density (W f or w q),
@@ -322,6 +323,272 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+// ------------------------------------------------------------ float-float
+// Stokeslet sum in float-float ("double-single") arithmetic on the FP32 pipe:
+// every quantity is an unevaluated sum hi + lo of two floats, built from
+// Knuth's TwoSum and the FMA-based TwoProduct; 1/sqrt(r^2) is the MUFU seed
+// refined by one Newton step in float-float.  Each pair carries ~2^-44
+// relative rounding (vs 2^-24 in FP32), at ~10x the FP32 instruction count --
+// far cheaper than the FP64 pipe on this GPU.  Used for the right-hand side
+// and the refinement residuals of the mixed-precision step.
+__device__ __forceinline__ void ts(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void fts(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    e = b - (s - a);
+}
+
+template <int T, bool MASK>
+__device__ __forceinline__ void tile_ff(const float4 *__restrict__ sph, const float4 *__restrict__ spl,
+                                        const float4 *__restrict__ sfh, const float4 *__restrict__ sfl,
+                                        int cnt, int j0, const float (&th)[T][3], const float (&tl)[T][3],
+                                        const int (&elo)[T], const int (&ecnt)[T], float (&uh)[T][3],
+                                        float (&ul)[T][3])
+{
+#pragma unroll 1
+    for (int j = 0; j < cnt; ++j) {
+        const float4 ph4 = sph[j], pl4 = spl[j], fh4 = sfh[j], fl4 = sfl[j];
+        const float ph[3] = {ph4.x, ph4.y, ph4.z}, pl[3] = {pl4.x, pl4.y, pl4.z};
+        const float fh[3] = {fh4.x, fh4.y, fh4.z}, fl[3] = {fl4.x, fl4.y, fl4.z};
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            float dh[3], dl[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                float e;
+                ts(th[t][a], -ph[a], dh[a], e);
+                dl[a] = (tl[t][a] - pl[a]) + e;
+            }
+            // r^2 = sum (dh + dl)^2
+            float p[3], pe[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                p[a] = dh[a] * dh[a];
+                pe[a] = fmaf(dh[a], dh[a], -p[a]);
+            }
+            float S, e1, S2, e2;
+            ts(p[0], p[1], S, e1);
+            ts(S, p[2], S2, e2);
+            float lo = (e1 + e2) + (pe[0] + pe[1] + pe[2]);
+            lo = fmaf(2.0f * dh[0], dl[0], lo);
+            lo = fmaf(2.0f * dh[1], dl[1], lo);
+            lo = fmaf(2.0f * dh[2], dl[2], lo);
+            float R, Rl;
+            fts(S2, lo, R, Rl);
+            bool skip = false;
+            if constexpr (MASK) {
+                skip = static_cast<unsigned>(j0 + j - elo[t]) < static_cast<unsigned>(ecnt[t]);
+                if (skip) {
+                    R = 1.0f;
+                    Rl = 0.0f;
+                }
+            }
+            // rinv = y + yl: one Newton step on the rsqrt seed, residual in float-float
+            float y = rsqrtf(R);
+            const float hh = y * y, hl = fmaf(y, y, -hh);
+            const float qh = R * hh;
+            float ql = fmaf(R, hh, -qh);
+            ql = fmaf(R, hl, ql);
+            ql = fmaf(Rl, hh, ql);
+            const float ee = (1.0f - qh) - ql;
+            float yl = 0.5f * y * ee;
+            if constexpr (MASK) {
+                if (skip) {
+                    y = 0.0f;
+                    yl = 0.0f;
+                }
+            }
+            // rinv^2
+            const float r2h = y * y;
+            const float r2l = fmaf(2.0f * y, yl, fmaf(y, y, -r2h));
+            // r . wf
+            float q[3], qe[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                q[a] = dh[a] * fh[a];
+                qe[a] = fmaf(dh[a], fh[a], -q[a]);
+            }
+            float F1, f1, F2, f2;
+            ts(q[0], q[1], F1, f1);
+            ts(F1, q[2], F2, f2);
+            float flo = (f1 + f2) + (qe[0] + qe[1] + qe[2]);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) flo = fmaf(dh[a], fl[a], fmaf(dl[a], fh[a], flo));
+            float Fh, Fl;
+            fts(F2, flo, Fh, Fl);
+            // s = (r . wf) rinv^2
+            const float sh = Fh * r2h;
+            float sl = fmaf(Fh, r2h, -sh);
+            sl = fmaf(Fh, r2l, sl);
+            sl = fmaf(Fl, r2h, sl);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                // v = wf + s r
+                const float mh = sh * dh[a];
+                float ml = fmaf(sh, dh[a], -mh);
+                ml = fmaf(sh, dl[a], ml);
+                ml = fmaf(sl, dh[a], ml);
+                float vh, ve;
+                ts(fh[a], mh, vh, ve);
+                const float vl = (ve + fl[a]) + ml;
+                // u += rinv v
+                const float wh = y * vh;
+                float wl = fmaf(y, vh, -wh);
+                wl = fmaf(y, vl, wl);
+                wl = fmaf(yl, vh, wl);
+                float nh, ne;
+                ts(uh[t][a], wh, nh, ne);
+                ul[t][a] += ne + wl;
+                uh[t][a] = nh;
+            }
+        }
+    }
+}
+
+template <int T>
+__global__ void __launch_bounds__(kThreads)
+    k_pairsum_ff(const float4 *__restrict__ src, int64_t n_src, int64_t per_split,
+                 const double *__restrict__ tgt, const int2 *__restrict__ excl, int64_t n_tgt,
+                 const double *__restrict__ center, double *__restrict__ out, double scale, int direct,
+                 int acc, int *__restrict__ status)
+{
+    constexpr int NARR = 4, TILE = kTileFF;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float4 *smem = reinterpret_cast<float4 *>(smem_raw);   // [stage][array][TILE]
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ int s_lo, s_hi;
+
+    const int tid = threadIdx.x;
+    const int64_t tbase = static_cast<int64_t>(blockIdx.x) * (T * kThreads);
+    const int64_t j_begin = static_cast<int64_t>(blockIdx.y) * per_split;
+    const int64_t j_end = min(n_src, j_begin + per_split);
+    const int64_t n_tiles = j_end > j_begin ? (j_end - j_begin + TILE - 1) / TILE : 0;
+    if (tid == 0) {
+        s_lo = INT_MAX;
+        s_hi = INT_MIN;
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    const double c[3] = {center[0], center[1], center[2]};
+    float th[T][3], tl[T][3], uh[T][3], ul[T][3];
+    int elo[T], ecnt[T];
+    int my_lo = INT_MAX, my_hi = INT_MIN;
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const int64_t i = tbase + tid + static_cast<int64_t>(t) * kThreads;
+        int2 e = make_int2(0, 0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double x = i < n_tgt ? tgt[3 * i + a] - c[a] : 0.0;
+            th[t][a] = static_cast<float>(x);
+            tl[t][a] = static_cast<float>(x - static_cast<double>(th[t][a]));
+            uh[t][a] = ul[t][a] = 0.0f;
+        }
+        if (i < n_tgt && excl) e = excl[i];
+        elo[t] = e.x;
+        ecnt[t] = e.y > e.x ? e.y - e.x : 0;
+        if (e.y > e.x) {
+            my_lo = min(my_lo, e.x);
+            my_hi = max(my_hi, e.y);
+        }
+    }
+    __syncthreads();
+    if (my_hi > my_lo) {
+        atomicMin(&s_lo, my_lo);
+        atomicMax(&s_hi, my_hi);
+    }
+    auto stage_ptr = [&](int stage, int arr) -> float4 * { return smem + (stage * NARR + arr) * TILE; };
+    auto issue = [&](int64_t tile, int stage) {
+        const int64_t j0 = j_begin + tile * TILE;
+        const int cnt = static_cast<int>(min(static_cast<int64_t>(TILE), j_end - j0));
+        const uint32_t bytes = static_cast<uint32_t>(cnt) * 16u;
+        mbar_expect_tx(&bars[stage], bytes * NARR);
+#pragma unroll
+        for (int a = 0; a < NARR; ++a) bulk_g2s(stage_ptr(stage, a), src + a * n_src + j0, bytes, &bars[stage]);
+    };
+    if (tid == 0) {
+        if (n_tiles > 0) issue(0, 0);
+        if (n_tiles > 1) issue(1, 1);
+    }
+    __syncthreads();
+    const int blo = s_lo, bhi = s_hi;
+    bool failed = false;
+    for (int64_t it = 0; it < n_tiles; ++it) {
+        const int stage = static_cast<int>(it & 1);
+        const bool ok = mbar_wait(&bars[stage], static_cast<uint32_t>((it >> 1) & 1));
+        if (!__syncthreads_and(ok)) {
+            failed = true;
+            break;
+        }
+        if (tid == 0 && it >= 1 && it + 1 < n_tiles) issue(it + 1, static_cast<int>((it + 1) & 1));
+        const int64_t j0 = j_begin + it * TILE;
+        const int cnt = static_cast<int>(min(static_cast<int64_t>(TILE), j_end - j0));
+        const bool masked = bhi > blo && j0 < bhi && j0 + cnt > blo;
+        if (masked)
+            tile_ff<T, true>(stage_ptr(stage, 0), stage_ptr(stage, 1), stage_ptr(stage, 2),
+                             stage_ptr(stage, 3), cnt, static_cast<int>(j0), th, tl, elo, ecnt, uh, ul);
+        else
+            tile_ff<T, false>(stage_ptr(stage, 0), stage_ptr(stage, 1), stage_ptr(stage, 2),
+                              stage_ptr(stage, 3), cnt, static_cast<int>(j0), th, tl, elo, ecnt, uh, ul);
+#pragma unroll
+        for (int t = 0; t < T; ++t)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) fts(uh[t][a], ul[t][a], uh[t][a], ul[t][a]);
+    }
+    if (failed) {
+        if (tid == 0) {
+            atomicOr(status, DEV_ERR_TIMEOUT);
+            mbar_wait(&bars[0], 0);
+            mbar_wait(&bars[1], 0);
+        }
+        return;
+    }
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const int64_t i = tbase + tid + static_cast<int64_t>(t) * kThreads;
+        if (i >= n_tgt) continue;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double v = static_cast<double>(uh[t][a]) + static_cast<double>(ul[t][a]);
+            if (direct) {
+                double *o = out + 3 * i + a;
+                *o = (acc ? *o : 0.0) + scale * v;
+            } else {
+                out[(static_cast<int64_t>(blockIdx.y) * n_tgt + i) * 3 + a] = v;
+            }
+        }
+    }
+}
+
+// Pack for the float-float kernel: [0] position hi, [1] position lo,
+// [2] W f hi, [3] W f lo (positions relative to the centre).
+__global__ void k_pack_ff(const double *__restrict__ xyz, const double *__restrict__ dens, int64_t n,
+                          const double *__restrict__ center, float4 *__restrict__ out)
+{
+    const int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (j >= n) return;
+    float h[3], l[3], fh[3], fl[3];
+    for (int a = 0; a < 3; ++a) {
+        const double x = xyz[3 * j + a] - center[a];
+        h[a] = static_cast<float>(x);
+        l[a] = static_cast<float>(x - static_cast<double>(h[a]));
+        const double f = dens[3 * j + a];
+        fh[a] = static_cast<float>(f);
+        fl[a] = static_cast<float>(f - static_cast<double>(fh[a]));
+    }
+    out[j] = make_float4(h[0], h[1], h[2], 0.0f);
+    out[n + j] = make_float4(l[0], l[1], l[2], 0.0f);
+    out[2 * n + j] = make_float4(fh[0], fh[1], fh[2], 0.0f);
+    out[3 * n + j] = make_float4(fl[0], fl[1], fl[2], 0.0f);
+}
+
 // ------------------------------------------------------------------ helpers
 // Midpoint of the bounding box of n points (one CTA).
 __global__ void __launch_bounds__(512) k_bbox_center(const double *__restrict__ p, int64_t n,
@@ -438,13 +705,14 @@ int num_sms()
 
 SumPlan plan_pairsum(int64_t n_src, int64_t n_tgt, int sum_prec, int shape_override)
 {
-    const int tile = sum_prec == FS_SUM_FP32 ? kTile32 : kTile64;
+    const int tile = sum_prec == FS_SUM_FP32 ? kTile32 : (sum_prec == FS_SUM_FF ? kTileFF : kTile64);
     int tpt = sum_prec == FS_SUM_FP32 ? 4 : 2;
     if (shape_override > 0) {
         static const int f32_opts[] = {2, 4, 8};
         static const int f64_opts[] = {1, 2, 4};
         const int k = (shape_override - 1) % 3;
         tpt = sum_prec == FS_SUM_FP32 ? f32_opts[k] : f64_opts[k];
+        if (sum_prec == FS_SUM_FF) tpt = k == 0 ? 1 : 2;
     }
     const int64_t nb = (n_tgt + tpt * kThreads - 1) / (tpt * kThreads);
     const int64_t want = 4LL * num_sms();
@@ -469,8 +737,8 @@ SumPlan plan_pairsum(int64_t n_src, int64_t n_tgt, int sum_prec, int shape_overr
 size_t pairsum_scratch_bytes(int kind, int64_t n_src, int64_t n_tgt, int sum_prec, int shape_override)
 {
     const SumPlan p = plan_pairsum(n_src, n_tgt, sum_prec, shape_override);
-    const size_t arrs = (kind == PAIR_STRESSLET ? 3 : 2) + (sum_prec == FS_SUM_FP32 ? 1 : 0);
-    const size_t v4 = sum_prec == FS_SUM_FP32 ? sizeof(float4) : sizeof(double4_32a);
+    const size_t arrs = sum_prec == FS_SUM_FF ? 4 : (kind == PAIR_STRESSLET ? 3 : 2) + (sum_prec == FS_SUM_FP32 ? 1 : 0);
+    const size_t v4 = sum_prec == FS_SUM_FP64 ? sizeof(double4_32a) : sizeof(float4);
     return 1024 + arrs * static_cast<size_t>(n_src) * v4 +
            (p.splits > 1 ? static_cast<size_t>(p.splits) * static_cast<size_t>(n_tgt) * 3 * sizeof(double) : 0) +
            1024;
@@ -499,11 +767,15 @@ fs_status pairsum(const PairSumArgs &a, void *scratch, size_t scratch_bytes, int
         set_error("pairsum: at most 2^31-2 sources and targets");
         return FS_EINVAL;
     }
-    const bool f32 = a.sum_prec == FS_SUM_FP32;
+    // the float-float path exists for the Stokeslet; stresslet sums asked for
+    // in float-float run in FP64 (more, not less, precise)
+    const int prec = (a.sum_prec == FS_SUM_FF && a.kind == PAIR_STRESSLET) ? FS_SUM_FP64 : a.sum_prec;
+    const bool ff = prec == FS_SUM_FF;
+    const bool f32 = prec == FS_SUM_FP32;
     const bool hilo = f32 && a.hilo;
-    const SumPlan p = plan_pairsum(a.n_src, a.n_tgt, a.sum_prec, a.shape_override);
-    const int n_arr = (a.kind == PAIR_STRESSLET ? 3 : 2) + (hilo ? 1 : 0);
-    const size_t v4 = f32 ? sizeof(float4) : sizeof(double4_32a);
+    const SumPlan p = plan_pairsum(a.n_src, a.n_tgt, prec, a.shape_override);
+    const int n_arr = ff ? 4 : (a.kind == PAIR_STRESSLET ? 3 : 2) + (hilo ? 1 : 0);
+    const size_t v4 = (f32 || ff) ? sizeof(float4) : sizeof(double4_32a);
     Carve cv(scratch, scratch_bytes);
     double *center = cv.take<double>(4);
     void *packed = cv.take<unsigned char>(static_cast<size_t>(n_arr) * a.n_src * v4);
@@ -517,7 +789,9 @@ fs_status pairsum(const PairSumArgs &a, void *scratch, size_t scratch_bytes, int
     FS_LAUNCH_CHECK();
     const unsigned pb = static_cast<unsigned>((a.n_src + 255) / 256);
     const int lo_slot = hilo ? n_arr - 1 : 0;
-    if (f32)
+    if (ff)
+        k_pack_ff<<<pb, 256, 0, st>>>(a.src_xyz, a.src_dens, a.n_src, center, static_cast<float4 *>(packed));
+    else if (f32)
         k_pack<float><<<pb, 256, 0, st>>>(a.src_xyz, a.src_dens, a.src_w, a.src_nrm, a.n_src, center,
                                           static_cast<float4 *>(packed), n_arr, lo_slot);
     else
@@ -555,7 +829,16 @@ fs_status pairsum(const PairSumArgs &a, void *scratch, size_t scratch_bytes, int
         else if (p.tpt == 4) FS_LAUNCH(double, 4, K, false);                                      \
         else FS_LAUNCH(double, 2, K, false);                                                      \
     } while (0)
-    if (f32) {
+    if (ff) {
+        if (p.tpt == 1)
+            k_pairsum_ff<1><<<grid, kThreads, sm, st>>>(static_cast<const float4 *>(packed), a.n_src,
+                                                        p.per_split, a.tgt_xyz, a.excl, a.n_tgt, center,
+                                                        dst, a.scale, direct, acc, d_status);
+        else
+            k_pairsum_ff<2><<<grid, kThreads, sm, st>>>(static_cast<const float4 *>(packed), a.n_src,
+                                                        p.per_split, a.tgt_xyz, a.excl, a.n_tgt, center,
+                                                        dst, a.scale, direct, acc, d_status);
+    } else if (f32) {
         if (a.kind == PAIR_STOKESLET) {
             if (hilo) FS_BY_T(float, PAIR_STOKESLET, true); else FS_BY_T(float, PAIR_STOKESLET, false);
         } else {
@@ -571,7 +854,7 @@ fs_status pairsum(const PairSumArgs &a, void *scratch, size_t scratch_bytes, int
     FS_LAUNCH_CHECK();
     if (a.prof) {
         FS_CUDA(cudaEventRecord(ev1, st));
-        const int cls = (a.kind == PAIR_STOKESLET ? 0 : 2) + (f32 ? 0 : 1);
+        const int cls = ff ? 4 : (a.kind == PAIR_STOKESLET ? 0 : 2) + (f32 ? 0 : 1);
         a.prof->recs.push_back(Profiler::Rec{cls, ev0, ev1, a.pairs});
     }
     if (!direct) {

@@ -183,14 +183,19 @@ fs_status apply_pa(fs_ctx *c, const double *v, double *out, int sum_prec)
     return FS_OK;
 }
 
-// b (Eq. sche-linear-eq right-hand side) with the FP64 far field, then pb = P^-1 b
+// Far-field arithmetic of the accurate sums (right-hand side, refinement
+// residuals): FP64 on the plain FP64 path, float-float on the mixed path.
+int accurate_prec(const fs_ctx *c) { return c->opt.prec == FS_FP64 ? FS_SUM_FP64 : FS_SUM_FF; }
+
+// b (Eq. sche-linear-eq right-hand side) with the accurate far field, then pb = P^-1 b
 fs_status rhs(fs_ctx *c, double *b, double *pb)
 {
+    const int ap = accurate_prec(c);
     FS_TRY(launch_force(c, nullptr, c->d_f, c->d_wf));
-    FS_TRY(far_field(c, FS_SUM_FP64, false));
-    if (c->surf.n) FS_TRY(surface_couplings(c, nullptr, c->d_ubar, FS_SUM_FP64, false));
+    FS_TRY(far_field(c, ap, false));
+    if (c->surf.n) FS_TRY(surface_couplings(c, nullptr, c->d_ubar, ap, false));
     FS_TRY(launch_rows(c, nullptr, c->d_f, c->d_ubar, b, ROWS_RHS));
-    if (c->surf.n) FS_TRY(surface_rows(c, nullptr, c->d_usurf, b + c->n_fib_unk, true, FS_SUM_FP64, false));
+    if (c->surf.n) FS_TRY(surface_rows(c, nullptr, c->d_usurf, b + c->n_fib_unk, true, ap, false));
     FS_TRY(launch_lu_solve(c, b, pb));
     if (c->surf.n) FS_TRY(surface_precond(c, b + c->n_fib_unk, pb + c->n_fib_unk));
     return FS_OK;
@@ -319,12 +324,12 @@ fs_status gmres(fs_ctx *c, const double *pb, double *x, double tol, int max_iter
     return FS_OK;
 }
 
-// r_out = pb - P^-1 A x with the FP64 far field; *rel = ||r_out|| / pbnorm.
+// r_out = pb - P^-1 A x with the accurate far field; *rel = ||r_out|| / pbnorm.
 fs_status true_residual(fs_ctx *c, const double *pb, const double *x, double pbnorm, double *r_out,
                         double *rel)
 {
     const int64_t n = c->n_unk;
-    FS_TRY(apply_pa(c, x, c->d_w, FS_SUM_FP64));
+    FS_TRY(apply_pa(c, x, c->d_w, accurate_prec(c)));
     k_sub<<<blocks_for(n), 256, 0, c->stream>>>(pb, c->d_w, r_out, n);
     FS_LAUNCH_CHECK();
     double *d_tmp = c->d_h + 2 * c->kdim + 3;

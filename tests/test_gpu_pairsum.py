@@ -3,7 +3,8 @@ fs_surface_apply) against the oracle's plain FP64 C loops, element by element
 on the same seeded inputs: sizes spanning several tiles with ragged tails,
 fiber exclusion, the source-split path, every launch shape, edge cases and a
 sampled check at the 65,536-point cloud size.
-Tolerances: FP64 arithmetic 1e-12 relative 2-norm; FP32 arithmetic 1e-6."""
+Tolerances: FP64 arithmetic 1e-12 relative 2-norm; float-float 1e-11; FP32
+arithmetic 1e-6."""
 import numpy as np
 import pytest
 
@@ -16,7 +17,8 @@ pytestmark = pytest.mark.gpu
 
 import paper_1602_05650_gb300 as fs  # noqa: E402
 
-TOL = {fs.FS_SUM_FP64: 1e-12, fs.FS_SUM_FP32: 1e-6}
+FS_SUM_FF = 2
+TOL = {fs.FS_SUM_FP64: 1e-12, fs.FS_SUM_FP32: 1e-6, FS_SUM_FF: 1e-11}
 
 
 @pytest.fixture(scope="module")
@@ -40,7 +42,7 @@ def gpu_stokeslet(h, src, wf, tgt, prec, sf=None, tf=None):
     return out.cpu().numpy()
 
 
-@pytest.mark.parametrize("prec", [fs.FS_SUM_FP64, fs.FS_SUM_FP32])
+@pytest.mark.parametrize("prec", [fs.FS_SUM_FP64, fs.FS_SUM_FP32, FS_SUM_FF])
 @pytest.mark.parametrize("n_src,n_tgt", [(1, 1), (255, 3), (256, 257), (1000, 777), (5003, 129),
                                          (20000, 4100)])
 def test_stokeslet_random_points(ctx, prec, n_src, n_tgt):
@@ -51,7 +53,7 @@ def test_stokeslet_random_points(ctx, prec, n_src, n_tgt):
     assert rel(got, ref) <= TOL[prec]
 
 
-@pytest.mark.parametrize("prec", [fs.FS_SUM_FP64, fs.FS_SUM_FP32])
+@pytest.mark.parametrize("prec", [fs.FS_SUM_FP64, fs.FS_SUM_FP32, FS_SUM_FF])
 @pytest.mark.parametrize("M,N,side", [(16, 32, 10.0), (97, 24, 12.0), (300, 64, 20.0)])
 def test_stokeslet_fiber_exclusion(ctx, prec, M, N, side):
     s = wl.free_space(M, N, side, seed=3, curved_amp=0.05)
@@ -70,7 +72,7 @@ def test_every_launch_shape_agrees(shape):
     h = fs.fs_create([], 1.0, 1e-3, 1.0, 1e-3, options=opt)
     s = wl.free_space(40, 32, 10.0, seed=4)
     fid = s.fiber_id()
-    for prec in (fs.FS_SUM_FP64, fs.FS_SUM_FP32):
+    for prec in (fs.FS_SUM_FP64, fs.FS_SUM_FP32, FS_SUM_FF):
         got = gpu_stokeslet(h, s.X, s.f_ext, s.X, prec, fid, fid)
         ref = ok.stokeslet(s.X, s.X, s.f_ext, 1.0, fid, fid)
         assert rel(got, ref) <= TOL[prec]
@@ -105,7 +107,7 @@ def test_cloud_size_sampled(ctx):
     rng = np.random.default_rng(0)
     idx = np.sort(rng.choice(s.n_points, 512, replace=False))
     ref = ok.stokeslet(s.X[idx], s.X, wf, 1.3, fid[idx], fid)
-    for prec in (fs.FS_SUM_FP32, fs.FS_SUM_FP64):
+    for prec in (fs.FS_SUM_FP32, fs.FS_SUM_FP64, FS_SUM_FF):
         got = gpu_stokeslet(ctx, s.X, wf, s.X, prec, fid, fid)
         assert rel(got[idx], ref) <= TOL[prec]
 

@@ -3,9 +3,9 @@ same seeded suspensions.
 
 Tolerances.  With smooth external forcing (gravity-like, as in a sedimenting
 cloud) the oracle's GMRES velocity tracks its dense LAPACK solution to 1e-14
-at tol 1e-12, so the gates are: plain FP64 path within 1e-10 (1e-9 at N = 64,
-whose blocks have cond ~6e11), mixed path (FP32 far field + FP64 refinement)
-within 1e-8.  With i.i.d. N(0,1) force per node -- grid-scale noise the
+at tol 1e-12 for N <= 32, so the gates are: plain FP64 path within 1e-10,
+mixed path (FP32 far field + FP64 refinement) within 1e-8.  At N = 64 (blocks
+with cond ~6e11) the oracle's own GMRES-vs-dense spread is 4.1e-8.  With i.i.d. N(0,1) force per node -- grid-scale noise the
 Chebyshev representation cannot resolve -- the solution carries huge
 high-order coefficients and even the oracle's own GMRES (tol 1e-12) and dense
 solutions differ by 2.2e-8 in V for the 16 x 32 case; those cases are held to
@@ -85,7 +85,9 @@ def test_fp64_curved_ragged():
 def test_fp64_n64_two_steps():
     """Two consecutive steps; each is compared from the same input state (the
     free-end data of a step is ~N^6/dt times the rounding of its positions, so
-    trajectories from states that differ at 1e-13 separate by design)."""
+    trajectories from states that differ at 1e-13 separate by design).  At N = 64
+    the fiber blocks have cond ~6e11 and the oracle's own GMRES (tol 1e-14) and
+    dense solutions of this system differ by 4.1e-8 in V: gate 2e-7."""
     import copy
     from tests.gpu_helpers import dev, make_ctx
     s = gravity(wl.free_space(20, 64, 8.0, seed=3, curved_amp=0.05), (0.3, -0.2, -1.0))
@@ -100,7 +102,7 @@ def test_fp64_n64_two_steps():
         fs.fs_step(h)
         fs.fs_get_state(h, V=V, X=X)
         ref = oracle_step(state, tol=1e-14)
-        assert rel(V.cpu().numpy(), ref.V) <= 1e-9, step
+        assert rel(V.cpu().numpy(), ref.V) <= 2e-7, step
         assert rel(X.cpu().numpy(), ref.X_new) <= 1e-12, step
         state.X = X.cpu().numpy().copy()
     fs.fs_destroy(h)
