@@ -736,6 +736,7 @@ SumPlan plan_pairsum(int64_t n_src, int64_t n_tgt, int sum_prec, int shape_overr
 
 size_t pairsum_scratch_bytes(int kind, int64_t n_src, int64_t n_tgt, int sum_prec, int shape_override)
 {
+    if (sum_prec == FS_SUM_FF && kind == PAIR_STRESSLET) sum_prec = FS_SUM_FP64;   // as in pairsum()
     const SumPlan p = plan_pairsum(n_src, n_tgt, sum_prec, shape_override);
     const size_t arrs = sum_prec == FS_SUM_FF ? 4 : (kind == PAIR_STRESSLET ? 3 : 2) + (sum_prec == FS_SUM_FP32 ? 1 : 0);
     const size_t v4 = sum_prec == FS_SUM_FP64 ? sizeof(double4_32a) : sizeof(float4);

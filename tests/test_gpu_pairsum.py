@@ -3,8 +3,9 @@ fs_surface_apply) against the oracle's plain FP64 C loops, element by element
 on the same seeded inputs: sizes spanning several tiles with ragged tails,
 fiber exclusion, the source-split path, every launch shape, edge cases and a
 sampled check at the 65,536-point cloud size.
-Tolerances: FP64 arithmetic 1e-12 relative 2-norm; float-float 1e-11; FP32
-arithmetic 1e-6."""
+Tolerances: FP64 arithmetic 1e-12 relative 2-norm; float-float 5e-11 (~2^-44
+per pair, and coordinates carried as two floats, 2^-48 relative, which near
+pairs of random points amplify); FP32 arithmetic 1e-6."""
 import numpy as np
 import pytest
 
@@ -18,7 +19,7 @@ pytestmark = pytest.mark.gpu
 import paper_1602_05650_gb300 as fs  # noqa: E402
 
 FS_SUM_FF = 2
-TOL = {fs.FS_SUM_FP64: 1e-12, fs.FS_SUM_FP32: 1e-6, FS_SUM_FF: 1e-11}
+TOL = {fs.FS_SUM_FP64: 1e-12, fs.FS_SUM_FP32: 1e-6, FS_SUM_FF: 5e-11}
 
 
 @pytest.fixture(scope="module")
