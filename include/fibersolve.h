@@ -157,6 +157,30 @@ fs_status fs_stokeslet_apply(fs_ctx *ctx, const double *src_xyz, const double *s
                              const double *tgt_xyz, const int32_t *tgt_fiber, int64_t n_tgt,
                              double *out_u, int32_t sum_precision);
 
+/* Same sum as fs_stokeslet_apply, for callers that cannot let the library
+ * allocate device memory: applications whose own allocator owns or has
+ * reserved all of the GPU's memory (a cudaMalloc here could fail or fragment
+ * their pool), and latency-bound loops that cannot absorb the device-wide
+ * synchronisation of cudaMalloc / cudaFree.  (No counterpart in the paper: an
+ * interface addition of this library.)
+ *  - Needs no context: mu and the CUDA stream (cudaStream_t or NULL) are
+ *    arguments; arrays as in fs_stokeslet_apply (DEVICE arrays, fiber ids
+ *    optional and then non-decreasing over the sources).
+ *  - Allocates nothing: its scratch is a fixed 16 MiB array in device memory
+ *    that every GPU which loads this library holds until the process exits.
+ *    Requests needing more scratch (roughly beyond 65,536 sources and
+ *    targets in FP32) return FS_EINVAL with the size in fs_last_error().
+ *  - The first call on a device looks up that array's device address (no
+ *    allocation); make that first call before any stream capture.
+ *  - All calls share the one array and it keeps the previous call's
+ *    contents; calls that overlap on the GPU (different streams or threads
+ *    without ordering between them) race on it and give wrong results.
+ *  - Enqueued on `cuda_stream`; returns without synchronising. */
+fs_status fs_stokeslet_apply_noalloc(const double *src_xyz, const double *src_wf, int64_t n_src,
+                                     const int32_t *src_fiber, const double *tgt_xyz,
+                                     const int32_t *tgt_fiber, int64_t n_tgt, double *out_u,
+                                     double mu, int32_t sum_precision, void *cuda_stream);
+
 /* Direct double-layer (stresslet) sum (Eqs. stresslet, double-layer,
  * cortex-vel) at targets off the surface:
  *   out_u[i] = sum_j w_j T(tgt_i - y_j) : (q_j n_j),
