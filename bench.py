@@ -361,7 +361,8 @@ def main():
         "clocks": clk,
         "stokeslet_pairs_per_s_fp32": pairs_per_s,
         "kernels": per_class,
-        "step": {"gmres_iters": [i.iters for i in infos], "sweeps": [i.refine_sweeps for i in infos],
+        "step": {"inner_gmres_iters": [i.iters for i in infos],
+                 "outer_steps": [i.refine_sweeps for i in infos],
                  "resid": [i.resid for i in infos],
                  "t_ms_rhs_build_solve": [[round(i.t_ms[0], 2), round(i.t_ms[1], 2), round(i.t_ms[2], 2)]
                                           for i in infos]},

@@ -44,9 +44,10 @@ typedef enum {
 
 typedef enum {
     FS_FP64 = 0,   /* everything in FP64 (the plain FP64 GPU path) */
-    FS_MIXED = 1   /* FP32 far-field sums inside GMRES; iterative refinement whose
-                      right-hand side and residuals use the float-float far field
-                      and FP64 everywhere else */
+    FS_MIXED = 1   /* GMRES-based refinement: flexible GMRES on the operator whose far
+                      field is float-float (FP64-grade, on the FP32 pipe), each
+                      direction preconditioned by a GMRES solve with the FP32 far
+                      field; FP64 everywhere else; same stopping test as FS_FP64 */
 } fs_precision;
 
 typedef enum {
@@ -76,8 +77,9 @@ typedef struct {
                                ||P^-1 (b - A u)|| <= tol ||P^-1 b|| */
     int32_t max_iter;       /* GMRES iterations per solve (default 200) */
     int32_t restart;        /* GMRES restart length (default 60, at most 250) */
-    int32_t max_refine;     /* FS_MIXED: maximum refinement sweeps (default 6) */
-    double inner_tol;       /* FS_MIXED: relative tolerance of each inner solve (default 1e-6) */
+    int32_t max_refine;     /* reserved (default 6) */
+    double inner_tol;       /* FS_MIXED: relative tolerance of each inner FP32-far-field
+                               GMRES solve (default 1e-3) */
     double delta_over_L;    /* regularisation delta of K_delta as a fraction of L (default 0.01) */
     int32_t lsb;            /* 1 = local slender-body theory: drop K_delta (default 0) */
     int32_t use_graph;      /* reserved: capture the inner iteration in a CUDA graph */
@@ -103,9 +105,12 @@ typedef struct {
 } fs_kernel_stat;
 
 typedef struct {
-    int32_t iters;          /* total GMRES iterations (all sweeps) */
-    int32_t refine_sweeps;  /* outer refinement sweeps (1 for FS_FP64) */
-    double resid;           /* final preconditioned relative residual (FP64 far field) */
+    int32_t iters;          /* GMRES iterations: FS_FP64 all; FS_MIXED the inner (FP32
+                               far field) iterations summed over the outer steps */
+    int32_t refine_sweeps;  /* FS_MIXED: outer (flexible GMRES) steps, each applying the
+                               accurate operator once; FS_FP64: 1 */
+    double resid;           /* final preconditioned relative residual estimate of the
+                               (outer) GMRES recurrence, accurate operator */
     double t_ms[8];         /* host wall-clock ms: [0] right-hand side [1] geometry and
                                preconditioner build [2] solve [3] update [4] total;
                                others reserved (filled when info is requested) */

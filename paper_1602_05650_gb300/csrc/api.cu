@@ -81,7 +81,7 @@ fs_status fs_options_default(fs_options *o)
     o->max_iter = 200;
     o->restart = 60;
     o->max_refine = 6;
-    o->inner_tol = 1e-6;
+    o->inner_tol = 1e-3;
     o->delta_over_L = 0.01;
     o->lsb = 0;
     o->use_graph = 0;

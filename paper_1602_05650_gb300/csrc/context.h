@@ -115,9 +115,13 @@ struct fs_ctx {
     // Krylov workspace
     int kdim = 0;
     double *d_basis = nullptr, *d_b = nullptr, *d_x = nullptr, *d_r = nullptr, *d_w = nullptr,
-           *d_e = nullptr, *d_res = nullptr, *d_cor = nullptr, *d_pb = nullptr, *d_h = nullptr,
+           *d_e = nullptr, *d_pb = nullptr, *d_h = nullptr,
            *d_part = nullptr;
     double *h_pinned = nullptr;
+    // outer (flexible) Krylov space of the mixed-precision solve
+    int okdim = 0;
+    double *d_obasis = nullptr, *d_oz = nullptr, *d_oh = nullptr, *d_opart = nullptr, *d_ow = nullptr,
+           *d_or = nullptr, *oh_pinned = nullptr;
     fs::Surface surf;
     double *d_usurf = nullptr;    // fiber Stokeslets at the surface nodes [n_s][3]
     bool have_state = false, precond_ok = false, geometry_ok = false;

@@ -344,6 +344,11 @@ __global__ void __launch_bounds__(128) k_rows(FiberTable F, const double *__rest
 }
 
 // One CTA per (fiber, chunk of nb columns): B[:, col] = rows(e_col) with ubar = 0.
+// The inputs are unit vectors, so the generic force/velocity maps are
+// specialised by column type:
+//   sigma_a,j (j < N-4): f = -E dt g^4 T_j(alpha) e_a  (one component, no D_alpha)
+//   p_a,k              : f = 0 -> w = 0 (only the direct rows)
+//   tension            : T = column of Tn, f = g D_alpha(T X_s) (three components)
 __global__ void __launch_bounds__(256) k_block_build(FiberTable F, double *__restrict__ B, int nb)
 {
     extern __shared__ double bsm[];
@@ -352,20 +357,87 @@ __global__ void __launch_bounds__(256) k_block_build(FiberTable F, double *__res
     const int col0 = blockIdx.y * nb;
     if (col0 >= n) return;
     const int cnt = min(nb, n - col0);
-    double *us = bsm, *sig = us + nb * 4 * N, *Tv = sig + nb * 3 * N, *q = Tv + nb * N,
-           *f = q + nb * 3 * N, *w = f + nb * 3 * N;
+    double *us = bsm, *Tv = us + nb * 4 * N, *q = Tv + nb * N, *f = q + nb * 3 * N, *w = f + nb * 3 * N;
+    const double *Sig = fb.M_(fb.lay.Sig), *Tn = fb.M_(fb.lay.Tn), *D1 = fb.M_(fb.lay.D1);
+    const double *t = F.t + 3 * fb.n0;
+    const double g = fb.g, bend = -F.E * F.dt * g * g * g * g;
     for (int i = threadIdx.x; i < cnt * n; i += blockDim.x) {
         const int c = i / n, r = i % n;
         us[i] = (r == col0 + c) ? 1.0 : 0.0;
     }
+    // tension columns: T at the nodes and the product T X_s
+    for (int i = threadIdx.x; i < cnt * N; i += blockDim.x) {
+        const int c = i / N, k = i % N, col = col0 + c;
+        const double Tk = col >= 3 * N ? Tn[k * N + (col - 3 * N)] : 0.0;
+        Tv[i] = Tk;
+        q[3 * i] = Tk * t[3 * k];
+        q[3 * i + 1] = Tk * t[3 * k + 1];
+        q[3 * i + 2] = Tk * t[3 * k + 2];
+    }
     __syncthreads();
-    dev_sigma_T(fb, us, cnt, sig, Tv);
+    for (int i = threadIdx.x; i < cnt * N * 3; i += blockDim.x) {
+        const int c = i / (3 * N), r = i % (3 * N), k = r / 3, a = r % 3, col = col0 + c;
+        double v = 0.0;
+        if (col < 3 * N) {
+            const int ca = col / N, j = col % N;
+            if (ca == a && j < N - 4) v = bend * Sig[k * N + j];
+        } else {
+            const double *qc = q + c * 3 * N;
+            double s = 0.0;
+            for (int jj = 0; jj < N; ++jj) s += D1[k * N + jj] * qc[3 * jj + a];
+            v = g * s;
+        }
+        f[i] = v;
+    }
     __syncthreads();
-    dev_force_from(F, fb, sig, Tv, cnt, q, f);
-    __syncthreads();
-    dev_selfvel(F, fb, f, cnt, nullptr, w);
+    // w = M f + K_delta[f], skipping p columns (f = 0) and using the single
+    // nonzero component of sigma columns
+    const double *ml = F.mloc + 2 * fb.n0;
+    const double4_32a *kp = reinterpret_cast<const double4_32a *>(F.kp) + fb.kp0;
+    for (int i = threadIdx.x; i < cnt * N; i += blockDim.x) {
+        const int c = i / N, k = i % N, col = col0 + c;
+        const double *fc = f + c * 3 * N;
+        double wx = 0.0, wy = 0.0, wz = 0.0;
+        const bool pcol = col < 3 * N && (col % N) >= N - 4;
+        if (!pcol) {
+            const double fx = fc[3 * k], fy = fc[3 * k + 1], fz = fc[3 * k + 2];
+            const double tx = t[3 * k], ty = t[3 * k + 1], tz = t[3 * k + 2];
+            const double tf = tx * fx + ty * fy + tz * fz;
+            wx = ml[2 * k] * fx + ml[2 * k + 1] * tx * tf;
+            wy = ml[2 * k] * fy + ml[2 * k + 1] * ty * tf;
+            wz = ml[2 * k] * fz + ml[2 * k + 1] * tz * tf;
+            if (!F.lsb) {
+                if (col < 3 * N) {
+                    const int a = col / N;   // f = fa e_a
+                    for (int j = 0; j < N; ++j) {
+                        const double4_32a p = kp[k * N + j];
+                        const double fa = fc[3 * j + a];
+                        const double ha = a == 0 ? p.y : (a == 1 ? p.z : p.w);
+                        const double s = p.x * ha * fa;
+                        wx += s * p.y;
+                        wy += s * p.z;
+                        wz += s * p.w;
+                        if (a == 0) wx += p.x * fa; else if (a == 1) wy += p.x * fa; else wz += p.x * fa;
+                    }
+                } else {
+                    for (int j = 0; j < N; ++j) {
+                        const double4_32a p = kp[k * N + j];
+                        const double gx = fc[3 * j], gy = fc[3 * j + 1], gz = fc[3 * j + 2];
+                        const double hf = p.y * gx + p.z * gy + p.w * gz;
+                        wx += p.x * (gx + p.y * hf);
+                        wy += p.x * (gy + p.z * hf);
+                        wz += p.x * (gz + p.w * hf);
+                    }
+                }
+            }
+        }
+        w[3 * i] = wx;
+        w[3 * i + 1] = wy;
+        w[3 * i + 2] = wz;
+    }
     __syncthreads();
     dev_rows(F, fb, us, w, cnt, false, B + fb.blk0 + static_cast<int64_t>(col0) * n, n);
+    (void)Tv;
 }
 
 // Batched LU with partial pivoting, column-major n x n blocks, n = 4 N.
@@ -511,8 +583,8 @@ __global__ void __launch_bounds__(128) k_update(FiberTable F, const double *__re
 
 int build_cols(int N)
 {
-    // columns per CTA so that 17 N doubles per column stay within ~96 KB
-    int nb = static_cast<int>(96 * 1024 / (17 * 8 * static_cast<int64_t>(N)));
+    // columns per CTA so that 14 N doubles per column stay within ~96 KB
+    int nb = static_cast<int>(96 * 1024 / (14 * 8 * static_cast<int64_t>(N)));
     if (nb < 1) nb = 1;
     if (nb > 16) nb = 16;
     return nb;
@@ -552,7 +624,7 @@ fs_status launch_block_build(fs_ctx *c)
 {
     if (c->M == 0) return FS_OK;
     const int nb = build_cols(c->max_N);
-    const size_t sm = static_cast<size_t>(17) * nb * c->max_N * sizeof(double);
+    const size_t sm = static_cast<size_t>(14) * nb * c->max_N * sizeof(double);
     if (sm > 48 * 1024)
         FS_CUDA(cudaFuncSetAttribute(k_block_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(sm)));

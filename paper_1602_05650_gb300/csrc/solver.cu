@@ -202,26 +202,80 @@ fs_status rhs(fs_ctx *c, double *b, double *pb)
 }
 
 struct GmresResult {
-    int iters = 0;
-    double rel = 0.0;  // |g| / beta0 estimate
+    int iters = 0;          // Arnoldi steps (outer steps for the flexible solver)
+    int inner_iters = 0;    // flexible solver: inner GMRES iterations in total
+    double rel = 0.0;       // |g| / beta0 estimate
     bool converged = false;
 };
 
-// Restarted GMRES for (P^-1 A) x = pb, x0 = 0 (x overwritten); tolerance
-// relative to ||pb|| = ||P^-1 b||.
+// Storage of one Krylov space: basis V [(R+1) x n], optional flexible
+// directions Z [R x n], Hessenberg / norm scratch on the device and a pinned
+// host copy.
+struct Space {
+    int R;
+    double *V, *Z, *h, *part, *w, *r, *hpin;
+};
+
+Space inner_space(fs_ctx *c)
+{
+    return Space{c->kdim - 1, c->d_basis, nullptr, c->d_h, c->d_part, c->d_w, c->d_r, c->h_pinned};
+}
+
+Space outer_space(fs_ctx *c)
+{
+    return Space{c->okdim - 1, c->d_obasis, c->d_oz, c->d_oh, c->d_opart, c->d_ow, c->d_or, c->oh_pinned};
+}
+
+fs_status dev_norm_s(fs_ctx *c, const Space &sp, const double *v, int64_t n, double *dst)
+{
+    k_multidot<<<dim3(kDotBlocks, 1), 256, 0, c->stream>>>(v, 0, 1, v, n, sp.part);
+    FS_LAUNCH_CHECK();
+    k_finish_dots<<<1, 32, 0, c->stream>>>(sp.part, 1, dst, 0, 1);
+    FS_LAUNCH_CHECK();
+    return FS_OK;
+}
+
+fs_status read_scalar_s(fs_ctx *c, const Space &sp, const double *d, double *h)
+{
+    FS_CUDA(cudaMemcpyAsync(sp.hpin, d, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    FS_CUDA(cudaStreamSynchronize(c->stream));
+    *h = sp.hpin[0];
+    return FS_OK;
+}
+
+// out = operator(v): the preconditioned operator with the far field of `prec`
+struct Op {
+    int sum_prec;
+};
+
+// GMRES core for (P^-1 A) x = pb, x0 = 0, restarted after R steps, CGS2 and
+// Givens rotations.  With a flexible preconditioner (inner_prec >= 0) each
+// direction is z_j = an inner GMRES solve of (P^-1 A_inner) z = v_j to
+// inner_tol, the basis is built from (P^-1 A) z_j and x = Z y (FGMRES).
+fs_status gmres_core(fs_ctx *c, const Space &sp, const double *pb, double *x, double tol, int max_iter,
+                     int sum_prec, int inner_prec, double inner_tol, GmresResult *res);
+
 fs_status gmres(fs_ctx *c, const double *pb, double *x, double tol, int max_iter, int sum_prec,
                 GmresResult *res)
 {
+    return gmres_core(c, inner_space(c), pb, x, tol, max_iter, sum_prec, -1, 0.0, res);
+}
+
+fs_status gmres_core(fs_ctx *c, const Space &sp, const double *pb, double *x, double tol, int max_iter,
+                     int sum_prec, int inner_prec, double inner_tol, GmresResult *res)
+{
     const int64_t n = c->n_unk;
-    const int R = c->kdim - 1;
-    double *V = c->d_basis;
+    const int R = sp.R;
+    const int hs = R + 1;   // stride of the h buffer blocks
+    double *V = sp.V;
+    const bool flexible = inner_prec >= 0;
     *res = GmresResult();
     FS_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), c->stream));
-    FS_CUDA(cudaMemcpyAsync(c->d_r, pb, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    double *d_beta = c->d_h + 2 * c->kdim + 2;
-    FS_TRY(dev_norm(c, c->d_r, n, d_beta));
+    FS_CUDA(cudaMemcpyAsync(sp.r, pb, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    double *d_beta = sp.h + 2 * hs + 2;
+    FS_TRY(dev_norm_s(c, sp, sp.r, n, d_beta));
     double beta0;
-    FS_TRY(read_scalar(c, d_beta, &beta0));
+    FS_TRY(read_scalar_s(c, sp, d_beta, &beta0));
     if (!(beta0 > 0.0)) {
         res->converged = true;
         return FS_OK;
@@ -234,7 +288,7 @@ fs_status gmres(fs_ctx *c, const double *pb, double *x, double tol, int max_iter
     std::vector<double> H(static_cast<size_t>(R + 1) * R), cs(R), sn(R), g(R + 1), y(R);
     int total = 0;
     while (true) {
-        k_scale_by<<<blocks_for(n), 256, 0, c->stream>>>(c->d_r, d_beta, V, n);
+        k_scale_by<<<blocks_for(n), 256, 0, c->stream>>>(sp.r, d_beta, V, n);
         FS_LAUNCH_CHECK();
         std::fill(g.begin(), g.end(), 0.0);
         g[0] = beta;
@@ -242,27 +296,35 @@ fs_status gmres(fs_ctx *c, const double *pb, double *x, double tol, int max_iter
         bool done = false;
         for (int j = 0; j < R; ++j) {
             double *Vj = V + j * n, *Vn = V + (j + 1) * n;
-            FS_TRY(apply_pa(c, Vj, c->d_w, sum_prec));
-            double *h = c->d_h;
+            if (flexible) {
+                GmresResult ir;
+                double *Zj = sp.Z + j * n;
+                FS_TRY(gmres_core(c, inner_space(c), Vj, Zj, inner_tol, c->opt.max_iter, inner_prec, -1, 0.0,
+                                  &ir));
+                res->inner_iters += ir.iters;
+                FS_TRY(apply_pa(c, Zj, sp.w, sum_prec));
+            } else {
+                FS_TRY(apply_pa(c, Vj, sp.w, sum_prec));
+            }
+            double *h = sp.h;
             for (int pass = 0; pass < 2; ++pass) {   // CGS2
-                double *hp = h + (pass ? c->kdim : 0);
-                k_multidot<<<dim3(kDotBlocks, j + 1), 256, 0, c->stream>>>(V, n, j + 1, c->d_w, n,
-                                                                          c->d_part);
+                double *hp = h + (pass ? hs : 0);
+                k_multidot<<<dim3(kDotBlocks, j + 1), 256, 0, c->stream>>>(V, n, j + 1, sp.w, n, sp.part);
                 FS_LAUNCH_CHECK();
-                k_finish_dots<<<1, 256, 0, c->stream>>>(c->d_part, j + 1, hp, 0, 0);
+                k_finish_dots<<<1, 256, 0, c->stream>>>(sp.part, j + 1, hp, 0, 0);
                 FS_LAUNCH_CHECK();
-                k_axpy_multi<<<blocks_for(n), 256, 0, c->stream>>>(c->d_w, V, n, hp, j + 1, n);
+                k_axpy_multi<<<blocks_for(n), 256, 0, c->stream>>>(sp.w, V, n, hp, j + 1, n);
                 FS_LAUNCH_CHECK();
             }
-            FS_TRY(dev_norm(c, c->d_w, n, h + 2 * c->kdim));
-            k_scale_by<<<blocks_for(n), 256, 0, c->stream>>>(c->d_w, h + 2 * c->kdim, Vn, n);
+            FS_TRY(dev_norm_s(c, sp, sp.w, n, h + 2 * hs));
+            k_scale_by<<<blocks_for(n), 256, 0, c->stream>>>(sp.w, h + 2 * hs, Vn, n);
             FS_LAUNCH_CHECK();
-            FS_CUDA(cudaMemcpyAsync(c->h_pinned, h, (2 * c->kdim + 1) * sizeof(double),
-                                    cudaMemcpyDeviceToHost, c->stream));
+            FS_CUDA(cudaMemcpyAsync(sp.hpin, h, (2 * hs + 1) * sizeof(double), cudaMemcpyDeviceToHost,
+                                    c->stream));
             FS_CUDA(cudaStreamSynchronize(c->stream));
             double *hc = &H[static_cast<size_t>(j) * (R + 1)];   // column j, length R+1
-            for (int i = 0; i <= j; ++i) hc[i] = c->h_pinned[i] + c->h_pinned[c->kdim + i];
-            const double hn = c->h_pinned[2 * c->kdim];
+            for (int i = 0; i <= j; ++i) hc[i] = sp.hpin[i] + sp.hpin[hs + i];
+            const double hn = sp.hpin[2 * hs];
             hc[j + 1] = hn;
             if (!std::isfinite(hn)) {
                 set_error("gmres: non-finite Arnoldi vector");
@@ -293,27 +355,26 @@ fs_status gmres(fs_ctx *c, const double *pb, double *x, double tol, int max_iter
                 break;
             }
         }
-        // y = H^-1 g (upper triangular kcols x kcols), x += V y
+        // y = H^-1 g (upper triangular kcols x kcols), x += (V or Z) y
         for (int i = kcols - 1; i >= 0; --i) {
             double s = g[i];
             for (int l = i + 1; l < kcols; ++l) s -= H[static_cast<size_t>(l) * (R + 1) + i] * y[l];
             const double dii = H[static_cast<size_t>(i) * (R + 1) + i];
             y[i] = dii != 0.0 ? s / dii : 0.0;
         }
-        std::memcpy(c->h_pinned, y.data(), kcols * sizeof(double));
-        double *d_y = c->d_h + 3 * c->kdim + 4;
-        FS_CUDA(cudaMemcpyAsync(d_y, c->h_pinned, kcols * sizeof(double), cudaMemcpyHostToDevice,
-                                c->stream));
-        k_lincomb<<<blocks_for(n), 256, 0, c->stream>>>(x, V, n, d_y, kcols, n);
+        std::memcpy(sp.hpin, y.data(), kcols * sizeof(double));
+        double *d_y = sp.h + 3 * hs + 4;
+        FS_CUDA(cudaMemcpyAsync(d_y, sp.hpin, kcols * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        k_lincomb<<<blocks_for(n), 256, 0, c->stream>>>(x, flexible ? sp.Z : V, n, d_y, kcols, n);
         FS_LAUNCH_CHECK();
-        FS_CUDA(cudaStreamSynchronize(c->stream));   // h_pinned is reused below
+        FS_CUDA(cudaStreamSynchronize(c->stream));   // hpin is reused below
         if (done) break;
         // restart: r = pb - P^-1 A x
-        FS_TRY(apply_pa(c, x, c->d_w, sum_prec));
-        k_sub<<<blocks_for(n), 256, 0, c->stream>>>(pb, c->d_w, c->d_r, n);
+        FS_TRY(apply_pa(c, x, sp.w, sum_prec));
+        k_sub<<<blocks_for(n), 256, 0, c->stream>>>(pb, sp.w, sp.r, n);
         FS_LAUNCH_CHECK();
-        FS_TRY(dev_norm(c, c->d_r, n, d_beta));
-        FS_TRY(read_scalar(c, d_beta, &beta));
+        FS_TRY(dev_norm_s(c, sp, sp.r, n, d_beta));
+        FS_TRY(read_scalar_s(c, sp, d_beta, &beta));
         res->rel = beta / beta0;
         if (res->rel <= tol) {
             res->converged = true;
@@ -321,22 +382,6 @@ fs_status gmres(fs_ctx *c, const double *pb, double *x, double tol, int max_iter
         }
     }
     res->iters = total;
-    return FS_OK;
-}
-
-// r_out = pb - P^-1 A x with the accurate far field; *rel = ||r_out|| / pbnorm.
-fs_status true_residual(fs_ctx *c, const double *pb, const double *x, double pbnorm, double *r_out,
-                        double *rel)
-{
-    const int64_t n = c->n_unk;
-    FS_TRY(apply_pa(c, x, c->d_w, accurate_prec(c)));
-    k_sub<<<blocks_for(n), 256, 0, c->stream>>>(pb, c->d_w, r_out, n);
-    FS_LAUNCH_CHECK();
-    double *d_tmp = c->d_h + 2 * c->kdim + 3;
-    FS_TRY(dev_norm(c, r_out, n, d_tmp));
-    double rn;
-    FS_TRY(read_scalar(c, d_tmp, &rn));
-    *rel = pbnorm > 0.0 ? rn / pbnorm : 0.0;
     return FS_OK;
 }
 
@@ -464,11 +509,19 @@ fs_status context_init(fs_ctx *c, int M, const int32_t *ppf, const fs_boundary *
     FS_TRY(dalloc(&c->d_r, n));
     FS_TRY(dalloc(&c->d_w, n));
     FS_TRY(dalloc(&c->d_e, n));
-    FS_TRY(dalloc(&c->d_res, n));
-    FS_TRY(dalloc(&c->d_cor, n));
     FS_TRY(dalloc(&c->d_pb, n));
     FS_TRY(dalloc(&c->d_h, 4 * c->kdim + 8));
     FS_TRY(dalloc(&c->d_part, static_cast<size_t>(c->kdim) * kDotBlocks));
+    if (c->opt.prec == FS_MIXED) {
+        c->okdim = 17;   // outer (flexible) restart length 16
+        FS_TRY(dalloc(&c->d_obasis, static_cast<size_t>(c->okdim) * n));
+        FS_TRY(dalloc(&c->d_oz, static_cast<size_t>(c->okdim - 1) * n));
+        FS_TRY(dalloc(&c->d_oh, 4 * c->okdim + 8));
+        FS_TRY(dalloc(&c->d_opart, static_cast<size_t>(c->okdim) * kDotBlocks));
+        FS_TRY(dalloc(&c->d_ow, n));
+        FS_TRY(dalloc(&c->d_or, n));
+        FS_CUDA(cudaMallocHost(&c->oh_pinned, 4096 * sizeof(double)));
+    }
     if (c->surf.n) {
         const int ns = c->surf.n;
         FS_TRY(dalloc(&c->surf.y, 3 * ns));
@@ -496,11 +549,13 @@ void context_free(fs_ctx *c)
                     c->d_z_ptr, c->d_ops_off, c->d_ops, c->d_excl, c->d_X, c->d_L, c->d_fext,
                     c->d_t, c->d_tz, c->d_fknown, c->d_W, c->d_mloc, c->d_bc, c->d_kp, c->d_B,
                     c->d_piv, c->d_V, c->d_T, c->d_f, c->d_wf, c->d_ubar, c->d_basis, c->d_b,
-                    c->d_x, c->d_r, c->d_w, c->d_e, c->d_res, c->d_cor, c->d_pb, c->d_h, c->d_part, c->surf.y, c->surf.nrm,
+                    c->d_x, c->d_r, c->d_w, c->d_e, c->d_pb, c->d_obasis, c->d_oz, c->d_oh, c->d_opart, c->d_ow, c->d_or, c->d_h, c->d_part, c->surf.y, c->surf.nrm,
                     c->surf.w, c->surf.diag, c->d_usurf, c->surf.A, c->surf.tmp, c->surf.flux, c->surf.excl};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    if (c->oh_pinned) cudaFreeHost(c->oh_pinned);
+    c->oh_pinned = nullptr;
     c->prof.release_all();
     for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
     c->prof.pool.clear();
@@ -624,7 +679,6 @@ fs_status fs_step(fs_ctx *c, fs_step_info *info)
     FS_TRY(rhs(c, c->d_b, c->d_pb));
     FS_TRY(check_status(c));
     if (info) tms[0] = ms_since(t0) - tms[1];
-    const int64_t n = c->n_unk;
     int iters = 0, sweeps = 0;
     double rel = 0.0;
     bool converged = false;
@@ -636,37 +690,15 @@ fs_status fs_step(fs_ctx *c, fs_step_info *info)
         sweeps = 1;
         converged = gr.converged;
     } else {
-        double *d_tmp = c->d_h + 2 * c->kdim + 3;
-        FS_TRY(dev_norm(c, c->d_pb, n, d_tmp));
-        double pbnorm;
-        FS_TRY(read_scalar(c, d_tmp, &pbnorm));
-        double *u = c->d_x, *d_res = c->d_res, *d_cor = c->d_cor;
-        FS_CUDA(cudaMemsetAsync(u, 0, n * sizeof(double), c->stream));
-        FS_CUDA(cudaMemcpyAsync(d_res, c->d_pb, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-        fs_status st = FS_OK;
-        rel = 1.0;
-        for (sweeps = 0; sweeps < std::max(1, c->opt.max_refine);) {
-            GmresResult gr;
-            // the inner solve only needs to shrink this sweep's residual to (about) the target
-            const double inner = std::max(c->opt.inner_tol, 0.1 * c->opt.tol / std::max(rel, 1e-300));
-            st = gmres(c, d_res, d_cor, std::min(inner, 0.5), c->opt.max_iter, FS_SUM_FP32, &gr);
-            if (st != FS_OK) break;
-            iters += gr.iters;
-            ++sweeps;
-            k_add<<<blocks_for(n), 256, 0, c->stream>>>(u, d_cor, n);
-            if (cudaGetLastError() != cudaSuccess) {
-                st = FS_ECUDA;
-                set_error("fs_step: refinement update launch");
-                break;
-            }
-            st = true_residual(c, c->d_pb, u, pbnorm, d_res, &rel);
-            if (st != FS_OK) break;
-            if (rel <= c->opt.tol) {
-                converged = true;
-                break;
-            }
-        }
-        if (st != FS_OK) return st;
+        // mixed: flexible GMRES on the operator with the float-float far field,
+        // each direction preconditioned by an FP32-far-field GMRES solve
+        GmresResult gr;
+        FS_TRY(gmres_core(c, outer_space(c), c->d_pb, c->d_x, c->opt.tol, c->opt.max_iter,
+                          accurate_prec(c), FS_SUM_FP32, c->opt.inner_tol, &gr));
+        iters = gr.inner_iters;
+        sweeps = gr.iters;
+        rel = gr.rel;
+        converged = gr.converged;
     }
     FS_TRY(check_status(c));
     tms[2] = ms_since(t0) - tms[0] - tms[1];

@@ -113,18 +113,18 @@ def test_mixed_refined_matches_oracle():
     ref = oracle_step(s)
     V, T, _, infos = gpu_step(s, torch, prec=fs.FS_MIXED, tol=1e-10)
     assert rel(V, ref.V) <= 1e-8
-    assert infos[0].resid <= 1e-10 and infos[0].refine_sweeps >= 1
+    assert infos[0].resid <= 1e-10 and infos[0].refine_sweeps >= 2
 
 
 def test_mixed_point_forces_cloud_shape():
-    """Curved fibers, 64 points, N(0,1) point forces: the mixed path refined to
-    1e-10 against the oracle at 1e-12 (the velocity is only pinned to ~1e-6 by
-    the residual for this unresolved forcing, see the module docstring)."""
+    """Curved fibers, 64 points, N(0,1) point forces: the mixed path to 1e-10
+    against the oracle at 1e-12, gated like the FP64 N = 64 case (the oracle's
+    own GMRES-vs-dense spread at N = 64 is 4.1e-8)."""
     s = wl.free_space(48, 64, 12.0, seed=5, curved_amp=0.05)
     ref = oracle_step(s)
     V, T, _, infos = gpu_step(s, torch, prec=fs.FS_MIXED, tol=1e-10)
     assert infos[0].resid <= 1e-10
-    assert rel(V, ref.V) <= 2e-6
+    assert rel(V, ref.V) <= 2e-7
 
 
 def test_confined_small():
