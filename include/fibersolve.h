@@ -131,6 +131,23 @@ fs_status fs_create(fs_ctx **out, int32_t n_fibers, const int32_t *points_per_fi
                     double mu, double eps, double E, double dt,
                     const fs_boundary *boundary, const fs_options *opt, void *cuda_stream);
 
+/* A context holding n_systems independent free-space suspensions (fibers
+ * 0..fibers_per_system[0]-1 form system 0, and so on; points_per_fiber lists all
+ * fibers, system-major), sharing mu, eps, E and dt.  Every kernel launch of a
+ * step covers all systems (the far field of a target block sums only its own
+ * system's sources); GMRES runs per system (own Krylov space, own convergence)
+ * in lockstep.  State arrays of fs_set_state / fs_get_state cover all fibers.
+ * fs_step fails with FS_ENOTCONV (no update) if any system does not converge. */
+fs_status fs_create_batch(fs_ctx **out, int32_t n_systems, const int32_t *fibers_per_system,
+                          const int32_t *points_per_fiber, double mu, double eps, double E, double dt,
+                          const fs_options *opt, void *cuda_stream);
+
+/* Per-system results of the last fs_step of a batch context (arrays of
+ * n_systems, any may be NULL): GMRES iterations (inner iterations for
+ * FS_MIXED), outer steps, final relative residual estimate, converged flag. */
+fs_status fs_batch_info(const fs_ctx *ctx, int32_t *iters, int32_t *outer, double *resid,
+                        int32_t *converged);
+
 void fs_destroy(fs_ctx *ctx);
 
 /* Set the fiber state: node positions X [N_tot][3] (fiber-major, node k of

@@ -17,7 +17,7 @@ from . import _native
 from ._native import (FS_FP64, FS_MIXED, FS_SUM_FP32, FS_SUM_FP64, fs_boundary, fs_options,  # noqa: F401
                       fs_step_info)
 
-__all__ = ["fs_options_default", "fs_create", "fs_destroy", "fs_set_state", "fs_get_state",
+__all__ = ["fs_options_default", "fs_create", "fs_create_batch", "fs_batch_info", "fs_destroy", "fs_set_state", "fs_get_state",
            "fs_stokeslet_apply", "fs_stresslet_apply", "fs_surface_apply", "fs_build_precond",
            "fs_step", "fs_sizes", "fs_last_error", "fs_kernel_stats", "fs_kernel_launches",
            "fs_probe_fma", "FsError", "FS_FP64", "FS_MIXED",
@@ -109,6 +109,38 @@ def fs_create(points_per_fiber, mu: float, eps: float, E: float, dt: float, boun
     npts, nunk = ctypes.c_int64(), ctypes.c_int64()
     _check(lib.fs_sizes(out, ctypes.byref(npts), ctypes.byref(nunk)), "fs_sizes")
     return Handle(out, npts.value, nunk.value)
+
+
+def fs_create_batch(fibers_per_system, points_per_fiber, mu: float, eps: float, E: float, dt: float,
+                    options: Optional[fs_options] = None, stream=None) -> Handle:
+    """Independent free-space systems in one context (see include/fibersolve.h)."""
+    lib = _native.load()
+    fps, fps_p = _host_ptr(np.asarray(fibers_per_system), np.int32, "fibers_per_system")
+    ppf, ppf_p = _host_ptr(np.asarray(points_per_fiber), np.int32, "points_per_fiber")
+    st = None
+    if stream is not None:
+        st = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    out = ctypes.c_void_p()
+    _check(lib.fs_create_batch(ctypes.byref(out), int(fps.shape[0]), fps_p, ppf_p, float(mu), float(eps),
+                               float(E), float(dt), ctypes.byref(options) if options is not None else None,
+                               st), "fs_create_batch")
+    npts, nunk = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib.fs_sizes(out, ctypes.byref(npts), ctypes.byref(nunk)), "fs_sizes")
+    h = Handle(out, npts.value, nunk.value)
+    h.n_systems = int(fps.shape[0])
+    return h
+
+
+def fs_batch_info(h: Handle):
+    """Per-system iterations, outer steps, residual estimate, converged flag of the last step."""
+    S = getattr(h, "n_systems", 1)
+    it = np.zeros(S, np.int32)
+    ou = np.zeros(S, np.int32)
+    rs = np.zeros(S, np.float64)
+    cv = np.zeros(S, np.int32)
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    _check(_native.load().fs_batch_info(h.ptr, p(it), p(ou), p(rs), p(cv)), "fs_batch_info")
+    return {"iters": it, "outer": ou, "resid": rs, "converged": cv}
 
 
 def fs_destroy(h: Handle):

@@ -52,6 +52,9 @@ SIGNATURES = {
     "fs_create": (c_int32, [ctypes.POINTER(c_void_p), c_int32, P, c_double, c_double, c_double,
                             c_double, ctypes.POINTER(fs_boundary), ctypes.POINTER(fs_options), P]),
     "fs_destroy": (None, [P]),
+    "fs_create_batch": (c_int32, [ctypes.POINTER(c_void_p), c_int32, P, P, c_double, c_double, c_double,
+                                  c_double, ctypes.POINTER(fs_options), P]),
+    "fs_batch_info": (c_int32, [P, P, P, P, P]),
     "fs_set_state": (c_int32, [P, P, P, P, c_int32]),
     "fs_get_state": (c_int32, [P, P, P, P, c_int32]),
     "fs_stokeslet_apply": (c_int32, [P, P, P, c_int64, P, P, P, c_int64, P, c_int32]),

@@ -90,9 +90,9 @@ fs_status fs_options_default(fs_options *o)
     return FS_OK;
 }
 
-fs_status fs_create(fs_ctx **out, int32_t n_fibers, const int32_t *ppf, double mu, double eps,
-                    double E, double dt, const fs_boundary *boundary, const fs_options *opt,
-                    void *cuda_stream)
+static fs_status create_impl(fs_ctx **out, int32_t n_systems, const int32_t *fps, int32_t n_fibers,
+                             const int32_t *ppf, double mu, double eps, double E, double dt,
+                             const fs_boundary *boundary, const fs_options *opt, void *cuda_stream)
 {
     if (!out) {
         set_error("fs_create: out is NULL");
@@ -130,7 +130,7 @@ fs_status fs_create(fs_ctx **out, int32_t n_fibers, const int32_t *ppf, double m
     c->E = E;
     c->dt = dt;
     if (opt) c->opt = *opt; else fs_options_default(&c->opt);
-    fs_status s = context_init(c, n_fibers, ppf, boundary);
+    fs_status s = context_init(c, n_systems, fps, n_fibers, ppf, boundary);
     if (s != FS_OK) {
         context_free(c);
         delete c;
@@ -138,6 +138,40 @@ fs_status fs_create(fs_ctx **out, int32_t n_fibers, const int32_t *ppf, double m
     }
     *out = c;
     return FS_OK;
+}
+
+fs_status fs_create(fs_ctx **out, int32_t n_fibers, const int32_t *ppf, double mu, double eps,
+                    double E, double dt, const fs_boundary *boundary, const fs_options *opt,
+                    void *cuda_stream)
+{
+    return create_impl(out, 1, nullptr, n_fibers, ppf, mu, eps, E, dt, boundary, opt, cuda_stream);
+}
+
+fs_status fs_create_batch(fs_ctx **out, int32_t n_systems, const int32_t *fibers_per_system,
+                          const int32_t *points_per_fiber, double mu, double eps, double E, double dt,
+                          const fs_options *opt, void *cuda_stream)
+{
+    if (!out || n_systems < 1 || !fibers_per_system) {
+        set_error("fs_create_batch: need at least one system and fibers_per_system");
+        if (out) *out = nullptr;
+        return FS_EINVAL;
+    }
+    int64_t M = 0;
+    for (int s = 0; s < n_systems; ++s) {
+        if (fibers_per_system[s] < 1) {
+            set_error("fs_create_batch: system %d has no fiber", s);
+            *out = nullptr;
+            return FS_EINVAL;
+        }
+        M += fibers_per_system[s];
+    }
+    if (M >= (1LL << 31)) {
+        set_error("fs_create_batch: too many fibers");
+        *out = nullptr;
+        return FS_EINVAL;
+    }
+    return create_impl(out, n_systems, fibers_per_system, static_cast<int32_t>(M), points_per_fiber, mu, eps,
+                       E, dt, nullptr, opt, cuda_stream);
 }
 
 void fs_destroy(fs_ctx *c)

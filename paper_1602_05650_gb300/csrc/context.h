@@ -97,6 +97,18 @@ struct fs_ctx {
     std::vector<int64_t> node_ptr, unk_ptr, blk_ptr;
     std::map<int, int64_t> ops_offset;  // N -> offset in d_ops
     int max_N = 0;
+    // independent systems (fs_create_batch): consecutive fiber ranges
+    int S = 1;
+    std::vector<int> sys_fib_ptr;
+    std::vector<int64_t> sys_node_ptr, sys_unk_ptr;
+    std::vector<double> sys_self_pairs;
+    std::vector<int> all_sys;
+    std::vector<int> sys_iters, sys_outer, sys_conv;
+    std::vector<double> sys_resid;
+    int64_t chunk_cap = 0, work_cap = 0;
+    int4 *d_work = nullptr;
+    int4 *d_ich = nullptr, *d_isch = nullptr, *d_och = nullptr, *d_osch = nullptr;
+    int *d_ikk = nullptr, *d_okk = nullptr;
 
     // device
     int *d_status = nullptr;
@@ -133,7 +145,8 @@ struct fs_ctx {
 };
 
 namespace fs {
-fs_status context_init(fs_ctx *c, int M, const int32_t *ppf, const fs_boundary *b);
+fs_status context_init(fs_ctx *c, int S, const int32_t *fibers_per_system, int M, const int32_t *ppf,
+                       const fs_boundary *b);
 void context_free(fs_ctx *c);
 
 // fiber.cu

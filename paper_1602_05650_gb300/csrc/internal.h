@@ -107,6 +107,11 @@ struct PairSumArgs {
     bool hilo = true;                  // FP32: hi/lo-split coordinates
     bool accumulate = false;           // out += scale * sum instead of out = ...
     int shape_override = 0;
+    // batched systems: (target lo, target hi, source lo, source hi) per group;
+    // each target block then sums only its group's sources (no source splits)
+    const std::vector<int4> *groups = nullptr;
+    int4 *work_dev = nullptr;          // device buffer for the work list
+    int64_t work_cap = 0;
     Profiler *prof = nullptr;          // record the main kernel with CUDA events
     double pairs = 0.0;                // pairs evaluated (for the profiler)
 };

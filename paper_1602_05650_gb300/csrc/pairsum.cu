@@ -21,6 +21,7 @@
 //     a per-pair index test only in the tiles that overlap a CTA's exclusions;
 //   * sources may be split across CTAs so that small problems fill all SMs; the
 //     partial sums are then reduced in FP64 in a fixed order (deterministic).
+#include <algorithm>
 #include <climits>
 #include <cstdio>
 
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(kThreads)
     k_pairsum(const typename Vec4Of<R>::type *__restrict__ src, int64_t n_src, int64_t per_split,
               const double *__restrict__ tgt, const int2 *__restrict__ excl, int64_t n_tgt,
               const double *__restrict__ center, double *__restrict__ out, double scale, int direct,
-              int acc, int *__restrict__ status)
+              int acc, int *__restrict__ status, const int4 *__restrict__ work)
 {
     using V4 = typename Vec4Of<R>::type;
     using A = Arr<KIND, HILO>;
@@ -186,9 +187,20 @@ __global__ void __launch_bounds__(kThreads)
     __shared__ int s_lo, s_hi;
 
     const int tid = threadIdx.x;
-    const int64_t tbase = static_cast<int64_t>(blockIdx.x) * (T * kThreads);
-    const int64_t j_begin = static_cast<int64_t>(blockIdx.y) * per_split;
-    const int64_t j_end = min(n_src, j_begin + per_split);
+    // work item (batched systems): targets [x, x + y), sources [z, w)
+    int64_t tbase, t_end, j_begin, j_end;
+    if (work) {
+        const int4 wi = work[blockIdx.x];
+        tbase = wi.x;
+        t_end = static_cast<int64_t>(wi.x) + wi.y;
+        j_begin = wi.z;
+        j_end = wi.w;
+    } else {
+        tbase = static_cast<int64_t>(blockIdx.x) * (T * kThreads);
+        t_end = n_tgt;
+        j_begin = static_cast<int64_t>(blockIdx.y) * per_split;
+        j_end = min(n_src, j_begin + per_split);
+    }
     const int64_t n_tiles = j_end > j_begin ? (j_end - j_begin + TILE - 1) / TILE : 0;
 
     if (tid == 0) {
@@ -207,7 +219,7 @@ __global__ void __launch_bounds__(kThreads)
         const int64_t i = tbase + tid + static_cast<int64_t>(t) * kThreads;
         double x = 0.0, y = 0.0, z = 0.0;
         int2 e = make_int2(0, 0);
-        if (i < n_tgt) {
+        if (i < t_end) {
             x = tgt[3 * i + 0] - c0;
             y = tgt[3 * i + 1] - c1;
             z = tgt[3 * i + 2] - c2;
@@ -305,7 +317,7 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
     for (int t = 0; t < T; ++t) {
         const int64_t i = tbase + tid + static_cast<int64_t>(t) * kThreads;
-        if (i >= n_tgt) continue;
+        if (i >= t_end) continue;
         const double ux = static_cast<double>(sx[t]) + static_cast<double>(cx[t]);
         const double uy = static_cast<double>(sy[t]) + static_cast<double>(cy[t]);
         const double uz = static_cast<double>(sz[t]) + static_cast<double>(cz[t]);
@@ -456,7 +468,7 @@ __global__ void __launch_bounds__(kThreads)
     k_pairsum_ff(const float4 *__restrict__ src, int64_t n_src, int64_t per_split,
                  const double *__restrict__ tgt, const int2 *__restrict__ excl, int64_t n_tgt,
                  const double *__restrict__ center, double *__restrict__ out, double scale, int direct,
-                 int acc, int *__restrict__ status)
+                 int acc, int *__restrict__ status, const int4 *__restrict__ work)
 {
     constexpr int NARR = 4, TILE = kTileFF;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -465,9 +477,20 @@ __global__ void __launch_bounds__(kThreads)
     __shared__ int s_lo, s_hi;
 
     const int tid = threadIdx.x;
-    const int64_t tbase = static_cast<int64_t>(blockIdx.x) * (T * kThreads);
-    const int64_t j_begin = static_cast<int64_t>(blockIdx.y) * per_split;
-    const int64_t j_end = min(n_src, j_begin + per_split);
+    // work item (batched systems): targets [x, x + y), sources [z, w)
+    int64_t tbase, t_end, j_begin, j_end;
+    if (work) {
+        const int4 wi = work[blockIdx.x];
+        tbase = wi.x;
+        t_end = static_cast<int64_t>(wi.x) + wi.y;
+        j_begin = wi.z;
+        j_end = wi.w;
+    } else {
+        tbase = static_cast<int64_t>(blockIdx.x) * (T * kThreads);
+        t_end = n_tgt;
+        j_begin = static_cast<int64_t>(blockIdx.y) * per_split;
+        j_end = min(n_src, j_begin + per_split);
+    }
     const int64_t n_tiles = j_end > j_begin ? (j_end - j_begin + TILE - 1) / TILE : 0;
     if (tid == 0) {
         s_lo = INT_MAX;
@@ -486,12 +509,12 @@ __global__ void __launch_bounds__(kThreads)
         int2 e = make_int2(0, 0);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const double x = i < n_tgt ? tgt[3 * i + a] - c[a] : 0.0;
+            const double x = i < t_end ? tgt[3 * i + a] - c[a] : 0.0;
             th[t][a] = static_cast<float>(x);
             tl[t][a] = static_cast<float>(x - static_cast<double>(th[t][a]));
             uh[t][a] = ul[t][a] = 0.0f;
         }
-        if (i < n_tgt && excl) e = excl[i];
+        if (i < t_end && excl) e = excl[i];
         elo[t] = e.x;
         ecnt[t] = e.y > e.x ? e.y - e.x : 0;
         if (e.y > e.x) {
@@ -553,7 +576,7 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
     for (int t = 0; t < T; ++t) {
         const int64_t i = tbase + tid + static_cast<int64_t>(t) * kThreads;
-        if (i >= n_tgt) continue;
+        if (i >= t_end) continue;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const double v = static_cast<double>(uh[t][a]) + static_cast<double>(ul[t][a]);
@@ -780,7 +803,7 @@ fs_status pairsum(const PairSumArgs &a, void *scratch, size_t scratch_bytes, int
     Carve cv(scratch, scratch_bytes);
     double *center = cv.take<double>(4);
     void *packed = cv.take<unsigned char>(static_cast<size_t>(n_arr) * a.n_src * v4);
-    const int direct = p.splits == 1;
+    int direct = p.splits == 1;
     double *part = direct ? nullptr : cv.take<double>(static_cast<size_t>(p.splits) * a.n_tgt * 3);
     if (cv.used > scratch_bytes) {
         set_error("pairsum: scratch too small (%zu > %zu bytes)", cv.used, scratch_bytes);
@@ -799,10 +822,33 @@ fs_status pairsum(const PairSumArgs &a, void *scratch, size_t scratch_bytes, int
         k_pack<double><<<pb, 256, 0, st>>>(a.src_xyz, a.src_dens, a.src_w, a.src_nrm, a.n_src, center,
                                            static_cast<double4_32a *>(packed), n_arr, 0);
     FS_LAUNCH_CHECK();
-    const dim3 grid(static_cast<unsigned>((a.n_tgt + p.tpt * kThreads - 1) / (p.tpt * kThreads)),
-                    static_cast<unsigned>(p.splits));
+    dim3 grid(static_cast<unsigned>((a.n_tgt + p.tpt * kThreads - 1) / (p.tpt * kThreads)),
+              static_cast<unsigned>(p.splits));
     const size_t sm = static_cast<size_t>(n_arr) * 2 * p.tile * v4;
-    double *dst = direct ? a.out : part;
+    const int4 *work = nullptr;
+    if (a.groups) {
+        // one work item per block of tpt x threads targets of a group, sources of
+        // that group only; largest source ranges first
+        std::vector<int4> items;
+        const int chunk = p.tpt * kThreads;
+        for (const int4 &g : *a.groups)
+            for (int t0 = g.x; t0 < g.y; t0 += chunk)
+                items.push_back(make_int4(t0, std::min(chunk, g.y - t0), g.z, g.w));
+        std::stable_sort(items.begin(), items.end(),
+                         [](const int4 &u, const int4 &v) { return (u.w - u.z) > (v.w - v.z); });
+        if (items.empty()) return FS_OK;
+        if (static_cast<int64_t>(items.size()) > a.work_cap) {
+            set_error("pairsum: %zu work items exceed the capacity %lld", items.size(),
+                      static_cast<long long>(a.work_cap));
+            return FS_EINVAL;
+        }
+        FS_CUDA(cudaMemcpyAsync(a.work_dev, items.data(), items.size() * sizeof(int4),
+                                cudaMemcpyHostToDevice, st));
+        work = a.work_dev;
+        grid = dim3(static_cast<unsigned>(items.size()), 1);
+        direct = 1;
+    }
+    double *dst = (direct || work) ? a.out : part;
     const int acc = a.accumulate ? 1 : 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (a.prof) {
@@ -817,7 +863,7 @@ fs_status pairsum(const PairSumArgs &a, void *scratch, size_t scratch_bytes, int
 #define FS_LAUNCH(R, TT, K, HL)                                                                   \
     k_pairsum<R, TT, K, HL><<<grid, kThreads, sm, st>>>(                                         \
         static_cast<const Vec4Of<R>::type *>(packed), a.n_src, p.per_split, a.tgt_xyz, a.excl,   \
-        a.n_tgt, center, dst, a.scale, direct, acc, d_status)
+        a.n_tgt, center, dst, a.scale, direct, acc, d_status, work)
 #define FS_BY_T(R, K, HL)                                                                         \
     do {                                                                                          \
         if (p.tpt == 2) FS_LAUNCH(R, 2, K, HL);                                                   \
@@ -834,11 +880,11 @@ fs_status pairsum(const PairSumArgs &a, void *scratch, size_t scratch_bytes, int
         if (p.tpt == 1)
             k_pairsum_ff<1><<<grid, kThreads, sm, st>>>(static_cast<const float4 *>(packed), a.n_src,
                                                         p.per_split, a.tgt_xyz, a.excl, a.n_tgt, center,
-                                                        dst, a.scale, direct, acc, d_status);
+                                                        dst, a.scale, direct, acc, d_status, work);
         else
             k_pairsum_ff<2><<<grid, kThreads, sm, st>>>(static_cast<const float4 *>(packed), a.n_src,
                                                         p.per_split, a.tgt_xyz, a.excl, a.n_tgt, center,
-                                                        dst, a.scale, direct, acc, d_status);
+                                                        dst, a.scale, direct, acc, d_status, work);
     } else if (f32) {
         if (a.kind == PAIR_STOKESLET) {
             if (hilo) FS_BY_T(float, PAIR_STOKESLET, true); else FS_BY_T(float, PAIR_STOKESLET, false);
@@ -858,7 +904,7 @@ fs_status pairsum(const PairSumArgs &a, void *scratch, size_t scratch_bytes, int
         const int cls = ff ? 4 : (a.kind == PAIR_STOKESLET ? 0 : 2) + (f32 ? 0 : 1);
         a.prof->recs.push_back(Profiler::Rec{cls, ev0, ev1, a.pairs});
     }
-    if (!direct) {
+    if (!direct && !work) {
         const int64_t n3 = a.n_tgt * 3;
         k_reduce_splits<<<static_cast<unsigned>((n3 + 255) / 256), 256, 0, st>>>(part, p.splits, n3,
                                                                                  a.scale, acc, a.out);

@@ -18,80 +18,6 @@
 namespace fs {
 namespace {
 
-constexpr int kDotBlocks = 64;
-
-__global__ void k_multidot(const double *__restrict__ V, int64_t ld, int k,
-                           const double *__restrict__ w, int64_t n, double *__restrict__ part)
-{
-    // part[i * kDotBlocks + b] = sum over chunk b of V_i . w
-    __shared__ double red[8];
-    const int i = blockIdx.y;
-    const int64_t chunk = (n + kDotBlocks - 1) / kDotBlocks;
-    const int64_t e0 = blockIdx.x * chunk, e1 = min(n, e0 + chunk);
-    const double *v = V + i * ld;
-    double s = 0.0;
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) s += v[e] * w[e];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int wv = 0; wv < static_cast<int>(blockDim.x >> 5); ++wv) t += red[wv];
-        part[i * kDotBlocks + blockIdx.x] = t;
-    }
-}
-
-// h[i] (+)= sum_b part[i][b]; if do_sqrt, h[0] = sqrt(h[0]) (norm)
-__global__ void k_finish_dots(const double *__restrict__ part, int k, double *__restrict__ h, int add,
-                              int do_sqrt)
-{
-    const int i = threadIdx.x;
-    if (i >= k) return;
-    double s = 0.0;
-    for (int b = 0; b < kDotBlocks; ++b) s += part[i * kDotBlocks + b];
-    if (do_sqrt) s = sqrt(s);
-    h[i] = add ? h[i] + s : s;
-}
-
-// w -= sum_i h[i] V_i
-__global__ void k_axpy_multi(double *__restrict__ w, const double *__restrict__ V, int64_t ld,
-                             const double *__restrict__ h, int k, int64_t n)
-{
-    const int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-    if (e >= n) return;
-    double s = 0.0;
-    for (int i = 0; i < k; ++i) s += h[i] * V[i * ld + e];
-    w[e] -= s;
-}
-
-// out = in / (*nrm)  (zero if the norm is zero)
-__global__ void k_scale_by(const double *__restrict__ in, const double *__restrict__ nrm,
-                           double *__restrict__ out, int64_t n)
-{
-    const int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-    if (e >= n) return;
-    const double d = *nrm;
-    out[e] = d > 0.0 ? in[e] / d : 0.0;
-}
-
-// x += sum_i y[i] V_i
-__global__ void k_lincomb(double *__restrict__ x, const double *__restrict__ V, int64_t ld,
-                          const double *__restrict__ y, int k, int64_t n)
-{
-    const int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-    if (e >= n) return;
-    double s = 0.0;
-    for (int i = 0; i < k; ++i) s += y[i] * V[i * ld + e];
-    x[e] += s;
-}
-
-// out = a - b
-__global__ void k_sub(const double *__restrict__ a, const double *__restrict__ b,
-                      double *__restrict__ out, int64_t n)
-{
-    const int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-    if (e < n) out[e] = a[e] - b[e];
-}
 
 __global__ void k_add(double *__restrict__ x, const double *__restrict__ e, int64_t n)
 {
@@ -115,26 +41,188 @@ fs_status dalloc(T **p, size_t n)
     return FS_OK;
 }
 
-// ||v|| into d_h[slot] (device) -- uses d_part
-fs_status dev_norm(fs_ctx *c, const double *v, int64_t n, double *dst)
+// ------------------------------------------------------ segmented Krylov kernels
+// Vectors hold several independent systems back to back.  Work is described by
+// chunks (int4: first element, length <= kChunk, system, 0) covering the
+// active systems only; per-system scalars live in h[s * SH + offset].
+constexpr int kChunk = 4096;
+
+// part[i * nch + c] = sum over chunk c of V_i . w
+__global__ void k_seg_dot(const double *__restrict__ V, int64_t ld, const double *__restrict__ w,
+                          const int4 *__restrict__ ch, int nch, double *__restrict__ part)
 {
-    k_multidot<<<dim3(kDotBlocks, 1), 256, 0, c->stream>>>(v, 0, 1, v, n, c->d_part);
+    __shared__ double red[8];
+    const int c = blockIdx.x, i = blockIdx.y;
+    const int4 q = ch[c];
+    const double *v = V + i * ld;
+    double s = 0.0;
+    for (int e = threadIdx.x; e < q.y; e += blockDim.x) s += v[q.x + e] * w[q.x + e];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int wv = 0; wv < static_cast<int>(blockDim.x >> 5); ++wv) t += red[wv];
+        part[static_cast<int64_t>(i) * nch + c] = t;
+    }
+}
+
+// h[s * SH + off + i] = sum of part[i][c] over the chunks of active system slot b
+// (sch[b] = (system, first chunk, end chunk)); sqrt when do_sqrt
+__global__ void k_seg_finish(const double *__restrict__ part, int k, int nch, const int4 *__restrict__ sch,
+                             double *__restrict__ h, int SH, int off, int do_sqrt)
+{
+    const int4 q = sch[blockIdx.x];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        double s = 0.0;
+        for (int c = q.y; c < q.z; ++c) s += part[static_cast<int64_t>(i) * nch + c];
+        h[static_cast<int64_t>(q.x) * SH + off + i] = do_sqrt ? sqrt(s) : s;
+    }
+}
+
+// w -= sum_{i<k} h[s SH + off + i] V_i  on active chunks
+__global__ void k_seg_axpy(double *__restrict__ w, const double *__restrict__ V, int64_t ld,
+                           const double *__restrict__ h, int SH, int off, int k,
+                           const int4 *__restrict__ ch)
+{
+    const int4 q = ch[blockIdx.x];
+    const double *hs = h + static_cast<int64_t>(q.z) * SH + off;
+    for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < q.y; e += gridDim.y * blockDim.x) {
+        const int64_t g = q.x + e;
+        double s = 0.0;
+        for (int i = 0; i < k; ++i) s += hs[i] * V[i * ld + g];
+        w[g] -= s;
+    }
+}
+
+// out = in / h[s SH + off]  (0 if the norm is 0)
+__global__ void k_seg_scale(const double *__restrict__ in, const double *__restrict__ h, int SH, int off,
+                            double *__restrict__ out, const int4 *__restrict__ ch)
+{
+    const int4 q = ch[blockIdx.x];
+    const double d = h[static_cast<int64_t>(q.z) * SH + off];
+    for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < q.y; e += gridDim.y * blockDim.x)
+        out[q.x + e] = d > 0.0 ? in[q.x + e] / d : 0.0;
+}
+
+// x += sum_{i < kk[s]} y[s SH + off + i] V_i
+__global__ void k_seg_lincomb(double *__restrict__ x, const double *__restrict__ V, int64_t ld,
+                              const double *__restrict__ h, int SH, int off, const int *__restrict__ kk,
+                              const int4 *__restrict__ ch)
+{
+    const int4 q = ch[blockIdx.x];
+    const double *ys = h + static_cast<int64_t>(q.z) * SH + off;
+    const int k = kk[q.z];
+    for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < q.y; e += gridDim.y * blockDim.x) {
+        const int64_t g = q.x + e;
+        double s = 0.0;
+        for (int i = 0; i < k; ++i) s += ys[i] * V[i * ld + g];
+        x[g] += s;
+    }
+}
+
+// mode 0: out = 0; 1: out = a; 2: out = a - b   (on active chunks)
+__global__ void k_seg_set(double *__restrict__ out, const double *__restrict__ a,
+                          const double *__restrict__ b, int mode, const int4 *__restrict__ ch)
+{
+    const int4 q = ch[blockIdx.x];
+    for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < q.y; e += gridDim.y * blockDim.x) {
+        const int64_t g = q.x + e;
+        out[g] = mode == 0 ? 0.0 : (mode == 1 ? a[g] : a[g] - b[g]);
+    }
+}
+
+// ------------------------------------------------------ segmented GMRES (host)
+struct SysState {
+    double beta0 = 0.0, beta = 0.0, rel = 0.0;
+    int its = 0, inner = 0, kk = 0;
+    bool conv = false, done = false;
+    std::vector<double> H, cs, sn, g, y;
+};
+
+// One Krylov space: basis V [(R+1) x n], flexible directions Z [R x n],
+// per-system scalars h [S x SH], reduction partials, work vectors, chunk lists.
+struct Space {
+    int R;
+    double *V, *Z, *h, *part, *w, *r, *hpin;
+    int4 *d_ch, *d_sch;
+    int *d_kk;
+    int nch = 0, nsch = 0;
+};
+
+Space inner_space(fs_ctx *c)
+{
+    return Space{c->kdim - 1, c->d_basis, nullptr, c->d_h, c->d_part, c->d_w, c->d_r, c->h_pinned,
+                 c->d_ich, c->d_isch, c->d_ikk};
+}
+
+Space outer_space(fs_ctx *c)
+{
+    return Space{c->okdim - 1, c->d_obasis, c->d_oz, c->d_oh, c->d_opart, c->d_ow, c->d_or, c->oh_pinned,
+                 c->d_och, c->d_osch, c->d_okk};
+}
+
+int SHof(const Space &sp) { return 4 * (sp.R + 1) + 8; }
+
+// chunk lists of the given active systems
+fs_status seg_build(fs_ctx *c, Space &sp, const std::vector<int> &act)
+{
+    std::vector<int4> ch, sch;
+    for (int s : act) {
+        const int64_t lo = c->sys_unk_ptr[s], hi = c->sys_unk_ptr[s + 1];
+        const int first = static_cast<int>(ch.size());
+        for (int64_t e = lo; e < hi; e += kChunk)
+            ch.push_back(make_int4(static_cast<int>(e), static_cast<int>(std::min<int64_t>(kChunk, hi - e)), s, 0));
+        sch.push_back(make_int4(s, first, static_cast<int>(ch.size()), 0));
+    }
+    if (static_cast<int64_t>(ch.size()) > c->chunk_cap || static_cast<int>(sch.size()) > c->S) {
+        set_error("gmres: chunk list exceeds its capacity");
+        return FS_EINVAL;
+    }
+    sp.nch = static_cast<int>(ch.size());
+    sp.nsch = static_cast<int>(sch.size());
+    if (sp.nch) {
+        FS_CUDA(cudaMemcpyAsync(sp.d_ch, ch.data(), ch.size() * sizeof(int4), cudaMemcpyHostToDevice, c->stream));
+        FS_CUDA(cudaMemcpyAsync(sp.d_sch, sch.data(), sch.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                                c->stream));
+    }
+    return FS_OK;
+}
+
+dim3 seg_grid(const Space &sp) { return dim3(static_cast<unsigned>(sp.nch), kChunk / 256); }
+
+// h[s SH + off + i] = V_i . w  (i < k) for the active systems
+fs_status seg_dots(fs_ctx *c, const Space &sp, const double *V, int64_t ld, int k, const double *w, int off,
+                   bool do_sqrt)
+{
+    if (!sp.nch) return FS_OK;
+    k_seg_dot<<<dim3(sp.nch, k), 256, 0, c->stream>>>(V, ld, w, sp.d_ch, sp.nch, sp.part);
     FS_LAUNCH_CHECK();
-    k_finish_dots<<<1, 32, 0, c->stream>>>(c->d_part, 1, dst, 0, 1);
+    k_seg_finish<<<sp.nsch, 128, 0, c->stream>>>(sp.part, k, sp.nch, sp.d_sch, sp.h, SHof(sp), off,
+                                                  do_sqrt ? 1 : 0);
     FS_LAUNCH_CHECK();
     return FS_OK;
 }
 
-fs_status read_scalar(fs_ctx *c, const double *d, double *h)
+fs_status seg_set(fs_ctx *c, const Space &sp, double *out, const double *a, const double *b, int mode)
 {
-    FS_CUDA(cudaMemcpyAsync(c->h_pinned, d, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (!sp.nch) return FS_OK;
+    k_seg_set<<<seg_grid(sp), 256, 0, c->stream>>>(out, a, b, mode, sp.d_ch);
+    FS_LAUNCH_CHECK();
+    return FS_OK;
+}
+
+fs_status fetch_h(fs_ctx *c, const Space &sp)
+{
+    FS_CUDA(cudaMemcpyAsync(sp.hpin, sp.h, static_cast<size_t>(c->S) * SHof(sp) * sizeof(double),
+                            cudaMemcpyDeviceToHost, c->stream));
     FS_CUDA(cudaStreamSynchronize(c->stream));
-    *h = c->h_pinned[0];
     return FS_OK;
 }
 
-// Far field at the fiber nodes: ubar = (1/8 pi mu) sum_{other fibers} G0 W f
-fs_status far_field(fs_ctx *c, int sum_prec, bool hilo)
+// Far field at the fiber nodes for the active systems (each target block sums
+// its own system's sources only): ubar = (1/8 pi mu) sum_{other fibers} G0 W f
+fs_status far_field(fs_ctx *c, int sum_prec, bool hilo, const std::vector<int> *act)
 {
     PairSumArgs a;
     a.kind = PAIR_STOKESLET;
@@ -149,14 +237,28 @@ fs_status far_field(fs_ctx *c, int sum_prec, bool hilo)
     a.sum_prec = sum_prec;
     a.hilo = hilo;
     a.shape_override = c->opt.tile_override;
-    int64_t self = 0;
-    for (int m = 0; m < c->M; ++m) self += int64_t(c->Nm[m]) * c->Nm[m];
-    a.pairs = double(c->n_tot) * double(c->n_tot) - double(self);
+    std::vector<int4> groups;
+    double pairs = 0.0;
+    if (c->S > 1 && act) {
+        for (int s : *act) {
+            const int lo = static_cast<int>(c->sys_node_ptr[s]), hi = static_cast<int>(c->sys_node_ptr[s + 1]);
+            groups.push_back(make_int4(lo, hi, lo, hi));
+            pairs += double(hi - lo) * double(hi - lo) - c->sys_self_pairs[s];
+        }
+        a.groups = &groups;
+        a.work_dev = c->d_work;
+        a.work_cap = c->work_cap;
+    } else {
+        for (int s = 0; s < c->S; ++s) pairs += double(c->sys_node_ptr[s + 1] - c->sys_node_ptr[s]) *
+                                                double(c->sys_node_ptr[s + 1] - c->sys_node_ptr[s]) -
+                                                c->sys_self_pairs[s];
+    }
+    a.pairs = pairs;
     a.prof = c->opt.profile ? &c->prof : nullptr;
     FS_TRY(c->scratch.reserve(pairsum_scratch_bytes(a.kind, a.n_src, a.n_tgt, sum_prec, a.shape_override),
                               c->stream));
     FS_TRY(pairsum(a, c->scratch.ptr, c->scratch.bytes, c->d_status, c->stream));
-    c->pairs_last += c->n_tot * c->n_tot - self;
+    c->pairs_last += static_cast<int64_t>(pairs);
     return FS_OK;
 }
 
@@ -165,11 +267,12 @@ fs_status far_field(fs_ctx *c, int sum_prec, bool hilo)
 //            coupling rows Rw(ubar) pass through the block solves (the block's
 //            own rounding is never amplified by its inverse, cond ~1e9);
 //   surface: D^-1 (S q + fiber Stokeslets)  -- D the Jacobi diagonal.
-// sum_prec selects the far-field arithmetic.
-fs_status apply_pa(fs_ctx *c, const double *v, double *out, int sum_prec)
+// sum_prec selects the far-field arithmetic; act restricts the far field to
+// those systems (results of other systems are not meaningful).
+fs_status apply_pa(fs_ctx *c, const double *v, double *out, int sum_prec, const std::vector<int> *act)
 {
     FS_TRY(launch_force(c, v, c->d_f, c->d_wf));
-    FS_TRY(far_field(c, sum_prec, false));
+    FS_TRY(far_field(c, sum_prec, false, act));
     const double *q = c->surf.n ? v + c->n_fib_unk : nullptr;
     if (c->surf.n) FS_TRY(surface_couplings(c, q, c->d_ubar, sum_prec, false));
     FS_TRY(launch_rows(c, nullptr, c->d_f, c->d_ubar, c->d_e, ROWS_COUPLING));
@@ -183,8 +286,8 @@ fs_status apply_pa(fs_ctx *c, const double *v, double *out, int sum_prec)
     return FS_OK;
 }
 
-// Far-field arithmetic of the accurate sums (right-hand side, refinement
-// residuals): FP64 on the plain FP64 path, float-float on the mixed path.
+// Far-field arithmetic of the accurate sums (right-hand side, outer operator):
+// FP64 on the plain FP64 path, float-float on the mixed path.
 int accurate_prec(const fs_ctx *c) { return c->opt.prec == FS_FP64 ? FS_SUM_FP64 : FS_SUM_FF; }
 
 // b (Eq. sche-linear-eq right-hand side) with the accurate far field, then pb = P^-1 b
@@ -192,7 +295,7 @@ fs_status rhs(fs_ctx *c, double *b, double *pb)
 {
     const int ap = accurate_prec(c);
     FS_TRY(launch_force(c, nullptr, c->d_f, c->d_wf));
-    FS_TRY(far_field(c, ap, false));
+    FS_TRY(far_field(c, ap, false, &c->all_sys));
     if (c->surf.n) FS_TRY(surface_couplings(c, nullptr, c->d_ubar, ap, false));
     FS_TRY(launch_rows(c, nullptr, c->d_f, c->d_ubar, b, ROWS_RHS));
     if (c->surf.n) FS_TRY(surface_rows(c, nullptr, c->d_usurf, b + c->n_fib_unk, true, ap, false));
@@ -201,187 +304,164 @@ fs_status rhs(fs_ctx *c, double *b, double *pb)
     return FS_OK;
 }
 
-struct GmresResult {
-    int iters = 0;          // Arnoldi steps (outer steps for the flexible solver)
-    int inner_iters = 0;    // flexible solver: inner GMRES iterations in total
-    double rel = 0.0;       // |g| / beta0 estimate
-    bool converged = false;
-};
-
-// Storage of one Krylov space: basis V [(R+1) x n], optional flexible
-// directions Z [R x n], Hessenberg / norm scratch on the device and a pinned
-// host copy.
-struct Space {
-    int R;
-    double *V, *Z, *h, *part, *w, *r, *hpin;
-};
-
-Space inner_space(fs_ctx *c)
-{
-    return Space{c->kdim - 1, c->d_basis, nullptr, c->d_h, c->d_part, c->d_w, c->d_r, c->h_pinned};
-}
-
-Space outer_space(fs_ctx *c)
-{
-    return Space{c->okdim - 1, c->d_obasis, c->d_oz, c->d_oh, c->d_opart, c->d_ow, c->d_or, c->oh_pinned};
-}
-
-fs_status dev_norm_s(fs_ctx *c, const Space &sp, const double *v, int64_t n, double *dst)
-{
-    k_multidot<<<dim3(kDotBlocks, 1), 256, 0, c->stream>>>(v, 0, 1, v, n, sp.part);
-    FS_LAUNCH_CHECK();
-    k_finish_dots<<<1, 32, 0, c->stream>>>(sp.part, 1, dst, 0, 1);
-    FS_LAUNCH_CHECK();
-    return FS_OK;
-}
-
-fs_status read_scalar_s(fs_ctx *c, const Space &sp, const double *d, double *h)
-{
-    FS_CUDA(cudaMemcpyAsync(sp.hpin, d, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    FS_CUDA(cudaStreamSynchronize(c->stream));
-    *h = sp.hpin[0];
-    return FS_OK;
-}
-
-// out = operator(v): the preconditioned operator with the far field of `prec`
-struct Op {
-    int sum_prec;
-};
-
-// GMRES core for (P^-1 A) x = pb, x0 = 0, restarted after R steps, CGS2 and
-// Givens rotations.  With a flexible preconditioner (inner_prec >= 0) each
-// direction is z_j = an inner GMRES solve of (P^-1 A_inner) z = v_j to
-// inner_tol, the basis is built from (P^-1 A) z_j and x = Z y (FGMRES).
-fs_status gmres_core(fs_ctx *c, const Space &sp, const double *pb, double *x, double tol, int max_iter,
-                     int sum_prec, int inner_prec, double inner_tol, GmresResult *res);
-
-fs_status gmres(fs_ctx *c, const double *pb, double *x, double tol, int max_iter, int sum_prec,
-                GmresResult *res)
-{
-    return gmres_core(c, inner_space(c), pb, x, tol, max_iter, sum_prec, -1, 0.0, res);
-}
-
-fs_status gmres_core(fs_ctx *c, const Space &sp, const double *pb, double *x, double tol, int max_iter,
-                     int sum_prec, int inner_prec, double inner_tol, GmresResult *res)
+// Restarted GMRES for (P^-1 A) x = pb, x0 = 0, on each system in `want`
+// independently (lockstep: one operator application per iteration for all
+// running systems), CGS2 and Givens rotations per system; x overwritten on
+// those systems.  With inner_prec >= 0 each direction is z_j = an inner GMRES
+// solve of (P^-1 A_inner) z = v_j to inner_tol and x = Z y (flexible GMRES).
+fs_status gmres_seg(fs_ctx *c, Space &sp, const double *pb, double *x, double tol, int max_iter,
+                    int sum_prec, int inner_prec, double inner_tol, const std::vector<int> &want,
+                    std::vector<SysState> &st)
 {
     const int64_t n = c->n_unk;
-    const int R = sp.R;
-    const int hs = R + 1;   // stride of the h buffer blocks
-    double *V = sp.V;
+    const int R = sp.R, hs = R + 1, SH = SHof(sp);
     const bool flexible = inner_prec >= 0;
-    *res = GmresResult();
-    FS_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), c->stream));
-    FS_CUDA(cudaMemcpyAsync(sp.r, pb, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    double *d_beta = sp.h + 2 * hs + 2;
-    FS_TRY(dev_norm_s(c, sp, sp.r, n, d_beta));
-    double beta0;
-    FS_TRY(read_scalar_s(c, sp, d_beta, &beta0));
-    if (!(beta0 > 0.0)) {
-        res->converged = true;
-        return FS_OK;
-    }
-    if (!std::isfinite(beta0)) {
-        set_error("gmres: non-finite right-hand side");
-        return FS_ENUMERIC;
-    }
-    double beta = beta0;
-    std::vector<double> H(static_cast<size_t>(R + 1) * R), cs(R), sn(R), g(R + 1), y(R);
-    int total = 0;
-    while (true) {
-        k_scale_by<<<blocks_for(n), 256, 0, c->stream>>>(sp.r, d_beta, V, n);
-        FS_LAUNCH_CHECK();
-        std::fill(g.begin(), g.end(), 0.0);
-        g[0] = beta;
-        int kcols = 0;
-        bool done = false;
-        for (int j = 0; j < R; ++j) {
-            double *Vj = V + j * n, *Vn = V + (j + 1) * n;
-            if (flexible) {
-                GmresResult ir;
-                double *Zj = sp.Z + j * n;
-                FS_TRY(gmres_core(c, inner_space(c), Vj, Zj, inner_tol, c->opt.max_iter, inner_prec, -1, 0.0,
-                                  &ir));
-                res->inner_iters += ir.iters;
-                FS_TRY(apply_pa(c, Zj, sp.w, sum_prec));
-            } else {
-                FS_TRY(apply_pa(c, Vj, sp.w, sum_prec));
-            }
-            double *h = sp.h;
-            for (int pass = 0; pass < 2; ++pass) {   // CGS2
-                double *hp = h + (pass ? hs : 0);
-                k_multidot<<<dim3(kDotBlocks, j + 1), 256, 0, c->stream>>>(V, n, j + 1, sp.w, n, sp.part);
-                FS_LAUNCH_CHECK();
-                k_finish_dots<<<1, 256, 0, c->stream>>>(sp.part, j + 1, hp, 0, 0);
-                FS_LAUNCH_CHECK();
-                k_axpy_multi<<<blocks_for(n), 256, 0, c->stream>>>(sp.w, V, n, hp, j + 1, n);
-                FS_LAUNCH_CHECK();
-            }
-            FS_TRY(dev_norm_s(c, sp, sp.w, n, h + 2 * hs));
-            k_scale_by<<<blocks_for(n), 256, 0, c->stream>>>(sp.w, h + 2 * hs, Vn, n);
-            FS_LAUNCH_CHECK();
-            FS_CUDA(cudaMemcpyAsync(sp.hpin, h, (2 * hs + 1) * sizeof(double), cudaMemcpyDeviceToHost,
-                                    c->stream));
-            FS_CUDA(cudaStreamSynchronize(c->stream));
-            double *hc = &H[static_cast<size_t>(j) * (R + 1)];   // column j, length R+1
-            for (int i = 0; i <= j; ++i) hc[i] = sp.hpin[i] + sp.hpin[hs + i];
-            const double hn = sp.hpin[2 * hs];
-            hc[j + 1] = hn;
-            if (!std::isfinite(hn)) {
-                set_error("gmres: non-finite Arnoldi vector");
+    double *V = sp.V;
+    st.assign(c->S, SysState());
+    std::vector<int> act = want;
+    FS_TRY(seg_build(c, sp, act));
+    FS_TRY(seg_set(c, sp, x, nullptr, nullptr, 0));
+    FS_TRY(seg_set(c, sp, sp.r, pb, nullptr, 1));
+    FS_TRY(seg_dots(c, sp, sp.r, 0, 1, sp.r, 2 * hs + 2, true));
+    FS_TRY(fetch_h(c, sp));
+    {
+        std::vector<int> keep;
+        for (int s : act) {
+            SysState &q = st[s];
+            q.beta0 = q.beta = sp.hpin[static_cast<int64_t>(s) * SH + 2 * hs + 2];
+            if (!std::isfinite(q.beta0)) {
+                set_error("gmres: non-finite right-hand side (system %d)", s);
                 return FS_ENUMERIC;
             }
-            for (int i = 0; i < j; ++i) {
-                const double t = cs[i] * hc[i] + sn[i] * hc[i + 1];
-                hc[i + 1] = -sn[i] * hc[i] + cs[i] * hc[i + 1];
-                hc[i] = t;
+            if (!(q.beta0 > 0.0)) {
+                q.conv = q.done = true;
+                continue;
             }
-            const double d = std::hypot(hc[j], hc[j + 1]);
-            cs[j] = d > 0.0 ? hc[j] / d : 1.0;
-            sn[j] = d > 0.0 ? hc[j + 1] / d : 0.0;
-            hc[j] = d;
-            hc[j + 1] = 0.0;
-            g[j + 1] = -sn[j] * g[j];
-            g[j] = cs[j] * g[j];
-            ++total;
-            kcols = j + 1;
-            res->rel = std::fabs(g[j + 1]) / beta0;
-            if (res->rel <= tol) {
-                res->converged = true;
-                done = true;
-                break;
-            }
-            if (hn == 0.0 || total >= max_iter) {
-                done = true;
-                break;
-            }
+            q.H.assign(static_cast<size_t>(R + 1) * R, 0.0);
+            q.cs.assign(R, 0.0);
+            q.sn.assign(R, 0.0);
+            q.g.assign(R + 1, 0.0);
+            q.y.assign(R, 0.0);
+            keep.push_back(s);
         }
-        // y = H^-1 g (upper triangular kcols x kcols), x += (V or Z) y
-        for (int i = kcols - 1; i >= 0; --i) {
-            double s = g[i];
-            for (int l = i + 1; l < kcols; ++l) s -= H[static_cast<size_t>(l) * (R + 1) + i] * y[l];
-            const double dii = H[static_cast<size_t>(i) * (R + 1) + i];
-            y[i] = dii != 0.0 ? s / dii : 0.0;
-        }
-        std::memcpy(sp.hpin, y.data(), kcols * sizeof(double));
-        double *d_y = sp.h + 3 * hs + 4;
-        FS_CUDA(cudaMemcpyAsync(d_y, sp.hpin, kcols * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-        k_lincomb<<<blocks_for(n), 256, 0, c->stream>>>(x, flexible ? sp.Z : V, n, d_y, kcols, n);
-        FS_LAUNCH_CHECK();
-        FS_CUDA(cudaStreamSynchronize(c->stream));   // hpin is reused below
-        if (done) break;
-        // restart: r = pb - P^-1 A x
-        FS_TRY(apply_pa(c, x, sp.w, sum_prec));
-        k_sub<<<blocks_for(n), 256, 0, c->stream>>>(pb, sp.w, sp.r, n);
-        FS_LAUNCH_CHECK();
-        FS_TRY(dev_norm_s(c, sp, sp.r, n, d_beta));
-        FS_TRY(read_scalar_s(c, sp, d_beta, &beta));
-        res->rel = beta / beta0;
-        if (res->rel <= tol) {
-            res->converged = true;
-            break;
-        }
+        act.swap(keep);
     }
-    res->iters = total;
+    while (!act.empty()) {
+        FS_TRY(seg_build(c, sp, act));
+        k_seg_scale<<<seg_grid(sp), 256, 0, c->stream>>>(sp.r, sp.h, SH, 2 * hs + 2, V, sp.d_ch);
+        FS_LAUNCH_CHECK();
+        for (int s : act) {
+            SysState &q = st[s];
+            std::fill(q.g.begin(), q.g.end(), 0.0);
+            q.g[0] = q.beta;
+            q.kk = 0;
+        }
+        std::vector<int> running = act;
+        for (int j = 0; j < R && !running.empty(); ++j) {
+            double *Vj = V + j * n, *Vn = V + (j + 1) * n;
+            if (flexible) {
+                double *Zj = sp.Z + j * n;
+                Space isp = inner_space(c);
+                std::vector<SysState> ist;
+                FS_TRY(gmres_seg(c, isp, Vj, Zj, inner_tol, c->opt.max_iter, inner_prec, -1, 0.0, running, ist));
+                for (int s : running) st[s].inner += ist[s].its;
+                FS_TRY(apply_pa(c, Zj, sp.w, sum_prec, &running));
+            } else {
+                FS_TRY(apply_pa(c, Vj, sp.w, sum_prec, &running));
+            }
+            for (int pass = 0; pass < 2; ++pass) {   // CGS2
+                const int off = pass ? hs : 0;
+                FS_TRY(seg_dots(c, sp, V, n, j + 1, sp.w, off, false));
+                k_seg_axpy<<<seg_grid(sp), 256, 0, c->stream>>>(sp.w, V, n, sp.h, SH, off, j + 1, sp.d_ch);
+                FS_LAUNCH_CHECK();
+            }
+            FS_TRY(seg_dots(c, sp, sp.w, 0, 1, sp.w, 2 * hs, true));
+            k_seg_scale<<<seg_grid(sp), 256, 0, c->stream>>>(sp.w, sp.h, SH, 2 * hs, Vn, sp.d_ch);
+            FS_LAUNCH_CHECK();
+            FS_TRY(fetch_h(c, sp));
+            std::vector<int> still;
+            for (int s : running) {
+                SysState &q = st[s];
+                const double *hp = sp.hpin + static_cast<int64_t>(s) * SH;
+                double *hc = &q.H[static_cast<size_t>(j) * (R + 1)];
+                for (int i = 0; i <= j; ++i) hc[i] = hp[i] + hp[hs + i];
+                const double hn = hp[2 * hs];
+                hc[j + 1] = hn;
+                if (!std::isfinite(hn)) {
+                    set_error("gmres: non-finite Arnoldi vector (system %d)", s);
+                    return FS_ENUMERIC;
+                }
+                for (int i = 0; i < j; ++i) {
+                    const double t = q.cs[i] * hc[i] + q.sn[i] * hc[i + 1];
+                    hc[i + 1] = -q.sn[i] * hc[i] + q.cs[i] * hc[i + 1];
+                    hc[i] = t;
+                }
+                const double d = std::hypot(hc[j], hc[j + 1]);
+                q.cs[j] = d > 0.0 ? hc[j] / d : 1.0;
+                q.sn[j] = d > 0.0 ? hc[j + 1] / d : 0.0;
+                hc[j] = d;
+                hc[j + 1] = 0.0;
+                q.g[j + 1] = -q.sn[j] * q.g[j];
+                q.g[j] = q.cs[j] * q.g[j];
+                ++q.its;
+                q.kk = j + 1;
+                q.rel = std::fabs(q.g[j + 1]) / q.beta0;
+                if (q.rel <= tol) {
+                    q.conv = q.done = true;
+                } else if (hn == 0.0 || q.its >= max_iter) {
+                    q.done = true;
+                } else {
+                    still.push_back(s);
+                }
+            }
+            if (still.size() != running.size()) {
+                running.swap(still);
+                if (!running.empty()) FS_TRY(seg_build(c, sp, running));
+            }
+        }
+        // y = H^-1 g per system; x += (V or Z) y on the systems of this cycle
+        std::vector<int> kk(c->S, 0);
+        for (int s : act) {
+            SysState &q = st[s];
+            const int k = q.kk;
+            for (int i = k - 1; i >= 0; --i) {
+                double sum = q.g[i];
+                for (int l = i + 1; l < k; ++l) sum -= q.H[static_cast<size_t>(l) * (R + 1) + i] * q.y[l];
+                const double dii = q.H[static_cast<size_t>(i) * (R + 1) + i];
+                q.y[i] = dii != 0.0 ? sum / dii : 0.0;
+            }
+            kk[s] = k;
+            std::memcpy(sp.hpin + static_cast<int64_t>(s) * SH + 3 * hs + 4, q.y.data(), k * sizeof(double));
+        }
+        FS_CUDA(cudaMemcpyAsync(sp.h, sp.hpin, static_cast<size_t>(c->S) * SH * sizeof(double),
+                                cudaMemcpyHostToDevice, c->stream));
+        FS_CUDA(cudaMemcpyAsync(sp.d_kk, kk.data(), c->S * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+        FS_TRY(seg_build(c, sp, act));
+        k_seg_lincomb<<<seg_grid(sp), 256, 0, c->stream>>>(x, flexible ? sp.Z : V, n, sp.h, SH, 3 * hs + 4,
+                                                           sp.d_kk, sp.d_ch);
+        FS_LAUNCH_CHECK();
+        FS_CUDA(cudaStreamSynchronize(c->stream));   // hpin and kk are reused below
+        std::vector<int> again;
+        for (int s : act)
+            if (!st[s].done) again.push_back(s);
+        if (again.empty()) break;
+        // restart: r = pb - P^-1 A x on the systems that continue
+        act.swap(again);
+        FS_TRY(seg_build(c, sp, act));
+        FS_TRY(apply_pa(c, x, sp.w, sum_prec, &act));
+        FS_TRY(seg_set(c, sp, sp.r, pb, sp.w, 2));
+        FS_TRY(seg_dots(c, sp, sp.r, 0, 1, sp.r, 2 * hs + 2, true));
+        FS_TRY(fetch_h(c, sp));
+        std::vector<int> keep;
+        for (int s : act) {
+            SysState &q = st[s];
+            q.beta = sp.hpin[static_cast<int64_t>(s) * SH + 2 * hs + 2];
+            q.rel = q.beta / q.beta0;
+            if (q.rel <= tol) q.conv = q.done = true;
+            else keep.push_back(s);
+        }
+        act.swap(keep);
+    }
     return FS_OK;
 }
 
@@ -410,7 +490,8 @@ double ms_since(std::chrono::steady_clock::time_point t0)
 
 }  // namespace
 
-fs_status context_init(fs_ctx *c, int M, const int32_t *ppf, const fs_boundary *bd)
+fs_status context_init(fs_ctx *c, int S, const int32_t *fps, int M, const int32_t *ppf,
+                       const fs_boundary *bd)
 {
     c->M = M;
     c->Nm.assign(ppf, ppf + M);
@@ -434,10 +515,38 @@ fs_status context_init(fs_ctx *c, int M, const int32_t *ppf, const fs_boundary *
     c->n_z = zp[M];
     c->surf.n = bd ? bd->n_nodes : 0;
     c->n_unk = c->n_fib_unk + 3 * int64_t(c->surf.n);
-    if (c->n_tot >= (1LL << 31) - 1) {
-        set_error("fs_create: at most 2^31-2 points");
+    if (c->n_tot >= (1LL << 31) - 1 || c->n_unk >= (1LL << 31) - 1) {
+        set_error("fs_create: at most 2^31-2 points and unknowns");
         return FS_EINVAL;
     }
+    // independent systems: consecutive fiber ranges
+    c->S = std::max(1, S);
+    c->sys_fib_ptr.assign(c->S + 1, 0);
+    if (S >= 1 && fps) {
+        for (int s = 0; s < S; ++s) c->sys_fib_ptr[s + 1] = c->sys_fib_ptr[s] + fps[s];
+        if (c->sys_fib_ptr[S] != M) {
+            set_error("fs_create_batch: fibers per system sum to %d, not %d", c->sys_fib_ptr[S], M);
+            return FS_EINVAL;
+        }
+    } else {
+        c->sys_fib_ptr[1] = M;
+    }
+    c->sys_node_ptr.assign(c->S + 1, 0);
+    c->sys_unk_ptr.assign(c->S + 1, 0);
+    c->sys_self_pairs.assign(c->S, 0.0);
+    c->all_sys.resize(c->S);
+    for (int s = 0; s < c->S; ++s) {
+        c->all_sys[s] = s;
+        c->sys_node_ptr[s + 1] = c->node_ptr[c->sys_fib_ptr[s + 1]];
+        c->sys_unk_ptr[s + 1] = c->unk_ptr[c->sys_fib_ptr[s + 1]];
+        for (int m = c->sys_fib_ptr[s]; m < c->sys_fib_ptr[s + 1]; ++m)
+            c->sys_self_pairs[s] += double(ppf[m]) * double(ppf[m]);
+    }
+    c->sys_unk_ptr[c->S] = c->n_unk;   // the periphery unknowns belong to the (single) system
+    c->sys_iters.assign(c->S, 0);
+    c->sys_outer.assign(c->S, 0);
+    c->sys_resid.assign(c->S, 0.0);
+    c->sys_conv.assign(c->S, 0);
     FS_TRY(dalloc(&c->d_status, 1));
     FS_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
     FS_CUDA(cudaMallocHost(&c->h_pinned, 4096 * sizeof(double)));
@@ -510,17 +619,33 @@ fs_status context_init(fs_ctx *c, int M, const int32_t *ppf, const fs_boundary *
     FS_TRY(dalloc(&c->d_w, n));
     FS_TRY(dalloc(&c->d_e, n));
     FS_TRY(dalloc(&c->d_pb, n));
-    FS_TRY(dalloc(&c->d_h, 4 * c->kdim + 8));
-    FS_TRY(dalloc(&c->d_part, static_cast<size_t>(c->kdim) * kDotBlocks));
+    c->chunk_cap = n / kChunk + c->S + 2;
+    int64_t items = c->S;
+    for (int s = 0; s < c->S; ++s) items += (c->sys_node_ptr[s + 1] - c->sys_node_ptr[s] + 127) / 128;
+    c->work_cap = items;
+    FS_TRY(dalloc(&c->d_work, static_cast<size_t>(c->work_cap)));
+    const size_t SHi = 4 * size_t(c->kdim) + 8;
+    FS_TRY(dalloc(&c->d_h, c->S * SHi));
+    FS_TRY(dalloc(&c->d_part, static_cast<size_t>(c->kdim) * c->chunk_cap));
+    FS_TRY(dalloc(&c->d_ich, static_cast<size_t>(c->chunk_cap)));
+    FS_TRY(dalloc(&c->d_isch, static_cast<size_t>(c->S)));
+    FS_TRY(dalloc(&c->d_ikk, static_cast<size_t>(c->S)));
+    FS_CUDA(cudaFreeHost(c->h_pinned));
+    c->h_pinned = nullptr;
+    FS_CUDA(cudaMallocHost(&c->h_pinned, c->S * SHi * sizeof(double)));
     if (c->opt.prec == FS_MIXED) {
         c->okdim = 17;   // outer (flexible) restart length 16
+        const size_t SHo = 4 * size_t(c->okdim) + 8;
         FS_TRY(dalloc(&c->d_obasis, static_cast<size_t>(c->okdim) * n));
         FS_TRY(dalloc(&c->d_oz, static_cast<size_t>(c->okdim - 1) * n));
-        FS_TRY(dalloc(&c->d_oh, 4 * c->okdim + 8));
-        FS_TRY(dalloc(&c->d_opart, static_cast<size_t>(c->okdim) * kDotBlocks));
+        FS_TRY(dalloc(&c->d_oh, c->S * SHo));
+        FS_TRY(dalloc(&c->d_opart, static_cast<size_t>(c->okdim) * c->chunk_cap));
         FS_TRY(dalloc(&c->d_ow, n));
         FS_TRY(dalloc(&c->d_or, n));
-        FS_CUDA(cudaMallocHost(&c->oh_pinned, 4096 * sizeof(double)));
+        FS_TRY(dalloc(&c->d_och, static_cast<size_t>(c->chunk_cap)));
+        FS_TRY(dalloc(&c->d_osch, static_cast<size_t>(c->S)));
+        FS_TRY(dalloc(&c->d_okk, static_cast<size_t>(c->S)));
+        FS_CUDA(cudaMallocHost(&c->oh_pinned, c->S * SHo * sizeof(double)));
     }
     if (c->surf.n) {
         const int ns = c->surf.n;
@@ -549,7 +674,7 @@ void context_free(fs_ctx *c)
                     c->d_z_ptr, c->d_ops_off, c->d_ops, c->d_excl, c->d_X, c->d_L, c->d_fext,
                     c->d_t, c->d_tz, c->d_fknown, c->d_W, c->d_mloc, c->d_bc, c->d_kp, c->d_B,
                     c->d_piv, c->d_V, c->d_T, c->d_f, c->d_wf, c->d_ubar, c->d_basis, c->d_b,
-                    c->d_x, c->d_r, c->d_w, c->d_e, c->d_pb, c->d_obasis, c->d_oz, c->d_oh, c->d_opart, c->d_ow, c->d_or, c->d_h, c->d_part, c->surf.y, c->surf.nrm,
+                    c->d_x, c->d_r, c->d_w, c->d_e, c->d_pb, c->d_obasis, c->d_oz, c->d_oh, c->d_opart, c->d_ow, c->d_or, c->d_work, c->d_ich, c->d_isch, c->d_ikk, c->d_och, c->d_osch, c->d_okk, c->d_h, c->d_part, c->surf.y, c->surf.nrm,
                     c->surf.w, c->surf.diag, c->d_usurf, c->surf.A, c->surf.tmp, c->surf.flux, c->surf.excl};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -682,23 +807,30 @@ fs_status fs_step(fs_ctx *c, fs_step_info *info)
     int iters = 0, sweeps = 0;
     double rel = 0.0;
     bool converged = false;
+    std::vector<SysState> st;
     if (c->opt.prec == FS_FP64) {
-        GmresResult gr;
-        FS_TRY(gmres(c, c->d_pb, c->d_x, c->opt.tol, c->opt.max_iter, FS_SUM_FP64, &gr));
-        iters = gr.iters;
-        rel = gr.rel;
-        sweeps = 1;
-        converged = gr.converged;
+        Space sp = inner_space(c);
+        FS_TRY(gmres_seg(c, sp, c->d_pb, c->d_x, c->opt.tol, c->opt.max_iter, FS_SUM_FP64, -1, 0.0,
+                         c->all_sys, st));
     } else {
         // mixed: flexible GMRES on the operator with the float-float far field,
         // each direction preconditioned by an FP32-far-field GMRES solve
-        GmresResult gr;
-        FS_TRY(gmres_core(c, outer_space(c), c->d_pb, c->d_x, c->opt.tol, c->opt.max_iter,
-                          accurate_prec(c), FS_SUM_FP32, c->opt.inner_tol, &gr));
-        iters = gr.inner_iters;
-        sweeps = gr.iters;
-        rel = gr.rel;
-        converged = gr.converged;
+        Space sp = outer_space(c);
+        FS_TRY(gmres_seg(c, sp, c->d_pb, c->d_x, c->opt.tol, c->opt.max_iter, accurate_prec(c), FS_SUM_FP32,
+                         c->opt.inner_tol, c->all_sys, st));
+    }
+    converged = true;
+    for (int s = 0; s < c->S; ++s) {
+        const SysState &q = st[s];
+        const int it = c->opt.prec == FS_FP64 ? q.its : q.inner;
+        iters = std::max(iters, it);
+        sweeps = std::max(sweeps, c->opt.prec == FS_FP64 ? 1 : q.its);
+        rel = std::max(rel, q.rel);
+        converged = converged && q.conv;
+        c->sys_iters[s] = it;
+        c->sys_outer[s] = q.its;
+        c->sys_resid[s] = q.rel;
+        c->sys_conv[s] = q.conv ? 1 : 0;
     }
     FS_TRY(check_status(c));
     tms[2] = ms_since(t0) - tms[0] - tms[1];
@@ -723,6 +855,22 @@ fs_status fs_step(fs_ctx *c, fs_step_info *info)
         tms[4] = ms_since(t0);
         tms[3] = tms[4] - tms[0] - tms[1] - tms[2];
         std::memcpy(info->t_ms, tms, sizeof(tms));
+    }
+    return FS_OK;
+}
+
+fs_status fs_batch_info(const fs_ctx *c, int32_t *iters, int32_t *outer, double *resid,
+                        int32_t *converged)
+{
+    if (!c) {
+        set_error("fs_batch_info: NULL context");
+        return FS_EINVAL;
+    }
+    for (int s = 0; s < c->S; ++s) {
+        if (iters) iters[s] = c->sys_iters[s];
+        if (outer) outer[s] = c->sys_outer[s];
+        if (resid) resid[s] = c->sys_resid[s];
+        if (converged) converged[s] = c->sys_conv[s];
     }
     return FS_OK;
 }
