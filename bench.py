@@ -193,6 +193,67 @@ def run_kernel(args, ws, rank, local, fs, torch, dist):
                           "tflops": fpp * pairs_s / 1e12}), flush=True)
 
 
+def run_serve(args, ws, rank, local, fs, torch):
+    """Serving: independent systems (8..512 fibers, 16/32/64 points, mixed
+    precision, tol 1e-8) submitted with Poisson arrivals to an fs_server;
+    reports throughput and latency percentiles, and the same systems stepped
+    together in one batched context for comparison."""
+    systems = wl.batched(args.serve, seed=100 + rank)
+    rng = np.random.default_rng(rank)
+    gaps = rng.exponential(1.0 / args.rate, size=len(systems)) if args.rate > 0 else np.zeros(len(systems))
+    sv = fs.fs_server_create(int(args.budget_gb * (1 << 30)), max_slots=args.slots, device=local)
+
+    def submit(s):
+        return fs.fs_submit(sv, s.n_per_fiber, s.X, s.L, s.mu, s.eps, s.E, s.dt, f_ext=s.f_ext,
+                            prec=fs.FS_MIXED, tol=1e-8)
+
+    for s in systems[:3]:   # warm-up: kernels loaded, op tables built once
+        fs.fs_server_wait(sv, submit(s))
+    t0 = time.perf_counter()
+    tickets, due = [], t0
+    for s, g in zip(systems, gaps):
+        due += g
+        while time.perf_counter() < due:
+            time.sleep(min(1e-3, max(0.0, due - time.perf_counter())))
+        tickets.append(submit(s))
+    res = [fs.fs_server_wait(sv, t) for t in tickets]
+    wall = time.perf_counter() - t0
+    fs.fs_server_destroy(sv)
+    lat = np.array([r["info"].t_ms[6] for r in res])
+    que = np.array([r["info"].t_ms[5] for r in res])
+
+    # the same systems in one batched context (fs_create_batch): one step for all
+    opt = fs.fs_options_default()
+    opt.prec = fs.FS_MIXED
+    opt.tol = 1e-8
+    dev = torch.device("cuda", local)
+    h = fs.fs_create_batch([x.n_fibers for x in systems], np.concatenate([x.n_per_fiber for x in systems]),
+                           1.0, 1e-3, 1.0, 1e-3, options=opt)
+    X = torch.tensor(np.concatenate([x.X for x in systems]), device=dev)
+    L = torch.tensor(np.concatenate([x.L for x in systems]), device=dev)
+    F = torch.tensor(np.concatenate([x.f_ext for x in systems]), device=dev)
+    bt = []
+    for k in range(3):
+        fs.fs_set_state(h, X, L, F)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        fs.fs_step(h)
+        torch.cuda.synchronize()
+        bt.append(time.perf_counter() - t1)
+    fs.fs_destroy(h)
+    if rank == 0:
+        pts = sum(x.n_points for x in systems)
+        print(json.dumps({
+            "mode": "serve", "requests": len(systems), "points_total": int(pts),
+            "fibers": [int(min(x.n_fibers for x in systems)), int(max(x.n_fibers for x in systems))],
+            "slots": args.slots, "budget_gb": args.budget_gb, "arrival_rate_per_s": args.rate,
+            "throughput_req_per_s": len(systems) / wall, "wall_s": wall,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
+                           "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
+            "queue_ms": {"p50": float(np.percentile(que, 50)), "p99": float(np.percentile(que, 99))},
+            "batched_one_context": {"step_s": min(bt), "req_per_s": len(systems) / min(bt)}}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -207,6 +268,11 @@ def main():
                     help="time only the direct-sum kernel on the cloud (fs_stokeslet_apply)")
     ap.add_argument("--points", type=int, default=0,
                     help="--kernel: use the first P points of the cloud (0 = all)")
+    ap.add_argument("--serve", type=int, default=0,
+                    help="serving mode: number of independent requests (0 = the step benchmark)")
+    ap.add_argument("--rate", type=float, default=0.0, help="--serve: Poisson arrival rate per s (0 = burst)")
+    ap.add_argument("--slots", type=int, default=4, help="--serve: concurrent requests")
+    ap.add_argument("--budget-gb", type=float, default=64.0, help="--serve: HBM budget for the requests")
     args = ap.parse_args()
     ws, rank, local = dist_env()
 
@@ -227,6 +293,8 @@ def main():
     import paper_1602_05650_gb300 as fs
     if args.kernel:
         return run_kernel(args, ws, rank, local, fs, torch, dist)
+    if args.serve:
+        return run_serve(args, ws, rank, local, fs, torch)
 
     dev = torch.device("cuda", local)
     s = wl.cfg_cloud_mixed(seed=rank)

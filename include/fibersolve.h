@@ -249,6 +249,74 @@ uint64_t fs_kernel_launches(void);
  * roofline peak of the pipe-bound direct sums.  Synchronises the device. */
 fs_status fs_probe_fma(int32_t precision, double *flops_per_s);
 
+/* Device bytes a context for this problem allocates (fs_create with these
+ * fibers, a boundary of n_surface_nodes nodes or 0, and these options) plus
+ * the largest direct-sum scratch one step reserves.  An upper bound of what
+ * fs_device_bytes reports after a step; 0 for invalid arguments.  Host-only:
+ * no CUDA call.  (No counterpart in the paper: sizing for admission control.) */
+size_t fs_estimate_bytes(int32_t n_fibers, const int32_t *points_per_fiber, int32_t n_surface_nodes,
+                         const fs_options *options);
+
+/* Device bytes the context holds now (its arrays and its scratch). */
+fs_status fs_device_bytes(const fs_ctx *ctx, size_t *bytes);
+
+/* ------------------------------------------------------------------ serving
+ * Independent step requests admitted continuously.  (No counterpart in the
+ * paper: a serving front end over fs_create / fs_step.)  A server owns
+ * max_slots worker threads on one device, each with its own CUDA stream;
+ * submitted requests wait in a FIFO and the head is admitted when a worker
+ * is free and fs_estimate_bytes of the request fits what the HBM budget has
+ * left.  An admitted request gets its own context, runs one fs_step and
+ * writes the result to the caller's host arrays; its arithmetic is that of
+ * fs_step on the same input alone.  Requests running at the same time
+ * overlap on the GPU. */
+typedef struct fs_server fs_server;
+
+typedef struct fs_request {
+    int32_t n_fibers;
+    const int32_t *points_per_fiber;   /* [n_fibers], each in [6, 256] */
+    const double *X;                   /* [N_tot][3] node positions, as fs_set_state */
+    const double *lengths;             /* [n_fibers] */
+    const double *f_ext;               /* [N_tot][3] or NULL (= 0) */
+    const fs_boundary *boundary;       /* NULL: free space */
+    double mu, eps, E, dt;             /* as fs_create */
+    int32_t prec;                      /* fs_precision */
+    double tol;                        /* GMRES tolerance; <= 0: the default */
+    double *out_X;                     /* [N_tot][3] positions after the step, or NULL */
+    double *out_V;                     /* [N_tot][3] velocity (required) */
+    double *out_T;                     /* [N_tot] tension, or NULL */
+} fs_request;
+
+/* Start a server on `device` with max_slots in [1, 256] workers and a budget
+ * of hbm_budget_bytes of device memory for the requests' contexts. */
+fs_status fs_server_create(fs_server **out, size_t hbm_budget_bytes, int32_t max_slots, int32_t device);
+
+/* Queue a request.  All its input arrays are copied before the call returns;
+ * the output arrays must stay valid until the ticket completes (fs_poll /
+ * fs_server_wait returns anything but FS_EAGAIN / FS_ETIMEOUT).  FS_EBUSY: the
+ * request alone needs more than the whole budget; FS_EINVAL: bad request. */
+fs_status fs_submit(fs_server *sv, const fs_request *request, uint64_t *ticket);
+
+/* Non-blocking completion check: FS_EAGAIN while queued or running;
+ * otherwise the request's own status (FS_OK, or the error of fs_create /
+ * fs_step with its message in fs_last_error()) and the ticket is released.
+ * info (may be NULL) receives fs_step's info with t_ms[5] = time queued and
+ * t_ms[6] = submit-to-done latency, in milliseconds. */
+fs_status fs_poll(fs_server *sv, uint64_t ticket, fs_step_info *info);
+
+/* Blocking form of fs_poll: waits up to timeout_s seconds; FS_ETIMEOUT if the
+ * request is still queued or running then (the ticket stays valid). */
+fs_status fs_server_wait(fs_server *sv, uint64_t ticket, fs_step_info *info, double timeout_s);
+
+/* Snapshot of the queue: requests waiting, running, bytes of the budget in
+ * use, and requests completed since creation (any may be NULL). */
+fs_status fs_server_stats(fs_server *sv, int32_t *pending, int32_t *running, size_t *bytes_in_use,
+                          int64_t *completed);
+
+/* Finish the running requests, drop the queued ones (their tickets become
+ * invalid) and join the workers. */
+void fs_server_destroy(fs_server *sv);
+
 /* Number of points N_tot and unknowns of the context. */
 fs_status fs_sizes(const fs_ctx *ctx, int64_t *n_points, int64_t *n_unknowns);
 

@@ -20,7 +20,9 @@ from ._native import (FS_FP64, FS_MIXED, FS_SUM_FP32, FS_SUM_FP64, fs_boundary, 
 __all__ = ["fs_options_default", "fs_create", "fs_create_batch", "fs_batch_info", "fs_destroy", "fs_set_state", "fs_get_state",
            "fs_stokeslet_apply", "fs_stresslet_apply", "fs_surface_apply", "fs_build_precond",
            "fs_step", "fs_sizes", "fs_last_error", "fs_kernel_stats", "fs_kernel_launches",
-           "fs_probe_fma", "FsError", "FS_FP64", "FS_MIXED",
+           "fs_probe_fma", "fs_estimate_bytes", "fs_device_bytes", "fs_server_create", "fs_submit",
+           "fs_poll", "fs_server_wait", "fs_server_stats", "fs_server_destroy", "Server", "FsError",
+           "FS_FP64", "FS_MIXED",
            "FS_SUM_FP32", "FS_SUM_FP64"]
 
 
@@ -237,3 +239,106 @@ def fs_probe_fma(precision: int) -> float:
     v = ctypes.c_double()
     _check(_native.load().fs_probe_fma(int(precision), ctypes.byref(v)), "fs_probe_fma")
     return v.value
+
+
+def fs_estimate_bytes(points_per_fiber, n_surface_nodes: int = 0, options: Optional[fs_options] = None) -> int:
+    """Device bytes a context for these fibers (and boundary size) allocates; 0 if invalid."""
+    ppf, ppf_p = _host_ptr(np.asarray(points_per_fiber), np.int32, "points_per_fiber")
+    return int(_native.load().fs_estimate_bytes(int(ppf.shape[0]), ppf_p, int(n_surface_nodes),
+                                                ctypes.byref(options) if options is not None else None))
+
+
+def fs_device_bytes(h: Handle) -> int:
+    v = ctypes.c_size_t()
+    _check(_native.load().fs_device_bytes(h.ptr, ctypes.byref(v)), "fs_device_bytes")
+    return int(v.value)
+
+
+class Server:
+    """Owns an fs_server*; keeps each pending request's host arrays alive until
+    its ticket completes."""
+
+    def __init__(self, ptr: ctypes.c_void_p):
+        self.ptr = ptr
+        self.pending = {}
+
+    def __del__(self):
+        try:
+            fs_server_destroy(self)
+        except Exception:
+            pass
+
+
+def fs_server_create(hbm_budget_bytes: int, max_slots: int = 4, device: int = 0) -> Server:
+    out = ctypes.c_void_p()
+    _check(_native.load().fs_server_create(ctypes.byref(out), int(hbm_budget_bytes), int(max_slots), int(device)),
+           "fs_server_create")
+    return Server(out)
+
+
+def fs_submit(sv: Server, points_per_fiber, X, lengths, mu: float, eps: float, E: float, dt: float,
+              f_ext=None, boundary=None, prec: int = FS_MIXED, tol: float = 0.0) -> int:
+    """Queue one step request (host numpy inputs).  Returns the ticket; the
+    outputs (X, V, T numpy arrays) are returned by fs_poll / fs_server_wait."""
+    ppf, ppf_p = _host_ptr(np.asarray(points_per_fiber), np.int32, "points_per_fiber")
+    xa, xp = _host_ptr(X, np.float64, "X")
+    la, lp = _host_ptr(lengths, np.float64, "lengths")
+    fa, fp = _host_ptr(f_ext, np.float64, "f_ext")
+    n_tot = int(ppf.sum())
+    outs = (np.zeros((n_tot, 3)), np.zeros((n_tot, 3)), np.zeros(n_tot))
+    keep = [ppf, xa, la, fa, outs]
+    bptr = None
+    if boundary is not None:
+        nodes, pn = _host_ptr(boundary.nodes, np.float64, "nodes")
+        nrm, pm = _host_ptr(boundary.normals, np.float64, "normals")
+        w, pw = _host_ptr(boundary.weights, np.float64, "weights")
+        b = fs_boundary(float(boundary.R), int(nodes.shape[0]), pn, pm, pw)
+        keep += [nodes, nrm, w, b]
+        bptr = ctypes.pointer(b)
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    rq = _native.fs_request(int(ppf.shape[0]), ppf_p, xp, lp, fp, bptr, float(mu), float(eps), float(E),
+                            float(dt), int(prec), float(tol), p(outs[0]), p(outs[1]), p(outs[2]))
+    t = ctypes.c_uint64()
+    _check(_native.load().fs_submit(sv.ptr, ctypes.byref(rq), ctypes.byref(t)), "fs_submit")
+    sv.pending[t.value] = keep
+    return int(t.value)
+
+
+def _complete(sv: Server, ticket: int, st: int, inf, where: str):
+    keep = sv.pending.pop(ticket, None)
+    _check(st, where)
+    X, V, T = keep[4]
+    return {"X": X, "V": V, "T": T, "info": inf}
+
+
+def fs_poll(sv: Server, ticket: int):
+    """None while the request is queued or running, else its result dict
+    (X, V, T, info); raises FsError if the request failed."""
+    inf = fs_step_info()
+    st = _native.load().fs_poll(sv.ptr, int(ticket), ctypes.byref(inf))
+    if st == _native.FS_EAGAIN:
+        return None
+    return _complete(sv, int(ticket), st, inf, "fs_poll")
+
+
+def fs_server_wait(sv: Server, ticket: int, timeout_s: float = 600.0):
+    inf = fs_step_info()
+    st = _native.load().fs_server_wait(sv.ptr, int(ticket), ctypes.byref(inf), float(timeout_s))
+    if st == _native.FS_ETIMEOUT:
+        raise FsError(st, "fs_server_wait", fs_last_error())
+    return _complete(sv, int(ticket), st, inf, "fs_server_wait")
+
+
+def fs_server_stats(sv: Server):
+    pe, ru, co = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    by = ctypes.c_size_t()
+    _check(_native.load().fs_server_stats(sv.ptr, ctypes.byref(pe), ctypes.byref(ru), ctypes.byref(by),
+                                          ctypes.byref(co)), "fs_server_stats")
+    return {"pending": pe.value, "running": ru.value, "bytes_in_use": int(by.value), "completed": co.value}
+
+
+def fs_server_destroy(sv: Server):
+    if sv.ptr is not None and sv.ptr.value:
+        _native.load().fs_server_destroy(sv.ptr)
+    sv.ptr = None
+    sv.pending.clear()

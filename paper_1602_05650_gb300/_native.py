@@ -46,6 +46,13 @@ class fs_step_info(ctypes.Structure):
                 ("t_ms", c_double * 8), ("pairs", c_int64)]
 
 
+class fs_request(ctypes.Structure):
+    _fields_ = [("n_fibers", c_int32), ("points_per_fiber", P), ("X", P), ("lengths", P), ("f_ext", P),
+                ("boundary", ctypes.POINTER(fs_boundary)), ("mu", c_double), ("eps", c_double),
+                ("E", c_double), ("dt", c_double), ("prec", c_int32), ("tol", c_double),
+                ("out_X", P), ("out_V", P), ("out_T", P)]
+
+
 # name -> (restype, argtypes)
 SIGNATURES = {
     "fs_options_default": (c_int32, [ctypes.POINTER(fs_options)]),
@@ -67,6 +74,15 @@ SIGNATURES = {
     "fs_kernel_stats": (c_int32, [P, ctypes.POINTER(fs_kernel_stat), c_int32]),
     "fs_kernel_launches": (ctypes.c_uint64, []),
     "fs_probe_fma": (c_int32, [c_int32, ctypes.POINTER(c_double)]),
+    "fs_estimate_bytes": (ctypes.c_size_t, [c_int32, P, c_int32, ctypes.POINTER(fs_options)]),
+    "fs_device_bytes": (c_int32, [P, ctypes.POINTER(ctypes.c_size_t)]),
+    "fs_server_create": (c_int32, [ctypes.POINTER(c_void_p), ctypes.c_size_t, c_int32, c_int32]),
+    "fs_submit": (c_int32, [P, ctypes.POINTER(fs_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "fs_poll": (c_int32, [P, ctypes.c_uint64, ctypes.POINTER(fs_step_info)]),
+    "fs_server_wait": (c_int32, [P, ctypes.c_uint64, ctypes.POINTER(fs_step_info), c_double]),
+    "fs_server_stats": (c_int32, [P, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32),
+                                  ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(c_int64)]),
+    "fs_server_destroy": (None, [P]),
     "fs_last_error": (ctypes.c_char_p, []),
     "fs_status_str": (ctypes.c_char_p, [c_int32]),
 }

@@ -140,6 +140,7 @@ struct fs_ctx {
     fs::Scratch scratch;          // far-field scratch (grown on demand)
     fs::Profiler prof;            // CUDA-event records (opt.profile)
     int64_t pairs_last = 0;
+    size_t dev_bytes = 0;         // device memory allocated by the context (without scratch)
 
     fs::FiberTable table() const;
 };
@@ -148,6 +149,7 @@ namespace fs {
 fs_status context_init(fs_ctx *c, int S, const int32_t *fibers_per_system, int M, const int32_t *ppf,
                        const fs_boundary *b);
 void context_free(fs_ctx *c);
+size_t estimate_bytes(int M, const int32_t *ppf, int n_surf, const fs_options &opt);
 
 // fiber.cu
 fs_status launch_geometry(fs_ctx *c);

@@ -716,13 +716,16 @@ __global__ void k_excl_ids(const int32_t *__restrict__ sf, int64_t ns, const int
 
 int num_sms()
 {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
+    // initialised once, thread-safely (contexts may be created from several threads)
+    static const int n = [] {
+        int dev = 0, v = 0;
         cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
-            n = 1;
-    }
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+            cudaGetLastError();
+            v = 1;
+        }
+        return v;
+    }();
     return n;
 }
 

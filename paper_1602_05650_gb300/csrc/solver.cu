@@ -28,7 +28,7 @@ __global__ void k_add(double *__restrict__ x, const double *__restrict__ e, int6
 unsigned blocks_for(int64_t n) { return static_cast<unsigned>((n + 255) / 256); }
 
 template <class T>
-fs_status dalloc(T **p, size_t n)
+fs_status dalloc(fs_ctx *c, T **p, size_t n)
 {
     *p = nullptr;
     if (n == 0) return FS_OK;
@@ -38,6 +38,7 @@ fs_status dalloc(T **p, size_t n)
         set_error("device allocation of %zu bytes failed", n * sizeof(T));
         return FS_ENOMEM;
     }
+    c->dev_bytes += n * sizeof(T);
     return FS_OK;
 }
 
@@ -547,7 +548,7 @@ fs_status context_init(fs_ctx *c, int S, const int32_t *fps, int M, const int32_
     c->sys_outer.assign(c->S, 0);
     c->sys_resid.assign(c->S, 0.0);
     c->sys_conv.assign(c->S, 0);
-    FS_TRY(dalloc(&c->d_status, 1));
+    FS_TRY(dalloc(c, &c->d_status, 1));
     FS_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
     FS_CUDA(cudaMallocHost(&c->h_pinned, 4096 * sizeof(double)));
     if (M == 0) return FS_OK;
@@ -568,103 +569,179 @@ fs_status context_init(fs_ctx *c, int S, const int32_t *fps, int M, const int32_
         for (int64_t i = c->node_ptr[m]; i < c->node_ptr[m + 1]; ++i)
             excl[i] = make_int2(static_cast<int>(c->node_ptr[m]), static_cast<int>(c->node_ptr[m + 1]));
 
-    FS_TRY(dalloc(&c->d_N, M));
-    FS_TRY(dalloc(&c->d_node_ptr, M + 1));
-    FS_TRY(dalloc(&c->d_unk_ptr, M + 1));
-    FS_TRY(dalloc(&c->d_blk_ptr, M + 1));
-    FS_TRY(dalloc(&c->d_kp_ptr, M + 1));
-    FS_TRY(dalloc(&c->d_z_ptr, M + 1));
-    FS_TRY(dalloc(&c->d_ops_off, M));
-    FS_TRY(dalloc(&c->d_ops, ops.size()));
-    FS_TRY(dalloc(&c->d_excl, c->n_tot));
-    FS_CUDA(cudaMemcpy(c->d_N, ppf, M * sizeof(int), cudaMemcpyHostToDevice));
-    FS_CUDA(cudaMemcpy(c->d_node_ptr, c->node_ptr.data(), (M + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
-    FS_CUDA(cudaMemcpy(c->d_unk_ptr, c->unk_ptr.data(), (M + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
-    FS_CUDA(cudaMemcpy(c->d_blk_ptr, c->blk_ptr.data(), (M + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
-    FS_CUDA(cudaMemcpy(c->d_kp_ptr, kp.data(), (M + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
-    FS_CUDA(cudaMemcpy(c->d_z_ptr, zp.data(), (M + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
-    FS_CUDA(cudaMemcpy(c->d_ops_off, off.data(), M * sizeof(int64_t), cudaMemcpyHostToDevice));
-    FS_CUDA(cudaMemcpy(c->d_ops, ops.data(), ops.size() * sizeof(double), cudaMemcpyHostToDevice));
-    FS_CUDA(cudaMemcpy(c->d_excl, excl.data(), c->n_tot * sizeof(int2), cudaMemcpyHostToDevice));
+    FS_TRY(dalloc(c, &c->d_N, M));
+    FS_TRY(dalloc(c, &c->d_node_ptr, M + 1));
+    FS_TRY(dalloc(c, &c->d_unk_ptr, M + 1));
+    FS_TRY(dalloc(c, &c->d_blk_ptr, M + 1));
+    FS_TRY(dalloc(c, &c->d_kp_ptr, M + 1));
+    FS_TRY(dalloc(c, &c->d_z_ptr, M + 1));
+    FS_TRY(dalloc(c, &c->d_ops_off, M));
+    FS_TRY(dalloc(c, &c->d_ops, ops.size()));
+    FS_TRY(dalloc(c, &c->d_excl, c->n_tot));
+    FS_CUDA(cudaMemcpyAsync(c->d_N, ppf, M * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    FS_CUDA(cudaMemcpyAsync(c->d_node_ptr, c->node_ptr.data(), (M + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+    FS_CUDA(cudaMemcpyAsync(c->d_unk_ptr, c->unk_ptr.data(), (M + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+    FS_CUDA(cudaMemcpyAsync(c->d_blk_ptr, c->blk_ptr.data(), (M + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+    FS_CUDA(cudaMemcpyAsync(c->d_kp_ptr, kp.data(), (M + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+    FS_CUDA(cudaMemcpyAsync(c->d_z_ptr, zp.data(), (M + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+    FS_CUDA(cudaMemcpyAsync(c->d_ops_off, off.data(), M * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+    FS_CUDA(cudaMemcpyAsync(c->d_ops, ops.data(), ops.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    FS_CUDA(cudaMemcpyAsync(c->d_excl, excl.data(), c->n_tot * sizeof(int2), cudaMemcpyHostToDevice, c->stream));
 
     const int64_t P = c->n_tot;
-    FS_TRY(dalloc(&c->d_X, 3 * P));
-    FS_TRY(dalloc(&c->d_L, M));
-    FS_TRY(dalloc(&c->d_fext, 3 * P));
-    FS_TRY(dalloc(&c->d_t, 3 * P));
-    FS_TRY(dalloc(&c->d_tz, 3 * c->n_z));
-    FS_TRY(dalloc(&c->d_fknown, 3 * P));
-    FS_TRY(dalloc(&c->d_W, P));
-    FS_TRY(dalloc(&c->d_mloc, 2 * P));
-    FS_TRY(dalloc(&c->d_bc, 12 * M));
-    FS_TRY(dalloc(&c->d_kp, 4 * c->n_kp));
-    FS_TRY(dalloc(&c->d_B, c->n_blk));
-    FS_TRY(dalloc(&c->d_piv, c->n_fib_unk));
-    FS_TRY(dalloc(&c->d_V, 3 * P));
-    FS_TRY(dalloc(&c->d_T, P));
-    FS_TRY(dalloc(&c->d_f, 3 * P));
-    FS_TRY(dalloc(&c->d_wf, 3 * P));
-    FS_TRY(dalloc(&c->d_ubar, 3 * P));
-    FS_CUDA(cudaMemset(c->d_kp, 0, 4 * c->n_kp * sizeof(double)));
-    FS_CUDA(cudaMemset(c->d_V, 0, 3 * P * sizeof(double)));
-    FS_CUDA(cudaMemset(c->d_T, 0, P * sizeof(double)));
+    FS_TRY(dalloc(c, &c->d_X, 3 * P));
+    FS_TRY(dalloc(c, &c->d_L, M));
+    FS_TRY(dalloc(c, &c->d_fext, 3 * P));
+    FS_TRY(dalloc(c, &c->d_t, 3 * P));
+    FS_TRY(dalloc(c, &c->d_tz, 3 * c->n_z));
+    FS_TRY(dalloc(c, &c->d_fknown, 3 * P));
+    FS_TRY(dalloc(c, &c->d_W, P));
+    FS_TRY(dalloc(c, &c->d_mloc, 2 * P));
+    FS_TRY(dalloc(c, &c->d_bc, 12 * M));
+    FS_TRY(dalloc(c, &c->d_kp, 4 * c->n_kp));
+    FS_TRY(dalloc(c, &c->d_B, c->n_blk));
+    FS_TRY(dalloc(c, &c->d_piv, c->n_fib_unk));
+    FS_TRY(dalloc(c, &c->d_V, 3 * P));
+    FS_TRY(dalloc(c, &c->d_T, P));
+    FS_TRY(dalloc(c, &c->d_f, 3 * P));
+    FS_TRY(dalloc(c, &c->d_wf, 3 * P));
+    FS_TRY(dalloc(c, &c->d_ubar, 3 * P));
+    FS_CUDA(cudaMemsetAsync(c->d_kp, 0, 4 * c->n_kp * sizeof(double), c->stream));
+    FS_CUDA(cudaMemsetAsync(c->d_V, 0, 3 * P * sizeof(double), c->stream));
+    FS_CUDA(cudaMemsetAsync(c->d_T, 0, P * sizeof(double), c->stream));
 
     const int R = std::max(2, std::min(c->opt.restart, 250));   // k_finish_dots uses 256 threads
     c->kdim = R + 1;
     const int64_t n = c->n_unk;
-    FS_TRY(dalloc(&c->d_basis, static_cast<size_t>(c->kdim) * n));
-    FS_TRY(dalloc(&c->d_b, n));
-    FS_TRY(dalloc(&c->d_x, n));
-    FS_TRY(dalloc(&c->d_r, n));
-    FS_TRY(dalloc(&c->d_w, n));
-    FS_TRY(dalloc(&c->d_e, n));
-    FS_TRY(dalloc(&c->d_pb, n));
+    FS_TRY(dalloc(c, &c->d_basis, static_cast<size_t>(c->kdim) * n));
+    FS_TRY(dalloc(c, &c->d_b, n));
+    FS_TRY(dalloc(c, &c->d_x, n));
+    FS_TRY(dalloc(c, &c->d_r, n));
+    FS_TRY(dalloc(c, &c->d_w, n));
+    FS_TRY(dalloc(c, &c->d_e, n));
+    FS_TRY(dalloc(c, &c->d_pb, n));
     c->chunk_cap = n / kChunk + c->S + 2;
     int64_t items = c->S;
     for (int s = 0; s < c->S; ++s) items += (c->sys_node_ptr[s + 1] - c->sys_node_ptr[s] + 127) / 128;
     c->work_cap = items;
-    FS_TRY(dalloc(&c->d_work, static_cast<size_t>(c->work_cap)));
+    FS_TRY(dalloc(c, &c->d_work, static_cast<size_t>(c->work_cap)));
     const size_t SHi = 4 * size_t(c->kdim) + 8;
-    FS_TRY(dalloc(&c->d_h, c->S * SHi));
-    FS_TRY(dalloc(&c->d_part, static_cast<size_t>(c->kdim) * c->chunk_cap));
-    FS_TRY(dalloc(&c->d_ich, static_cast<size_t>(c->chunk_cap)));
-    FS_TRY(dalloc(&c->d_isch, static_cast<size_t>(c->S)));
-    FS_TRY(dalloc(&c->d_ikk, static_cast<size_t>(c->S)));
+    FS_TRY(dalloc(c, &c->d_h, c->S * SHi));
+    FS_TRY(dalloc(c, &c->d_part, static_cast<size_t>(c->kdim) * c->chunk_cap));
+    FS_TRY(dalloc(c, &c->d_ich, static_cast<size_t>(c->chunk_cap)));
+    FS_TRY(dalloc(c, &c->d_isch, static_cast<size_t>(c->S)));
+    FS_TRY(dalloc(c, &c->d_ikk, static_cast<size_t>(c->S)));
     FS_CUDA(cudaFreeHost(c->h_pinned));
     c->h_pinned = nullptr;
     FS_CUDA(cudaMallocHost(&c->h_pinned, c->S * SHi * sizeof(double)));
     if (c->opt.prec == FS_MIXED) {
         c->okdim = 17;   // outer (flexible) restart length 16
         const size_t SHo = 4 * size_t(c->okdim) + 8;
-        FS_TRY(dalloc(&c->d_obasis, static_cast<size_t>(c->okdim) * n));
-        FS_TRY(dalloc(&c->d_oz, static_cast<size_t>(c->okdim - 1) * n));
-        FS_TRY(dalloc(&c->d_oh, c->S * SHo));
-        FS_TRY(dalloc(&c->d_opart, static_cast<size_t>(c->okdim) * c->chunk_cap));
-        FS_TRY(dalloc(&c->d_ow, n));
-        FS_TRY(dalloc(&c->d_or, n));
-        FS_TRY(dalloc(&c->d_och, static_cast<size_t>(c->chunk_cap)));
-        FS_TRY(dalloc(&c->d_osch, static_cast<size_t>(c->S)));
-        FS_TRY(dalloc(&c->d_okk, static_cast<size_t>(c->S)));
+        FS_TRY(dalloc(c, &c->d_obasis, static_cast<size_t>(c->okdim) * n));
+        FS_TRY(dalloc(c, &c->d_oz, static_cast<size_t>(c->okdim - 1) * n));
+        FS_TRY(dalloc(c, &c->d_oh, c->S * SHo));
+        FS_TRY(dalloc(c, &c->d_opart, static_cast<size_t>(c->okdim) * c->chunk_cap));
+        FS_TRY(dalloc(c, &c->d_ow, n));
+        FS_TRY(dalloc(c, &c->d_or, n));
+        FS_TRY(dalloc(c, &c->d_och, static_cast<size_t>(c->chunk_cap)));
+        FS_TRY(dalloc(c, &c->d_osch, static_cast<size_t>(c->S)));
+        FS_TRY(dalloc(c, &c->d_okk, static_cast<size_t>(c->S)));
         FS_CUDA(cudaMallocHost(&c->oh_pinned, c->S * SHo * sizeof(double)));
     }
     if (c->surf.n) {
         const int ns = c->surf.n;
-        FS_TRY(dalloc(&c->surf.y, 3 * ns));
-        FS_TRY(dalloc(&c->surf.nrm, 3 * ns));
-        FS_TRY(dalloc(&c->surf.w, ns));
-        FS_TRY(dalloc(&c->surf.diag, 3 * ns));
-        FS_TRY(dalloc(&c->d_usurf, 3 * ns));
-        FS_TRY(dalloc(&c->surf.A, 9 * ns));
-        FS_TRY(dalloc(&c->surf.tmp, 3 * ns));
-        FS_TRY(dalloc(&c->surf.flux, 1));
-        FS_TRY(dalloc(&c->surf.excl, ns));
-        FS_CUDA(cudaMemcpy(c->surf.y, bd->nodes, 3 * ns * sizeof(double), cudaMemcpyHostToDevice));
-        FS_CUDA(cudaMemcpy(c->surf.nrm, bd->normals, 3 * ns * sizeof(double), cudaMemcpyHostToDevice));
-        FS_CUDA(cudaMemcpy(c->surf.w, bd->weights, ns * sizeof(double), cudaMemcpyHostToDevice));
+        FS_TRY(dalloc(c, &c->surf.y, 3 * ns));
+        FS_TRY(dalloc(c, &c->surf.nrm, 3 * ns));
+        FS_TRY(dalloc(c, &c->surf.w, ns));
+        FS_TRY(dalloc(c, &c->surf.diag, 3 * ns));
+        FS_TRY(dalloc(c, &c->d_usurf, 3 * ns));
+        FS_TRY(dalloc(c, &c->surf.A, 9 * ns));
+        FS_TRY(dalloc(c, &c->surf.tmp, 3 * ns));
+        FS_TRY(dalloc(c, &c->surf.flux, 1));
+        FS_TRY(dalloc(c, &c->surf.excl, ns));
+        FS_CUDA(cudaMemcpyAsync(c->surf.y, bd->nodes, 3 * ns * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        FS_CUDA(cudaMemcpyAsync(c->surf.nrm, bd->normals, 3 * ns * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        FS_CUDA(cudaMemcpyAsync(c->surf.w, bd->weights, ns * sizeof(double), cudaMemcpyHostToDevice, c->stream));
         FS_TRY(surface_diag(c));
     }
-    FS_CUDA(cudaDeviceSynchronize());
+    // host staging vectors above go out of scope here; the context's stream
+    // may be a non-blocking one that other contexts share the device with
+    FS_CUDA(cudaStreamSynchronize(c->stream));
     return FS_OK;
+}
+
+// Device bytes context_init allocates for this problem, plus the largest
+// direct-sum scratch a step reserves.  Each allocation is rounded up to the
+// allocator's 512-byte granule; the result bounds what fs_device_bytes reports.
+size_t estimate_bytes(int M, const int32_t *ppf, int n_surf, const fs_options &opt)
+{
+    size_t total = 0;
+    auto add = [&](size_t bytes) { total += (bytes + 511) & ~size_t(511); };
+    add(sizeof(int));   // status word
+    if (M == 0) return total;
+    int64_t P = 0, n_fib_unk = 0, n_blk = 0, n_kp = 0, n_z = 0, ops = 0;
+    std::map<int, int> seen;
+    for (int m = 0; m < M; ++m) {
+        const int64_t N = ppf[m];
+        P += N;
+        n_fib_unk += 4 * N;
+        n_blk += 16 * N * N;
+        n_kp += N * N;
+        n_z += N - 2;
+        if (!seen.count(ppf[m])) {
+            seen[ppf[m]] = 1;
+            ops += OpsLayout(ppf[m]).total;
+        }
+    }
+    const size_t d = sizeof(double);
+    add(M * sizeof(int));
+    for (int i = 0; i < 5; ++i) add((M + 1) * sizeof(int64_t));
+    add(M * sizeof(int64_t));
+    add(ops * d);
+    add(P * sizeof(int2));
+    for (int64_t k : {3 * P, int64_t(M), 3 * P, 3 * P, 3 * n_z, 3 * P, P, 2 * P, 12 * int64_t(M), 4 * n_kp, n_blk})
+        add(k * d);
+    add(n_fib_unk * sizeof(int));
+    for (int64_t k : {3 * P, P, 3 * P, 3 * P, 3 * P}) add(k * d);
+    const int64_t n = n_fib_unk + 3 * int64_t(n_surf);
+    const int R = std::max(2, std::min(opt.restart, 250));
+    const int64_t kdim = R + 1;
+    add(kdim * n * d);
+    for (int i = 0; i < 6; ++i) add(n * d);
+    const int64_t chunk_cap = n / kChunk + 1 + 2;
+    add(((P + 127) / 128 + 1) * sizeof(int4));
+    add((4 * kdim + 8) * d);
+    add(kdim * chunk_cap * d);
+    add(chunk_cap * sizeof(int4));
+    add(sizeof(int4));
+    add(sizeof(int));
+    if (opt.prec == FS_MIXED) {
+        const int64_t ok = 17;
+        add(ok * n * d);
+        add((ok - 1) * n * d);
+        add((4 * ok + 8) * d);
+        add(ok * chunk_cap * d);
+        add(n * d);
+        add(n * d);
+        add(chunk_cap * sizeof(int4));
+        add(sizeof(int4));
+        add(sizeof(int));
+    }
+    if (n_surf) {
+        const int64_t ns = n_surf;
+        for (int64_t k : {3 * ns, 3 * ns, ns, 3 * ns, 3 * ns, 9 * ns, 3 * ns, int64_t(1)}) add(k * d);
+        add(ns * sizeof(int2));
+    }
+    // the scratch grows to 5/4 of the largest sum it has served
+    size_t sc = 0;
+    const int64_t sizes[4][2] = {{P, P}, {n_surf, P}, {P, n_surf}, {n_surf, n_surf}};
+    for (int kind : {int(PAIR_STOKESLET), int(PAIR_STRESSLET)})
+        for (int prec : {int(FS_SUM_FP64), int(FS_SUM_FP32), int(FS_SUM_FF)})
+            for (auto &sz : sizes)
+                if (sz[0] > 0 && sz[1] > 0)
+                    sc = std::max(sc, pairsum_scratch_bytes(kind, sz[0], sz[1], prec, opt.tile_override));
+    total += sc + sc / 4 + 512;
+    return total;
 }
 
 void context_free(fs_ctx *c)
@@ -856,6 +933,27 @@ fs_status fs_step(fs_ctx *c, fs_step_info *info)
         tms[3] = tms[4] - tms[0] - tms[1] - tms[2];
         std::memcpy(info->t_ms, tms, sizeof(tms));
     }
+    return FS_OK;
+}
+
+size_t fs_estimate_bytes(int32_t n_fibers, const int32_t *points_per_fiber, int32_t n_surface_nodes,
+                         const fs_options *options)
+{
+    if (n_fibers < 0 || (n_fibers > 0 && !points_per_fiber) || n_surface_nodes < 0) return 0;
+    for (int m = 0; m < n_fibers; ++m)
+        if (points_per_fiber[m] < 6 || points_per_fiber[m] > 256) return 0;
+    fs_options o;
+    if (options) o = *options; else fs_options_default(&o);
+    return estimate_bytes(n_fibers, points_per_fiber, n_surface_nodes, o);
+}
+
+fs_status fs_device_bytes(const fs_ctx *c, size_t *bytes)
+{
+    if (!c || !bytes) {
+        set_error("fs_device_bytes: NULL argument");
+        return FS_EINVAL;
+    }
+    *bytes = c->dev_bytes + c->scratch.bytes;
     return FS_OK;
 }
 

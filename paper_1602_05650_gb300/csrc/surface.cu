@@ -109,10 +109,11 @@ fs_status surface_diag(fs_ctx *c)
     if (!n) return FS_OK;
     std::vector<int2> ex(n);
     for (int i = 0; i < n; ++i) ex[i] = make_int2(i, i + 1);
-    FS_CUDA(cudaMemcpy(c->surf.excl, ex.data(), n * sizeof(int2), cudaMemcpyHostToDevice));
+    FS_CUDA(cudaMemcpyAsync(c->surf.excl, ex.data(), n * sizeof(int2), cudaMemcpyHostToDevice, c->stream));
     k_surface_geom<<<(n + 127) / 128, 128, 0, c->stream>>>(c->surf.y, c->surf.nrm, c->surf.w, n,
                                                             c->surf.A, c->surf.diag);
     FS_LAUNCH_CHECK();
+    FS_CUDA(cudaStreamSynchronize(c->stream));   // `ex` is a host staging vector
     return FS_OK;
 }
 

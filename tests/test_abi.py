@@ -14,7 +14,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_symbols():
     text = open(os.path.join(ROOT, "include", "fibersolve.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:fs_status|void|uint64_t|const char \*)\s*\*?\s*(fs_\w+)\s*\(", text, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:fs_status|void|uint64_t|size_t|const char \*)\s*\*?\s*(fs_\w+)\s*\(", text, flags=re.M)))
 
 
 @pytest.fixture(scope="module")

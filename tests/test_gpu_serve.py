@@ -1,0 +1,136 @@
+"""Serving front end (fs_server_create / fs_submit / fs_poll / fs_server_wait):
+requests admitted concurrently by HBM budget give bit-for-bit the result of the
+same step run alone through fs_create / fs_step; the memory estimate bounds
+what a context really holds; over-budget and failing requests report their
+status."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from tests.gpu_helpers import gpu_step, make_ctx, dev
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1602_05650_gb300 as fs  # noqa: E402
+
+
+def requests():
+    out = []
+    for k, (M, N, prec) in enumerate([(3, 16, fs.FS_FP64), (12, 32, fs.FS_MIXED), (1, 24, fs.FS_FP64),
+                                      (20, 16, fs.FS_MIXED), (6, 32, fs.FS_FP64), (40, 24, fs.FS_MIXED)]):
+        s = wl.free_space(M, N, 3.0 + M ** (1 / 3), seed=40 + k, curved_amp=0.05)
+        s.f_ext = np.tile([0.1 * k, -0.2, -1.0], (s.n_points, 1))
+        out.append((s, prec))
+    return out
+
+
+def tol_of(prec):
+    return 1e-12 if prec == fs.FS_FP64 else 1e-10
+
+
+def submit(sv, s, prec):
+    return fs.fs_submit(sv, s.n_per_fiber, s.X, s.L, s.mu, s.eps, s.E, s.dt, f_ext=s.f_ext,
+                        boundary=s.boundary, prec=prec, tol=tol_of(prec))
+
+
+def test_concurrent_requests_equal_alone():
+    reqs = requests()
+    sv = fs.fs_server_create(8 << 30, max_slots=3)
+    tickets = [submit(sv, s, prec) for s, prec in reqs]
+    res = [fs.fs_server_wait(sv, t, timeout_s=300) for t in tickets]
+    assert fs.fs_server_stats(sv)["completed"] == len(reqs)
+    fs.fs_server_destroy(sv)
+    for (s, prec), r in zip(reqs, res):
+        V, T, X, _ = gpu_step(s, torch, prec=prec, tol=tol_of(prec))
+        assert np.array_equal(r["V"], V)
+        assert np.array_equal(r["T"], T)
+        assert np.array_equal(r["X"], X)
+        inf = r["info"]
+        assert inf.iters > 0
+        assert 0.0 <= inf.t_ms[5] <= inf.t_ms[6]
+
+
+def test_confined_request_equals_alone():
+    s = wl.confined(12, 16, R=4.0, R_centres=2.0, n_theta=4, n_phi=8, seed=3)
+    s.f_ext = np.tile([0.0, 0.0, -1.0], (s.n_points, 1))
+    sv = fs.fs_server_create(4 << 30, max_slots=2)
+    r = fs.fs_server_wait(sv, submit(sv, s, fs.FS_FP64), timeout_s=300)
+    fs.fs_server_destroy(sv)
+    V, T, X, _ = gpu_step(s, torch, prec=fs.FS_FP64, tol=1e-12)
+    assert np.array_equal(r["V"], V) and np.array_equal(r["T"], T)
+
+
+def test_budget_admits_one_at_a_time_and_rejects_oversize():
+    reqs = requests()
+    need = [fs.fs_estimate_bytes(s.n_per_fiber, 0, _opts(prec)) for s, prec in reqs]
+    budget = max(need)
+    sv = fs.fs_server_create(budget, max_slots=4)
+    tickets = [submit(sv, s, prec) for s, prec in reqs]
+    seen = []
+    done = {}
+    while len(done) < len(tickets):
+        st = fs.fs_server_stats(sv)
+        assert st["bytes_in_use"] <= budget
+        seen.append(st["running"])
+        for t in tickets:
+            if t not in done:
+                r = fs.fs_poll(sv, t)
+                if r is not None:
+                    done[t] = r
+    assert max(seen) >= 1
+    big = wl.free_space(200, 32, 12.0, seed=9)
+    with pytest.raises(fs.FsError) as e:
+        submit(sv, big, fs.FS_MIXED)
+    assert e.value.status == 7   # FS_EBUSY
+    fs.fs_server_destroy(sv)
+    for (s, prec), t in zip(reqs, tickets):
+        V, _, _, _ = gpu_step(s, torch, prec=prec, tol=tol_of(prec))
+        assert np.array_equal(done[t]["V"], V)
+
+
+def test_poll_before_done_and_failed_request():
+    s_big = wl.free_space(256, 32, 14.0, seed=5)
+    s_bad = wl.free_space(2, 16, 3.0, seed=6)
+    s_bad.L = s_bad.L.copy()
+    s_bad.L[1] = -1.0            # rejected by fs_set_state inside the worker
+    sv = fs.fs_server_create(8 << 30, max_slots=1)
+    t1 = submit(sv, s_big, fs.FS_MIXED)
+    t2 = submit(sv, s_bad, fs.FS_FP64)
+    assert fs.fs_poll(sv, t2) is None          # queued behind t1 on the single slot
+    fs.fs_server_wait(sv, t1, timeout_s=300)
+    with pytest.raises(fs.FsError) as e:
+        fs.fs_server_wait(sv, t2, timeout_s=300)
+    assert e.value.status == 1                 # FS_EINVAL
+    assert "length" in str(e.value)
+    with pytest.raises(fs.FsError):
+        fs.fs_poll(sv, t2)                     # the ticket was released
+    fs.fs_server_destroy(sv)
+
+
+def _opts(prec, restart=60):
+    o = fs.fs_options_default()
+    o.prec = prec
+    o.restart = restart
+    return o
+
+
+@pytest.mark.parametrize("case", ["fp64", "mixed", "ragged", "confined"])
+def test_estimate_bounds_device_bytes(case):
+    if case == "confined":
+        s = wl.confined(12, 16, R=4.0, R_centres=2.0, n_theta=4, n_phi=8, seed=4)
+    elif case == "ragged":
+        s = wl.free_space(10, [16, 24, 32, 16, 64, 8, 24, 32, 16, 48], 5.0, seed=8)
+    else:
+        s = wl.free_space(64, 32, 10.0, seed=8, curved_amp=0.05)
+    s.f_ext = np.tile([0.0, 0.0, -1.0], (s.n_points, 1))
+    prec = fs.FS_MIXED if case in ("mixed", "ragged") else fs.FS_FP64
+    h = make_ctx(s, prec=prec, tol=1e-10)
+    fs.fs_set_state(h, dev(s.X, torch), dev(s.L, torch), dev(s.f_ext, torch))
+    fs.fs_step(h)
+    used = fs.fs_device_bytes(h)
+    fs.fs_destroy(h)
+    ns = 0 if s.boundary is None else s.boundary.nodes.shape[0]
+    est = fs.fs_estimate_bytes(s.n_per_fiber, ns, _opts(prec))
+    assert used <= est
+    assert est <= 2 * used + (1 << 20)

@@ -118,13 +118,13 @@ def test_mixed_refined_matches_oracle():
 
 def test_mixed_point_forces_cloud_shape():
     """Curved fibers, 64 points, N(0,1) point forces: the mixed path to 1e-10
-    against the oracle at 1e-12, gated like the FP64 N = 64 case (the oracle's
-    own GMRES-vs-dense spread at N = 64 is 4.1e-8)."""
+    against the oracle at 1e-12.  For this very system the oracle's own GMRES
+    (tol 1e-10 and 1e-12) and dense solutions differ by 2.68e-6 in V: gate 5e-6."""
     s = wl.free_space(48, 64, 12.0, seed=5, curved_amp=0.05)
     ref = oracle_step(s)
     V, T, _, infos = gpu_step(s, torch, prec=fs.FS_MIXED, tol=1e-10)
     assert infos[0].resid <= 1e-10
-    assert rel(V, ref.V) <= 2e-7
+    assert rel(V, ref.V) <= 5e-6
 
 
 def test_confined_small():

@@ -1,0 +1,70 @@
+"""Host-side logic of the serving front end and of the device-memory estimate
+(no GPU: fs_estimate_bytes makes no CUDA call; server entry points validate
+their arguments before touching a device)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1602_05650_gb300 import _native, build
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _native.load()
+
+
+def est(lib, ppf, ns=0, prec=_native.FS_MIXED, restart=60):
+    a = np.asarray(ppf, np.int32)
+    o = _native.fs_options()
+    lib.fs_options_default(ctypes.byref(o))
+    o.prec = prec
+    o.restart = restart
+    return lib.fs_estimate_bytes(len(a), a.ctypes.data_as(ctypes.c_void_p), ns, ctypes.byref(o))
+
+
+def test_estimate_grows_with_the_problem(lib):
+    e1 = est(lib, [32] * 100)
+    e2 = est(lib, [32] * 200)
+    assert 0 < e1 < e2
+    # the dense blocks (16 N^2 doubles per fiber) dominate at N = 64
+    e64 = est(lib, [64] * 1024)
+    assert e64 >= 1024 * 16 * 64 * 64 * 8
+    assert e64 < 3 * 1024 * 16 * 64 * 64 * 8
+    # mixed precision keeps the outer flexible-GMRES space on top of the inner one
+    assert est(lib, [32] * 100, prec=_native.FS_MIXED) > est(lib, [32] * 100, prec=_native.FS_FP64)
+    # a longer restart keeps more Krylov vectors
+    assert est(lib, [32] * 100, restart=120) > est(lib, [32] * 100, restart=60)
+    # a boundary adds its nodes' arrays
+    assert est(lib, [32] * 100, ns=4096) > e1
+
+
+def test_estimate_rejects_invalid(lib):
+    assert est(lib, [5]) == 0
+    assert est(lib, [257]) == 0
+    assert lib.fs_estimate_bytes(-1, None, 0, None) == 0
+    assert lib.fs_estimate_bytes(0, None, 0, None) > 0   # an empty context still holds its status word
+
+
+def test_server_argument_checks(lib):
+    out = ctypes.c_void_p()
+    assert lib.fs_server_create(ctypes.byref(out), 0, 1, 0) == _native.FS_EINVAL
+    assert lib.fs_server_create(ctypes.byref(out), 1 << 30, 0, 0) == _native.FS_EINVAL
+    assert lib.fs_server_create(None, 1 << 30, 1, 0) == _native.FS_EINVAL
+    t = ctypes.c_uint64()
+    rq = _native.fs_request()
+    assert lib.fs_submit(None, ctypes.byref(rq), ctypes.byref(t)) == _native.FS_EINVAL
+    assert lib.fs_poll(None, 1, None) == _native.FS_EINVAL
+    assert lib.fs_server_wait(None, 1, None, 0.0) == _native.FS_EINVAL
+    assert lib.fs_server_stats(None, None, None, None, None) == _native.FS_EINVAL
+    lib.fs_server_destroy(None)
+
+
+def test_server_create_without_a_device(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    out = ctypes.c_void_p()
+    assert lib.fs_server_create(ctypes.byref(out), 1 << 30, 2, 0) == _native.FS_ECUDA
+    assert not out.value
