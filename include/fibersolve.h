@@ -79,13 +79,18 @@ typedef struct {
     int32_t restart;        /* GMRES restart length (default 60, at most 250) */
     int32_t max_refine;     /* reserved (default 6) */
     double inner_tol;       /* FS_MIXED: relative tolerance of each inner FP32-far-field
-                               GMRES solve (default 1e-3) */
+                               GMRES solve (default 1e-5) */
     double delta_over_L;    /* regularisation delta of K_delta as a fraction of L (default 0.01) */
     int32_t lsb;            /* 1 = local slender-body theory: drop K_delta (default 0) */
     int32_t use_graph;      /* reserved: capture the inner iteration in a CUDA graph */
     int32_t tile_override;  /* 0 = autotuned far-field launch shape, else a shape id */
     int32_t profile;        /* 1 = bracket every direct-sum kernel with CUDA events on the
                                context's stream (read with fs_kernel_stats) (default 0) */
+    int32_t relax;          /* FS_MIXED: 1 = once the outer residual r satisfies
+                               1e-6 |r| / |P^-1 b| <= tol / 20, evaluate further outer
+                               directions with the FP32 hi/lo far field instead of
+                               float-float (inexact-Krylov relaxation; the residual
+                               they can still add stays below tol / 20) (default 1) */
 } fs_options;
 
 /* Direct-sum kernel classes reported by fs_kernel_stats. */

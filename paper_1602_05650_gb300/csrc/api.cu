@@ -81,12 +81,13 @@ fs_status fs_options_default(fs_options *o)
     o->max_iter = 200;
     o->restart = 60;
     o->max_refine = 6;
-    o->inner_tol = 1e-3;
+    o->inner_tol = 1e-5;
     o->delta_over_L = 0.01;
     o->lsb = 0;
     o->use_graph = 0;
     o->tile_override = 0;
     o->profile = 0;
+    o->relax = 1;
     return FS_OK;
 }
 

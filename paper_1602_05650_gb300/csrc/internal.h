@@ -69,13 +69,19 @@ struct Carve {
 // ---------------------------------------------------------------- direct sums
 enum : int { PAIR_STOKESLET = 0, PAIR_STRESSLET = 1 };
 
-// Launch plan of the tiled direct sums.
+// Launch plan of the tiled direct sums: nb target blocks of tb = tpt x
+// threads targets, nt source tiles, W = nb x nt block-tile pairs shared out
+// to `grid` CTAs (one wave) in equal contiguous runs.
 struct SumPlan {
     int tpt;          // targets per thread
-    int splits;       // source splits (CTAs along y)
-    int64_t per_split;
     int tile;         // sources per shared-memory stage
     int threads;      // threads per CTA
+    int tb;           // targets per block
+    int n_arr;        // packed per-source arrays
+    size_t v4;        // bytes per packed array element
+    size_t smem;      // dynamic shared memory per CTA
+    int64_t nb, nt, W;
+    int grid;
 };
 
 // CUDA-event records of direct-sum kernel launches (opt.profile).
@@ -116,9 +122,12 @@ struct PairSumArgs {
     double pairs = 0.0;                // pairs evaluated (for the profiler)
 };
 
-SumPlan plan_pairsum(int64_t n_src, int64_t n_tgt, int sum_prec, int shape_override);
-size_t pairsum_scratch_bytes(int kind, int64_t n_src, int64_t n_tgt, int sum_prec,
-                             int shape_override);
+// slots > 0: CTAs one wave may hold (an upper bound will do); 0: ask the
+// current device (SMs x resident CTAs of the chosen kernel).
+SumPlan plan_pairsum(int kind, int64_t n_src, int64_t n_tgt, int sum_prec, bool hilo, int shape_override,
+                     int slots);
+size_t pairsum_scratch_bytes(int kind, int64_t n_src, int64_t n_tgt, int sum_prec, int shape_override,
+                             int slots = 0);
 // Enqueue the sum on `st`; scratch must hold pairsum_scratch_bytes(...) bytes.
 fs_status pairsum(const PairSumArgs &a, void *scratch, size_t scratch_bytes, int *d_status,
                   cudaStream_t st);

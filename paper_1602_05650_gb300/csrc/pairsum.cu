@@ -24,6 +24,9 @@
 #include <algorithm>
 #include <climits>
 #include <cstdio>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "internal.h"
 
@@ -42,6 +45,64 @@ template <int KIND, bool HILO>
 struct Arr {
     static constexpr int base = KIND == PAIR_STRESSLET ? 3 : 2;
     static constexpr int n = base + (HILO ? 1 : 0);
+};
+
+// A CTA's share of a sum.  Default (stream-K) mode: a contiguous run of tiles
+// g in [g0, g0 + n_run) of the flattened (target block, source tile) space,
+// g = block * nt + tile, with g0 = c W / G for CTA c of G: every CTA of the
+// single wave gets the same number of tiles to within one, whatever the
+// problem's shape.  A run crosses target blocks; each block it touches is a
+// "piece" whose partial sums go to slot (c + block) of the partial array.
+// Work-list mode (batched systems): one item = one target block against its
+// system's source range, written directly.
+struct Run {
+    int64_t g0 = 0, n_run = 0, nt = 0, n_src = 0;
+    int4 wi = make_int4(0, 0, 0, 0);
+    bool work = false;
+    int tile = 0, tb = 0;
+
+    __device__ Run(const int4 *work_list, int64_t nt_, int64_t W, int G, int64_t n_src_, int tile_, int tb_)
+        : nt(nt_), n_src(n_src_), work(work_list != nullptr), tile(tile_), tb(tb_)
+    {
+        if (work) {
+            wi = work_list[blockIdx.x];
+            n_run = wi.w > wi.z ? (static_cast<int64_t>(wi.w) - wi.z + tile - 1) / tile : 0;
+        } else {
+            const int64_t c = blockIdx.x;
+            g0 = c * W / G;
+            n_run = (c + 1) * W / G - g0;
+        }
+    }
+    // sources of tile `it` of the run: [j0, j0 + cnt)
+    __device__ void src(int64_t it, int64_t &j0, int &cnt) const
+    {
+        int64_t end;
+        if (work) {
+            j0 = wi.z + it * tile;
+            end = wi.w;
+        } else {
+            j0 = ((g0 + it) % nt) * tile;
+            end = n_src;
+        }
+        cnt = static_cast<int>(min(static_cast<int64_t>(tile), end - j0));
+    }
+    // the piece starting at tile `it`: targets [tbase, t_end), length in tiles, target block
+    __device__ void piece(int64_t it, int64_t n_tgt, int64_t &tbase, int64_t &t_end, int64_t &len,
+                          int64_t &blk) const
+    {
+        if (work) {
+            tbase = wi.x;
+            t_end = static_cast<int64_t>(wi.x) + wi.y;
+            len = n_run;
+            blk = 0;
+        } else {
+            const int64_t g = g0 + it;
+            blk = g / nt;
+            len = min(nt - (g - blk * nt), n_run - it);
+            tbase = blk * tb;
+            t_end = n_tgt;
+        }
+    }
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -170,167 +231,166 @@ __device__ __forceinline__ void tile_sum(const typename Vec4Of<R>::type *__restr
     }
 }
 
-// out (direct): out[i] = (acc ? out[i] : 0) + scale * sum;  else partial[split][i] = sum
+// Work-list mode: out[i] = (acc ? out[i] : 0) + scale * sum.  Stream-K mode:
+// part[(c + block) * TB + local][3] = this CTA's partial sum (reduced by
+// k_reduce_streamk).
 template <class R, int T, int KIND, bool HILO>
 __global__ void __launch_bounds__(kThreads)
-    k_pairsum(const typename Vec4Of<R>::type *__restrict__ src, int64_t n_src, int64_t per_split,
+    k_pairsum(const typename Vec4Of<R>::type *__restrict__ src, int64_t n_src, int64_t nt, int64_t W, int G,
               const double *__restrict__ tgt, const int2 *__restrict__ excl, int64_t n_tgt,
-              const double *__restrict__ center, double *__restrict__ out, double scale, int direct,
-              int acc, int *__restrict__ status, const int4 *__restrict__ work)
+              const double *__restrict__ center, double *__restrict__ out, double *__restrict__ part,
+              double scale, int acc, int *__restrict__ status, const int4 *__restrict__ work)
 {
     using V4 = typename Vec4Of<R>::type;
     using A = Arr<KIND, HILO>;
     constexpr int TILE = sizeof(R) == 4 ? kTile32 : kTile64;
+    constexpr int TB = T * kThreads;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     V4 *smem = reinterpret_cast<V4 *>(smem_raw);   // [stage][array][TILE]
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ int s_lo, s_hi;
 
     const int tid = threadIdx.x;
-    // work item (batched systems): targets [x, x + y), sources [z, w)
-    int64_t tbase, t_end, j_begin, j_end;
-    if (work) {
-        const int4 wi = work[blockIdx.x];
-        tbase = wi.x;
-        t_end = static_cast<int64_t>(wi.x) + wi.y;
-        j_begin = wi.z;
-        j_end = wi.w;
-    } else {
-        tbase = static_cast<int64_t>(blockIdx.x) * (T * kThreads);
-        t_end = n_tgt;
-        j_begin = static_cast<int64_t>(blockIdx.y) * per_split;
-        j_end = min(n_src, j_begin + per_split);
-    }
-    const int64_t n_tiles = j_end > j_begin ? (j_end - j_begin + TILE - 1) / TILE : 0;
-
+    const Run run(work, nt, W, G, n_src, TILE, TB);
     if (tid == 0) {
-        s_lo = INT_MAX;
-        s_hi = INT_MIN;
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    const double c0 = center[0], c1 = center[1], c2 = center[2];
-    R tx[T], ty[T], tz[T], lx[T], ly[T], lz[T];
-    int elo[T], ecnt[T];
-    int my_lo = INT_MAX, my_hi = INT_MIN;
-#pragma unroll
-    for (int t = 0; t < T; ++t) {
-        const int64_t i = tbase + tid + static_cast<int64_t>(t) * kThreads;
-        double x = 0.0, y = 0.0, z = 0.0;
-        int2 e = make_int2(0, 0);
-        if (i < t_end) {
-            x = tgt[3 * i + 0] - c0;
-            y = tgt[3 * i + 1] - c1;
-            z = tgt[3 * i + 2] - c2;
-            if (excl) e = excl[i];
-        }
-        tx[t] = static_cast<R>(x);
-        ty[t] = static_cast<R>(y);
-        tz[t] = static_cast<R>(z);
-        lx[t] = static_cast<R>(x - static_cast<double>(tx[t]));
-        ly[t] = static_cast<R>(y - static_cast<double>(ty[t]));
-        lz[t] = static_cast<R>(z - static_cast<double>(tz[t]));
-        elo[t] = e.x;
-        ecnt[t] = e.y > e.x ? e.y - e.x : 0;
-        if (e.y > e.x) {
-            my_lo = min(my_lo, e.x);
-            my_hi = max(my_hi, e.y);
-        }
-    }
     __syncthreads();
-    if (my_hi > my_lo) {
-        atomicMin(&s_lo, my_lo);
-        atomicMax(&s_hi, my_hi);
-    }
     auto stage_ptr = [&](int stage, int arr) -> V4 * { return smem + (stage * A::n + arr) * TILE; };
-    auto issue = [&](int64_t tile, int stage) {
-        const int64_t j0 = j_begin + tile * TILE;
-        const int cnt = static_cast<int>(min(static_cast<int64_t>(TILE), j_end - j0));
+    auto issue = [&](int64_t it) {
+        int64_t j0;
+        int cnt;
+        run.src(it, j0, cnt);
+        const int stage = static_cast<int>(it & 1);
         const uint32_t bytes = static_cast<uint32_t>(cnt) * static_cast<uint32_t>(sizeof(V4));
         mbar_expect_tx(&bars[stage], bytes * A::n);
 #pragma unroll
         for (int a = 0; a < A::n; ++a) bulk_g2s(stage_ptr(stage, a), src + a * n_src + j0, bytes, &bars[stage]);
     };
     if (tid == 0) {
-        if (n_tiles > 0) issue(0, 0);
-        if (n_tiles > 1) issue(1, 1);
+        if (run.n_run > 0) issue(0);
+        if (run.n_run > 1) issue(1);
     }
-    __syncthreads();
-    const int blo = s_lo, bhi = s_hi;
-
-    // FP32: compensated cross-tile sums (s, c); FP64: plain accumulation in s
-    R sx[T], sy[T], sz[T], cx[T], cy[T], cz[T];
-#pragma unroll
-    for (int t = 0; t < T; ++t) sx[t] = sy[t] = sz[t] = cx[t] = cy[t] = cz[t] = R(0);
-
+    const double c0 = center[0], c1 = center[1], c2 = center[2];
     bool failed = false;
-    for (int64_t it = 0; it < n_tiles; ++it) {
-        const int stage = static_cast<int>(it & 1);
-        const bool ok = mbar_wait(&bars[stage], static_cast<uint32_t>((it >> 1) & 1));
-        if (!__syncthreads_and(ok)) {
-            failed = true;
-            break;
+    int64_t it = 0;
+    do {
+        int64_t tbase, t_end, len, blk;
+        run.piece(it, n_tgt, tbase, t_end, len, blk);
+        // this piece's targets in registers, and the block's exclusion bounds
+        if (tid == 0) {
+            s_lo = INT_MAX;
+            s_hi = INT_MIN;
         }
-        // every thread has finished tile it-1, so its stage can be refilled
-        if (tid == 0 && it >= 1 && it + 1 < n_tiles) issue(it + 1, static_cast<int>((it + 1) & 1));
-        const int64_t j0 = j_begin + it * TILE;
-        const int cnt = static_cast<int>(min(static_cast<int64_t>(TILE), j_end - j0));
-        const bool masked = bhi > blo && j0 < bhi && j0 + cnt > blo;
-        const V4 *p0 = stage_ptr(stage, 0), *p1 = stage_ptr(stage, 1);
-        const V4 *pn = stage_ptr(stage, KIND == PAIR_STRESSLET ? 2 : 1);
-        const V4 *pl = stage_ptr(stage, A::base < A::n ? A::base : 0);
-        if constexpr (sizeof(R) == 4) {
-            R ax[T], ay[T], az[T];
+        R tx[T], ty[T], tz[T], lx[T], ly[T], lz[T];
+        int elo[T], ecnt[T];
+        int my_lo = INT_MAX, my_hi = INT_MIN;
 #pragma unroll
-            for (int t = 0; t < T; ++t) ax[t] = ay[t] = az[t] = R(0);
-            if (masked)
-                tile_sum<R, T, KIND, HILO, true>(p0, p1, pn, pl, cnt, static_cast<int>(j0), tx, ty, tz,
-                                                 lx, ly, lz, elo, ecnt, ax, ay, az);
-            else
-                tile_sum<R, T, KIND, HILO, false>(p0, p1, pn, pl, cnt, static_cast<int>(j0), tx, ty, tz,
-                                                  lx, ly, lz, elo, ecnt, ax, ay, az);
-#pragma unroll
-            for (int t = 0; t < T; ++t) {
-                two_sum(sx[t], cx[t], ax[t]);
-                two_sum(sy[t], cy[t], ay[t]);
-                two_sum(sz[t], cz[t], az[t]);
+        for (int t = 0; t < T; ++t) {
+            const int64_t i = tbase + tid + static_cast<int64_t>(t) * kThreads;
+            double x = 0.0, y = 0.0, z = 0.0;
+            int2 e = make_int2(0, 0);
+            if (i < t_end) {
+                x = tgt[3 * i + 0] - c0;
+                y = tgt[3 * i + 1] - c1;
+                z = tgt[3 * i + 2] - c2;
+                if (excl) e = excl[i];
             }
-        } else {
-            if (masked)
-                tile_sum<R, T, KIND, false, true>(p0, p1, pn, pl, cnt, static_cast<int>(j0), tx, ty, tz,
-                                                  lx, ly, lz, elo, ecnt, sx, sy, sz);
-            else
-                tile_sum<R, T, KIND, false, false>(p0, p1, pn, pl, cnt, static_cast<int>(j0), tx, ty, tz,
-                                                   lx, ly, lz, elo, ecnt, sx, sy, sz);
+            tx[t] = static_cast<R>(x);
+            ty[t] = static_cast<R>(y);
+            tz[t] = static_cast<R>(z);
+            lx[t] = static_cast<R>(x - static_cast<double>(tx[t]));
+            ly[t] = static_cast<R>(y - static_cast<double>(ty[t]));
+            lz[t] = static_cast<R>(z - static_cast<double>(tz[t]));
+            elo[t] = e.x;
+            ecnt[t] = e.y > e.x ? e.y - e.x : 0;
+            if (e.y > e.x) {
+                my_lo = min(my_lo, e.x);
+                my_hi = max(my_hi, e.y);
+            }
         }
-    }
+        __syncthreads();
+        if (my_hi > my_lo) {
+            atomicMin(&s_lo, my_lo);
+            atomicMax(&s_hi, my_hi);
+        }
+        __syncthreads();
+        const int blo = s_lo, bhi = s_hi;
+
+        // FP32: compensated cross-tile sums (s, c); FP64: plain accumulation in s
+        R sx[T], sy[T], sz[T], cx[T], cy[T], cz[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) sx[t] = sy[t] = sz[t] = cx[t] = cy[t] = cz[t] = R(0);
+        for (int64_t q = 0; q < len; ++q, ++it) {
+            const int stage = static_cast<int>(it & 1);
+            const bool ok = mbar_wait(&bars[stage], static_cast<uint32_t>((it >> 1) & 1));
+            if (!__syncthreads_and(ok)) {
+                failed = true;
+                break;
+            }
+            // every thread has finished tile it-1, so its stage can be refilled
+            if (tid == 0 && it >= 1 && it + 1 < run.n_run) issue(it + 1);
+            int64_t j0;
+            int cnt;
+            run.src(it, j0, cnt);
+            const bool masked = bhi > blo && j0 < bhi && j0 + cnt > blo;
+            const V4 *p0 = stage_ptr(stage, 0), *p1 = stage_ptr(stage, 1);
+            const V4 *pn = stage_ptr(stage, KIND == PAIR_STRESSLET ? 2 : 1);
+            const V4 *pl = stage_ptr(stage, A::base < A::n ? A::base : 0);
+            if constexpr (sizeof(R) == 4) {
+                R ax[T], ay[T], az[T];
+#pragma unroll
+                for (int t = 0; t < T; ++t) ax[t] = ay[t] = az[t] = R(0);
+                if (masked)
+                    tile_sum<R, T, KIND, HILO, true>(p0, p1, pn, pl, cnt, static_cast<int>(j0), tx, ty, tz,
+                                                     lx, ly, lz, elo, ecnt, ax, ay, az);
+                else
+                    tile_sum<R, T, KIND, HILO, false>(p0, p1, pn, pl, cnt, static_cast<int>(j0), tx, ty, tz,
+                                                      lx, ly, lz, elo, ecnt, ax, ay, az);
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
+                    two_sum(sx[t], cx[t], ax[t]);
+                    two_sum(sy[t], cy[t], ay[t]);
+                    two_sum(sz[t], cz[t], az[t]);
+                }
+            } else {
+                if (masked)
+                    tile_sum<R, T, KIND, false, true>(p0, p1, pn, pl, cnt, static_cast<int>(j0), tx, ty, tz,
+                                                      lx, ly, lz, elo, ecnt, sx, sy, sz);
+                else
+                    tile_sum<R, T, KIND, false, false>(p0, p1, pn, pl, cnt, static_cast<int>(j0), tx, ty, tz,
+                                                       lx, ly, lz, elo, ecnt, sx, sy, sz);
+            }
+        }
+        if (failed) break;
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int64_t i = tbase + tid + static_cast<int64_t>(t) * kThreads;
+            if (i >= t_end) continue;
+            const double ux = static_cast<double>(sx[t]) + static_cast<double>(cx[t]);
+            const double uy = static_cast<double>(sy[t]) + static_cast<double>(cy[t]);
+            const double uz = static_cast<double>(sz[t]) + static_cast<double>(cz[t]);
+            if (work) {
+                double *o = out + 3 * i;
+                o[0] = (acc ? o[0] : 0.0) + scale * ux;
+                o[1] = (acc ? o[1] : 0.0) + scale * uy;
+                o[2] = (acc ? o[2] : 0.0) + scale * uz;
+            } else {
+                double *o = part + ((static_cast<int64_t>(blockIdx.x) + blk) * TB + tid + t * kThreads) * 3;
+                o[0] = ux;
+                o[1] = uy;
+                o[2] = uz;
+            }
+        }
+    } while (it < run.n_run);
     if (failed) {
         if (tid == 0) {
             atomicOr(status, DEV_ERR_TIMEOUT);
             // let copies already in flight land before the CTA exits (bounded)
             mbar_wait(&bars[0], 0);
             mbar_wait(&bars[1], 0);
-        }
-        return;
-    }
-#pragma unroll
-    for (int t = 0; t < T; ++t) {
-        const int64_t i = tbase + tid + static_cast<int64_t>(t) * kThreads;
-        if (i >= t_end) continue;
-        const double ux = static_cast<double>(sx[t]) + static_cast<double>(cx[t]);
-        const double uy = static_cast<double>(sy[t]) + static_cast<double>(cy[t]);
-        const double uz = static_cast<double>(sz[t]) + static_cast<double>(cz[t]);
-        if (direct) {
-            double *o = out + 3 * i;
-            o[0] = (acc ? o[0] : 0.0) + scale * ux;
-            o[1] = (acc ? o[1] : 0.0) + scale * uy;
-            o[2] = (acc ? o[2] : 0.0) + scale * uz;
-        } else {
-            double *o = out + (static_cast<int64_t>(blockIdx.y) * n_tgt + i) * 3;
-            o[0] = ux;
-            o[1] = uy;
-            o[2] = uz;
         }
     }
 }
@@ -465,127 +525,124 @@ __device__ __forceinline__ void tile_ff(const float4 *__restrict__ sph, const fl
 
 template <int T>
 __global__ void __launch_bounds__(kThreads)
-    k_pairsum_ff(const float4 *__restrict__ src, int64_t n_src, int64_t per_split,
+    k_pairsum_ff(const float4 *__restrict__ src, int64_t n_src, int64_t nt, int64_t W, int G,
                  const double *__restrict__ tgt, const int2 *__restrict__ excl, int64_t n_tgt,
-                 const double *__restrict__ center, double *__restrict__ out, double scale, int direct,
-                 int acc, int *__restrict__ status, const int4 *__restrict__ work)
+                 const double *__restrict__ center, double *__restrict__ out, double *__restrict__ part,
+                 double scale, int acc, int *__restrict__ status, const int4 *__restrict__ work)
 {
-    constexpr int NARR = 4, TILE = kTileFF;
+    constexpr int NARR = 4, TILE = kTileFF, TB = T * kThreads;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float4 *smem = reinterpret_cast<float4 *>(smem_raw);   // [stage][array][TILE]
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ int s_lo, s_hi;
 
     const int tid = threadIdx.x;
-    // work item (batched systems): targets [x, x + y), sources [z, w)
-    int64_t tbase, t_end, j_begin, j_end;
-    if (work) {
-        const int4 wi = work[blockIdx.x];
-        tbase = wi.x;
-        t_end = static_cast<int64_t>(wi.x) + wi.y;
-        j_begin = wi.z;
-        j_end = wi.w;
-    } else {
-        tbase = static_cast<int64_t>(blockIdx.x) * (T * kThreads);
-        t_end = n_tgt;
-        j_begin = static_cast<int64_t>(blockIdx.y) * per_split;
-        j_end = min(n_src, j_begin + per_split);
-    }
-    const int64_t n_tiles = j_end > j_begin ? (j_end - j_begin + TILE - 1) / TILE : 0;
+    const Run run(work, nt, W, G, n_src, TILE, TB);
     if (tid == 0) {
-        s_lo = INT_MAX;
-        s_hi = INT_MIN;
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    const double c[3] = {center[0], center[1], center[2]};
-    float th[T][3], tl[T][3], uh[T][3], ul[T][3];
-    int elo[T], ecnt[T];
-    int my_lo = INT_MAX, my_hi = INT_MIN;
-#pragma unroll
-    for (int t = 0; t < T; ++t) {
-        const int64_t i = tbase + tid + static_cast<int64_t>(t) * kThreads;
-        int2 e = make_int2(0, 0);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const double x = i < t_end ? tgt[3 * i + a] - c[a] : 0.0;
-            th[t][a] = static_cast<float>(x);
-            tl[t][a] = static_cast<float>(x - static_cast<double>(th[t][a]));
-            uh[t][a] = ul[t][a] = 0.0f;
-        }
-        if (i < t_end && excl) e = excl[i];
-        elo[t] = e.x;
-        ecnt[t] = e.y > e.x ? e.y - e.x : 0;
-        if (e.y > e.x) {
-            my_lo = min(my_lo, e.x);
-            my_hi = max(my_hi, e.y);
-        }
-    }
     __syncthreads();
-    if (my_hi > my_lo) {
-        atomicMin(&s_lo, my_lo);
-        atomicMax(&s_hi, my_hi);
-    }
     auto stage_ptr = [&](int stage, int arr) -> float4 * { return smem + (stage * NARR + arr) * TILE; };
-    auto issue = [&](int64_t tile, int stage) {
-        const int64_t j0 = j_begin + tile * TILE;
-        const int cnt = static_cast<int>(min(static_cast<int64_t>(TILE), j_end - j0));
+    auto issue = [&](int64_t it) {
+        int64_t j0;
+        int cnt;
+        run.src(it, j0, cnt);
+        const int stage = static_cast<int>(it & 1);
         const uint32_t bytes = static_cast<uint32_t>(cnt) * 16u;
         mbar_expect_tx(&bars[stage], bytes * NARR);
 #pragma unroll
         for (int a = 0; a < NARR; ++a) bulk_g2s(stage_ptr(stage, a), src + a * n_src + j0, bytes, &bars[stage]);
     };
     if (tid == 0) {
-        if (n_tiles > 0) issue(0, 0);
-        if (n_tiles > 1) issue(1, 1);
+        if (run.n_run > 0) issue(0);
+        if (run.n_run > 1) issue(1);
     }
-    __syncthreads();
-    const int blo = s_lo, bhi = s_hi;
+    const double c[3] = {center[0], center[1], center[2]};
     bool failed = false;
-    for (int64_t it = 0; it < n_tiles; ++it) {
-        const int stage = static_cast<int>(it & 1);
-        const bool ok = mbar_wait(&bars[stage], static_cast<uint32_t>((it >> 1) & 1));
-        if (!__syncthreads_and(ok)) {
-            failed = true;
-            break;
+    int64_t it = 0;
+    do {
+        int64_t tbase, t_end, len, blk;
+        run.piece(it, n_tgt, tbase, t_end, len, blk);
+        if (tid == 0) {
+            s_lo = INT_MAX;
+            s_hi = INT_MIN;
         }
-        if (tid == 0 && it >= 1 && it + 1 < n_tiles) issue(it + 1, static_cast<int>((it + 1) & 1));
-        const int64_t j0 = j_begin + it * TILE;
-        const int cnt = static_cast<int>(min(static_cast<int64_t>(TILE), j_end - j0));
-        const bool masked = bhi > blo && j0 < bhi && j0 + cnt > blo;
-        if (masked)
-            tile_ff<T, true>(stage_ptr(stage, 0), stage_ptr(stage, 1), stage_ptr(stage, 2),
-                             stage_ptr(stage, 3), cnt, static_cast<int>(j0), th, tl, elo, ecnt, uh, ul);
-        else
-            tile_ff<T, false>(stage_ptr(stage, 0), stage_ptr(stage, 1), stage_ptr(stage, 2),
-                              stage_ptr(stage, 3), cnt, static_cast<int>(j0), th, tl, elo, ecnt, uh, ul);
+        float th[T][3], tl[T][3], uh[T][3], ul[T][3];
+        int elo[T], ecnt[T];
+        int my_lo = INT_MAX, my_hi = INT_MIN;
 #pragma unroll
-        for (int t = 0; t < T; ++t)
+        for (int t = 0; t < T; ++t) {
+            const int64_t i = tbase + tid + static_cast<int64_t>(t) * kThreads;
+            int2 e = make_int2(0, 0);
 #pragma unroll
-            for (int a = 0; a < 3; ++a) fts(uh[t][a], ul[t][a], uh[t][a], ul[t][a]);
-    }
+            for (int a = 0; a < 3; ++a) {
+                const double x = i < t_end ? tgt[3 * i + a] - c[a] : 0.0;
+                th[t][a] = static_cast<float>(x);
+                tl[t][a] = static_cast<float>(x - static_cast<double>(th[t][a]));
+                uh[t][a] = ul[t][a] = 0.0f;
+            }
+            if (i < t_end && excl) e = excl[i];
+            elo[t] = e.x;
+            ecnt[t] = e.y > e.x ? e.y - e.x : 0;
+            if (e.y > e.x) {
+                my_lo = min(my_lo, e.x);
+                my_hi = max(my_hi, e.y);
+            }
+        }
+        __syncthreads();
+        if (my_hi > my_lo) {
+            atomicMin(&s_lo, my_lo);
+            atomicMax(&s_hi, my_hi);
+        }
+        __syncthreads();
+        const int blo = s_lo, bhi = s_hi;
+        for (int64_t q = 0; q < len; ++q, ++it) {
+            const int stage = static_cast<int>(it & 1);
+            const bool ok = mbar_wait(&bars[stage], static_cast<uint32_t>((it >> 1) & 1));
+            if (!__syncthreads_and(ok)) {
+                failed = true;
+                break;
+            }
+            if (tid == 0 && it >= 1 && it + 1 < run.n_run) issue(it + 1);
+            int64_t j0;
+            int cnt;
+            run.src(it, j0, cnt);
+            const bool masked = bhi > blo && j0 < bhi && j0 + cnt > blo;
+            if (masked)
+                tile_ff<T, true>(stage_ptr(stage, 0), stage_ptr(stage, 1), stage_ptr(stage, 2),
+                                 stage_ptr(stage, 3), cnt, static_cast<int>(j0), th, tl, elo, ecnt, uh, ul);
+            else
+                tile_ff<T, false>(stage_ptr(stage, 0), stage_ptr(stage, 1), stage_ptr(stage, 2),
+                                  stage_ptr(stage, 3), cnt, static_cast<int>(j0), th, tl, elo, ecnt, uh, ul);
+#pragma unroll
+            for (int t = 0; t < T; ++t)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) fts(uh[t][a], ul[t][a], uh[t][a], ul[t][a]);
+        }
+        if (failed) break;
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int64_t i = tbase + tid + static_cast<int64_t>(t) * kThreads;
+            if (i >= t_end) continue;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const double v = static_cast<double>(uh[t][a]) + static_cast<double>(ul[t][a]);
+                if (work) {
+                    double *o = out + 3 * i + a;
+                    *o = (acc ? *o : 0.0) + scale * v;
+                } else {
+                    part[((static_cast<int64_t>(blockIdx.x) + blk) * TB + tid + t * kThreads) * 3 + a] = v;
+                }
+            }
+        }
+    } while (it < run.n_run);
     if (failed) {
         if (tid == 0) {
             atomicOr(status, DEV_ERR_TIMEOUT);
             mbar_wait(&bars[0], 0);
             mbar_wait(&bars[1], 0);
-        }
-        return;
-    }
-#pragma unroll
-    for (int t = 0; t < T; ++t) {
-        const int64_t i = tbase + tid + static_cast<int64_t>(t) * kThreads;
-        if (i >= t_end) continue;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const double v = static_cast<double>(uh[t][a]) + static_cast<double>(ul[t][a]);
-            if (direct) {
-                double *o = out + 3 * i + a;
-                *o = (acc ? *o : 0.0) + scale * v;
-            } else {
-                out[(static_cast<int64_t>(blockIdx.y) * n_tgt + i) * 3 + a] = v;
-            }
         }
     }
 }
@@ -683,14 +740,31 @@ __global__ void k_pack(const double *__restrict__ xyz, const double *__restrict_
     }
 }
 
-__global__ void k_reduce_splits(const double *__restrict__ part, int splits, int64_t n3,
-                                double scale, int acc, double *__restrict__ out)
+// Sum of the stream-K partials of target i: the CTAs c_lo..c_hi whose runs
+// cover target block b (the CTAs holding its first and last tile, and all
+// between), in ascending order (deterministic).  CTA c holds tiles
+// [floor(c W / G), floor((c + 1) W / G)); the largest c with floor(c W / G) <= t
+// is ceil((t + 1) G / W) - 1.
+__global__ void k_reduce_streamk(const double *__restrict__ part, int64_t n_tgt, int tb, int64_t nt,
+                                 int64_t W, int G, double scale, int acc, double *__restrict__ out)
 {
     const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-    if (i >= n3) return;
-    double s = 0.0;
-    for (int k = 0; k < splits; ++k) s += part[k * n3 + i];
-    out[i] = (acc ? out[i] : 0.0) + scale * s;
+    if (i >= n_tgt) return;
+    const int64_t b = i / tb, l = i - b * tb;
+    const int64_t t0 = b * nt, t1 = (b + 1) * nt - 1;
+    const int64_t c_lo = ((t0 + 1) * G + W - 1) / W - 1;
+    const int64_t c_hi = ((t1 + 1) * G + W - 1) / W - 1;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int64_t c = c_lo; c <= c_hi; ++c) {
+        const double *q = part + ((c + b) * tb + l) * 3;
+        s0 += q[0];
+        s1 += q[1];
+        s2 += q[2];
+    }
+    double *o = out + 3 * i;
+    o[0] = (acc ? o[0] : 0.0) + scale * s0;
+    o[1] = (acc ? o[1] : 0.0) + scale * s1;
+    o[2] = (acc ? o[2] : 0.0) + scale * s2;
 }
 
 __global__ void k_excl_ids(const int32_t *__restrict__ sf, int64_t ns, const int32_t *__restrict__ tf,
@@ -729,46 +803,90 @@ int num_sms()
     return n;
 }
 
-SumPlan plan_pairsum(int64_t n_src, int64_t n_tgt, int sum_prec, int shape_override)
+namespace {
+
+// Kernel instantiation for (kind, precision, hi/lo, targets per thread).
+const void *kernel_of(int kind, int prec, bool hilo, int tpt)
 {
-    const int tile = sum_prec == FS_SUM_FP32 ? kTile32 : (sum_prec == FS_SUM_FF ? kTileFF : kTile64);
-    int tpt = sum_prec == FS_SUM_FP32 ? 4 : 2;
+#define FS_K(R, TT, K, HL) reinterpret_cast<const void *>(&k_pairsum<R, TT, K, HL>)
+#define FS_K_T(R, K, HL) (tpt == 2 ? FS_K(R, 2, K, HL) : tpt == 8 ? FS_K(R, 8, K, HL) : FS_K(R, 4, K, HL))
+#define FS_K_T64(K) (tpt == 1 ? FS_K(double, 1, K, false) : tpt == 4 ? FS_K(double, 4, K, false) \
+                                                          : FS_K(double, 2, K, false))
+    if (prec == FS_SUM_FF)
+        return tpt == 1 ? reinterpret_cast<const void *>(&k_pairsum_ff<1>)
+                        : reinterpret_cast<const void *>(&k_pairsum_ff<2>);
+    if (prec == FS_SUM_FP32) {
+        if (kind == PAIR_STOKESLET) return hilo ? FS_K_T(float, PAIR_STOKESLET, true) : FS_K_T(float, PAIR_STOKESLET, false);
+        return hilo ? FS_K_T(float, PAIR_STRESSLET, true) : FS_K_T(float, PAIR_STRESSLET, false);
+    }
+    return kind == PAIR_STOKESLET ? FS_K_T64(PAIR_STOKESLET) : FS_K_T64(PAIR_STRESSLET);
+#undef FS_K_T64
+#undef FS_K_T
+#undef FS_K
+}
+
+// Resident CTAs per SM of a kernel at kThreads threads and `smem` dynamic
+// shared memory (occupancy calculator, cached per kernel and size).
+int resident_ctas(const void *k, size_t smem)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void *, size_t>, int> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_pair(k, smem);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kThreads, smem) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        n = 1;
+    }
+    cache[key] = n;
+    return n;
+}
+
+}  // namespace
+
+SumPlan plan_pairsum(int kind, int64_t n_src, int64_t n_tgt, int sum_prec, bool hilo, int shape_override,
+                     int slots)
+{
+    if (sum_prec == FS_SUM_FF && kind == PAIR_STRESSLET) sum_prec = FS_SUM_FP64;   // as in pairsum()
+    const bool f32 = sum_prec == FS_SUM_FP32, ff = sum_prec == FS_SUM_FF;
+    hilo = hilo && f32;
+    SumPlan p;
+    p.tile = f32 ? kTile32 : (ff ? kTileFF : kTile64);
+    p.tpt = f32 ? 4 : 2;
     if (shape_override > 0) {
         static const int f32_opts[] = {2, 4, 8};
         static const int f64_opts[] = {1, 2, 4};
         const int k = (shape_override - 1) % 3;
-        tpt = sum_prec == FS_SUM_FP32 ? f32_opts[k] : f64_opts[k];
-        if (sum_prec == FS_SUM_FF) tpt = k == 0 ? 1 : 2;
+        p.tpt = f32 ? f32_opts[k] : f64_opts[k];
+        if (ff) p.tpt = k == 0 ? 1 : 2;
     }
-    const int64_t nb = (n_tgt + tpt * kThreads - 1) / (tpt * kThreads);
-    const int64_t want = 4LL * num_sms();
-    int64_t splits = nb > 0 ? (want + nb - 1) / nb : 1;
-    const int64_t max_split = n_src / (2 * tile);
-    if (splits > max_split) splits = max_split;
-    if (splits < 1) splits = 1;
-    int64_t per = (n_src + splits - 1) / splits;
-    per = (per + tile - 1) / tile * tile;
-    if (per < tile) per = tile;
-    splits = (n_src + per - 1) / per;
-    if (splits < 1) splits = 1;
-    SumPlan p;
-    p.tpt = tpt;
-    p.splits = static_cast<int>(splits);
-    p.per_split = per;
-    p.tile = tile;
     p.threads = kThreads;
+    p.tb = p.tpt * kThreads;
+    p.n_arr = ff ? 4 : (kind == PAIR_STRESSLET ? 3 : 2) + (hilo ? 1 : 0);
+    p.v4 = (f32 || ff) ? sizeof(float4) : sizeof(double4_32a);
+    p.smem = static_cast<size_t>(p.n_arr) * 2 * p.tile * p.v4;
+    p.nb = (n_tgt + p.tb - 1) / p.tb;
+    p.nt = (n_src + p.tile - 1) / p.tile;
+    p.W = p.nb * p.nt;
+    if (slots <= 0) slots = num_sms() * resident_ctas(kernel_of(kind, sum_prec, hilo, p.tpt), p.smem);
+    p.grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(p.W, slots)));
     return p;
 }
 
-size_t pairsum_scratch_bytes(int kind, int64_t n_src, int64_t n_tgt, int sum_prec, int shape_override)
+size_t pairsum_scratch_bytes(int kind, int64_t n_src, int64_t n_tgt, int sum_prec, int shape_override,
+                             int slots)
 {
-    if (sum_prec == FS_SUM_FF && kind == PAIR_STRESSLET) sum_prec = FS_SUM_FP64;   // as in pairsum()
-    const SumPlan p = plan_pairsum(n_src, n_tgt, sum_prec, shape_override);
-    const size_t arrs = sum_prec == FS_SUM_FF ? 4 : (kind == PAIR_STRESSLET ? 3 : 2) + (sum_prec == FS_SUM_FP32 ? 1 : 0);
-    const size_t v4 = sum_prec == FS_SUM_FP64 ? sizeof(double4_32a) : sizeof(float4);
-    return 1024 + arrs * static_cast<size_t>(n_src) * v4 +
-           (p.splits > 1 ? static_cast<size_t>(p.splits) * static_cast<size_t>(n_tgt) * 3 * sizeof(double) : 0) +
-           1024;
+    size_t most = 0;
+    // FP32 sums may run with or without hi/lo coordinates: size for the larger
+    for (bool hilo : {false, true}) {
+        const SumPlan p = plan_pairsum(kind, n_src, n_tgt, sum_prec, hilo, shape_override, slots);
+        const size_t packed = static_cast<size_t>(p.n_arr) * static_cast<size_t>(n_src) * p.v4;
+        const size_t part = static_cast<size_t>(p.grid + p.nb) * static_cast<size_t>(p.tb) * 3 * sizeof(double);
+        most = std::max(most, 4 * 256 + packed + part + 1024);
+    }
+    return most;
 }
 
 fs_status exclusion_from_ids(const int32_t *src_fiber, int64_t n_src, const int32_t *tgt_fiber,
@@ -800,40 +918,18 @@ fs_status pairsum(const PairSumArgs &a, void *scratch, size_t scratch_bytes, int
     const bool ff = prec == FS_SUM_FF;
     const bool f32 = prec == FS_SUM_FP32;
     const bool hilo = f32 && a.hilo;
-    const SumPlan p = plan_pairsum(a.n_src, a.n_tgt, prec, a.shape_override);
-    const int n_arr = ff ? 4 : (a.kind == PAIR_STRESSLET ? 3 : 2) + (hilo ? 1 : 0);
-    const size_t v4 = (f32 || ff) ? sizeof(float4) : sizeof(double4_32a);
+    const SumPlan p = plan_pairsum(a.kind, a.n_src, a.n_tgt, prec, hilo, a.shape_override, 0);
     Carve cv(scratch, scratch_bytes);
     double *center = cv.take<double>(4);
-    void *packed = cv.take<unsigned char>(static_cast<size_t>(n_arr) * a.n_src * v4);
-    int direct = p.splits == 1;
-    double *part = direct ? nullptr : cv.take<double>(static_cast<size_t>(p.splits) * a.n_tgt * 3);
-    if (cv.used > scratch_bytes) {
-        set_error("pairsum: scratch too small (%zu > %zu bytes)", cv.used, scratch_bytes);
-        return FS_EINVAL;
-    }
-    k_bbox_center<<<1, 512, 0, st>>>(a.src_xyz, a.n_src, center);
-    FS_LAUNCH_CHECK();
-    const unsigned pb = static_cast<unsigned>((a.n_src + 255) / 256);
-    const int lo_slot = hilo ? n_arr - 1 : 0;
-    if (ff)
-        k_pack_ff<<<pb, 256, 0, st>>>(a.src_xyz, a.src_dens, a.n_src, center, static_cast<float4 *>(packed));
-    else if (f32)
-        k_pack<float><<<pb, 256, 0, st>>>(a.src_xyz, a.src_dens, a.src_w, a.src_nrm, a.n_src, center,
-                                          static_cast<float4 *>(packed), n_arr, lo_slot);
-    else
-        k_pack<double><<<pb, 256, 0, st>>>(a.src_xyz, a.src_dens, a.src_w, a.src_nrm, a.n_src, center,
-                                           static_cast<double4_32a *>(packed), n_arr, 0);
-    FS_LAUNCH_CHECK();
-    dim3 grid(static_cast<unsigned>((a.n_tgt + p.tpt * kThreads - 1) / (p.tpt * kThreads)),
-              static_cast<unsigned>(p.splits));
-    const size_t sm = static_cast<size_t>(n_arr) * 2 * p.tile * v4;
+    void *packed = cv.take<unsigned char>(static_cast<size_t>(p.n_arr) * a.n_src * p.v4);
     const int4 *work = nullptr;
+    unsigned grid = static_cast<unsigned>(p.grid);
+    double *part = nullptr;
     if (a.groups) {
         // one work item per block of tpt x threads targets of a group, sources of
         // that group only; largest source ranges first
         std::vector<int4> items;
-        const int chunk = p.tpt * kThreads;
+        const int chunk = p.tb;
         for (const int4 &g : *a.groups)
             for (int t0 = g.x; t0 < g.y; t0 += chunk)
                 items.push_back(make_int4(t0, std::min(chunk, g.y - t0), g.z, g.w));
@@ -848,10 +944,27 @@ fs_status pairsum(const PairSumArgs &a, void *scratch, size_t scratch_bytes, int
         FS_CUDA(cudaMemcpyAsync(a.work_dev, items.data(), items.size() * sizeof(int4),
                                 cudaMemcpyHostToDevice, st));
         work = a.work_dev;
-        grid = dim3(static_cast<unsigned>(items.size()), 1);
-        direct = 1;
+        grid = static_cast<unsigned>(items.size());
+    } else {
+        part = cv.take<double>(static_cast<size_t>(p.grid + p.nb) * p.tb * 3);
     }
-    double *dst = (direct || work) ? a.out : part;
+    if (cv.used > scratch_bytes) {
+        set_error("pairsum: scratch too small (%zu > %zu bytes)", cv.used, scratch_bytes);
+        return FS_EINVAL;
+    }
+    k_bbox_center<<<1, 512, 0, st>>>(a.src_xyz, a.n_src, center);
+    FS_LAUNCH_CHECK();
+    const unsigned pb = static_cast<unsigned>((a.n_src + 255) / 256);
+    const int lo_slot = hilo ? p.n_arr - 1 : 0;
+    if (ff)
+        k_pack_ff<<<pb, 256, 0, st>>>(a.src_xyz, a.src_dens, a.n_src, center, static_cast<float4 *>(packed));
+    else if (f32)
+        k_pack<float><<<pb, 256, 0, st>>>(a.src_xyz, a.src_dens, a.src_w, a.src_nrm, a.n_src, center,
+                                          static_cast<float4 *>(packed), p.n_arr, lo_slot);
+    else
+        k_pack<double><<<pb, 256, 0, st>>>(a.src_xyz, a.src_dens, a.src_w, a.src_nrm, a.n_src, center,
+                                           static_cast<double4_32a *>(packed), p.n_arr, 0);
+    FS_LAUNCH_CHECK();
     const int acc = a.accumulate ? 1 : 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (a.prof) {
@@ -863,54 +976,35 @@ fs_status pairsum(const PairSumArgs &a, void *scratch, size_t scratch_bytes, int
         }
         FS_CUDA(cudaEventRecord(ev0, st));
     }
-#define FS_LAUNCH(R, TT, K, HL)                                                                   \
-    k_pairsum<R, TT, K, HL><<<grid, kThreads, sm, st>>>(                                         \
-        static_cast<const Vec4Of<R>::type *>(packed), a.n_src, p.per_split, a.tgt_xyz, a.excl,   \
-        a.n_tgt, center, dst, a.scale, direct, acc, d_status, work)
-#define FS_BY_T(R, K, HL)                                                                         \
-    do {                                                                                          \
-        if (p.tpt == 2) FS_LAUNCH(R, 2, K, HL);                                                   \
-        else if (p.tpt == 8) FS_LAUNCH(R, 8, K, HL);                                              \
-        else FS_LAUNCH(R, 4, K, HL);                                                              \
-    } while (0)
-#define FS_BY_T64(K)                                                                              \
-    do {                                                                                          \
-        if (p.tpt == 1) FS_LAUNCH(double, 1, K, false);                                           \
-        else if (p.tpt == 4) FS_LAUNCH(double, 4, K, false);                                      \
-        else FS_LAUNCH(double, 2, K, false);                                                      \
-    } while (0)
-    if (ff) {
-        if (p.tpt == 1)
-            k_pairsum_ff<1><<<grid, kThreads, sm, st>>>(static_cast<const float4 *>(packed), a.n_src,
-                                                        p.per_split, a.tgt_xyz, a.excl, a.n_tgt, center,
-                                                        dst, a.scale, direct, acc, d_status, work);
-        else
-            k_pairsum_ff<2><<<grid, kThreads, sm, st>>>(static_cast<const float4 *>(packed), a.n_src,
-                                                        p.per_split, a.tgt_xyz, a.excl, a.n_tgt, center,
-                                                        dst, a.scale, direct, acc, d_status, work);
-    } else if (f32) {
-        if (a.kind == PAIR_STOKESLET) {
-            if (hilo) FS_BY_T(float, PAIR_STOKESLET, true); else FS_BY_T(float, PAIR_STOKESLET, false);
-        } else {
-            if (hilo) FS_BY_T(float, PAIR_STRESSLET, true); else FS_BY_T(float, PAIR_STRESSLET, false);
+    {
+        const void *src = packed;
+        int64_t n_src = a.n_src, nt = p.nt, W = p.W, n_tgt = a.n_tgt;
+        int G = p.grid;
+        const double *tgt = a.tgt_xyz;
+        const int2 *excl = a.excl;
+        double *out = a.out;
+        double scale = a.scale;
+        int accv = acc;
+        int *status = d_status;
+        void *args[] = {&src, &n_src, &nt, &W, &G, &tgt, &excl, &n_tgt, &center, &out, &part, &scale, &accv,
+                        &status, &work};
+        const cudaError_t e = cudaLaunchKernel(kernel_of(a.kind, prec, hilo, p.tpt), dim3(grid), dim3(kThreads),
+                                               args, p.smem, st);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error("pairsum: launch failed: %s", cudaGetErrorString(e));
+            return FS_ECUDA;
         }
-    } else {
-        if (a.kind == PAIR_STOKESLET) FS_BY_T64(PAIR_STOKESLET);
-        else FS_BY_T64(PAIR_STRESSLET);
     }
-#undef FS_BY_T64
-#undef FS_BY_T
-#undef FS_LAUNCH
     FS_LAUNCH_CHECK();
     if (a.prof) {
         FS_CUDA(cudaEventRecord(ev1, st));
         const int cls = ff ? 4 : (a.kind == PAIR_STOKESLET ? 0 : 2) + (f32 ? 0 : 1);
         a.prof->recs.push_back(Profiler::Rec{cls, ev0, ev1, a.pairs});
     }
-    if (!direct && !work) {
-        const int64_t n3 = a.n_tgt * 3;
-        k_reduce_splits<<<static_cast<unsigned>((n3 + 255) / 256), 256, 0, st>>>(part, p.splits, n3,
-                                                                                 a.scale, acc, a.out);
+    if (!work) {
+        k_reduce_streamk<<<static_cast<unsigned>((a.n_tgt + 255) / 256), 256, 0, st>>>(
+            part, a.n_tgt, p.tb, p.nt, p.W, p.grid, a.scale, acc, a.out);
         FS_LAUNCH_CHECK();
     }
     return FS_OK;

@@ -270,22 +270,31 @@ fs_status far_field(fs_ctx *c, int sum_prec, bool hilo, const std::vector<int> *
 //   surface: D^-1 (S q + fiber Stokeslets)  -- D the Jacobi diagonal.
 // sum_prec selects the far-field arithmetic; act restricts the far field to
 // those systems (results of other systems are not meaningful).
-fs_status apply_pa(fs_ctx *c, const double *v, double *out, int sum_prec, const std::vector<int> *act)
+fs_status apply_pa(fs_ctx *c, const double *v, double *out, int sum_prec, const std::vector<int> *act,
+                   bool hilo = false)
 {
     FS_TRY(launch_force(c, v, c->d_f, c->d_wf));
-    FS_TRY(far_field(c, sum_prec, false, act));
+    FS_TRY(far_field(c, sum_prec, hilo, act));
     const double *q = c->surf.n ? v + c->n_fib_unk : nullptr;
-    if (c->surf.n) FS_TRY(surface_couplings(c, q, c->d_ubar, sum_prec, false));
+    if (c->surf.n) FS_TRY(surface_couplings(c, q, c->d_ubar, sum_prec, hilo));
     FS_TRY(launch_rows(c, nullptr, c->d_f, c->d_ubar, c->d_e, ROWS_COUPLING));
     FS_TRY(launch_lu_solve(c, c->d_e, out));
     k_add<<<blocks_for(c->n_fib_unk), 256, 0, c->stream>>>(out, v, c->n_fib_unk);
     FS_LAUNCH_CHECK();
     if (c->surf.n) {
-        FS_TRY(surface_rows(c, q, c->d_usurf, c->d_e + c->n_fib_unk, false, sum_prec, false));
+        FS_TRY(surface_rows(c, q, c->d_usurf, c->d_e + c->n_fib_unk, false, sum_prec, hilo));
         FS_TRY(surface_precond(c, c->d_e + c->n_fib_unk, out + c->n_fib_unk));
     }
     return FS_OK;
 }
+
+// Inexact-Krylov relaxation of the outer operator (mixed precision): an
+// operator error of relative size eta on a direction taken when the residual
+// is r adds at most about eta |r| to the final residual, so once
+// kEtaFP32 |r| / |P^-1 b| <= kRelaxShare tol the FP32 hi/lo far field
+// (relative error below kEtaFP32) is accurate enough for further directions.
+constexpr double kEtaFP32 = 1e-6;
+constexpr double kRelaxShare = 0.05;
 
 // Far-field arithmetic of the accurate sums (right-hand side, outer operator):
 // FP64 on the plain FP64 path, float-float on the mixed path.
@@ -366,7 +375,12 @@ fs_status gmres_seg(fs_ctx *c, Space &sp, const double *pb, double *x, double to
                 std::vector<SysState> ist;
                 FS_TRY(gmres_seg(c, isp, Vj, Zj, inner_tol, c->opt.max_iter, inner_prec, -1, 0.0, running, ist));
                 for (int s : running) st[s].inner += ist[s].its;
-                FS_TRY(apply_pa(c, Zj, sp.w, sum_prec, &running));
+                // the largest current residual among the running systems decides
+                double rel_now = 0.0;
+                for (int s : running) rel_now = std::max(rel_now, std::fabs(st[s].g[j]) / st[s].beta0);
+                const bool relax = c->opt.relax && sum_prec == FS_SUM_FF && kEtaFP32 * rel_now <= kRelaxShare * tol;
+                if (relax) FS_TRY(apply_pa(c, Zj, sp.w, FS_SUM_FP32, &running, true));
+                else FS_TRY(apply_pa(c, Zj, sp.w, sum_prec, &running));
             } else {
                 FS_TRY(apply_pa(c, Vj, sp.w, sum_prec, &running));
             }
@@ -670,6 +684,10 @@ fs_status context_init(fs_ctx *c, int S, const int32_t *fps, int M, const int32_
     return FS_OK;
 }
 
+// Upper bound of the CTAs one wave of a direct sum may hold (SMs x resident
+// CTAs per SM); lets the estimate run without asking a device.
+constexpr int kSlotsBound = 8192;
+
 // Device bytes context_init allocates for this problem, plus the largest
 // direct-sum scratch a step reserves.  Each allocation is rounded up to the
 // allocator's 512-byte granule; the result bounds what fs_device_bytes reports.
@@ -739,7 +757,8 @@ size_t estimate_bytes(int M, const int32_t *ppf, int n_surf, const fs_options &o
         for (int prec : {int(FS_SUM_FP64), int(FS_SUM_FP32), int(FS_SUM_FF)})
             for (auto &sz : sizes)
                 if (sz[0] > 0 && sz[1] > 0)
-                    sc = std::max(sc, pairsum_scratch_bytes(kind, sz[0], sz[1], prec, opt.tile_override));
+                    sc = std::max(sc, pairsum_scratch_bytes(kind, sz[0], sz[1], prec, opt.tile_override,
+                                                            kSlotsBound));
     total += sc + sc / 4 + 512;
     return total;
 }

@@ -14,8 +14,12 @@ def dev(a, torch, dtype=None):
     return torch.tensor(np.ascontiguousarray(a), dtype=dtype or torch.float64, device="cuda:0")
 
 
-def make_ctx(s, prec=fs.FS_FP64, tol=1e-12, lsb=False, delta_over_L=0.01, restart=60, max_iter=300):
+def make_ctx(s, prec=fs.FS_FP64, tol=1e-12, lsb=False, delta_over_L=0.01, restart=60, max_iter=300,
+             relax=None, profile=False):
     opt = fs.fs_options_default()
+    if relax is not None:
+        opt.relax = 1 if relax else 0
+    opt.profile = 1 if profile else 0
     opt.prec = prec
     opt.tol = tol
     opt.lsb = 1 if lsb else 0

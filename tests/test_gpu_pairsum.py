@@ -1,8 +1,9 @@
 """GPU parity of the direct sums (fs_stokeslet_apply, fs_stresslet_apply,
 fs_surface_apply) against the oracle's plain FP64 C loops, element by element
 on the same seeded inputs: sizes spanning several tiles with ragged tails,
-fiber exclusion, the source-split path, every launch shape, edge cases and a
-sampled check at the 65,536-point cloud size.
+fiber exclusion, the one-wave work split (runs of source tiles that end
+inside a target block, several CTAs per block, many blocks per CTA), every
+launch shape, edge cases and a sampled check at the 65,536-point cloud size.
 Tolerances: FP64 arithmetic 1e-12 relative 2-norm; float-float 5e-11 (~2^-44
 per pair, and coordinates carried as two floats, 2^-48 relative, which near
 pairs of random points amplify); FP32 arithmetic 1e-6."""
@@ -45,7 +46,7 @@ def gpu_stokeslet(h, src, wf, tgt, prec, sf=None, tf=None):
 
 @pytest.mark.parametrize("prec", [fs.FS_SUM_FP64, fs.FS_SUM_FP32, FS_SUM_FF])
 @pytest.mark.parametrize("n_src,n_tgt", [(1, 1), (255, 3), (256, 257), (1000, 777), (5003, 129),
-                                         (20000, 4100)])
+                                         (20000, 4100), (60000, 700), (700, 60000), (20011, 19997)])
 def test_stokeslet_random_points(ctx, prec, n_src, n_tgt):
     src, wf = random_points(n_src, 1)
     tgt, _ = random_points(n_tgt, 2)

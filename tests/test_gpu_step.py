@@ -127,6 +127,30 @@ def test_mixed_point_forces_cloud_shape():
     assert rel(V, ref.V) <= 5e-6
 
 
+def test_relaxed_outer_operator_matches_float_float():
+    """Mixed path with the inexact-Krylov relaxation (later outer directions
+    on the FP32 hi/lo far field) against the same solve with every outer
+    direction in float-float: same tolerance reached, velocities equal to well
+    within the tolerance, fewer float-float sums."""
+    from tests.gpu_helpers import dev, make_ctx
+    s = wl.free_space(48, 64, 12.0, seed=5, curved_amp=0.05)
+    out = {}
+    for relax in (False, True):
+        h = make_ctx(s, prec=fs.FS_MIXED, tol=1e-10, relax=relax, profile=True)
+        X = dev(s.X, torch)
+        fs.fs_set_state(h, X, dev(s.L, torch), dev(s.f_ext, torch))
+        inf = fs.fs_step(h)
+        V = torch.empty_like(X)
+        fs.fs_get_state(h, V=V)
+        ks = fs.fs_kernel_stats(h)
+        fs.fs_destroy(h)
+        assert inf.resid <= 1e-10
+        out[relax] = (V.cpu().numpy(), ks[4][0], ks[0][0])
+    assert rel(out[True][0], out[False][0]) <= 1e-8
+    assert out[True][1] < out[False][1]     # float-float launches
+    assert out[True][2] > out[False][2]     # FP32 launches
+
+
 def test_confined_small():
     s = gravity(wl.confined(12, 16, R=4.0, R_centres=2.0, n_theta=4, n_phi=8, seed=5))
     ref = oracle_step(s)
