@@ -77,7 +77,8 @@ typedef struct {
                                ||P^-1 (b - A u)|| <= tol ||P^-1 b|| */
     int32_t max_iter;       /* GMRES iterations per solve (default 200) */
     int32_t restart;        /* GMRES restart length (default 60, at most 250) */
-    int32_t max_refine;     /* reserved (default 6) */
+    int32_t max_refine;     /* FS_MIXED, free space, relax = 1: at most this many float-float
+                               true residuals per step (default 6; normally one is used) */
     double inner_tol;       /* FS_MIXED: relative tolerance of each inner FP32-far-field
                                GMRES solve (default 1e-5) */
     double delta_over_L;    /* regularisation delta of K_delta as a fraction of L (default 0.01) */
@@ -86,11 +87,17 @@ typedef struct {
     int32_t tile_override;  /* 0 = autotuned far-field launch shape, else a shape id */
     int32_t profile;        /* 1 = bracket every direct-sum kernel with CUDA events on the
                                context's stream (read with fs_kernel_stats) (default 0) */
-    int32_t relax;          /* FS_MIXED: 1 = once the outer residual r satisfies
-                               1e-6 |r| / |P^-1 b| <= tol / 20, evaluate further outer
-                               directions with the FP32 hi/lo far field instead of
-                               float-float (inexact-Krylov relaxation; the residual
-                               they can still add stays below tol / 20) (default 1) */
+    int32_t relax;          /* FS_MIXED: 1 = evaluate the far field in float-float only
+                               where the residual needs it (default 1).  Free space: GMRES
+                               on the FP32-far-field operator with an FP32 right-hand side
+                               to inner_tol, ONE float-float true residual r (one far field
+                               of the known force plus the solution's force), then GMRES on
+                               the FP32 hi/lo operator for the correction until
+                               |r - P^-1 A d| <= tol |P^-1 b| (its operator error, relative
+                               ~1e-7, acts on a correction of size |r|).  With a periphery:
+                               flexible GMRES whose outer directions switch from float-float
+                               to FP32 hi/lo once 1e-6 |r| <= tol |P^-1 b| / 20.
+                               0 = flexible GMRES with every outer direction in float-float */
 } fs_options;
 
 /* Direct-sum kernel classes reported by fs_kernel_stats. */

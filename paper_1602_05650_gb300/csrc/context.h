@@ -154,7 +154,7 @@ size_t estimate_bytes(int M, const int32_t *ppf, int n_surf, const fs_options &o
 // fiber.cu
 fs_status launch_geometry(fs_ctx *c);
 // f (and W f) at the nodes from the unknowns u (or f_known when u == nullptr)
-fs_status launch_force(fs_ctx *c, const double *u, double *f, double *wf);
+fs_status launch_force(fs_ctx *c, const double *u, double *f, double *wf, bool add_known = false);
 // rows of the fiber equations; mode 0: out = B u + Rw(ubar); 1: right-hand side
 // b = -(rows of the known force and free-end data + Rw(ubar)); 2: out = Rw(ubar)
 enum : int { ROWS_FULL = 0, ROWS_RHS = 1, ROWS_COUPLING = 2 };

@@ -295,8 +295,11 @@ __device__ void dev_rows(const FiberTable &F, const Fib &fb, const double *us, c
 }
 
 // ---------------------------------------------------------------- kernels
+// f = force of u (or the known force when u is NULL), wf = W f.  add_known:
+// f = the known force, wf = W (known force + force of u) -- the density whose
+// far field is the coupling of the known force plus that of u.
 __global__ void __launch_bounds__(128) k_force(FiberTable F, const double *__restrict__ u,
-                                               double *__restrict__ f, double *__restrict__ wf)
+                                               double *__restrict__ f, double *__restrict__ wf, int add_known)
 {
     extern __shared__ double fsm[];
     const Fib fb(F, blockIdx.x);
@@ -314,8 +317,14 @@ __global__ void __launch_bounds__(128) k_force(FiberTable F, const double *__res
         __syncthreads();
     }
     for (int i = threadIdx.x; i < 3 * N; i += blockDim.x) {
-        f[3 * fb.n0 + i] = fl[i];
-        wf[3 * fb.n0 + i] = F.W[fb.n0 + i / 3] * fl[i];
+        if (u && add_known) {
+            const double fk = F.fknown[3 * fb.n0 + i];
+            f[3 * fb.n0 + i] = fk;
+            wf[3 * fb.n0 + i] = F.W[fb.n0 + i / 3] * (fk + fl[i]);
+        } else {
+            f[3 * fb.n0 + i] = fl[i];
+            wf[3 * fb.n0 + i] = F.W[fb.n0 + i / 3] * fl[i];
+        }
     }
 }
 
@@ -601,11 +610,11 @@ fs_status launch_geometry(fs_ctx *c)
     return FS_OK;
 }
 
-fs_status launch_force(fs_ctx *c, const double *u, double *f, double *wf)
+fs_status launch_force(fs_ctx *c, const double *u, double *f, double *wf, bool add_known)
 {
     if (c->M == 0) return FS_OK;
     const size_t sm = static_cast<size_t>(14 * c->max_N) * sizeof(double);
-    k_force<<<c->M, 128, sm, c->stream>>>(c->table(), u, f, wf);
+    k_force<<<c->M, 128, sm, c->stream>>>(c->table(), u, f, wf, add_known ? 1 : 0);
     FS_LAUNCH_CHECK();
     return FS_OK;
 }

@@ -135,7 +135,7 @@ __global__ void k_seg_set(double *__restrict__ out, const double *__restrict__ a
 
 // ------------------------------------------------------ segmented GMRES (host)
 struct SysState {
-    double beta0 = 0.0, beta = 0.0, rel = 0.0;
+    double beta0 = 0.0, beta = 0.0, rel = 0.0, res = 0.0, lim = 0.0;
     int its = 0, inner = 0, kk = 0;
     bool conv = false, done = false;
     std::vector<double> H, cs, sn, g, y;
@@ -300,17 +300,40 @@ constexpr double kRelaxShare = 0.05;
 // FP64 on the plain FP64 path, float-float on the mixed path.
 int accurate_prec(const fs_ctx *c) { return c->opt.prec == FS_FP64 ? FS_SUM_FP64 : FS_SUM_FF; }
 
-// b (Eq. sche-linear-eq right-hand side) with the accurate far field, then pb = P^-1 b
-fs_status rhs(fs_ctx *c, double *b, double *pb)
+// b (Eq. sche-linear-eq right-hand side), then pb = P^-1 b; far field in
+// `ap` arithmetic (the accurate one by default)
+fs_status rhs(fs_ctx *c, double *b, double *pb, int ap = -1, bool hilo = false)
 {
-    const int ap = accurate_prec(c);
+    if (ap < 0) ap = accurate_prec(c);
     FS_TRY(launch_force(c, nullptr, c->d_f, c->d_wf));
-    FS_TRY(far_field(c, ap, false, &c->all_sys));
-    if (c->surf.n) FS_TRY(surface_couplings(c, nullptr, c->d_ubar, ap, false));
+    FS_TRY(far_field(c, ap, hilo, &c->all_sys));
+    if (c->surf.n) FS_TRY(surface_couplings(c, nullptr, c->d_ubar, ap, hilo));
     FS_TRY(launch_rows(c, nullptr, c->d_f, c->d_ubar, b, ROWS_RHS));
-    if (c->surf.n) FS_TRY(surface_rows(c, nullptr, c->d_usurf, b + c->n_fib_unk, true, ap, false));
+    if (c->surf.n) FS_TRY(surface_rows(c, nullptr, c->d_usurf, b + c->n_fib_unk, true, ap, hilo));
     FS_TRY(launch_lu_solve(c, b, pb));
     if (c->surf.n) FS_TRY(surface_precond(c, b + c->n_fib_unk, pb + c->n_fib_unk));
+    return FS_OK;
+}
+
+__global__ void k_sub(double *__restrict__ out, const double *__restrict__ v, int64_t n)
+{
+    const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (i < n) out[i] -= v[i];
+}
+
+// Preconditioned residual r = P^-1 b - (P^-1 A) x of the fiber system (free
+// space) with ONE far field: the coupling of the known force and that of x's
+// force are the far field of the sum of the two densities (the sum is linear
+// in the density), so
+//   r = P^-1 rows_rhs(f_known, ubar[W (f_known + f(x))]) - x.
+fs_status true_residual(fs_ctx *c, const double *x, double *r, int sum_prec)
+{
+    FS_TRY(launch_force(c, x, c->d_f, c->d_wf, true));
+    FS_TRY(far_field(c, sum_prec, false, &c->all_sys));
+    FS_TRY(launch_rows(c, nullptr, c->d_f, c->d_ubar, c->d_e, ROWS_RHS));
+    FS_TRY(launch_lu_solve(c, c->d_e, r));
+    k_sub<<<blocks_for(c->n_fib_unk), 256, 0, c->stream>>>(r, x, c->n_fib_unk);
+    FS_LAUNCH_CHECK();
     return FS_OK;
 }
 
@@ -321,7 +344,8 @@ fs_status rhs(fs_ctx *c, double *b, double *pb)
 // solve of (P^-1 A_inner) z = v_j to inner_tol and x = Z y (flexible GMRES).
 fs_status gmres_seg(fs_ctx *c, Space &sp, const double *pb, double *x, double tol, int max_iter,
                     int sum_prec, int inner_prec, double inner_tol, const std::vector<int> &want,
-                    std::vector<SysState> &st)
+                    std::vector<SysState> &st, bool hilo = false, const std::vector<double> *tol_abs = nullptr,
+                    double partial_rel = 0.0)
 {
     const int64_t n = c->n_unk;
     const int R = sp.R, hs = R + 1, SH = SHof(sp);
@@ -343,7 +367,14 @@ fs_status gmres_seg(fs_ctx *c, Space &sp, const double *pb, double *x, double to
                 set_error("gmres: non-finite right-hand side (system %d)", s);
                 return FS_ENUMERIC;
             }
-            if (!(q.beta0 > 0.0)) {
+            // converged when |residual| <= lim (tol |pb| unless given per system)
+            q.lim = tol_abs ? (*tol_abs)[s] : tol * q.beta0;
+            // a correction too large for this operator's accuracy to finish the
+            // solve is only taken part of the way (another true residual follows)
+            if (partial_rel > 0.0 && kEtaFP32 * q.beta0 > kRelaxShare * q.lim)
+                q.lim = std::max(q.lim, partial_rel * q.beta0);
+            q.res = q.beta0;
+            if (!(q.beta0 > 0.0) || q.beta0 <= q.lim) {
                 q.conv = q.done = true;
                 continue;
             }
@@ -376,13 +407,13 @@ fs_status gmres_seg(fs_ctx *c, Space &sp, const double *pb, double *x, double to
                 FS_TRY(gmres_seg(c, isp, Vj, Zj, inner_tol, c->opt.max_iter, inner_prec, -1, 0.0, running, ist));
                 for (int s : running) st[s].inner += ist[s].its;
                 // the largest current residual among the running systems decides
-                double rel_now = 0.0;
-                for (int s : running) rel_now = std::max(rel_now, std::fabs(st[s].g[j]) / st[s].beta0);
-                const bool relax = c->opt.relax && sum_prec == FS_SUM_FF && kEtaFP32 * rel_now <= kRelaxShare * tol;
+                bool relax = c->opt.relax && sum_prec == FS_SUM_FF;
+                for (int s : running)
+                    relax = relax && kEtaFP32 * std::fabs(st[s].g[j]) <= kRelaxShare * st[s].lim;
                 if (relax) FS_TRY(apply_pa(c, Zj, sp.w, FS_SUM_FP32, &running, true));
                 else FS_TRY(apply_pa(c, Zj, sp.w, sum_prec, &running));
             } else {
-                FS_TRY(apply_pa(c, Vj, sp.w, sum_prec, &running));
+                FS_TRY(apply_pa(c, Vj, sp.w, sum_prec, &running, hilo));
             }
             for (int pass = 0; pass < 2; ++pass) {   // CGS2
                 const int off = pass ? hs : 0;
@@ -420,8 +451,9 @@ fs_status gmres_seg(fs_ctx *c, Space &sp, const double *pb, double *x, double to
                 q.g[j] = q.cs[j] * q.g[j];
                 ++q.its;
                 q.kk = j + 1;
-                q.rel = std::fabs(q.g[j + 1]) / q.beta0;
-                if (q.rel <= tol) {
+                q.res = std::fabs(q.g[j + 1]);
+                q.rel = q.res / q.beta0;
+                if (q.res <= q.lim) {
                     q.conv = q.done = true;
                 } else if (hn == 0.0 || q.its >= max_iter) {
                     q.done = true;
@@ -463,7 +495,7 @@ fs_status gmres_seg(fs_ctx *c, Space &sp, const double *pb, double *x, double to
         // restart: r = pb - P^-1 A x on the systems that continue
         act.swap(again);
         FS_TRY(seg_build(c, sp, act));
-        FS_TRY(apply_pa(c, x, sp.w, sum_prec, &act));
+        FS_TRY(apply_pa(c, x, sp.w, sum_prec, &act, hilo));
         FS_TRY(seg_set(c, sp, sp.r, pb, sp.w, 2));
         FS_TRY(seg_dots(c, sp, sp.r, 0, 1, sp.r, 2 * hs + 2, true));
         FS_TRY(fetch_h(c, sp));
@@ -471,8 +503,9 @@ fs_status gmres_seg(fs_ctx *c, Space &sp, const double *pb, double *x, double to
         for (int s : act) {
             SysState &q = st[s];
             q.beta = sp.hpin[static_cast<int64_t>(s) * SH + 2 * hs + 2];
+            q.res = q.beta;
             q.rel = q.beta / q.beta0;
-            if (q.rel <= tol) q.conv = q.done = true;
+            if (q.res <= q.lim) q.conv = q.done = true;
             else keep.push_back(s);
         }
         act.swap(keep);
@@ -897,36 +930,90 @@ fs_status fs_step(fs_ctx *c, fs_step_info *info)
         FS_CUDA(cudaStreamSynchronize(c->stream));
         tms[1] = ms_since(t0);
     }
-    FS_TRY(rhs(c, c->d_b, c->d_pb));
+    // mixed precision on free-space systems: solve with an FP32 right-hand
+    // side, then one float-float true residual and an FP32 hi/lo correction
+    const bool split = c->opt.prec == FS_MIXED && c->surf.n == 0 && c->opt.relax;
+    if (split) FS_TRY(rhs(c, c->d_b, c->d_pb, FS_SUM_FP32, true));
+    else FS_TRY(rhs(c, c->d_b, c->d_pb));
     FS_TRY(check_status(c));
     if (info) tms[0] = ms_since(t0) - tms[1];
     int iters = 0, sweeps = 0;
     double rel = 0.0;
     bool converged = false;
     std::vector<SysState> st;
+    std::vector<int> its(c->S, 0), outer(c->S, 0);
+    std::vector<double> resid(c->S, 0.0);
+    std::vector<char> conv(c->S, 0);
     if (c->opt.prec == FS_FP64) {
         Space sp = inner_space(c);
         FS_TRY(gmres_seg(c, sp, c->d_pb, c->d_x, c->opt.tol, c->opt.max_iter, FS_SUM_FP64, -1, 0.0,
                          c->all_sys, st));
+        for (int s = 0; s < c->S; ++s) {
+            its[s] = st[s].its;
+            outer[s] = 1;
+            resid[s] = st[s].rel;
+            conv[s] = st[s].conv;
+        }
+    } else if (split) {
+        // (1) x1: GMRES on the FP32-far-field operator with the FP32 right-hand
+        //     side, to the inner tolerance (or tol if tighter);
+        // (2) r1 = P^-1 b - (P^-1 A) x1 with one float-float far field;
+        // (3) d: GMRES on the FP32 hi/lo operator for (P^-1 A) d = r1 until
+        //     |r1 - (P^-1 A) d| <= tol |P^-1 b|.  Its operator error (relative
+        //     ~1e-7) acts on a correction of size |r1| (~inner tol |P^-1 b|).
+        //     A residual too large for that (kEtaFP32 |r1| > kRelaxShare tol
+        //     |P^-1 b|) is reduced 1e3-fold and the residual recomputed.
+        Space sp = inner_space(c);
+        std::vector<SysState> s1, s2;
+        FS_TRY(gmres_seg(c, sp, c->d_pb, c->d_x, std::min(c->opt.inner_tol, 0.1), c->opt.max_iter, FS_SUM_FP32,
+                         -1, 0.0, c->all_sys, s1));
+        std::vector<double> lim(c->S, 0.0);
+        for (int s = 0; s < c->S; ++s) {
+            lim[s] = c->opt.tol * s1[s].beta0;
+            its[s] = s1[s].its;
+            outer[s] = 1;
+        }
+        const int sweeps_max = std::max(1, c->opt.max_refine);
+        for (int sw = 0; sw < sweeps_max; ++sw) {
+            FS_TRY(true_residual(c, c->d_x, c->d_b, accurate_prec(c)));
+            const bool last = sw + 1 == sweeps_max;
+            FS_TRY(gmres_seg(c, sp, c->d_b, c->d_pb, c->opt.tol, c->opt.max_iter, FS_SUM_FP32, -1, 0.0,
+                             c->all_sys, s2, true, &lim, last ? 0.0 : 1e-3));
+            k_add<<<blocks_for(c->n_fib_unk), 256, 0, c->stream>>>(c->d_x, c->d_pb, c->n_fib_unk);
+            FS_LAUNCH_CHECK();
+            bool again = false;
+            for (int s = 0; s < c->S; ++s) {
+                its[s] += s2[s].its;
+                if (s2[s].its > 0) ++outer[s];
+                resid[s] = s1[s].beta0 > 0.0 ? s2[s].res / s1[s].beta0 : 0.0;
+                conv[s] = s2[s].conv && s2[s].res <= lim[s];
+                if (!last && kEtaFP32 * s2[s].beta0 > kRelaxShare * lim[s]) again = true;
+            }
+            if (!again) break;
+        }
     } else {
         // mixed: flexible GMRES on the operator with the float-float far field,
         // each direction preconditioned by an FP32-far-field GMRES solve
         Space sp = outer_space(c);
         FS_TRY(gmres_seg(c, sp, c->d_pb, c->d_x, c->opt.tol, c->opt.max_iter, accurate_prec(c), FS_SUM_FP32,
                          c->opt.inner_tol, c->all_sys, st));
+        for (int s = 0; s < c->S; ++s) {
+            its[s] = st[s].inner;
+            outer[s] = st[s].its;
+            resid[s] = st[s].rel;
+            conv[s] = st[s].conv;
+        }
     }
     converged = true;
     for (int s = 0; s < c->S; ++s) {
-        const SysState &q = st[s];
-        const int it = c->opt.prec == FS_FP64 ? q.its : q.inner;
-        iters = std::max(iters, it);
-        sweeps = std::max(sweeps, c->opt.prec == FS_FP64 ? 1 : q.its);
-        rel = std::max(rel, q.rel);
-        converged = converged && q.conv;
-        c->sys_iters[s] = it;
-        c->sys_outer[s] = q.its;
-        c->sys_resid[s] = q.rel;
-        c->sys_conv[s] = q.conv ? 1 : 0;
+        iters = std::max(iters, its[s]);
+        sweeps = std::max(sweeps, outer[s]);
+        rel = std::max(rel, resid[s]);
+        converged = converged && conv[s];
+        c->sys_iters[s] = its[s];
+        c->sys_outer[s] = outer[s];
+        c->sys_resid[s] = resid[s];
+        c->sys_conv[s] = conv[s] ? 1 : 0;
     }
     FS_TRY(check_status(c));
     tms[2] = ms_since(t0) - tms[0] - tms[1];
