@@ -73,6 +73,9 @@ struct FiberTable {
     double *mloc;    // [N_tot][2] local operator coefficients (see k_geometry)
     double *bc;      // [M][12] free-end data X''(+-1)/dt, X'''(+-1)/dt
     double *kp;      // [sum N^2][4] K_delta pair records (a_kj, rhat)
+    // block-build scratch (offsets from blk_ptr: 16 N^2 per fiber)
+    double *ftau;    // [3 N^2] per fiber: force of each tension column, [a][l][j]
+    double *wsc;     // [12 N^2] per fiber: w = (M + K_delta) f of each column, [col][b N + k]
 };
 
 struct Surface {
@@ -121,6 +124,8 @@ struct fs_ctx {
     double *d_t = nullptr, *d_tz = nullptr, *d_fknown = nullptr, *d_W = nullptr, *d_mloc = nullptr,
            *d_bc = nullptr, *d_kp = nullptr;
     double *d_B = nullptr;        // column-major blocks, LU factors after build
+    double *d_ftau = nullptr;     // block-build scratch: tension-column forces (3 N^2 per fiber)
+    double *d_wsc = nullptr;      // block-build scratch: w of every column (12 N^2 per fiber)
     int *d_piv = nullptr;
     double *d_V = nullptr, *d_T = nullptr;
     double *d_f = nullptr, *d_wf = nullptr, *d_ubar = nullptr;

@@ -10,9 +10,8 @@
 //   k_rows        w = M f + K_delta[f] + ubar at the nodes and the 4N rows:
 //                 velocity rows -V(y) + P_y w, free-end rows, tension rows
 //                 X_s(z) . D_z w (Eq. main-inextensibility), T(+-1) = 0.
-//   k_block_build the self block of Eq. prec, column by column: the same
-//                 force/velocity/row map applied to unit vectors with ubar = 0,
-//                 written column-major.
+//   k_build_*     the self block of Eq. prec for unit columns with ubar = 0,
+//                 column-major, as GEMM-shaped products (see "block build").
 //   k_lu / k_lu_solve  batched LU with partial pivoting and its triangular
 //                 solves (the preconditioner apply, Sec. 3.3).
 //   k_update      V, T at the nodes and X <- X + dt V.
@@ -352,220 +351,490 @@ __global__ void __launch_bounds__(128) k_rows(FiberTable F, const double *__rest
     dev_rows(F, fb, us, w, 1, mode == 1, out + fb.u0, 0);
 }
 
-// One CTA per (fiber, chunk of nb columns): B[:, col] = rows(e_col) with ubar = 0.
-// The inputs are unit vectors, so the generic force/velocity maps are
-// specialised by column type:
-//   sigma_a,j (j < N-4): f = -E dt g^4 T_j(alpha) e_a  (one component, no D_alpha)
-//   p_a,k              : f = 0 -> w = 0 (only the direct rows)
-//   tension            : T = column of Tn, f = g D_alpha(T X_s) (three components)
-__global__ void __launch_bounds__(256) k_block_build(FiberTable F, double *__restrict__ B, int nb)
+// ------------------------------------------------------------- block build
+// The self block of Eq. prec, B = Rd + Rw W with W = S F for the unit columns:
+//   F  force at the nodes of each unknown (Sec. 3.2 discrete force):
+//      sigma_a,j  f = -E dt g^4 (Sig column j) e_a   (one component)
+//      p_a,k      f = 0
+//      tension j  f = g D_alpha (T_j X_s),  T_j = column j of Tn   (three)
+//   S  velocity at the nodes of a nodal force density: the local operator M
+//      (Eq. main-sb-local) on the diagonal and the K_delta pair records
+//      a_kl (I + rhat rhat) off it (Eq. sb-stokes-reg);
+//   Rw velocity rows P_y w_a and tension rows X_s(z) . D_z w;
+//   Rd the unknowns' direct rows: -V(y), the free-end rows, T at the ends.
+// Three GEMM-shaped kernels with 64 x 64 output tiles, 4 x 4 FP64 register
+// tiles per thread and the inner dimension staged through shared memory in
+// chunks of 32: k_build_ftau (tension-column forces), k_build_w (W, with S
+// generated on the fly from the pair records), k_build_rows (Rw W + Rd in the
+// epilogue); k_build_direct writes the rows that do not involve w.
+constexpr int kBT = 64, kBK = 32;
+
+// F_tau[a][l][j] = g sum_q D1[l][q] Tn[q][j] t_{q,a}; grid (M, 3)
+__global__ void __launch_bounds__(256) k_build_ftau(FiberTable F)
 {
-    extern __shared__ double bsm[];
     const Fib fb(F, blockIdx.x);
-    const int N = fb.N, n = 4 * N;
-    const int col0 = blockIdx.y * nb;
-    if (col0 >= n) return;
-    const int cnt = min(nb, n - col0);
-    double *us = bsm, *Tv = us + nb * 4 * N, *q = Tv + nb * N, *f = q + nb * 3 * N, *w = f + nb * 3 * N;
-    const double *Sig = fb.M_(fb.lay.Sig), *Tn = fb.M_(fb.lay.Tn), *D1 = fb.M_(fb.lay.D1);
+    const int N = fb.N, a = blockIdx.y;
+    const double *D1 = fb.M_(fb.lay.D1), *Tn = fb.M_(fb.lay.Tn);
     const double *t = F.t + 3 * fb.n0;
-    const double g = fb.g, bend = -F.E * F.dt * g * g * g * g;
-    for (int i = threadIdx.x; i < cnt * n; i += blockDim.x) {
-        const int c = i / n, r = i % n;
-        us[i] = (r == col0 + c) ? 1.0 : 0.0;
+    double *out = F.ftau + fb.blk0 / 16 * 3 + static_cast<int64_t>(a) * N * N;
+    for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+        const int l = idx / N, jj = idx - l * N;
+        double sum = 0.0;
+        for (int q = 0; q < N; ++q) sum = fma(D1[l * N + q] * t[3 * q + a], Tn[q * N + jj], sum);
+        out[idx] = fb.g * sum;
     }
-    // tension columns: T at the nodes and the product T X_s
-    for (int i = threadIdx.x; i < cnt * N; i += blockDim.x) {
-        const int c = i / N, k = i % N, col = col0 + c;
-        const double Tk = col >= 3 * N ? Tn[k * N + (col - 3 * N)] : 0.0;
-        Tv[i] = Tk;
-        q[3 * i] = Tk * t[3 * k];
-        q[3 * i + 1] = Tk * t[3 * k + 1];
-        q[3 * i + 2] = Tk * t[3 * k + 2];
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < cnt * N * 3; i += blockDim.x) {
-        const int c = i / (3 * N), r = i % (3 * N), k = r / 3, a = r % 3, col = col0 + c;
-        double v = 0.0;
-        if (col < 3 * N) {
-            const int ca = col / N, j = col % N;
-            if (ca == a && j < N - 4) v = bend * Sig[k * N + j];
-        } else {
-            const double *qc = q + c * 3 * N;
-            double s = 0.0;
-            for (int jj = 0; jj < N; ++jj) s += D1[k * N + jj] * qc[3 * jj + a];
-            v = g * s;
-        }
-        f[i] = v;
-    }
-    __syncthreads();
-    // w = M f + K_delta[f], skipping p columns (f = 0) and using the single
-    // nonzero component of sigma columns
-    const double *ml = F.mloc + 2 * fb.n0;
-    const double4_32a *kp = reinterpret_cast<const double4_32a *>(F.kp) + fb.kp0;
-    for (int i = threadIdx.x; i < cnt * N; i += blockDim.x) {
-        const int c = i / N, k = i % N, col = col0 + c;
-        const double *fc = f + c * 3 * N;
-        double wx = 0.0, wy = 0.0, wz = 0.0;
-        const bool pcol = col < 3 * N && (col % N) >= N - 4;
-        if (!pcol) {
-            const double fx = fc[3 * k], fy = fc[3 * k + 1], fz = fc[3 * k + 2];
-            const double tx = t[3 * k], ty = t[3 * k + 1], tz = t[3 * k + 2];
-            const double tf = tx * fx + ty * fy + tz * fz;
-            wx = ml[2 * k] * fx + ml[2 * k + 1] * tx * tf;
-            wy = ml[2 * k] * fy + ml[2 * k + 1] * ty * tf;
-            wz = ml[2 * k] * fz + ml[2 * k + 1] * tz * tf;
-            if (!F.lsb) {
-                if (col < 3 * N) {
-                    const int a = col / N;   // f = fa e_a
-                    for (int j = 0; j < N; ++j) {
-                        const double4_32a p = kp[k * N + j];
-                        const double fa = fc[3 * j + a];
-                        const double ha = a == 0 ? p.y : (a == 1 ? p.z : p.w);
-                        const double s = p.x * ha * fa;
-                        wx += s * p.y;
-                        wy += s * p.z;
-                        wz += s * p.w;
-                        if (a == 0) wx += p.x * fa; else if (a == 1) wy += p.x * fa; else wz += p.x * fa;
-                    }
-                } else {
-                    for (int j = 0; j < N; ++j) {
-                        const double4_32a p = kp[k * N + j];
-                        const double gx = fc[3 * j], gy = fc[3 * j + 1], gz = fc[3 * j + 2];
-                        const double hf = p.y * gx + p.z * gy + p.w * gz;
-                        wx += p.x * (gx + p.y * hf);
-                        wy += p.x * (gy + p.z * hf);
-                        wz += p.x * (gz + p.w * hf);
-                    }
-                }
-            }
-        }
-        w[3 * i] = wx;
-        w[3 * i + 1] = wy;
-        w[3 * i + 2] = wz;
-    }
-    __syncthreads();
-    dev_rows(F, fb, us, w, cnt, false, B + fb.blk0 + static_cast<int64_t>(col0) * n, n);
-    (void)Tv;
 }
 
-// Batched LU with partial pivoting, column-major n x n blocks, n = 4 N.
-template <bool SMEM>
+// S[(k,b),(l,a)] of the fiber (rows and columns component-major, b N + k).
+__device__ __forceinline__ double s_entry(const FiberTable &F, const Fib &fb, int k, int b, int l, int a)
+{
+    if (k == l) {
+        const double *ml = F.mloc + 2 * (fb.n0 + k);
+        const double *t = F.t + 3 * (fb.n0 + k);
+        return (a == b ? ml[0] : 0.0) + ml[1] * t[b] * t[a];
+    }
+    if (F.lsb) return 0.0;
+    const double4_32a p = reinterpret_cast<const double4_32a *>(F.kp)[fb.kp0 + static_cast<int64_t>(k) * fb.N + l];
+    const double rb = b == 0 ? p.y : (b == 1 ? p.z : p.w);
+    const double ra = a == 0 ? p.y : (a == 1 ? p.z : p.w);
+    return p.x * ((a == b ? 1.0 : 0.0) + rb * ra);
+}
+
+// One 64 x 64 tile of C += A B with A and B supplied element-wise by the
+// callables; inner dimension K in chunks of kBK through shared memory.
+// Thread (cg, rg) = (tid % 16, tid / 16) owns rows 4 rg.., columns 4 cg...
+// B_KFAST: consecutive threads fetch consecutive inner indices of one B
+// column (B stored column by column), else consecutive columns.
+template <bool B_KFAST, class FA, class FB>
+__device__ __forceinline__ void tile_gemm(int K, FA a_of, FB b_of, double (&acc)[4][4], double *sA, double *sB)
+{
+    const int tid = threadIdx.x, cg = tid & 15, rg = tid >> 4;
+    for (int k0 = 0; k0 < K; k0 += kBK) {
+        for (int idx = tid; idx < kBT * kBK; idx += 256) {
+            const int r = idx / kBK, kk = idx - r * kBK;
+            sA[kk * (kBT + 1) + r] = k0 + kk < K ? a_of(r, k0 + kk) : 0.0;
+        }
+        for (int idx = tid; idx < kBK * kBT; idx += 256) {
+            int kk, cc;
+            if (B_KFAST) {
+                cc = idx / kBK;
+                kk = idx - cc * kBK;
+            } else {
+                kk = idx / kBT;
+                cc = idx - kk * kBT;
+            }
+            sB[kk * (kBT + 1) + cc] = k0 + kk < K ? b_of(k0 + kk, cc) : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < kBK; ++kk) {
+            double av[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = sA[kk * (kBT + 1) + 4 * rg + i];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) bv[jj] = sB[kk * (kBT + 1) + 4 * cg + jj];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fma(av[i], bv[jj], acc[i][jj]);
+        }
+        __syncthreads();
+    }
+}
+
+// W = S F for the sigma and tension columns; grid (M, row tiles of 3N,
+// column tiles): tiles below 3 ct_s hold the sigma columns of component
+// ap = tile / ct_s, the others the tension columns.
+__global__ void __launch_bounds__(256) k_build_w(FiberTable F)
+{
+    __shared__ double sA[kBK * (kBT + 1)], sB[kBK * (kBT + 1)];
+    const Fib fb(F, blockIdx.x);
+    const int N = fb.N;
+    const int r0 = blockIdx.y * kBT;
+    const int ct_s = (N - 4 + kBT - 1) / kBT, ct_t = (N + kBT - 1) / kBT;
+    const int ct = blockIdx.z;
+    if (r0 >= 3 * N || ct >= 3 * ct_s + ct_t) return;
+    const bool sig = ct < 3 * ct_s;
+    const int ap = sig ? ct / ct_s : 0;
+    const int j0 = sig ? (ct - ap * ct_s) * kBT : (ct - 3 * ct_s) * kBT;
+    const int ncol = sig ? N - 4 : N;
+    const double bend = -F.E * F.dt * fb.g * fb.g * fb.g * fb.g;
+    const double *Sig = fb.M_(fb.lay.Sig);
+    const double *ftau = F.ftau + fb.blk0 / 16 * 3;
+    double acc[4][4] = {};
+    if (sig) {
+        // inner l over N: S[(k,b),(l,ap)] Phi[l][j],  Phi = bend Sig
+        auto a_of = [&](int r, int l) -> double {
+            const int row = r0 + r;
+            if (row >= 3 * N || l >= N) return 0.0;
+            return s_entry(F, fb, row % N, row / N, l, ap);
+        };
+        auto b_of = [&](int l, int cc) -> double {
+            const int jj = j0 + cc;
+            return (l < N && jj < ncol) ? bend * Sig[l * N + jj] : 0.0;
+        };
+        tile_gemm<false>(N, a_of, b_of, acc, sA, sB);
+    } else {
+        // inner (a, l) over 3N: S[(k,b),(l,a)] F_tau[a][l][j]
+        auto a_of = [&](int r, int q) -> double {
+            const int row = r0 + r;
+            if (row >= 3 * N || q >= 3 * N) return 0.0;
+            return s_entry(F, fb, row % N, row / N, q % N, q / N);
+        };
+        auto b_of = [&](int q, int cc) -> double {
+            const int jj = j0 + cc;
+            return (q < 3 * N && jj < ncol) ? ftau[static_cast<int64_t>(q) * N + jj] : 0.0;
+        };
+        tile_gemm<false>(3 * N, a_of, b_of, acc, sA, sB);
+    }
+    const int tid = threadIdx.x, cg = tid & 15, rg = tid >> 4;
+    double *W = F.wsc + fb.blk0 / 4 * 3;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            const int row = r0 + 4 * rg + i, j = j0 + 4 * cg + jj;
+            if (row < 3 * N && j < ncol) {
+                const int col = sig ? ap * N + j : 3 * N + j;
+                W[static_cast<int64_t>(col) * 3 * N + row] = acc[i][jj];
+            }
+        }
+}
+
+// Rows that involve w, for all 4N columns: velocity rows (a, i < N-4):
+//   P_y w_a - [col is c_a,j] V_y[i][j];  tension rows i < N-2: X_s(z_i) . D_z w.
+// Grid (M, row tiles, column tiles of 4N): row tiles below 3 rt_v hold the
+// velocity rows of component a = tile / rt_v (inner N), the others tension
+// rows (inner 3N).
+__global__ void __launch_bounds__(256) k_build_rows(FiberTable F, double *__restrict__ B)
+{
+    __shared__ double sA[kBK * (kBT + 1)], sB[kBK * (kBT + 1)];
+    const Fib fb(F, blockIdx.x);
+    const int N = fb.N, n = 4 * N;
+    const int rt_v = (N - 4 + kBT - 1) / kBT, rt_t = (N - 2 + kBT - 1) / kBT;
+    const int rt = blockIdx.y, c0 = blockIdx.z * kBT;
+    if (rt >= 3 * rt_v + rt_t || c0 >= n) return;
+    const bool vel = rt < 3 * rt_v;
+    const int a = vel ? rt / rt_v : 0;
+    const int i0 = vel ? (rt - a * rt_v) * kBT : (rt - 3 * rt_v) * kBT;
+    const int nrow = vel ? N - 4 : N - 2;
+    const double *W = F.wsc + fb.blk0 / 4 * 3;
+    const double *Py = fb.M_(fb.lay.Py), *Vy = fb.M_(fb.lay.Vy), *Dz = fb.M_(fb.lay.Dz);
+    const double *tz = F.tz + 3 * fb.z0;
+    double acc[4][4] = {};
+    auto b_of_w = [&](int q, int cc) -> double {   // W[col][q], q component-major
+        const int col = c0 + cc;
+        return col < n ? W[static_cast<int64_t>(col) * 3 * N + q] : 0.0;
+    };
+    if (vel) {
+        auto a_of = [&](int r, int k) -> double {
+            const int i = i0 + r;
+            return (i < nrow && k < N) ? Py[i * N + k] : 0.0;
+        };
+        auto b_of = [&](int k, int cc) -> double { return b_of_w(a * N + k, cc); };
+        tile_gemm<true>(N, a_of, b_of, acc, sA, sB);
+    } else {
+        auto a_of = [&](int r, int q) -> double {
+            const int i = i0 + r;
+            if (i >= nrow || q >= 3 * N) return 0.0;
+            const int b = q / N, k = q - b * N;
+            return tz[3 * i + b] * Dz[i * N + k];
+        };
+        tile_gemm<true>(3 * N, a_of, b_of_w, acc, sA, sB);
+    }
+    const int tid = threadIdx.x, cg = tid & 15, rg = tid >> 4;
+    double *Bm = B + fb.blk0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            const int r = i0 + 4 * rg + i, col = c0 + 4 * cg + jj;
+            if (r >= nrow || col >= n) continue;
+            double v = acc[i][jj];
+            int row;
+            if (vel) {
+                row = a * N + r;
+                if (col < 3 * N && col / N == a) v -= Vy[r * N + (col - a * N)];
+            } else {
+                row = 3 * N + r;
+            }
+            Bm[static_cast<int64_t>(col) * n + row] = v;
+        }
+}
+
+// Rows without w: the free-end rows (second and third derivative of V_a at
+// alpha = +1 and -1, Eq. bc-free) and T(+1), T(-1); grid M.
+__global__ void __launch_bounds__(256) k_build_direct(FiberTable F, double *__restrict__ B)
+{
+    const Fib fb(F, blockIdx.x);
+    const int N = fb.N, n = 4 * N;
+    const double *V2 = fb.M_(fb.lay.V2), *V3 = fb.M_(fb.lay.V3), *Tn = fb.M_(fb.lay.Tn);
+    double *Bm = B + fb.blk0;
+    for (int idx = threadIdx.x; idx < 14 * n; idx += blockDim.x) {
+        const int rr = idx / n, col = idx - rr * n;
+        double v = 0.0;
+        int row;
+        if (rr < 12) {
+            const int a = rr / 4, q = rr % 4;   // row a N + N-4 + q
+            row = a * N + N - 4 + q;
+            if (col < 3 * N && col / N == a) {
+                const int j = col - a * N;
+                v = q < 2 ? V2[q * N + j] : V3[(q - 2) * N + j];
+            }
+        } else {
+            const int node = rr == 12 ? 0 : N - 1;
+            row = 3 * N + N - 2 + (rr - 12);
+            if (col >= 3 * N) v = Tn[node * N + (col - 3 * N)];
+        }
+        Bm[static_cast<int64_t>(col) * n + row] = v;
+    }
+}
+
+// Batched LU with partial pivoting of the column-major n x n fiber blocks
+// (n = 4 N), one CTA per fiber, blocked right-looking: for each panel of BW
+// columns,
+//   1. factor the (n - k0) x BW panel in shared memory (pivot search, row
+//      swap, scaling and rank-1 updates within the panel);
+//   2. apply the panel's row swaps to the other columns;
+//   3. U12 = L11^-1 A12 (unit lower triangle of the panel);
+//   4. A22 -= L21 U12 in 64 x 64 tiles, 4 x 4 register tiles per thread.
+// The trailing matrix is read and written once per panel instead of once per
+// column; the pivots (and so the factors) are those of the column-by-column
+// algorithm.  piv[k] = p: rows k and p were exchanged at step k.
+constexpr int kLuTC = 64;   // trailing-update tile width
+
+template <int BW>
 __global__ void __launch_bounds__(256) k_lu(FiberTable F, double *__restrict__ B, int *__restrict__ piv,
                                             int *__restrict__ status)
 {
+    constexpr int TC = kLuTC, UL = TC + 1;
     extern __shared__ double lsm[];
     __shared__ double rv[8];
     __shared__ int ri[8];
-    __shared__ int s_p;
+    __shared__ int s_piv[BW];
     const Fib fb(F, blockIdx.x);
     const int n = 4 * fb.N;
-    double *Ag = B + fb.blk0;
-    double *A = SMEM ? lsm : Ag;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    if (SMEM) {
-        for (int i = tid; i < n * n; i += nt) A[i] = Ag[i];
-        __syncthreads();
-    }
-    for (int k = 0; k < n; ++k) {
-        double best = -1.0;
-        int bi = k;
-        for (int i = k + tid; i < n; i += nt) {
-            const double v = fabs(A[static_cast<int64_t>(k) * n + i]);
-            if (v > best) {
-                best = v;
-                bi = i;
-            }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ov > best || (ov == best && oi < bi)) {
-                best = ov;
-                bi = oi;
-            }
-        }
-        if ((tid & 31) == 0) {
-            rv[tid >> 5] = best;
-            ri[tid >> 5] = bi;
+    double *A = B + fb.blk0;
+    int *pv = piv + fb.u0;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    double *P = lsm;                                   // panel, column-major, ld m
+    double *U = lsm + static_cast<size_t>(n) * BW;     // U12 tile [BW][UL]
+    for (int k0 = 0; k0 < n; k0 += BW) {
+        const int kb = min(BW, n - k0), m = n - k0;
+        for (int idx = tid; idx < kb * m; idx += 256) {
+            const int c = idx / m, r = idx - c * m;
+            P[idx] = A[static_cast<int64_t>(k0 + c) * n + k0 + r];
         }
         __syncthreads();
-        if (tid == 0) {
-            double b = rv[0];
-            int p = ri[0];
-            for (int wv = 1; wv < nt / 32; ++wv)
-                if (rv[wv] > b || (rv[wv] == b && ri[wv] < p)) {
-                    b = rv[wv];
-                    p = ri[wv];
+        // 1. the panel
+        for (int j = 0; j < kb; ++j) {
+            double best = -1.0;
+            int bi = j;
+            for (int r = j + tid; r < m; r += 256) {
+                const double v = fabs(P[j * m + r]);
+                if (v > best) {
+                    best = v;
+                    bi = r;
                 }
-            s_p = p;
-            piv[fb.u0 + k] = p;
-            if (!(b > 0.0)) atomicOr(status, DEV_ERR_NUMERIC);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ov > best || (ov == best && oi < bi)) {
+                    best = ov;
+                    bi = oi;
+                }
+            }
+            if (lane == 0) {
+                rv[wid] = best;
+                ri[wid] = bi;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                double b = rv[0];
+                int p = ri[0];
+                for (int wv = 1; wv < 8; ++wv)
+                    if (rv[wv] > b || (rv[wv] == b && ri[wv] < p)) {
+                        b = rv[wv];
+                        p = ri[wv];
+                    }
+                s_piv[j] = p;
+                pv[k0 + j] = k0 + p;
+                if (!(b > 0.0)) atomicOr(status, DEV_ERR_NUMERIC);
+            }
+            __syncthreads();
+            const int p = s_piv[j];
+            if (p != j)
+                for (int c = tid; c < kb; c += 256) {
+                    const double t = P[c * m + j];
+                    P[c * m + j] = P[c * m + p];
+                    P[c * m + p] = t;
+                }
+            __syncthreads();
+            const double pvv = P[j * m + j];
+            const double inv = pvv != 0.0 ? 1.0 / pvv : 0.0;
+            for (int r = j + 1 + tid; r < m; r += 256) P[j * m + r] *= inv;
+            __syncthreads();
+            const int rows = m - j - 1, cols = kb - j - 1;
+            for (int idx = tid; idx < rows * cols; idx += 256) {
+                const int c = j + 1 + idx / rows, r = j + 1 + idx % rows;
+                P[c * m + r] -= P[j * m + r] * P[c * m + j];
+            }
+            __syncthreads();
+        }
+        for (int idx = tid; idx < kb * m; idx += 256) {
+            const int c = idx / m, r = idx - c * m;
+            A[static_cast<int64_t>(k0 + c) * n + k0 + r] = P[idx];
+        }
+        // 2. the panel's swaps on the columns left and right of it
+        for (int col = tid; col < n; col += 256) {
+            if (col >= k0 && col < k0 + kb) continue;
+            double *Ac = A + static_cast<int64_t>(col) * n + k0;
+            for (int j = 0; j < kb; ++j) {
+                const int p = s_piv[j];
+                if (p != j) {
+                    const double t = Ac[j];
+                    Ac[j] = Ac[p];
+                    Ac[p] = t;
+                }
+            }
         }
         __syncthreads();
-        const int p = s_p;
-        if (p != k)
-            for (int j = tid; j < n; j += nt) {
-                const int64_t cj = static_cast<int64_t>(j) * n;
-                const double tmp = A[cj + k];
-                A[cj + k] = A[cj + p];
-                A[cj + p] = tmp;
+        const int nr = n - k0 - kb;
+        if (nr > 0) {
+            // 3. U12 = L11^-1 A12, one column per thread
+            for (int col = k0 + kb + tid; col < n; col += 256) {
+                double *Ac = A + static_cast<int64_t>(col) * n + k0;   // this thread's column only
+                for (int c = 0; c + 1 < kb; ++c) {
+                    const double uc = Ac[c];
+                    for (int r = c + 1; r < kb; ++r) Ac[r] = fma(-P[c * m + r], uc, Ac[r]);
+                }
             }
-        __syncthreads();
-        const double pv = A[static_cast<int64_t>(k) * n + k];
-        const double inv = pv != 0.0 ? 1.0 / pv : 0.0;
-        for (int i = k + 1 + tid; i < n; i += nt) A[static_cast<int64_t>(k) * n + i] *= inv;
-        __syncthreads();
-        const int m2 = n - k - 1;
-        for (int idx = tid; idx < m2 * m2; idx += nt) {
-            const int j = k + 1 + idx / m2, i = k + 1 + idx % m2;
-            A[static_cast<int64_t>(j) * n + i] -=
-                A[static_cast<int64_t>(k) * n + i] * A[static_cast<int64_t>(j) * n + k];
+            __syncthreads();
+            // 4. A22 -= L21 U12
+            const int cg = tid & 15, rg = tid >> 4;
+            double *A22 = A + static_cast<int64_t>(k0 + kb) * n + k0 + kb;
+            for (int c0 = 0; c0 < nr; c0 += TC) {
+                const int tcn = min(TC, nr - c0);
+                for (int idx = tid; idx < kb * TC; idx += 256) {
+                    const int cc = idx / kb, kk = idx - cc * kb;
+                    U[kk * UL + cc] = cc < tcn ? A[static_cast<int64_t>(k0 + kb + c0 + cc) * n + k0 + kk] : 0.0;
+                }
+                __syncthreads();
+                for (int r0 = 0; r0 < nr; r0 += 64) {
+                    const int rb = r0 + 4 * rg, cb = c0 + 4 * cg;
+                    double acc[4][4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int jj = 0; jj < 4; ++jj)
+                            acc[i][jj] = (rb + i < nr && cb + jj < nr)
+                                             ? A22[static_cast<int64_t>(cb + jj) * n + rb + i] : 0.0;
+                    for (int kk = 0; kk < kb; ++kk) {
+                        double a[4], w[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) a[i] = rb + i < nr ? P[kk * m + kb + rb + i] : 0.0;
+#pragma unroll
+                        for (int jj = 0; jj < 4; ++jj) w[jj] = U[kk * UL + 4 * cg + jj];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+#pragma unroll
+                            for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fma(-a[i], w[jj], acc[i][jj]);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int jj = 0; jj < 4; ++jj)
+                            if (rb + i < nr && cb + jj < nr)
+                                A22[static_cast<int64_t>(cb + jj) * n + rb + i] = acc[i][jj];
+                }
+                __syncthreads();
+            }
         }
         __syncthreads();
     }
-    if (SMEM)
-        for (int i = tid; i < n * n; i += nt) Ag[i] = A[i];
 }
 
+// x = P^-1 in with the factors of k_lu, one CTA per fiber: row exchanges, then
+// blocked forward (unit L) and backward (U) substitution -- one warp solves
+// each BW x BW diagonal block from shared memory, all threads update the
+// remaining entries with the block's columns (coalesced column reads).
+template <int BW>
 __global__ void __launch_bounds__(256) k_lu_solve(FiberTable F, const double *__restrict__ B,
                                                   const int *__restrict__ piv,
                                                   const double *__restrict__ in,
                                                   double *__restrict__ out)
 {
+    constexpr int DL = BW + 1;
     extern __shared__ double ssm[];
     const Fib fb(F, blockIdx.x);
     const int n = 4 * fb.N;
     const double *A = B + fb.blk0;
-    double *y = ssm;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int i = tid; i < n; i += nt) y[i] = in[fb.u0 + i];
+    double *y = ssm, *D = ssm + n;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < n; i += blockDim.x) y[i] = in[fb.u0 + i];
     __syncthreads();
     if (tid == 0)
         for (int k = 0; k < n; ++k) {
             const int p = piv[fb.u0 + k];
             if (p != k) {
-                const double tmp = y[k];
+                const double t = y[k];
                 y[k] = y[p];
-                y[p] = tmp;
+                y[p] = t;
             }
         }
     __syncthreads();
-    for (int k = 0; k < n - 1; ++k) {
-        const double yk = y[k];
-        const double *col = A + static_cast<int64_t>(k) * n;
-        for (int i = k + 1 + tid; i < n; i += nt) y[i] -= col[i] * yk;
+    for (int j0 = 0; j0 < n; j0 += BW) {
+        const int jb = min(BW, n - j0);
+        for (int idx = tid; idx < jb * jb; idx += blockDim.x) {
+            const int c = idx / jb, r = idx - c * jb;
+            D[c * DL + r] = A[static_cast<int64_t>(j0 + c) * n + j0 + r];
+        }
+        __syncthreads();
+        if (tid < 32) {
+            double v = tid < jb ? y[j0 + tid] : 0.0;
+            for (int c = 0; c < jb; ++c) {
+                const double yc = __shfl_sync(0xffffffffu, v, c);
+                if (tid > c && tid < jb) v -= D[c * DL + tid] * yc;
+            }
+            if (tid < jb) y[j0 + tid] = v;
+        }
+        __syncthreads();
+        for (int i = j0 + jb + tid; i < n; i += blockDim.x) {
+            double sum = y[i];
+            for (int c = 0; c < jb; ++c) sum -= A[static_cast<int64_t>(j0 + c) * n + i] * y[j0 + c];
+            y[i] = sum;
+        }
         __syncthreads();
     }
-    for (int k = n - 1; k >= 0; --k) {
-        const double *col = A + static_cast<int64_t>(k) * n;
-        if (tid == 0) y[k] = col[k] != 0.0 ? y[k] / col[k] : 0.0;
+    for (int j1 = n; j1 > 0; j1 -= BW) {
+        const int j0 = max(0, j1 - BW), jb = j1 - j0;
+        for (int idx = tid; idx < jb * jb; idx += blockDim.x) {
+            const int c = idx / jb, r = idx - c * jb;
+            D[c * DL + r] = A[static_cast<int64_t>(j0 + c) * n + j0 + r];
+        }
         __syncthreads();
-        const double yk = y[k];
-        for (int i = tid; i < k; i += nt) y[i] -= col[i] * yk;
+        if (tid < 32) {
+            double v = tid < jb ? y[j0 + tid] : 0.0;
+            for (int c = jb - 1; c >= 0; --c) {
+                if (tid == c) {
+                    const double d = D[c * DL + c];
+                    v = d != 0.0 ? v / d : 0.0;
+                }
+                const double yc = __shfl_sync(0xffffffffu, v, c);
+                if (tid < c) v -= D[c * DL + tid] * yc;
+            }
+            if (tid < jb) y[j0 + tid] = v;
+        }
+        __syncthreads();
+        for (int i = tid; i < j0; i += blockDim.x) {
+            double sum = y[i];
+            for (int c = 0; c < jb; ++c) sum -= A[static_cast<int64_t>(j0 + c) * n + i] * y[j0 + c];
+            y[i] = sum;
+        }
         __syncthreads();
     }
-    for (int i = tid; i < n; i += nt) out[fb.u0 + i] = y[i];
+    for (int i = tid; i < n; i += blockDim.x) out[fb.u0 + i] = y[i];
 }
 
 __global__ void __launch_bounds__(128) k_update(FiberTable F, const double *__restrict__ u,
@@ -588,15 +857,6 @@ __global__ void __launch_bounds__(128) k_update(FiberTable F, const double *__re
             T[fb.n0 + k] = s;
         }
     }
-}
-
-int build_cols(int N)
-{
-    // columns per CTA so that 14 N doubles per column stay within ~96 KB
-    int nb = static_cast<int>(96 * 1024 / (14 * 8 * static_cast<int64_t>(N)));
-    if (nb < 1) nb = 1;
-    if (nb > 16) nb = 16;
-    return nb;
 }
 
 }  // namespace
@@ -632,28 +892,36 @@ fs_status launch_rows(fs_ctx *c, const double *u, const double *f, const double 
 fs_status launch_block_build(fs_ctx *c)
 {
     if (c->M == 0) return FS_OK;
-    const int nb = build_cols(c->max_N);
-    const size_t sm = static_cast<size_t>(14) * nb * c->max_N * sizeof(double);
-    if (sm > 48 * 1024)
-        FS_CUDA(cudaFuncSetAttribute(k_block_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     static_cast<int>(sm)));
-    const dim3 grid(c->M, (4 * c->max_N + nb - 1) / nb);
-    k_block_build<<<grid, 256, sm, c->stream>>>(c->table(), c->d_B, nb);
+    const int N = c->max_N;
+    const FiberTable T = c->table();
+    k_build_ftau<<<dim3(c->M, 3), 256, 0, c->stream>>>(T);
+    FS_LAUNCH_CHECK();
+    const int ct = 3 * ((N - 4 + kBT - 1) / kBT) + (N + kBT - 1) / kBT;
+    k_build_w<<<dim3(c->M, (3 * N + kBT - 1) / kBT, ct), 256, 0, c->stream>>>(T);
+    FS_LAUNCH_CHECK();
+    const int rt = 3 * ((N - 4 + kBT - 1) / kBT) + (N - 2 + kBT - 1) / kBT;
+    k_build_rows<<<dim3(c->M, rt, (4 * N + kBT - 1) / kBT), 256, 0, c->stream>>>(T, c->d_B);
+    FS_LAUNCH_CHECK();
+    k_build_direct<<<c->M, 256, 0, c->stream>>>(T, c->d_B);
     FS_LAUNCH_CHECK();
     return FS_OK;
 }
 
+// Panel width of the blocked LU: 32 while the panel (n x 32 doubles) and the
+// trailing tile fit comfortably in shared memory, else 16.
+int lu_panel(int n) { return n <= 640 ? 32 : 16; }
+
 fs_status launch_lu_factor(fs_ctx *c)
 {
     if (c->M == 0) return FS_OK;
-    const int n = 4 * c->max_N;
-    const size_t sm = static_cast<size_t>(n) * n * sizeof(double);
-    if (sm <= 200 * 1024) {
-        FS_CUDA(cudaFuncSetAttribute(k_lu<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     static_cast<int>(sm)));
-        k_lu<true><<<c->M, 256, sm, c->stream>>>(c->table(), c->d_B, c->d_piv, c->d_status);
+    const int n = 4 * c->max_N, bw = lu_panel(n);
+    const size_t sm = (static_cast<size_t>(n) * bw + static_cast<size_t>(bw) * (kLuTC + 1)) * sizeof(double);
+    if (bw == 32) {
+        FS_CUDA(cudaFuncSetAttribute(k_lu<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
+        k_lu<32><<<c->M, 256, sm, c->stream>>>(c->table(), c->d_B, c->d_piv, c->d_status);
     } else {
-        k_lu<false><<<c->M, 256, 0, c->stream>>>(c->table(), c->d_B, c->d_piv, c->d_status);
+        FS_CUDA(cudaFuncSetAttribute(k_lu<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
+        k_lu<16><<<c->M, 256, sm, c->stream>>>(c->table(), c->d_B, c->d_piv, c->d_status);
     }
     FS_LAUNCH_CHECK();
     return FS_OK;
@@ -662,8 +930,8 @@ fs_status launch_lu_factor(fs_ctx *c)
 fs_status launch_lu_solve(fs_ctx *c, const double *in, double *out)
 {
     if (c->M == 0) return FS_OK;
-    const size_t sm = static_cast<size_t>(4 * c->max_N) * sizeof(double);
-    k_lu_solve<<<c->M, 256, sm, c->stream>>>(c->table(), c->d_B, c->d_piv, in, out);
+    const size_t sm = (static_cast<size_t>(4 * c->max_N) + 32 * 33) * sizeof(double);
+    k_lu_solve<32><<<c->M, 256, sm, c->stream>>>(c->table(), c->d_B, c->d_piv, in, out);
     FS_LAUNCH_CHECK();
     return FS_OK;
 }

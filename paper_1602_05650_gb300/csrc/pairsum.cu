@@ -670,13 +670,18 @@ __global__ void k_pack_ff(const double *__restrict__ xyz, const double *__restri
 }
 
 // ------------------------------------------------------------------ helpers
-// Midpoint of the bounding box of n points (one CTA).
-__global__ void __launch_bounds__(512) k_bbox_center(const double *__restrict__ p, int64_t n,
-                                                     double *__restrict__ center)
+// Midpoint of the bounding box of n points, in two passes: kBoxParts CTAs
+// reduce strided slices to partial boxes part[cta][6], then one CTA combines
+// them (min / max are exact, so the result does not depend on the split).
+constexpr int kBoxParts = 128;
+
+__global__ void __launch_bounds__(256) k_bbox_part(const double *__restrict__ p, int64_t n,
+                                                   double *__restrict__ part)
 {
-    __shared__ double smin[3][16], smax[3][16];
+    __shared__ double sm[6][8];
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
         for (int a = 0; a < 3; ++a) {
             const double v = p[3 * i + a];
             lo[a] = fmin(lo[a], v);
@@ -690,19 +695,28 @@ __global__ void __launch_bounds__(512) k_bbox_center(const double *__restrict__ 
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (l == 0)
         for (int a = 0; a < 3; ++a) {
-            smin[a][w] = lo[a];
-            smax[a][w] = hi[a];
+            sm[a][w] = lo[a];
+            sm[3 + a][w] = hi[a];
         }
     __syncthreads();
-    if (threadIdx.x < 3) {
-        const int a = threadIdx.x;
-        double mn = INFINITY, mx = -INFINITY;
-        for (int k = 0; k < static_cast<int>(blockDim.x >> 5); ++k) {
-            mn = fmin(mn, smin[a][k]);
-            mx = fmax(mx, smax[a][k]);
-        }
-        center[a] = (n > 0 && mn <= mx) ? 0.5 * (mn + mx) : 0.0;
+    if (threadIdx.x < 6) {
+        const int q = threadIdx.x;
+        double v = q < 3 ? INFINITY : -INFINITY;
+        for (int k = 0; k < static_cast<int>(blockDim.x >> 5); ++k) v = q < 3 ? fmin(v, sm[q][k]) : fmax(v, sm[q][k]);
+        part[blockIdx.x * 6 + q] = v;
     }
+}
+
+__global__ void k_bbox_center(const double *__restrict__ part, int parts, int64_t n, double *__restrict__ center)
+{
+    const int a = threadIdx.x;
+    if (a >= 3) return;
+    double mn = INFINITY, mx = -INFINITY;
+    for (int k = 0; k < parts; ++k) {
+        mn = fmin(mn, part[k * 6 + a]);
+        mx = fmax(mx, part[k * 6 + 3 + a]);
+    }
+    center[a] = (n > 0 && mn <= mx) ? 0.5 * (mn + mx) : 0.0;
 }
 
 // Pack sources: arrays [0] position (hi), [1] density x weight, [2] normal, [last] lo.
@@ -884,7 +898,7 @@ size_t pairsum_scratch_bytes(int kind, int64_t n_src, int64_t n_tgt, int sum_pre
         const SumPlan p = plan_pairsum(kind, n_src, n_tgt, sum_prec, hilo, shape_override, slots);
         const size_t packed = static_cast<size_t>(p.n_arr) * static_cast<size_t>(n_src) * p.v4;
         const size_t part = static_cast<size_t>(p.grid + p.nb) * static_cast<size_t>(p.tb) * 3 * sizeof(double);
-        most = std::max(most, 4 * 256 + packed + part + 1024);
+        most = std::max(most, 4 * 256 + 6 * kBoxParts * sizeof(double) + packed + part + 1024);
     }
     return most;
 }
@@ -921,6 +935,7 @@ fs_status pairsum(const PairSumArgs &a, void *scratch, size_t scratch_bytes, int
     const SumPlan p = plan_pairsum(a.kind, a.n_src, a.n_tgt, prec, hilo, a.shape_override, 0);
     Carve cv(scratch, scratch_bytes);
     double *center = cv.take<double>(4);
+    double *box = cv.take<double>(6 * kBoxParts);
     void *packed = cv.take<unsigned char>(static_cast<size_t>(p.n_arr) * a.n_src * p.v4);
     const int4 *work = nullptr;
     unsigned grid = static_cast<unsigned>(p.grid);
@@ -952,7 +967,9 @@ fs_status pairsum(const PairSumArgs &a, void *scratch, size_t scratch_bytes, int
         set_error("pairsum: scratch too small (%zu > %zu bytes)", cv.used, scratch_bytes);
         return FS_EINVAL;
     }
-    k_bbox_center<<<1, 512, 0, st>>>(a.src_xyz, a.n_src, center);
+    k_bbox_part<<<kBoxParts, 256, 0, st>>>(a.src_xyz, a.n_src, box);
+    FS_LAUNCH_CHECK();
+    k_bbox_center<<<1, 32, 0, st>>>(box, kBoxParts, a.n_src, center);
     FS_LAUNCH_CHECK();
     const unsigned pb = static_cast<unsigned>((a.n_src + 255) / 256);
     const int lo_slot = hilo ? p.n_arr - 1 : 0;

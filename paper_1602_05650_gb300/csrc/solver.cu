@@ -647,6 +647,10 @@ fs_status context_init(fs_ctx *c, int S, const int32_t *fps, int M, const int32_
     FS_TRY(dalloc(c, &c->d_bc, 12 * M));
     FS_TRY(dalloc(c, &c->d_kp, 4 * c->n_kp));
     FS_TRY(dalloc(c, &c->d_B, c->n_blk));
+    FS_TRY(dalloc(c, &c->d_ftau, c->n_blk / 16 * 3));
+    FS_TRY(dalloc(c, &c->d_wsc, c->n_blk / 4 * 3));
+    // the p columns of w are never written: they stay zero (f = 0 there)
+    FS_CUDA(cudaMemsetAsync(c->d_wsc, 0, static_cast<size_t>(c->n_blk / 4 * 3) * sizeof(double), c->stream));
     FS_TRY(dalloc(c, &c->d_piv, c->n_fib_unk));
     FS_TRY(dalloc(c, &c->d_V, 3 * P));
     FS_TRY(dalloc(c, &c->d_T, P));
@@ -750,7 +754,8 @@ size_t estimate_bytes(int M, const int32_t *ppf, int n_surf, const fs_options &o
     add(M * sizeof(int64_t));
     add(ops * d);
     add(P * sizeof(int2));
-    for (int64_t k : {3 * P, int64_t(M), 3 * P, 3 * P, 3 * n_z, 3 * P, P, 2 * P, 12 * int64_t(M), 4 * n_kp, n_blk})
+    for (int64_t k : {3 * P, int64_t(M), 3 * P, 3 * P, 3 * n_z, 3 * P, P, 2 * P, 12 * int64_t(M), 4 * n_kp, n_blk,
+                      n_blk / 16 * 3, n_blk / 4 * 3})
         add(k * d);
     add(n_fib_unk * sizeof(int));
     for (int64_t k : {3 * P, P, 3 * P, 3 * P, 3 * P}) add(k * d);
@@ -801,7 +806,7 @@ void context_free(fs_ctx *c)
     if (c->stream) cudaStreamSynchronize(c->stream);
     void *ptrs[] = {c->d_status, c->d_N, c->d_node_ptr, c->d_unk_ptr, c->d_blk_ptr, c->d_kp_ptr,
                     c->d_z_ptr, c->d_ops_off, c->d_ops, c->d_excl, c->d_X, c->d_L, c->d_fext,
-                    c->d_t, c->d_tz, c->d_fknown, c->d_W, c->d_mloc, c->d_bc, c->d_kp, c->d_B,
+                    c->d_t, c->d_tz, c->d_fknown, c->d_W, c->d_mloc, c->d_bc, c->d_kp, c->d_B, c->d_ftau, c->d_wsc,
                     c->d_piv, c->d_V, c->d_T, c->d_f, c->d_wf, c->d_ubar, c->d_basis, c->d_b,
                     c->d_x, c->d_r, c->d_w, c->d_e, c->d_pb, c->d_obasis, c->d_oz, c->d_oh, c->d_opart, c->d_ow, c->d_or, c->d_work, c->d_ich, c->d_isch, c->d_ikk, c->d_och, c->d_osch, c->d_okk, c->d_h, c->d_part, c->surf.y, c->surf.nrm,
                     c->surf.w, c->surf.diag, c->d_usurf, c->surf.A, c->surf.tmp, c->surf.flux, c->surf.excl};
@@ -845,6 +850,8 @@ fs::FiberTable fs_ctx::table() const
     F.mloc = d_mloc;
     F.bc = d_bc;
     F.kp = d_kp;
+    F.ftau = d_ftau;
+    F.wsc = d_wsc;
     return F;
 }
 
