@@ -34,7 +34,8 @@ import workloads as wl  # noqa: E402
 # and the float-float evaluation of the Stokeslet (218, FMA = 2, counted from
 # the float-float formula; the rsqrt seed is on the SFU)
 FLOPS_PER_PAIR = {"stokeslet": 27.0, "stresslet": 31.0, "stokeslet_ff": 218.0}
-KS_NAMES = ["stokeslet_fp32", "stokeslet_fp64", "stresslet_fp32", "stresslet_fp64", "stokeslet_ff"]
+KS_NAMES = ["stokeslet_fp32", "stokeslet_fp64", "stresslet_fp32", "stresslet_fp64", "stokeslet_ff",
+            "stokeslet_fp32_plain"]
 WORKLOAD = "cloud-1024x64: 1,024 curved fibers x 64 Chebyshev points (65,536 points), [0,40]^3"
 
 
@@ -168,9 +169,11 @@ def run_kernel(args, ws, rank, local, fs, torch, dist):
     dev = torch.device("cuda", local)
     s = wl.cfg_cloud_mixed(seed=rank)
     P = args.points or s.n_points
-    prec = {"stokeslet_fp32": fs.FS_SUM_FP32, "stokeslet_fp64": fs.FS_SUM_FP64, "stokeslet_ff": 2}[args.kernel]
+    prec = {"stokeslet_fp32": fs.FS_SUM_FP32, "stokeslet_fp64": fs.FS_SUM_FP64, "stokeslet_ff": fs.FS_SUM_FF,
+            "stokeslet_fp32_plain": fs.FS_SUM_FP32_PLAIN}[args.kernel]
     opt = fs.fs_options_default()
     opt.profile = 1
+    opt.tile_override = args.tile
     stream = torch.cuda.Stream(device=dev)
     h = fs.fs_create([], s.mu, s.eps, s.E, s.dt, options=opt, stream=stream)
     X = torch.tensor(s.X[:P], dtype=torch.float64, device=dev)
@@ -183,12 +186,13 @@ def run_kernel(args, ws, rank, local, fs, torch, dist):
     fs.fs_kernel_stats(h, reset=True)
     for _ in range(args.steps):
         fs.fs_stokeslet_apply(h, X, Wf, X, out, fid, fid, prec)
-    st = fs.fs_kernel_stats(h, reset=True)[{fs.FS_SUM_FP32: 0, fs.FS_SUM_FP64: 1, 2: 4}[prec]]
+    st = fs.fs_kernel_stats(h, reset=True)[{fs.FS_SUM_FP32: 0, fs.FS_SUM_FP64: 1, fs.FS_SUM_FF: 4,
+                                            fs.FS_SUM_FP32_PLAIN: 5}[prec]]
     fs.fs_destroy(h)
     if rank == 0:
         pairs_s = st[2] / (st[1] * 1e-3)
         fpp = FLOPS_PER_PAIR["stokeslet_ff" if args.kernel == "stokeslet_ff" else "stokeslet"]
-        print(json.dumps({"kernel": args.kernel, "points": P, "launches": st[0],
+        print(json.dumps({"kernel": args.kernel, "tile": args.tile, "points": P, "launches": st[0],
                           "ms_per_launch": st[1] / st[0], "pairs_per_s": pairs_s,
                           "tflops": fpp * pairs_s / 1e12}), flush=True)
 
@@ -264,7 +268,8 @@ def main():
                     help="GMRES iterations assumed for the reference arm's extrapolation")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--kernel", choices=["stokeslet_fp32", "stokeslet_fp64", "stokeslet_ff"], default=None,
+    ap.add_argument("--kernel", choices=["stokeslet_fp32", "stokeslet_fp64", "stokeslet_ff", "stokeslet_fp32_plain"],
+                    default=None,
                     help="time only the direct-sum kernel on the cloud (fs_stokeslet_apply)")
     ap.add_argument("--points", type=int, default=0,
                     help="--kernel: use the first P points of the cloud (0 = all)")
@@ -272,6 +277,9 @@ def main():
                     help="relative tolerance of the inner FP32-far-field solves (0 = library default)")
     ap.add_argument("--no-relax", action="store_true",
                     help="every outer direction on the float-float far field (no inexact-Krylov relaxation)")
+    ap.add_argument("--tile", type=int, default=0,
+                    help="far-field launch shape id (0 = default; 1..3 = targets per thread FP32 2/4/8, "
+                         "float-float 1/2/4)")
     ap.add_argument("--serve", type=int, default=0,
                     help="serving mode: number of independent requests (0 = the step benchmark)")
     ap.add_argument("--rate", type=float, default=0.0, help="--serve: Poisson arrival rate per s (0 = burst)")
@@ -311,6 +319,7 @@ def main():
         opt.inner_tol = args.inner_tol
     if args.no_relax:
         opt.relax = 0
+    opt.tile_override = args.tile
     h = fs.fs_create(s.n_per_fiber, s.mu, s.eps, s.E, s.dt, options=opt, stream=stream)
     X = torch.tensor(s.X, dtype=torch.float64, device=dev)
     L = torch.tensor(s.L, dtype=torch.float64, device=dev)
@@ -399,8 +408,8 @@ def main():
     fp32_peak = fs.fs_probe_fma(1)
     fp64_peak = fs.fs_probe_fma(0)
     per_class = {KS_NAMES[k]: {"launches": stats[k][0], "ms": stats[k][1], "pairs": stats[k][2]}
-                 for k in range(5)}
-    dom = max(range(5), key=lambda k: stats[k][1])
+                 for k in range(6)}
+    dom = max(range(6), key=lambda k: stats[k][1])
     launches_d, total_ms, pairs = stats[dom]
     kind = "stresslet" if dom in (2, 3) else ("stokeslet_ff" if dom == 4 else "stokeslet")
     is64 = dom in (1, 3)

@@ -54,9 +54,12 @@ typedef enum {
     FS_SUM_FP64 = 0, /* direct sums in FP64 arithmetic */
     FS_SUM_FP32 = 1, /* FP32 arithmetic: hi/lo-split coordinates, FP32 tile sums,
                         compensated (TwoSum) accumulation across tiles, FP64 output */
-    FS_SUM_FF = 2    /* float-float ("double-single") arithmetic on the FP32 pipe,
+    FS_SUM_FF = 2,   /* float-float ("double-single") arithmetic on the FP32 pipe,
                         ~2^-44 relative rounding per pair (Stokeslet; stresslet
                         sums requested in FS_SUM_FF run in FP64) */
+    FS_SUM_FP32_PLAIN = 3 /* FS_SUM_FP32 without the lo parts of the coordinates:
+                        ~15% faster, coordinate rounding ~2^-24 of the extent of
+                        the sources (relative to their bounding-box centre) */
 } fs_sum_precision;
 
 /* Spherical no-slip periphery (Sec. 2.1, Eq. main-cortex-density) discretised
@@ -79,8 +82,9 @@ typedef struct {
     int32_t restart;        /* GMRES restart length (default 60, at most 250) */
     int32_t max_refine;     /* FS_MIXED, free space, relax = 1: at most this many float-float
                                true residuals per step (default 6; normally one is used) */
-    double inner_tol;       /* FS_MIXED: relative tolerance of each inner FP32-far-field
-                               GMRES solve (default 1e-5) */
+    double inner_tol;       /* FS_MIXED: relative tolerance of the FP32-far-field GMRES
+                               solves (the first stage of the free-space step, the inner
+                               solves of the flexible GMRES) (default 1e-6) */
     double delta_over_L;    /* regularisation delta of K_delta as a fraction of L (default 0.01) */
     int32_t lsb;            /* 1 = local slender-body theory: drop K_delta (default 0) */
     int32_t use_graph;      /* reserved: capture the inner iteration in a CUDA graph */
@@ -107,6 +111,7 @@ typedef enum {
     FS_KS_STRESSLET_FP32 = 2,
     FS_KS_STRESSLET_FP64 = 3,
     FS_KS_STOKESLET_FF = 4,
+    FS_KS_STOKESLET_FP32_PLAIN = 5,
     FS_KS_COUNT = 6
 } fs_kernel_class;
 

@@ -14,8 +14,8 @@ from typing import Optional
 import numpy as np
 
 from . import _native
-from ._native import (FS_FP64, FS_MIXED, FS_SUM_FP32, FS_SUM_FP64, fs_boundary, fs_options,  # noqa: F401
-                      fs_step_info)
+from ._native import (FS_FP64, FS_MIXED, FS_SUM_FF, FS_SUM_FP32, FS_SUM_FP32_PLAIN, FS_SUM_FP64,  # noqa: F401
+                      fs_boundary, fs_options, fs_step_info)
 
 __all__ = ["fs_options_default", "fs_create", "fs_create_batch", "fs_batch_info", "fs_destroy", "fs_set_state", "fs_get_state",
            "fs_stokeslet_apply", "fs_stresslet_apply", "fs_surface_apply", "fs_build_precond",
@@ -23,7 +23,7 @@ __all__ = ["fs_options_default", "fs_create", "fs_create_batch", "fs_batch_info"
            "fs_probe_fma", "fs_estimate_bytes", "fs_device_bytes", "fs_server_create", "fs_submit",
            "fs_poll", "fs_server_wait", "fs_server_stats", "fs_server_destroy", "Server", "FsError",
            "FS_FP64", "FS_MIXED",
-           "FS_SUM_FP32", "FS_SUM_FP64"]
+           "FS_SUM_FP32", "FS_SUM_FP64", "FS_SUM_FF", "FS_SUM_FP32_PLAIN"]
 
 
 class FsError(RuntimeError):

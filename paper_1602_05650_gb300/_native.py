@@ -20,7 +20,7 @@ P = c_void_p
 
 FS_OK, FS_EINVAL, FS_ENOMEM, FS_ECUDA, FS_ENOTCONV, FS_ENUMERIC, FS_EAGAIN, FS_EBUSY, FS_ETIMEOUT = range(9)
 FS_FP64, FS_MIXED = 0, 1
-FS_SUM_FP64, FS_SUM_FP32 = 0, 1
+FS_SUM_FP64, FS_SUM_FP32, FS_SUM_FF, FS_SUM_FP32_PLAIN = 0, 1, 2, 3
 
 
 class fs_boundary(ctypes.Structure):

@@ -81,7 +81,7 @@ fs_status fs_options_default(fs_options *o)
     o->max_iter = 200;
     o->restart = 60;
     o->max_refine = 6;
-    o->inner_tol = 1e-5;
+    o->inner_tol = 1e-6;
     o->delta_over_L = 0.01;
     o->lsb = 0;
     o->use_graph = 0;
@@ -207,10 +207,13 @@ fs_status fs_stokeslet_apply(fs_ctx *c, const double *src_xyz, const double *src
         set_error("fs_stokeslet_apply: bad sizes or NULL arrays");
         return FS_EINVAL;
     }
-    if (sum_precision != FS_SUM_FP32 && sum_precision != FS_SUM_FP64 && sum_precision != FS_SUM_FF) {
+    if (sum_precision != FS_SUM_FP32 && sum_precision != FS_SUM_FP64 && sum_precision != FS_SUM_FF &&
+        sum_precision != FS_SUM_FP32_PLAIN) {
         set_error("fs_stokeslet_apply: unknown precision %d", sum_precision);
         return FS_EINVAL;
     }
+    const bool plain = sum_precision == FS_SUM_FP32_PLAIN;
+    if (plain) sum_precision = FS_SUM_FP32;
     if (n_src >= (1LL << 31) - 1 || n_tgt >= (1LL << 31) - 1) {
         set_error("fs_stokeslet_apply: at most 2^31-2 sources and targets");
         return FS_EINVAL;
@@ -237,7 +240,7 @@ fs_status fs_stokeslet_apply(fs_ctx *c, const double *src_xyz, const double *src
     a.out = out_u;
     a.scale = 1.0 / (8.0 * M_PI * c->mu);
     a.sum_prec = sum_precision;
-    a.hilo = true;
+    a.hilo = !plain;
     a.shape_override = c->opt.tile_override;
     a.pairs = double(n_src) * double(n_tgt);
     a.prof = c->opt.profile ? &c->prof : nullptr;

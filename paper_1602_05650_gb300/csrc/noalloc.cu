@@ -66,10 +66,13 @@ fs_status fs_stokeslet_apply_noalloc(const double *src_xyz, const double *src_wf
         set_error("fs_stokeslet_apply_noalloc: bad sizes, NULL arrays or mu <= 0");
         return FS_EINVAL;
     }
-    if (sum_precision != FS_SUM_FP32 && sum_precision != FS_SUM_FP64 && sum_precision != FS_SUM_FF) {
+    if (sum_precision != FS_SUM_FP32 && sum_precision != FS_SUM_FP64 && sum_precision != FS_SUM_FF &&
+        sum_precision != FS_SUM_FP32_PLAIN) {
         set_error("fs_stokeslet_apply_noalloc: unknown precision %d", sum_precision);
         return FS_EINVAL;
     }
+    const bool plain = sum_precision == FS_SUM_FP32_PLAIN;
+    if (plain) sum_precision = FS_SUM_FP32;
     if (n_src >= (1LL << 31) - 1 || n_tgt >= (1LL << 31) - 1) {
         set_error("fs_stokeslet_apply_noalloc: at most 2^31-2 sources and targets");
         return FS_EINVAL;
@@ -104,7 +107,7 @@ fs_status fs_stokeslet_apply_noalloc(const double *src_xyz, const double *src_wf
     a.out = out_u;
     a.scale = 1.0 / (8.0 * M_PI * mu);
     a.sum_prec = sum_precision;
-    a.hilo = true;
+    a.hilo = !plain;
     return pairsum(a, b + 256 + excl_bytes, kNoAllocBytes - 256 - excl_bytes, d_status, st);
 }
 

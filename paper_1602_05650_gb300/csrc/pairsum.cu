@@ -828,7 +828,8 @@ const void *kernel_of(int kind, int prec, bool hilo, int tpt)
                                                           : FS_K(double, 2, K, false))
     if (prec == FS_SUM_FF)
         return tpt == 1 ? reinterpret_cast<const void *>(&k_pairsum_ff<1>)
-                        : reinterpret_cast<const void *>(&k_pairsum_ff<2>);
+                        : (tpt == 4 ? reinterpret_cast<const void *>(&k_pairsum_ff<4>)
+                                    : reinterpret_cast<const void *>(&k_pairsum_ff<2>));
     if (prec == FS_SUM_FP32) {
         if (kind == PAIR_STOKESLET) return hilo ? FS_K_T(float, PAIR_STOKESLET, true) : FS_K_T(float, PAIR_STOKESLET, false);
         return hilo ? FS_K_T(float, PAIR_STRESSLET, true) : FS_K_T(float, PAIR_STRESSLET, false);
@@ -868,13 +869,14 @@ SumPlan plan_pairsum(int kind, int64_t n_src, int64_t n_tgt, int sum_prec, bool 
     hilo = hilo && f32;
     SumPlan p;
     p.tile = f32 ? kTile32 : (ff ? kTileFF : kTile64);
-    p.tpt = f32 ? 4 : 2;
+    // measured on GB300 (65,536 points): FP32 8 targets per thread, float-float 4, FP64 2
+    p.tpt = f32 ? 8 : (ff ? 4 : 2);
     if (shape_override > 0) {
         static const int f32_opts[] = {2, 4, 8};
         static const int f64_opts[] = {1, 2, 4};
         const int k = (shape_override - 1) % 3;
         p.tpt = f32 ? f32_opts[k] : f64_opts[k];
-        if (ff) p.tpt = k == 0 ? 1 : 2;
+        if (ff) p.tpt = k == 0 ? 1 : (k == 1 ? 2 : 4);
     }
     p.threads = kThreads;
     p.tb = p.tpt * kThreads;
@@ -1016,7 +1018,8 @@ fs_status pairsum(const PairSumArgs &a, void *scratch, size_t scratch_bytes, int
     FS_LAUNCH_CHECK();
     if (a.prof) {
         FS_CUDA(cudaEventRecord(ev1, st));
-        const int cls = ff ? 4 : (a.kind == PAIR_STOKESLET ? 0 : 2) + (f32 ? 0 : 1);
+        const int cls = ff ? 4 : (f32 && !hilo && a.kind == PAIR_STOKESLET) ? 5
+                                                                         : (a.kind == PAIR_STOKESLET ? 0 : 2) + (f32 ? 0 : 1);
         a.prof->recs.push_back(Profiler::Rec{cls, ev0, ev1, a.pairs});
     }
     if (!work) {

@@ -41,7 +41,7 @@ def test_options_default_and_errors_without_gpu(lib):
     o = _native.fs_options()
     assert lib.fs_options_default(ctypes.byref(o)) == 0
     assert o.prec == _native.FS_MIXED and o.tol == 1e-8 and o.restart == 60
-    assert o.inner_tol == 1e-5 and o.relax == 1
+    assert o.inner_tol == 1e-6 and o.relax == 1
     assert lib.fs_options_default(None) == _native.FS_EINVAL
     assert b"NULL" in lib.fs_last_error()
     # argument validation happens before any device call
