@@ -369,22 +369,6 @@ __global__ void __launch_bounds__(128) k_rows(FiberTable F, const double *__rest
 // epilogue); k_build_direct writes the rows that do not involve w.
 constexpr int kBT = 64, kBK = 32;
 
-// F_tau[a][l][j] = g sum_q D1[l][q] Tn[q][j] t_{q,a}; grid (M, 3)
-__global__ void __launch_bounds__(256) k_build_ftau(FiberTable F)
-{
-    const Fib fb(F, blockIdx.x);
-    const int N = fb.N, a = blockIdx.y;
-    const double *D1 = fb.M_(fb.lay.D1), *Tn = fb.M_(fb.lay.Tn);
-    const double *t = F.t + 3 * fb.n0;
-    double *out = F.ftau + fb.blk0 / 16 * 3 + static_cast<int64_t>(a) * N * N;
-    for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
-        const int l = idx / N, jj = idx - l * N;
-        double sum = 0.0;
-        for (int q = 0; q < N; ++q) sum = fma(D1[l * N + q] * t[3 * q + a], Tn[q * N + jj], sum);
-        out[idx] = fb.g * sum;
-    }
-}
-
 // S[(k,b),(l,a)] of the fiber (rows and columns component-major, b N + k).
 __device__ __forceinline__ double s_entry(const FiberTable &F, const Fib &fb, int k, int b, int l, int a)
 {
@@ -440,6 +424,39 @@ __device__ __forceinline__ void tile_gemm(int K, FA a_of, FB b_of, double (&acc)
         }
         __syncthreads();
     }
+}
+
+// F_tau[a][l][j] = g sum_q D1[l][q] t_{q,a} Tn[q][j]; grid (M, 3 nt^2) with
+// nt = ceil(N / 64) output tiles per dimension.
+__global__ void __launch_bounds__(256) k_build_ftau(FiberTable F)
+{
+    __shared__ double sA[kBK * (kBT + 1)], sB[kBK * (kBT + 1)];
+    const Fib fb(F, blockIdx.x);
+    const int N = fb.N, nt = (N + kBT - 1) / kBT;
+    const int a = blockIdx.y / (nt * nt), rem = blockIdx.y - a * nt * nt;
+    if (a >= 3) return;
+    const int l0 = (rem / nt) * kBT, j0 = (rem % nt) * kBT;
+    const double *D1 = fb.M_(fb.lay.D1), *Tn = fb.M_(fb.lay.Tn);
+    const double *t = F.t + 3 * fb.n0;
+    auto a_of = [&](int r, int q) -> double {
+        const int l = l0 + r;
+        return (l < N && q < N) ? D1[l * N + q] * t[3 * q + a] : 0.0;
+    };
+    auto b_of = [&](int q, int cc) -> double {
+        const int j = j0 + cc;
+        return (q < N && j < N) ? Tn[q * N + j] : 0.0;
+    };
+    double acc[4][4] = {};
+    tile_gemm<false>(N, a_of, b_of, acc, sA, sB);
+    const int tid = threadIdx.x, cg = tid & 15, rg = tid >> 4;
+    double *out = F.ftau + fb.blk0 / 16 * 3 + static_cast<int64_t>(a) * N * N;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            const int l = l0 + 4 * rg + i, j = j0 + 4 * cg + jj;
+            if (l < N && j < N) out[l * N + j] = fb.g * acc[i][jj];
+        }
 }
 
 // W = S F for the sigma and tension columns; grid (M, row tiles of 3N,
@@ -600,7 +617,9 @@ __global__ void __launch_bounds__(256) k_build_direct(FiberTable F, double *__re
 //   4. A22 -= L21 U12 in 64 x 64 tiles, 4 x 4 register tiles per thread.
 // The trailing matrix is read and written once per panel instead of once per
 // column; the pivots (and so the factors) are those of the column-by-column
-// algorithm.  piv[k] = p: rows k and p were exchanged at step k.
+// algorithm.  On return piv holds the composed row permutation: row i of the
+// factored block is row piv[i] of the original, so the solve gathers
+// y_i = b_{piv[i]}.
 constexpr int kLuTC = 64;   // trailing-update tile width
 
 template <int BW>
@@ -619,6 +638,8 @@ __global__ void __launch_bounds__(256) k_lu(FiberTable F, double *__restrict__ B
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     double *P = lsm;                                   // panel, column-major, ld m
     double *U = lsm + static_cast<size_t>(n) * BW;     // U12 tile [BW][UL]
+    int *perm = reinterpret_cast<int *>(U + BW * UL);  // [n] row permutation
+    for (int i = tid; i < n; i += 256) perm[i] = i;
     for (int k0 = 0; k0 < n; k0 += BW) {
         const int kb = min(BW, n - k0), m = n - k0;
         for (int idx = tid; idx < kb * m; idx += 256) {
@@ -659,7 +680,9 @@ __global__ void __launch_bounds__(256) k_lu(FiberTable F, double *__restrict__ B
                         p = ri[wv];
                     }
                 s_piv[j] = p;
-                pv[k0 + j] = k0 + p;
+                const int t = perm[k0 + j];
+                perm[k0 + j] = perm[k0 + p];
+                perm[k0 + p] = t;
                 if (!(b > 0.0)) atomicOr(status, DEV_ERR_NUMERIC);
             }
             __syncthreads();
@@ -753,9 +776,10 @@ __global__ void __launch_bounds__(256) k_lu(FiberTable F, double *__restrict__ B
         }
         __syncthreads();
     }
+    for (int i = tid; i < n; i += 256) pv[i] = perm[i];
 }
 
-// x = P^-1 in with the factors of k_lu, one CTA per fiber: row exchanges, then
+// x = P^-1 in with the factors of k_lu, one CTA per fiber: row permutation, then
 // blocked forward (unit L) and backward (U) substitution -- one warp solves
 // each BW x BW diagonal block from shared memory, all threads update the
 // remaining entries with the block's columns (coalesced column reads).
@@ -772,17 +796,7 @@ __global__ void __launch_bounds__(256) k_lu_solve(FiberTable F, const double *__
     const double *A = B + fb.blk0;
     double *y = ssm, *D = ssm + n;
     const int tid = threadIdx.x;
-    for (int i = tid; i < n; i += blockDim.x) y[i] = in[fb.u0 + i];
-    __syncthreads();
-    if (tid == 0)
-        for (int k = 0; k < n; ++k) {
-            const int p = piv[fb.u0 + k];
-            if (p != k) {
-                const double t = y[k];
-                y[k] = y[p];
-                y[p] = t;
-            }
-        }
+    for (int i = tid; i < n; i += blockDim.x) y[i] = in[fb.u0 + piv[fb.u0 + i]];
     __syncthreads();
     for (int j0 = 0; j0 < n; j0 += BW) {
         const int jb = min(BW, n - j0);
@@ -801,8 +815,17 @@ __global__ void __launch_bounds__(256) k_lu_solve(FiberTable F, const double *__
         }
         __syncthreads();
         for (int i = j0 + jb + tid; i < n; i += blockDim.x) {
+            const double *Ai = A + static_cast<int64_t>(j0) * n + i;
             double sum = y[i];
-            for (int c = 0; c < jb; ++c) sum -= A[static_cast<int64_t>(j0 + c) * n + i] * y[j0 + c];
+            if (jb == BW) {   // full block: the BW column loads issued together
+                double av[BW];
+#pragma unroll
+                for (int c = 0; c < BW; ++c) av[c] = Ai[static_cast<int64_t>(c) * n];
+#pragma unroll
+                for (int c = 0; c < BW; ++c) sum = fma(-av[c], y[j0 + c], sum);
+            } else {
+                for (int c = 0; c < jb; ++c) sum = fma(-Ai[static_cast<int64_t>(c) * n], y[j0 + c], sum);
+            }
             y[i] = sum;
         }
         __syncthreads();
@@ -828,8 +851,17 @@ __global__ void __launch_bounds__(256) k_lu_solve(FiberTable F, const double *__
         }
         __syncthreads();
         for (int i = tid; i < j0; i += blockDim.x) {
+            const double *Ai = A + static_cast<int64_t>(j0) * n + i;
             double sum = y[i];
-            for (int c = 0; c < jb; ++c) sum -= A[static_cast<int64_t>(j0 + c) * n + i] * y[j0 + c];
+            if (jb == BW) {   // full block: the BW column loads issued together
+                double av[BW];
+#pragma unroll
+                for (int c = 0; c < BW; ++c) av[c] = Ai[static_cast<int64_t>(c) * n];
+#pragma unroll
+                for (int c = 0; c < BW; ++c) sum = fma(-av[c], y[j0 + c], sum);
+            } else {
+                for (int c = 0; c < jb; ++c) sum = fma(-Ai[static_cast<int64_t>(c) * n], y[j0 + c], sum);
+            }
             y[i] = sum;
         }
         __syncthreads();
@@ -894,7 +926,8 @@ fs_status launch_block_build(fs_ctx *c)
     if (c->M == 0) return FS_OK;
     const int N = c->max_N;
     const FiberTable T = c->table();
-    k_build_ftau<<<dim3(c->M, 3), 256, 0, c->stream>>>(T);
+    const int nt = (N + kBT - 1) / kBT;
+    k_build_ftau<<<dim3(c->M, 3 * nt * nt), 256, 0, c->stream>>>(T);
     FS_LAUNCH_CHECK();
     const int ct = 3 * ((N - 4 + kBT - 1) / kBT) + (N + kBT - 1) / kBT;
     k_build_w<<<dim3(c->M, (3 * N + kBT - 1) / kBT, ct), 256, 0, c->stream>>>(T);
@@ -909,13 +942,14 @@ fs_status launch_block_build(fs_ctx *c)
 
 // Panel width of the blocked LU: 32 while the panel (n x 32 doubles) and the
 // trailing tile fit comfortably in shared memory, else 16.
-int lu_panel(int n) { return n <= 640 ? 32 : 16; }
+int lu_panel(int n) { return n <= 128 ? 32 : 16; }
 
 fs_status launch_lu_factor(fs_ctx *c)
 {
     if (c->M == 0) return FS_OK;
     const int n = 4 * c->max_N, bw = lu_panel(n);
-    const size_t sm = (static_cast<size_t>(n) * bw + static_cast<size_t>(bw) * (kLuTC + 1)) * sizeof(double);
+    const size_t sm = (static_cast<size_t>(n) * bw + static_cast<size_t>(bw) * (kLuTC + 1)) * sizeof(double) +
+                      static_cast<size_t>(n) * sizeof(int);
     if (bw == 32) {
         FS_CUDA(cudaFuncSetAttribute(k_lu<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
         k_lu<32><<<c->M, 256, sm, c->stream>>>(c->table(), c->d_B, c->d_piv, c->d_status);
