@@ -197,6 +197,110 @@ def run_kernel(args, ws, rank, local, fs, torch, dist):
                           "tflops": fpp * pairs_s / 1e12}), flush=True)
 
 
+def _timed_steps(fs, torch, h, stream, X, L, F, steps, warmup):
+    """Every step from the same state; CUDA events on the context's stream."""
+    for _ in range(warmup):
+        fs.fs_set_state(h, X, L, F)
+        fs.fs_step(h, info=False)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    infos = []
+    e0.record(stream)
+    for _ in range(steps):
+        fs.fs_set_state(h, X, L, F)
+        infos.append(fs.fs_step(h, info=True))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, infos
+
+
+def run_workload(args, ws, rank, local, fs, torch):
+    """Secondary workloads (one JSON line each, not the headline):
+    confined  2,000 x 32 fibers in a radius-20 sphere with 12,288 surface nodes,
+              mixed and FP64 steps/s;
+    batched   256 independent systems (fibers log-uniform in [8, 512], N in
+              {16, 32, 64}) in one context, mixed steps/s and systems/s;
+    large     the 1,048,576-point direct Stokeslet sum (8,192 x 128 fibers in
+              [0,80]^3, own-fiber exclusion): FP32 hi/lo, FP32 plain and
+              float-float over all targets, FP64 over 16,384 sampled targets."""
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    out = {"workload": args.workload, "data": "synthetic"}
+    if args.workload in ("confined", "batched"):
+        if args.workload == "confined":
+            s = wl.cfg_confined(seed=rank)
+            systems = [s]
+        else:
+            systems = wl.batched(256, seed=rank)
+        res = {}
+        for name, prec in (("mixed", fs.FS_MIXED), ("fp64", fs.FS_FP64)):
+            if args.workload == "batched" and name == "fp64":
+                continue
+            opt = fs.fs_options_default()
+            opt.prec = prec
+            opt.tol = 1e-8
+            opt.profile = 1
+            if args.workload == "confined":
+                h = fs.fs_create(s.n_per_fiber, s.mu, s.eps, s.E, s.dt, boundary=s.boundary, options=opt,
+                                 stream=stream)
+            else:
+                h = fs.fs_create_batch([x.n_fibers for x in systems],
+                                       np.concatenate([x.n_per_fiber for x in systems]),
+                                       1.0, 1e-3, 1.0, 1e-3, options=opt, stream=stream)
+            X = torch.tensor(np.concatenate([x.X for x in systems]), device=dev)
+            L = torch.tensor(np.concatenate([x.L for x in systems]), device=dev)
+            F = torch.tensor(np.concatenate([x.f_ext for x in systems]), device=dev)
+            steps = 1 if name == "fp64" else args.steps
+            ms, infos = _timed_steps(fs, torch, h, stream, X, L, F, steps, 1 if name == "fp64" else args.warmup)
+            ks = fs.fs_kernel_stats(h)
+            fs.fs_destroy(h)
+            res[name] = {"ms_per_step": ms, "steps_per_s": 1e3 / ms, "iters": [i.iters for i in infos],
+                         "resid": [i.resid for i in infos],
+                         "t_ms_rhs_build_solve": [round(x, 2) for x in infos[0].t_ms[:3]],
+                         "kernels": {KS_NAMES[k]: [ks[k][0], round(ks[k][1], 2)] for k in range(6) if ks[k][0]}}
+        pts = sum(x.n_points for x in systems)
+        out.update({"points": int(pts), "systems": len(systems), "tol": 1e-8, "result": res})
+        if args.workload == "confined":
+            out["surface_nodes"] = int(s.boundary.nodes.shape[0])
+        else:
+            out["systems_per_s"] = len(systems) * res["mixed"]["steps_per_s"]
+            out["fibers"] = [int(min(x.n_fibers for x in systems)), int(max(x.n_fibers for x in systems))]
+    else:
+        s = wl.cfg_large_matvec(seed=rank)
+        opt = fs.fs_options_default()
+        opt.profile = 1
+        h = fs.fs_create([], s.mu, s.eps, s.E, s.dt, options=opt, stream=stream)
+        X = torch.tensor(s.X, device=dev)
+        Wf = torch.tensor(s.f_ext * 0.01, device=dev)
+        fid = torch.tensor(s.fiber_id(), dtype=torch.int32, device=dev)
+        res = {}
+        for name, prec, cls, nt in (("fp32_hilo", fs.FS_SUM_FP32, 0, s.n_points),
+                                    ("fp32_plain", fs.FS_SUM_FP32_PLAIN, 5, s.n_points),
+                                    ("float_float", fs.FS_SUM_FF, 4, s.n_points),
+                                    ("fp64_sampled", fs.FS_SUM_FP64, 1, 16384)):
+            idx = torch.linspace(0, s.n_points - 1, nt, device=dev).long()
+            T, tf = X[idx].contiguous(), fid[idx].contiguous()
+            out_u = torch.empty_like(T)
+            fs.fs_stokeslet_apply(h, X, Wf, T, out_u, fid, tf, prec)
+            torch.cuda.synchronize()
+            fs.fs_kernel_stats(h, reset=True)
+            reps = 2 if name != "fp64_sampled" else 1
+            for _ in range(reps):
+                fs.fs_stokeslet_apply(h, X, Wf, T, out_u, fid, tf, prec)
+            st = fs.fs_kernel_stats(h, reset=True)[cls]
+            pairs_s = st[2] / (st[1] * 1e-3)
+            fpp = FLOPS_PER_PAIR["stokeslet_ff" if cls == 4 else "stokeslet"]
+            res[name] = {"targets": int(nt), "ms_per_launch": st[1] / st[0], "pairs_per_s": pairs_s,
+                         "tflops": fpp * pairs_s / 1e12,
+                         "full_matvec_s": s.n_points * s.n_points / pairs_s}
+        fs.fs_destroy(h)
+        out.update({"points": int(s.n_points), "pairs_full": float(s.n_points) ** 2, "result": res,
+                    "fp32_vs_fp64_pairs_per_s": res["fp32_hilo"]["pairs_per_s"] / res["fp64_sampled"]["pairs_per_s"]})
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def run_serve(args, ws, rank, local, fs, torch):
     """Serving: independent systems (8..512 fibers, 16/32/64 points, mixed
     precision, tol 1e-8) submitted with Poisson arrivals to an fs_server;
@@ -280,6 +384,8 @@ def main():
     ap.add_argument("--tile", type=int, default=0,
                     help="far-field launch shape id (0 = default; 1..3 = targets per thread FP32 2/4/8, "
                          "float-float 1/2/4)")
+    ap.add_argument("--workload", choices=["confined", "batched", "large"], default=None,
+                    help="a secondary workload instead of the headline step benchmark")
     ap.add_argument("--serve", type=int, default=0,
                     help="serving mode: number of independent requests (0 = the step benchmark)")
     ap.add_argument("--rate", type=float, default=0.0, help="--serve: Poisson arrival rate per s (0 = burst)")
@@ -307,6 +413,8 @@ def main():
         return run_kernel(args, ws, rank, local, fs, torch, dist)
     if args.serve:
         return run_serve(args, ws, rank, local, fs, torch)
+    if args.workload:
+        return run_workload(args, ws, rank, local, fs, torch)
 
     dev = torch.device("cuda", local)
     s = wl.cfg_cloud_mixed(seed=rank)

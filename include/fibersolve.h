@@ -91,17 +91,18 @@ typedef struct {
     int32_t tile_override;  /* 0 = autotuned far-field launch shape, else a shape id */
     int32_t profile;        /* 1 = bracket every direct-sum kernel with CUDA events on the
                                context's stream (read with fs_kernel_stats) (default 0) */
-    int32_t relax;          /* FS_MIXED: 1 = evaluate the far field in float-float only
-                               where the residual needs it (default 1).  Free space: GMRES
-                               on the FP32-far-field operator with an FP32 right-hand side
-                               to inner_tol, ONE float-float true residual r (one far field
-                               of the known force plus the solution's force), then GMRES on
-                               the FP32 hi/lo operator for the correction until
-                               |r - P^-1 A d| <= tol |P^-1 b| (its operator error, relative
-                               ~1e-7, acts on a correction of size |r|).  With a periphery:
-                               flexible GMRES whose outer directions switch from float-float
-                               to FP32 hi/lo once 1e-6 |r| <= tol |P^-1 b| / 20.
-                               0 = flexible GMRES with every outer direction in float-float */
+    int32_t relax;          /* FS_MIXED: 1 = evaluate the far fields in float-float only
+                               where the residual needs it (default 1): GMRES on the
+                               FP32-far-field operator with an FP32 right-hand side to
+                               inner_tol, ONE float-float true residual r (one set of far
+                               fields of the known force plus the solution's force and of
+                               the periphery density), then GMRES on the FP32 hi/lo operator
+                               for the correction until |r - P^-1 A d| <= tol |P^-1 b| (its
+                               operator error, relative ~1e-7, acts on a correction of size
+                               |r|); a residual with 1e-6 |r| > tol |P^-1 b| / 20 is only
+                               reduced 1e3-fold before the next true residual.
+                               0 = flexible GMRES with every outer direction in float-float,
+                               each preconditioned by an FP32-far-field GMRES solve */
 } fs_options;
 
 /* Direct-sum kernel classes reported by fs_kernel_stats. */

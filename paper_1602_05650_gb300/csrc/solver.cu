@@ -288,11 +288,11 @@ fs_status apply_pa(fs_ctx *c, const double *v, double *out, int sum_prec, const 
     return FS_OK;
 }
 
-// Inexact-Krylov relaxation of the outer operator (mixed precision): an
-// operator error of relative size eta on a direction taken when the residual
-// is r adds at most about eta |r| to the final residual, so once
-// kEtaFP32 |r| / |P^-1 b| <= kRelaxShare tol the FP32 hi/lo far field
-// (relative error below kEtaFP32) is accurate enough for further directions.
+// Inexact-Krylov relaxation (mixed precision): an operator error of relative
+// size eta on a correction taken when the residual is r adds at most about
+// eta |r| to the final residual, so once kEtaFP32 |r| <= kRelaxShare tol
+// |P^-1 b| the FP32 hi/lo far field (relative error below kEtaFP32) is
+// accurate enough for the rest of the solve.
 constexpr double kEtaFP32 = 1e-6;
 constexpr double kRelaxShare = 0.05;
 
@@ -321,19 +321,35 @@ __global__ void k_sub(double *__restrict__ out, const double *__restrict__ v, in
     if (i < n) out[i] -= v[i];
 }
 
-// Preconditioned residual r = P^-1 b - (P^-1 A) x of the fiber system (free
-// space) with ONE far field: the coupling of the known force and that of x's
-// force are the far field of the sum of the two densities (the sum is linear
-// in the density), so
-//   r = P^-1 rows_rhs(f_known, ubar[W (f_known + f(x))]) - x.
+__global__ void k_negate(double *__restrict__ v, int64_t n)
+{
+    const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (i < n) v[i] = -v[i];
+}
+
+// Preconditioned residual r = P^-1 b - (P^-1 A) x with ONE set of far
+// fields: the couplings of the known force and of x's force are the fields of
+// the sum of the two densities (they are linear in the density), so
+//   fibers : r = P^-1 rows_rhs(f_known, ubar[W (f_known + f(x))] + T[q]) - x,
+//   surface: r = -D^-1 (S q + G[W (f_known + f(x))]),
+// q the periphery density part of x.
 fs_status true_residual(fs_ctx *c, const double *x, double *r, int sum_prec)
 {
     FS_TRY(launch_force(c, x, c->d_f, c->d_wf, true));
     FS_TRY(far_field(c, sum_prec, false, &c->all_sys));
+    const double *q = c->surf.n ? x + c->n_fib_unk : nullptr;
+    if (c->surf.n) FS_TRY(surface_couplings(c, q, c->d_ubar, sum_prec, false));
     FS_TRY(launch_rows(c, nullptr, c->d_f, c->d_ubar, c->d_e, ROWS_RHS));
     FS_TRY(launch_lu_solve(c, c->d_e, r));
     k_sub<<<blocks_for(c->n_fib_unk), 256, 0, c->stream>>>(r, x, c->n_fib_unk);
     FS_LAUNCH_CHECK();
+    if (c->surf.n) {
+        const int64_t n3 = 3 * int64_t(c->surf.n);
+        FS_TRY(surface_rows(c, q, c->d_usurf, c->d_e + c->n_fib_unk, false, sum_prec, false));
+        FS_TRY(surface_precond(c, c->d_e + c->n_fib_unk, r + c->n_fib_unk));
+        k_negate<<<blocks_for(n3), 256, 0, c->stream>>>(r + c->n_fib_unk, n3);
+        FS_LAUNCH_CHECK();
+    }
     return FS_OK;
 }
 
@@ -406,12 +422,7 @@ fs_status gmres_seg(fs_ctx *c, Space &sp, const double *pb, double *x, double to
                 std::vector<SysState> ist;
                 FS_TRY(gmres_seg(c, isp, Vj, Zj, inner_tol, c->opt.max_iter, inner_prec, -1, 0.0, running, ist));
                 for (int s : running) st[s].inner += ist[s].its;
-                // the largest current residual among the running systems decides
-                bool relax = c->opt.relax && sum_prec == FS_SUM_FF;
-                for (int s : running)
-                    relax = relax && kEtaFP32 * std::fabs(st[s].g[j]) <= kRelaxShare * st[s].lim;
-                if (relax) FS_TRY(apply_pa(c, Zj, sp.w, FS_SUM_FP32, &running, true));
-                else FS_TRY(apply_pa(c, Zj, sp.w, sum_prec, &running));
+                FS_TRY(apply_pa(c, Zj, sp.w, sum_prec, &running));
             } else {
                 FS_TRY(apply_pa(c, Vj, sp.w, sum_prec, &running, hilo));
             }
@@ -937,9 +948,9 @@ fs_status fs_step(fs_ctx *c, fs_step_info *info)
         FS_CUDA(cudaStreamSynchronize(c->stream));
         tms[1] = ms_since(t0);
     }
-    // mixed precision on free-space systems: solve with an FP32 right-hand
-    // side, then one float-float true residual and an FP32 hi/lo correction
-    const bool split = c->opt.prec == FS_MIXED && c->surf.n == 0 && c->opt.relax;
+    // mixed precision: solve with an FP32 right-hand side, then one
+    // float-float true residual and an FP32 hi/lo correction
+    const bool split = c->opt.prec == FS_MIXED && c->opt.relax;
     if (split) FS_TRY(rhs(c, c->d_b, c->d_pb, FS_SUM_FP32, true));
     else FS_TRY(rhs(c, c->d_b, c->d_pb));
     FS_TRY(check_status(c));
@@ -986,7 +997,7 @@ fs_status fs_step(fs_ctx *c, fs_step_info *info)
             const bool last = sw + 1 == sweeps_max;
             FS_TRY(gmres_seg(c, sp, c->d_b, c->d_pb, c->opt.tol, c->opt.max_iter, FS_SUM_FP32, -1, 0.0,
                              c->all_sys, s2, true, &lim, last ? 0.0 : 1e-3));
-            k_add<<<blocks_for(c->n_fib_unk), 256, 0, c->stream>>>(c->d_x, c->d_pb, c->n_fib_unk);
+            k_add<<<blocks_for(c->n_unk), 256, 0, c->stream>>>(c->d_x, c->d_pb, c->n_unk);
             FS_LAUNCH_CHECK();
             bool again = false;
             for (int s = 0; s < c->S; ++s) {
