@@ -55,8 +55,7 @@ typedef enum {
     FS_SUM_FP32 = 1, /* FP32 arithmetic: hi/lo-split coordinates, FP32 tile sums,
                         compensated (TwoSum) accumulation across tiles, FP64 output */
     FS_SUM_FF = 2,   /* float-float ("double-single") arithmetic on the FP32 pipe,
-                        ~2^-44 relative rounding per pair (Stokeslet; stresslet
-                        sums requested in FS_SUM_FF run in FP64) */
+                        ~2^-44 relative rounding per pair */
     FS_SUM_FP32_PLAIN = 3 /* FS_SUM_FP32 without the lo parts of the coordinates:
                         ~15% faster, coordinate rounding ~2^-24 of the extent of
                         the sources (relative to their bounding-box centre) */
@@ -113,7 +112,8 @@ typedef enum {
     FS_KS_STRESSLET_FP64 = 3,
     FS_KS_STOKESLET_FF = 4,
     FS_KS_STOKESLET_FP32_PLAIN = 5,
-    FS_KS_COUNT = 6
+    FS_KS_STRESSLET_FF = 6,
+    FS_KS_COUNT = 8
 } fs_kernel_class;
 
 typedef struct {

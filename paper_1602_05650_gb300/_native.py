@@ -38,7 +38,7 @@ class fs_kernel_stat(ctypes.Structure):
     _fields_ = [("launches", c_int64), ("total_ms", c_double), ("pairs", c_double)]
 
 
-FS_KS_COUNT = 6
+FS_KS_COUNT = 8
 
 
 class fs_step_info(ctypes.Structure):

@@ -523,14 +523,114 @@ __device__ __forceinline__ void tile_ff(const float4 *__restrict__ sph, const fl
     }
 }
 
-template <int T>
+// Float-float stresslet: u_i += r (r . wq)(r . n) rinv^5 over the tile
+// (the constant -3/(4 pi) is applied once at the end), every product and sum
+// in float-float as in tile_ff.  Arrays: position hi/lo, w q hi/lo, normal hi/lo.
+__device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, float &ph, float &pl)
+{
+    ph = ah * bh;
+    pl = fmaf(ah, bh, -ph);
+    pl = fmaf(ah, bl, pl);
+    pl = fmaf(al, bh, pl);
+}
+
+// (h, l) = a . b for float-float 3-vectors
+__device__ __forceinline__ void ff_dot3(const float (&ah)[3], const float (&al)[3], const float (&bh)[3],
+                                        const float (&bl)[3], float &h, float &l)
+{
+    float q[3], qe[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        q[a] = ah[a] * bh[a];
+        qe[a] = fmaf(ah[a], bh[a], -q[a]);
+    }
+    float F1, f1, F2, f2;
+    ts(q[0], q[1], F1, f1);
+    ts(F1, q[2], F2, f2);
+    float lo = (f1 + f2) + (qe[0] + qe[1] + qe[2]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) lo = fmaf(ah[a], bl[a], fmaf(al[a], bh[a], lo));
+    fts(F2, lo, h, l);
+}
+
+template <int T, bool MASK>
+__device__ __forceinline__ void tile_ff_stresslet(const float4 *__restrict__ sph, const float4 *__restrict__ spl,
+                                                  const float4 *__restrict__ sqh, const float4 *__restrict__ sql,
+                                                  const float4 *__restrict__ snh, const float4 *__restrict__ snl,
+                                                  int cnt, int j0, const float (&th)[T][3],
+                                                  const float (&tl)[T][3], const int (&elo)[T],
+                                                  const int (&ecnt)[T], float (&uh)[T][3], float (&ul)[T][3])
+{
+#pragma unroll 1
+    for (int j = 0; j < cnt; ++j) {
+        const float4 ph4 = sph[j], pl4 = spl[j], qh4 = sqh[j], ql4 = sql[j], nh4 = snh[j], nl4 = snl[j];
+        const float ph[3] = {ph4.x, ph4.y, ph4.z}, pl[3] = {pl4.x, pl4.y, pl4.z};
+        const float qh[3] = {qh4.x, qh4.y, qh4.z}, ql[3] = {ql4.x, ql4.y, ql4.z};
+        const float nh[3] = {nh4.x, nh4.y, nh4.z}, nl[3] = {nl4.x, nl4.y, nl4.z};
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            float dh[3], dl[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                float e;
+                ts(th[t][a], -ph[a], dh[a], e);
+                dl[a] = (tl[t][a] - pl[a]) + e;
+            }
+            float R, Rl;
+            ff_dot3(dh, dl, dh, dl, R, Rl);
+            bool skip = false;
+            if constexpr (MASK) {
+                skip = static_cast<unsigned>(j0 + j - elo[t]) < static_cast<unsigned>(ecnt[t]);
+                if (skip) {
+                    R = 1.0f;
+                    Rl = 0.0f;
+                }
+            }
+            // rinv = y + yl: one Newton step on the rsqrt seed
+            float y = rsqrtf(R);
+            const float hh = y * y, hl = fmaf(y, y, -hh);
+            const float qh2 = R * hh;
+            float ql2 = fmaf(R, hh, -qh2);
+            ql2 = fmaf(R, hl, ql2);
+            ql2 = fmaf(Rl, hh, ql2);
+            const float ee = (1.0f - qh2) - ql2;
+            float yl = 0.5f * y * ee;
+            if constexpr (MASK) {
+                if (skip) {
+                    y = 0.0f;
+                    yl = 0.0f;
+                }
+            }
+            float r2h, r2l, r4h, r4l, r5h, r5l;
+            ff_mul(y, yl, y, yl, r2h, r2l);
+            ff_mul(r2h, r2l, r2h, r2l, r4h, r4l);
+            ff_mul(r4h, r4l, y, yl, r5h, r5l);
+            float rqh, rql, rnh, rnl, ph2, pl2, sh, sl;
+            ff_dot3(dh, dl, qh, ql, rqh, rql);
+            ff_dot3(dh, dl, nh, nl, rnh, rnl);
+            ff_mul(rqh, rql, rnh, rnl, ph2, pl2);
+            ff_mul(ph2, pl2, r5h, r5l, sh, sl);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                float wh, wl;
+                ff_mul(sh, sl, dh[a], dl[a], wh, wl);
+                float nh2, ne;
+                ts(uh[t][a], wh, nh2, ne);
+                ul[t][a] += ne + wl;
+                uh[t][a] = nh2;
+            }
+        }
+    }
+}
+
+template <int T, int KIND>
 __global__ void __launch_bounds__(kThreads)
     k_pairsum_ff(const float4 *__restrict__ src, int64_t n_src, int64_t nt, int64_t W, int G,
                  const double *__restrict__ tgt, const int2 *__restrict__ excl, int64_t n_tgt,
                  const double *__restrict__ center, double *__restrict__ out, double *__restrict__ part,
                  double scale, int acc, int *__restrict__ status, const int4 *__restrict__ work)
 {
-    constexpr int NARR = 4, TILE = kTileFF, TB = T * kThreads;
+    constexpr int NARR = KIND == PAIR_STRESSLET ? 6 : 4, TILE = kTileFF, TB = T * kThreads;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float4 *smem = reinterpret_cast<float4 *>(smem_raw);   // [stage][array][TILE]
     __shared__ __align__(8) uint64_t bars[2];
@@ -610,12 +710,23 @@ __global__ void __launch_bounds__(kThreads)
             int cnt;
             run.src(it, j0, cnt);
             const bool masked = bhi > blo && j0 < bhi && j0 + cnt > blo;
-            if (masked)
-                tile_ff<T, true>(stage_ptr(stage, 0), stage_ptr(stage, 1), stage_ptr(stage, 2),
-                                 stage_ptr(stage, 3), cnt, static_cast<int>(j0), th, tl, elo, ecnt, uh, ul);
-            else
-                tile_ff<T, false>(stage_ptr(stage, 0), stage_ptr(stage, 1), stage_ptr(stage, 2),
-                                  stage_ptr(stage, 3), cnt, static_cast<int>(j0), th, tl, elo, ecnt, uh, ul);
+            if constexpr (KIND == PAIR_STRESSLET) {
+                if (masked)
+                    tile_ff_stresslet<T, true>(stage_ptr(stage, 0), stage_ptr(stage, 1), stage_ptr(stage, 2),
+                                               stage_ptr(stage, 3), stage_ptr(stage, 4), stage_ptr(stage, 5), cnt,
+                                               static_cast<int>(j0), th, tl, elo, ecnt, uh, ul);
+                else
+                    tile_ff_stresslet<T, false>(stage_ptr(stage, 0), stage_ptr(stage, 1), stage_ptr(stage, 2),
+                                                stage_ptr(stage, 3), stage_ptr(stage, 4), stage_ptr(stage, 5), cnt,
+                                                static_cast<int>(j0), th, tl, elo, ecnt, uh, ul);
+            } else {
+                if (masked)
+                    tile_ff<T, true>(stage_ptr(stage, 0), stage_ptr(stage, 1), stage_ptr(stage, 2),
+                                     stage_ptr(stage, 3), cnt, static_cast<int>(j0), th, tl, elo, ecnt, uh, ul);
+                else
+                    tile_ff<T, false>(stage_ptr(stage, 0), stage_ptr(stage, 1), stage_ptr(stage, 2),
+                                      stage_ptr(stage, 3), cnt, static_cast<int>(j0), th, tl, elo, ecnt, uh, ul);
+            }
 #pragma unroll
             for (int t = 0; t < T; ++t)
 #pragma unroll
@@ -649,24 +760,34 @@ __global__ void __launch_bounds__(kThreads)
 
 // Pack for the float-float kernel: [0] position hi, [1] position lo,
 // [2] W f hi, [3] W f lo (positions relative to the centre).
-__global__ void k_pack_ff(const double *__restrict__ xyz, const double *__restrict__ dens, int64_t n,
+// Stresslet (wgt and nrm given): [2], [3] w q hi/lo and [4], [5] the normal hi/lo.
+__global__ void k_pack_ff(const double *__restrict__ xyz, const double *__restrict__ dens,
+                          const double *__restrict__ wgt, const double *__restrict__ nrm, int64_t n,
                           const double *__restrict__ center, float4 *__restrict__ out)
 {
     const int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
     if (j >= n) return;
-    float h[3], l[3], fh[3], fl[3];
+    const double wj = wgt ? wgt[j] : 1.0;
+    float h[3], l[3], fh[3], fl[3], nh[3], nl[3];
     for (int a = 0; a < 3; ++a) {
         const double x = xyz[3 * j + a] - center[a];
         h[a] = static_cast<float>(x);
         l[a] = static_cast<float>(x - static_cast<double>(h[a]));
-        const double f = dens[3 * j + a];
+        const double f = wj * dens[3 * j + a];
         fh[a] = static_cast<float>(f);
         fl[a] = static_cast<float>(f - static_cast<double>(fh[a]));
+        const double v = nrm ? nrm[3 * j + a] : 0.0;
+        nh[a] = static_cast<float>(v);
+        nl[a] = static_cast<float>(v - static_cast<double>(nh[a]));
     }
     out[j] = make_float4(h[0], h[1], h[2], 0.0f);
     out[n + j] = make_float4(l[0], l[1], l[2], 0.0f);
     out[2 * n + j] = make_float4(fh[0], fh[1], fh[2], 0.0f);
     out[3 * n + j] = make_float4(fl[0], fl[1], fl[2], 0.0f);
+    if (nrm) {
+        out[4 * n + j] = make_float4(nh[0], nh[1], nh[2], 0.0f);
+        out[5 * n + j] = make_float4(nl[0], nl[1], nl[2], 0.0f);
+    }
 }
 
 // ------------------------------------------------------------------ helpers
@@ -826,10 +947,13 @@ const void *kernel_of(int kind, int prec, bool hilo, int tpt)
 #define FS_K_T(R, K, HL) (tpt == 2 ? FS_K(R, 2, K, HL) : tpt == 8 ? FS_K(R, 8, K, HL) : FS_K(R, 4, K, HL))
 #define FS_K_T64(K) (tpt == 1 ? FS_K(double, 1, K, false) : tpt == 4 ? FS_K(double, 4, K, false) \
                                                           : FS_K(double, 2, K, false))
-    if (prec == FS_SUM_FF)
-        return tpt == 1 ? reinterpret_cast<const void *>(&k_pairsum_ff<1>)
-                        : (tpt == 4 ? reinterpret_cast<const void *>(&k_pairsum_ff<4>)
-                                    : reinterpret_cast<const void *>(&k_pairsum_ff<2>));
+#define FS_KF(TT, K) reinterpret_cast<const void *>(&k_pairsum_ff<TT, K>)
+    if (prec == FS_SUM_FF) {
+        if (kind == PAIR_STRESSLET)
+            return tpt == 1 ? FS_KF(1, PAIR_STRESSLET) : (tpt == 4 ? FS_KF(4, PAIR_STRESSLET) : FS_KF(2, PAIR_STRESSLET));
+        return tpt == 1 ? FS_KF(1, PAIR_STOKESLET) : (tpt == 4 ? FS_KF(4, PAIR_STOKESLET) : FS_KF(2, PAIR_STOKESLET));
+    }
+#undef FS_KF
     if (prec == FS_SUM_FP32) {
         if (kind == PAIR_STOKESLET) return hilo ? FS_K_T(float, PAIR_STOKESLET, true) : FS_K_T(float, PAIR_STOKESLET, false);
         return hilo ? FS_K_T(float, PAIR_STRESSLET, true) : FS_K_T(float, PAIR_STRESSLET, false);
@@ -864,7 +988,6 @@ int resident_ctas(const void *k, size_t smem)
 SumPlan plan_pairsum(int kind, int64_t n_src, int64_t n_tgt, int sum_prec, bool hilo, int shape_override,
                      int slots)
 {
-    if (sum_prec == FS_SUM_FF && kind == PAIR_STRESSLET) sum_prec = FS_SUM_FP64;   // as in pairsum()
     const bool f32 = sum_prec == FS_SUM_FP32, ff = sum_prec == FS_SUM_FF;
     hilo = hilo && f32;
     SumPlan p;
@@ -880,7 +1003,7 @@ SumPlan plan_pairsum(int kind, int64_t n_src, int64_t n_tgt, int sum_prec, bool 
     }
     p.threads = kThreads;
     p.tb = p.tpt * kThreads;
-    p.n_arr = ff ? 4 : (kind == PAIR_STRESSLET ? 3 : 2) + (hilo ? 1 : 0);
+    p.n_arr = ff ? (kind == PAIR_STRESSLET ? 6 : 4) : (kind == PAIR_STRESSLET ? 3 : 2) + (hilo ? 1 : 0);
     p.v4 = (f32 || ff) ? sizeof(float4) : sizeof(double4_32a);
     p.smem = static_cast<size_t>(p.n_arr) * 2 * p.tile * p.v4;
     p.nb = (n_tgt + p.tb - 1) / p.tb;
@@ -928,9 +1051,7 @@ fs_status pairsum(const PairSumArgs &a, void *scratch, size_t scratch_bytes, int
         set_error("pairsum: at most 2^31-2 sources and targets");
         return FS_EINVAL;
     }
-    // the float-float path exists for the Stokeslet; stresslet sums asked for
-    // in float-float run in FP64 (more, not less, precise)
-    const int prec = (a.sum_prec == FS_SUM_FF && a.kind == PAIR_STRESSLET) ? FS_SUM_FP64 : a.sum_prec;
+    const int prec = a.sum_prec;
     const bool ff = prec == FS_SUM_FF;
     const bool f32 = prec == FS_SUM_FP32;
     const bool hilo = f32 && a.hilo;
@@ -976,7 +1097,9 @@ fs_status pairsum(const PairSumArgs &a, void *scratch, size_t scratch_bytes, int
     const unsigned pb = static_cast<unsigned>((a.n_src + 255) / 256);
     const int lo_slot = hilo ? p.n_arr - 1 : 0;
     if (ff)
-        k_pack_ff<<<pb, 256, 0, st>>>(a.src_xyz, a.src_dens, a.n_src, center, static_cast<float4 *>(packed));
+        k_pack_ff<<<pb, 256, 0, st>>>(a.src_xyz, a.src_dens, a.kind == PAIR_STRESSLET ? a.src_w : nullptr,
+                                      a.kind == PAIR_STRESSLET ? a.src_nrm : nullptr, a.n_src, center,
+                                      static_cast<float4 *>(packed));
     else if (f32)
         k_pack<float><<<pb, 256, 0, st>>>(a.src_xyz, a.src_dens, a.src_w, a.src_nrm, a.n_src, center,
                                           static_cast<float4 *>(packed), p.n_arr, lo_slot);
@@ -1018,8 +1141,9 @@ fs_status pairsum(const PairSumArgs &a, void *scratch, size_t scratch_bytes, int
     FS_LAUNCH_CHECK();
     if (a.prof) {
         FS_CUDA(cudaEventRecord(ev1, st));
-        const int cls = ff ? 4 : (f32 && !hilo && a.kind == PAIR_STOKESLET) ? 5
-                                                                         : (a.kind == PAIR_STOKESLET ? 0 : 2) + (f32 ? 0 : 1);
+        const int cls = ff ? (a.kind == PAIR_STOKESLET ? 4 : 6)
+                           : (f32 && !hilo && a.kind == PAIR_STOKESLET) ? 5
+                                                                      : (a.kind == PAIR_STOKESLET ? 0 : 2) + (f32 ? 0 : 1);
         a.prof->recs.push_back(Profiler::Rec{cls, ev0, ev1, a.pairs});
     }
     if (!work) {

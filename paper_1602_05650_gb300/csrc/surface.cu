@@ -216,7 +216,7 @@ fs_status fs_stresslet_apply(fs_ctx *c, const double *src_xyz, const double *src
         set_error("fs_stresslet_apply: bad arguments");
         return FS_EINVAL;
     }
-    if (sum_precision != FS_SUM_FP32 && sum_precision != FS_SUM_FP64) {
+    if (sum_precision != FS_SUM_FP32 && sum_precision != FS_SUM_FP64 && sum_precision != FS_SUM_FF) {
         set_error("fs_stresslet_apply: unknown precision %d", sum_precision);
         return FS_EINVAL;
     }
@@ -247,7 +247,7 @@ fs_status fs_surface_apply(fs_ctx *c, const double *q, double *out, int32_t sum_
         set_error("fs_surface_apply: context without periphery or NULL arrays");
         return FS_EINVAL;
     }
-    if (sum_precision != FS_SUM_FP32 && sum_precision != FS_SUM_FP64) {
+    if (sum_precision != FS_SUM_FP32 && sum_precision != FS_SUM_FP64 && sum_precision != FS_SUM_FF) {
         set_error("fs_surface_apply: unknown precision %d", sum_precision);
         return FS_EINVAL;
     }

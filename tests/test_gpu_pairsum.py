@@ -117,7 +117,7 @@ def test_cloud_size_sampled(ctx):
         assert rel(got[idx], ref) <= TOL[prec]
 
 
-@pytest.mark.parametrize("prec", [fs.FS_SUM_FP64, fs.FS_SUM_FP32])
+@pytest.mark.parametrize("prec", [fs.FS_SUM_FP64, fs.FS_SUM_FP32, FS_SUM_FF])
 def test_stresslet_off_surface(ctx, prec):
     b = wl.sphere_quadrature(20.0, 8, 24)
     rng = np.random.default_rng(7)
@@ -132,7 +132,7 @@ def test_stresslet_off_surface(ctx, prec):
     assert rel(out.cpu().numpy(), ref) <= TOL[prec]
 
 
-@pytest.mark.parametrize("prec", [fs.FS_SUM_FP64, fs.FS_SUM_FP32])
+@pytest.mark.parametrize("prec", [fs.FS_SUM_FP64, fs.FS_SUM_FP32, FS_SUM_FF])
 def test_surface_operator(prec):
     b = wl.sphere_quadrature(20.0, 8, 16)
     s = wl.confined(2, 16, R=20.0, R_centres=5.0, n_theta=8, n_phi=16, seed=1)
