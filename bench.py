@@ -92,7 +92,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_baseline(s, gpu_fp64_iters: int, budget_fibers: int = 24, budget_targets: int = 1024):
+def oracle_baseline(s, gpu_fp64_iters: int, budget_fibers: int = 256, budget_targets: int = 32768):
     """Time the CPU oracle on a bounded sample of the workload and scale to one
     step: per-fiber setup (geometry, self block, LU) for `budget_fibers` fibers
     scaled to all fibers, plus (1 + iters) far-field sums, each timed on
@@ -125,17 +125,21 @@ def oracle_baseline(s, gpu_fp64_iters: int, budget_fibers: int = 24, budget_targ
 
 
 def traffic_for(kernel_class: str):
-    """DRAM bytes per launch from a committed ncu capture, if it was taken on
-    the current source of the kernel (else None)."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+    the committed ncu summary profiles/traffic.txt, if it was taken on the
+    current source of the direct-sum kernels (else None).  Lines:
+    <kernel class> <bytes per launch> <sha1 of csrc/pairsum.cu>."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
     try:
         import hashlib
-        rec = json.load(open(p)).get(kernel_class)
         src = open(os.path.join(ROOT, "paper_1602_05650_gb300", "csrc", "pairsum.cu"), "rb").read()
-        if rec and rec.get("pairsum_sha1") == hashlib.sha1(src).hexdigest():
-            return rec.get("dram_bytes_per_launch")
+        sha = hashlib.sha1(src).hexdigest()
+        for line in open(p):
+            f = line.split()
+            if len(f) == 3 and not line.startswith("#") and f[0] == kernel_class and f[2] == sha:
+                return float(f[1])
     except Exception:
         return None
     return None
@@ -148,7 +152,7 @@ def run_reference(args, ws, rank):
     vals = []
     base = None
     for k in range(args.warmup + args.steps):
-        base = oracle_baseline(s, gpu_fp64_iters=args.ref_iters, budget_fibers=8, budget_targets=256)
+        base = oracle_baseline(s, gpu_fp64_iters=args.ref_iters, budget_fibers=32, budget_targets=2048)
         if k >= args.warmup:
             vals.append(base["seconds_per_step_extrapolated"])
     t = float(np.mean(vals))
@@ -369,7 +373,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--ref-iters", type=int, default=10,
+    ap.add_argument("--ref-iters", type=int, default=12,
                     help="GMRES iterations assumed for the reference arm's extrapolation")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")

@@ -127,6 +127,7 @@ struct fs_ctx {
     double *d_ftau = nullptr;     // block-build scratch: tension-column forces (3 N^2 per fiber)
     double *d_wsc = nullptr;      // block-build scratch: w of every column (12 N^2 per fiber)
     int *d_piv = nullptr;
+    double *d_dinv = nullptr;     // 1 / U_ii of the block LU factors
     double *d_V = nullptr, *d_T = nullptr;
     double *d_f = nullptr, *d_wf = nullptr, *d_ubar = nullptr;
     // Krylov workspace

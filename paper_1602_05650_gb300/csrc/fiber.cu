@@ -619,18 +619,21 @@ __global__ void __launch_bounds__(256) k_build_direct(FiberTable F, double *__re
 // column; the pivots (and so the factors) are those of the column-by-column
 // algorithm.  On return piv holds the composed row permutation: row i of the
 // factored block is row piv[i] of the original, so the solve gathers
-// y_i = b_{piv[i]}.
+// y_i = b_{piv[i]}; dinv holds 1 / U_ii (the solve multiplies instead of
+// dividing: a division is a multi-instruction FP64 sequence, and one lane at a
+// time would pay it for the whole warp).
 constexpr int kLuTC = 64;   // trailing-update tile width
 
 template <int BW>
 __global__ void __launch_bounds__(256) k_lu(FiberTable F, double *__restrict__ B, int *__restrict__ piv,
-                                            int *__restrict__ status)
+                                            double *__restrict__ dinv, int *__restrict__ status)
 {
     constexpr int TC = kLuTC, UL = TC + 1;
     extern __shared__ double lsm[];
     __shared__ double rv[8];
     __shared__ int ri[8];
     __shared__ int s_piv[BW];
+    __shared__ double s_inv;
     const Fib fb(F, blockIdx.x);
     const int n = 4 * fb.N;
     double *A = B + fb.blk0;
@@ -680,6 +683,8 @@ __global__ void __launch_bounds__(256) k_lu(FiberTable F, double *__restrict__ B
                         p = ri[wv];
                     }
                 s_piv[j] = p;
+                const double pvv = P[j * m + p];   // the pivot, row p before the exchange
+                s_inv = pvv != 0.0 ? 1.0 / pvv : 0.0;
                 const int t = perm[k0 + j];
                 perm[k0 + j] = perm[k0 + p];
                 perm[k0 + p] = t;
@@ -694,8 +699,7 @@ __global__ void __launch_bounds__(256) k_lu(FiberTable F, double *__restrict__ B
                     P[c * m + p] = t;
                 }
             __syncthreads();
-            const double pvv = P[j * m + j];
-            const double inv = pvv != 0.0 ? 1.0 / pvv : 0.0;
+            const double inv = s_inv;
             for (int r = j + 1 + tid; r < m; r += 256) P[j * m + r] *= inv;
             __syncthreads();
             const int rows = m - j - 1, cols = kb - j - 1;
@@ -776,7 +780,13 @@ __global__ void __launch_bounds__(256) k_lu(FiberTable F, double *__restrict__ B
         }
         __syncthreads();
     }
-    for (int i = tid; i < n; i += 256) pv[i] = perm[i];
+    for (int i = tid; i < n; i += 256) {
+        pv[i] = perm[i];
+        // reciprocals of U's diagonal for the solve (a zero pivot gives 0, as
+        // flagged in status above)
+        const double d = A[static_cast<int64_t>(i) * n + i];
+        dinv[fb.u0 + i] = d != 0.0 ? 1.0 / d : 0.0;
+    }
 }
 
 // x = P^-1 in with the factors of k_lu, one CTA per fiber: row permutation, then
@@ -786,6 +796,7 @@ __global__ void __launch_bounds__(256) k_lu(FiberTable F, double *__restrict__ B
 template <int BW>
 __global__ void __launch_bounds__(256) k_lu_solve(FiberTable F, const double *__restrict__ B,
                                                   const int *__restrict__ piv,
+                                                  const double *__restrict__ dinv,
                                                   const double *__restrict__ in,
                                                   double *__restrict__ out)
 {
@@ -840,10 +851,7 @@ __global__ void __launch_bounds__(256) k_lu_solve(FiberTable F, const double *__
         if (tid < 32) {
             double v = tid < jb ? y[j0 + tid] : 0.0;
             for (int c = jb - 1; c >= 0; --c) {
-                if (tid == c) {
-                    const double d = D[c * DL + c];
-                    v = d != 0.0 ? v / d : 0.0;
-                }
+                if (tid == c) v *= dinv[fb.u0 + j0 + c];
                 const double yc = __shfl_sync(0xffffffffu, v, c);
                 if (tid < c) v -= D[c * DL + tid] * yc;
             }
@@ -952,10 +960,10 @@ fs_status launch_lu_factor(fs_ctx *c)
                       static_cast<size_t>(n) * sizeof(int);
     if (bw == 32) {
         FS_CUDA(cudaFuncSetAttribute(k_lu<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
-        k_lu<32><<<c->M, 256, sm, c->stream>>>(c->table(), c->d_B, c->d_piv, c->d_status);
+        k_lu<32><<<c->M, 256, sm, c->stream>>>(c->table(), c->d_B, c->d_piv, c->d_dinv, c->d_status);
     } else {
         FS_CUDA(cudaFuncSetAttribute(k_lu<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
-        k_lu<16><<<c->M, 256, sm, c->stream>>>(c->table(), c->d_B, c->d_piv, c->d_status);
+        k_lu<16><<<c->M, 256, sm, c->stream>>>(c->table(), c->d_B, c->d_piv, c->d_dinv, c->d_status);
     }
     FS_LAUNCH_CHECK();
     return FS_OK;
@@ -965,7 +973,7 @@ fs_status launch_lu_solve(fs_ctx *c, const double *in, double *out)
 {
     if (c->M == 0) return FS_OK;
     const size_t sm = (static_cast<size_t>(4 * c->max_N) + 32 * 33) * sizeof(double);
-    k_lu_solve<32><<<c->M, 256, sm, c->stream>>>(c->table(), c->d_B, c->d_piv, in, out);
+    k_lu_solve<32><<<c->M, 256, sm, c->stream>>>(c->table(), c->d_B, c->d_piv, c->d_dinv, in, out);
     FS_LAUNCH_CHECK();
     return FS_OK;
 }

@@ -663,6 +663,7 @@ fs_status context_init(fs_ctx *c, int S, const int32_t *fps, int M, const int32_
     // the p columns of w are never written: they stay zero (f = 0 there)
     FS_CUDA(cudaMemsetAsync(c->d_wsc, 0, static_cast<size_t>(c->n_blk / 4 * 3) * sizeof(double), c->stream));
     FS_TRY(dalloc(c, &c->d_piv, c->n_fib_unk));
+    FS_TRY(dalloc(c, &c->d_dinv, c->n_fib_unk));
     FS_TRY(dalloc(c, &c->d_V, 3 * P));
     FS_TRY(dalloc(c, &c->d_T, P));
     FS_TRY(dalloc(c, &c->d_f, 3 * P));
@@ -769,6 +770,7 @@ size_t estimate_bytes(int M, const int32_t *ppf, int n_surf, const fs_options &o
                       n_blk / 16 * 3, n_blk / 4 * 3})
         add(k * d);
     add(n_fib_unk * sizeof(int));
+    add(n_fib_unk * sizeof(double));
     for (int64_t k : {3 * P, P, 3 * P, 3 * P, 3 * P}) add(k * d);
     const int64_t n = n_fib_unk + 3 * int64_t(n_surf);
     const int R = std::max(2, std::min(opt.restart, 250));
@@ -818,7 +820,7 @@ void context_free(fs_ctx *c)
     void *ptrs[] = {c->d_status, c->d_N, c->d_node_ptr, c->d_unk_ptr, c->d_blk_ptr, c->d_kp_ptr,
                     c->d_z_ptr, c->d_ops_off, c->d_ops, c->d_excl, c->d_X, c->d_L, c->d_fext,
                     c->d_t, c->d_tz, c->d_fknown, c->d_W, c->d_mloc, c->d_bc, c->d_kp, c->d_B, c->d_ftau, c->d_wsc,
-                    c->d_piv, c->d_V, c->d_T, c->d_f, c->d_wf, c->d_ubar, c->d_basis, c->d_b,
+                    c->d_piv, c->d_dinv, c->d_V, c->d_T, c->d_f, c->d_wf, c->d_ubar, c->d_basis, c->d_b,
                     c->d_x, c->d_r, c->d_w, c->d_e, c->d_pb, c->d_obasis, c->d_oz, c->d_oh, c->d_opart, c->d_ow, c->d_or, c->d_work, c->d_ich, c->d_isch, c->d_ikk, c->d_och, c->d_osch, c->d_okk, c->d_h, c->d_part, c->surf.y, c->surf.nrm,
                     c->surf.w, c->surf.diag, c->d_usurf, c->surf.A, c->surf.tmp, c->surf.flux, c->surf.excl};
     for (void *p : ptrs)
