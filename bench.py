@@ -228,7 +228,10 @@ def run_workload(args, ws, rank, local, fs, torch):
               {16, 32, 64}) in one context, mixed steps/s and systems/s;
     large     the 1,048,576-point direct Stokeslet sum (8,192 x 128 fibers in
               [0,80]^3, own-fiber exclusion): FP32 hi/lo, FP32 plain and
-              float-float over all targets, FP64 over 16,384 sampled targets."""
+              float-float over all targets, FP64 over 16,384 sampled targets;
+    sediment  the four sedimenting clouds of Sec. 4.3 (1,024 x 16 each) in
+              one batch, advanced --steps steps: steps/s and the settling
+              speeds relative to V_c."""
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     out = {"workload": args.workload, "data": "synthetic"}
@@ -271,6 +274,53 @@ def run_workload(args, ws, rank, local, fs, torch):
         else:
             out["systems_per_s"] = len(systems) * res["mixed"]["steps_per_s"]
             out["fibers"] = [int(min(x.n_fibers for x in systems)), int(max(x.n_fibers for x in systems))]
+    elif args.workload == "sediment":
+        # Sec. 4.3: the four clouds (1,024 fibers x 16 points, L/R0 = 0.15,
+        # 0.25, 0.32, 0.40, fibers at least 0.1 L apart) as one batch,
+        # advanced --steps steps after one untimed step
+        lens = (0.15, 0.25, 0.32, 0.40)
+        clouds = [wl.sedimenting_cloud(Lr, M=1024, N=16, seed=100 * rank + k) for k, Lr in enumerate(lens)]
+        opt = fs.fs_options_default()
+        opt.prec = fs.FS_MIXED
+        opt.tol = 1e-8
+        opt.profile = 1
+        h = fs.fs_create_batch([c.n_fibers for c in clouds], np.concatenate([c.n_per_fiber for c in clouds]),
+                               1.0, 0.01, 3.2e-3, clouds[0].dt, options=opt, stream=stream)
+        X = torch.tensor(np.concatenate([c.X for c in clouds]), device=dev)
+        fs.fs_set_state(h, X, torch.tensor(np.concatenate([c.L for c in clouds]), device=dev),
+                        torch.tensor(np.concatenate([c.f_ext for c in clouds]), device=dev))
+        sizes = np.cumsum([0] + [c.n_points for c in clouds])
+        V = torch.empty_like(X)
+        Xe = torch.empty_like(X)
+
+        def speeds():
+            fs.fs_get_state(h, V=V)
+            return [round(-V[sizes[k]:sizes[k + 1], 2].mean().item() / wl.cloud_velocity_scale(clouds[k]), 4)
+                    for k in range(4)]
+
+        fs.fs_step(h)
+        first = speeds()
+        fs.fs_get_state(h, X=Xe)
+        z0 = [Xe[sizes[k]:sizes[k + 1], 2].mean().item() for k in range(4)]
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        iters = []
+        for _ in range(args.steps):
+            iters.append(fs.fs_step(h, info=True).iters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        last = speeds()
+        fs.fs_get_state(h, X=Xe)
+        fs.fs_destroy(h)
+        drop = [round(z0[k] - Xe[sizes[k]:sizes[k + 1], 2].mean().item(), 5) for k in range(4)]
+        out.update({"L_over_R0": list(lens), "fibers_per_cloud": 1024, "points_per_fiber": 16,
+                    "points": int(sizes[-1]), "dt": clouds[0].dt, "steps": args.steps,
+                    "ms_per_step": ms, "steps_per_s": 1e3 / ms, "iters": iters,
+                    "settling_speed_over_Vc_first_step": first, "settling_speed_over_Vc_last_step": last,
+                    "centre_of_mass_drop_over_R0": drop})
     else:
         s = wl.cfg_large_matvec(seed=rank)
         opt = fs.fs_options_default()
@@ -389,7 +439,7 @@ def main():
     ap.add_argument("--tile", type=int, default=0,
                     help="far-field launch shape id (0 = default; 1..3 = targets per thread FP32 2/4/8, "
                          "float-float 1/2/4)")
-    ap.add_argument("--workload", choices=["confined", "batched", "large"], default=None,
+    ap.add_argument("--workload", choices=["confined", "batched", "large", "sediment"], default=None,
                     help="a secondary workload instead of the headline step benchmark")
     ap.add_argument("--serve", type=int, default=0,
                     help="serving mode: number of independent requests (0 = the step benchmark)")
