@@ -22,7 +22,11 @@ Velocity expression at the nodes (Eq. main-sb-local):
     K_delta (Eq. sb-stokes-reg) by Clenshaw-Curtis quadrature on the nodes.
 
 Rows (4N), rectangular collocation:
-    velocity   (N-4 per component, first-kind points y):  -V(y) + [P_y w](y) = 0
+    velocity   (N-4 per component, first-kind points y):  -V(y) + [P_y w](y) = 0,
+               with a growing or shrinking fiber (length rate Ldot, plus end
+               at alpha = 1): -V(y) + [P_y w](y) + (y + 1)(Ldot / L) X_alpha(y) = 0
+               (the nodes sit at fixed alpha = 2 s / L - 1, so they move with
+               the material velocity w plus the reparametrisation term)
     free ends  (Eq. bc-free, on X+):  V''(+-1) + X''(+-1)/dt = 0,
                                       V'''(+-1) + X'''(+-1)/dt = 0
     tension    (N-2 first-kind points z):  X_s(z) . [D_z w](z) = 0
@@ -90,7 +94,7 @@ class Fiber:
     frozen at the current step, forces implicit)."""
 
     def __init__(self, X: np.ndarray, L: float, f_ext: np.ndarray, mu: float, eps: float,
-                 E: float, dt: float, delta: float, lsb: bool = False):
+                 E: float, dt: float, delta: float, lsb: bool = False, Ldot: float = 0.0):
         N = X.shape[0]
         op = ops_for(N)
         self.N, self.op, self.L = N, op, L
@@ -107,6 +111,8 @@ class Fiber:
         X2 = cheb.interp_derivs_ext(X, pm, 2)                 # X_aa at alpha = +1, -1
         X3 = cheb.interp_derivs_ext(X, pm, 3)
         Xaaaa = cheb.interp_derivs_ext(X, Nld, 4)
+        Xa_y = np.asarray(cheb.interp_derivs_ext(X, cheb.first_kind_ld(N - 4), 1), dtype=float) \
+            if Ldot != 0.0 else None                            # X_alpha at the y points
         self.f_known = f_ext - E * g ** 4 * Xaaaa              # [N, 3]
         self.W = op.w * L / 2.0                                # source weights
         s = (op.alpha + 1.0) * L / 2.0
@@ -148,6 +154,11 @@ class Fiber:
             Rd[r0 + N - 2:r0 + N, a * N:(a + 1) * N] = op.V3_pm
             const[r0 + N - 4:r0 + N - 2] = X2[:, a] / dt
             const[r0 + N - 2:r0 + N] = X3[:, a] / dt
+            if Ldot != 0.0:
+                # growth (Sec. 2.4, kinetics): at fixed alpha the nodes move with
+                # the material velocity plus (alpha + 1)(Ldot / L) X_alpha, so the
+                # velocity rows -V + w = 0 become -V + w + R(y) = 0
+                const[r0:r0 + N - 4] = (op.y + 1.0) * (Ldot / L) * Xa_y[:, a]
             Rw[3 * N:4 * N - 2, a * N:(a + 1) * N] = self.tz[:, a:a + 1] * op.D_z
         Rd[4 * N - 2:4 * N, 3 * N:4 * N] = op.T_pm
         self.F, self.S, self.Rw, self.Rd, self.const = F, S, Rw, Rd, const

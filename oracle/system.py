@@ -37,11 +37,12 @@ class StepResult:
     u: np.ndarray          # full unknown vector
     iters: int
     resid: float
+    L_new: Optional[np.ndarray] = None   # [M] L + dt Ldot
 
 
 class System:
     def __init__(self, X, L, n_per_fiber, f_ext, mu=1.0, eps=1e-3, E=1.0, dt=1e-3,
-                 delta_over_L=0.01, lsb=False, boundary=None):
+                 delta_over_L=0.01, lsb=False, boundary=None, Ldot=None):
         self.mu = mu
         self.n_per = np.asarray(n_per_fiber, dtype=np.int64)
         self.ptr = np.concatenate([[0], np.cumsum(self.n_per)])
@@ -50,7 +51,10 @@ class System:
         for m in range(len(self.n_per)):
             a, b = self.ptr[m], self.ptr[m + 1]
             self.fibers.append(Fiber(self.X[a:b], float(L[m]), np.asarray(f_ext[a:b], float), mu,
-                                     eps, E, dt, delta_over_L * float(L[m]), lsb))
+                                     eps, E, dt, delta_over_L * float(L[m]), lsb,
+                                     0.0 if Ldot is None else float(Ldot[m])))
+        self.L = np.asarray(L, float)
+        self.Ldot = np.zeros(len(self.n_per)) if Ldot is None else np.asarray(Ldot, float)
         self.uptr = np.concatenate([[0], np.cumsum(4 * self.n_per)])
         self.fid = np.repeat(np.arange(len(self.n_per), dtype=np.int32), self.n_per)
         self.Wall = np.concatenate([f.W for f in self.fibers]) if self.fibers else np.zeros(0)
@@ -163,10 +167,12 @@ class System:
         V = np.concatenate([fb.velocity_nodes(um) for fb, um in zip(self.fibers, us)])
         T = np.concatenate([fb.tension_nodes(um) for fb, um in zip(self.fibers, us)])
         dt = self.fibers[0].dt if self.fibers else 0.0
-        return StepResult(V=V, T=T, X_new=self.X + dt * V, q=q, u=u, iters=its, resid=res)
+        return StepResult(V=V, T=T, X_new=self.X + dt * V, q=q, u=u, iters=its, resid=res,
+                          L_new=self.L + dt * self.Ldot)
 
 
-def from_suspension(s, delta_over_L=0.01, lsb=False) -> System:
-    """Build the system from a workloads.Suspension."""
+def from_suspension(s, delta_over_L=0.01, lsb=False, Ldot=None) -> System:
+    """Build the system from a workloads.Suspension (Ldot: per-fiber length
+    rates, None = fixed lengths)."""
     return System(s.X, s.L, s.n_per_fiber, s.f_ext, s.mu, s.eps, s.E, s.dt, delta_over_L, lsb,
-                  s.boundary)
+                  s.boundary, Ldot)
