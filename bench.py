@@ -231,7 +231,9 @@ def run_workload(args, ws, rank, local, fs, torch):
               float-float over all targets, FP64 over 16,384 sampled targets;
     sediment  the four sedimenting clouds of Sec. 4.3 (1,024 x 16 each) in
               one batch, advanced --steps steps: steps/s and the settling
-              speeds relative to V_c."""
+              speeds relative to V_c;
+    kinetics  1,024 growing and shrinking microtubules (dynamic instability
+              with the paper's rates), advanced --steps steps."""
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     out = {"workload": args.workload, "data": "synthetic"}
@@ -321,6 +323,48 @@ def run_workload(args, ws, rank, local, fs, torch):
                     "ms_per_step": ms, "steps_per_s": 1e3 / ms, "iters": iters,
                     "settling_speed_over_Vc_first_step": first, "settling_speed_over_Vc_last_step": last,
                     "centre_of_mass_drop_over_R0": drop})
+    elif args.workload == "kinetics":
+        # 1,024 straight microtubules (L in [5, 10] um, 32 points, eps 1e-3,
+        # E = 10 pN um^2, mu = 1 pN s / um^2) in a 60 um box, at least 0.1 L
+        # apart (closer pairs go unstable under plain quadrature), weak body force,
+        # dynamic instability with the rates of the paper's parameter table
+        # (V_g 0.12, V_s 0.288 um/s, f_cat = f_res = 0.014 / s), rescue at
+        # 2 um, dt = 0.1 s
+        s = wl.free_space(1024, 32, 60.0, seed=rank, L_range=(5.0, 10.0), E=10.0, dt=0.1, min_gap=0.1)
+        s.f_ext = np.tile([0.0, 0.0, -0.05], (s.n_points, 1))
+        kin_args = (s.dt, 0.12, 0.288, 0.014, 0.014, 2.0)
+        opt = fs.fs_options_default()
+        opt.prec = fs.FS_MIXED
+        opt.tol = 1e-8
+        opt.profile = 1
+        h = fs.fs_create(s.n_per_fiber, s.mu, s.eps, s.E, s.dt, options=opt, stream=stream)
+        X = torch.tensor(s.X, device=dev)
+        fs.fs_set_state(h, X, torch.tensor(s.L, device=dev), torch.tensor(s.f_ext, device=dev))
+        rng = np.random.default_rng(rank)
+        state = np.ones(s.n_fibers, dtype=np.int32)
+
+        def one_step(info):
+            nonlocal state
+            L = fs.fs_get_lengths(h, s.n_fibers)
+            state, Ld = fs.fs_dynamic_instability(state, L, rng.random(s.n_fibers), *kin_args)
+            fs.fs_set_growth(h, Ld)
+            return fs.fs_step(h, info=info)
+
+        for _ in range(args.warmup):
+            one_step(False)
+        L0 = fs.fs_get_lengths(h, s.n_fibers)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        iters = [one_step(True).iters for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        sec = (time.perf_counter() - t0) / args.steps
+        L1 = fs.fs_get_lengths(h, s.n_fibers)
+        fs.fs_destroy(h)
+        out.update({"points": int(s.n_points), "fibers": s.n_fibers, "dt_s": s.dt,
+                    "steps": args.steps, "ms_per_step": 1e3 * sec, "steps_per_s": 1.0 / sec,
+                    "timing": "host wall clock per step (state machine, rates upload and step)",
+                    "iters": iters, "mean_length_um": [float(L0.mean()), float(L1.mean())],
+                    "growing_fraction": float(state.mean())})
     else:
         s = wl.cfg_large_matvec(seed=rank)
         opt = fs.fs_options_default()
@@ -439,7 +483,7 @@ def main():
     ap.add_argument("--tile", type=int, default=0,
                     help="far-field launch shape id (0 = default; 1..3 = targets per thread FP32 2/4/8, "
                          "float-float 1/2/4)")
-    ap.add_argument("--workload", choices=["confined", "batched", "large", "sediment"], default=None,
+    ap.add_argument("--workload", choices=["confined", "batched", "large", "sediment", "kinetics"], default=None,
                     help="a secondary workload instead of the headline step benchmark")
     ap.add_argument("--serve", type=int, default=0,
                     help="serving mode: number of independent requests (0 = the step benchmark)")

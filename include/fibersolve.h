@@ -267,6 +267,37 @@ uint64_t fs_kernel_launches(void);
  * roofline peak of the pipe-bound direct sums.  Synchronises the device. */
 fs_status fs_probe_fma(int32_t precision, double *flops_per_s);
 
+/* Plus-end growth rates dL/dt per fiber [n_fibers] for the following steps
+ * (fiber (de)polymerization, Sec. 2.4 kinetics; 0 = fixed length, the
+ * default).  The nodes stay at alpha_k in alpha = 2 s / L - 1 (minus end at
+ * alpha = -1 fixed), so each step moves them by dt (w + (alpha + 1) kappa
+ * X+_alpha) -- w the material velocity of Eq. main-sb-local, X+ = X + dt V,
+ * kappa = Ldot / (L + dt Ldot), the reparametrisation term taken at the new
+ * time -- and sets L <- L + dt Ldot.  fs_get_state's V is then (X+ - X)/dt,
+ * the nodes' rate.  FS_EINVAL if some L + dt Ldot would not stay positive.
+ * Synchronises the context's stream. */
+fs_status fs_set_growth(fs_ctx *ctx, const double *Ldot, int32_t ptr_is_device);
+
+/* Current fiber lengths [n_fibers] (after growth).  Synchronises the stream. */
+fs_status fs_get_lengths(fs_ctx *ctx, double *lengths, int32_t ptr_is_device);
+
+/* Two-state dynamic instability (Sec. 5 kinetics: catastrophe and rescue of
+ * growing and shrinking plus ends).  Host arrays; no CUDA call.  For each of
+ * the n fibers, with one uniform random number u[i] in [0, 1) supplied by
+ * the caller: a growing fiber (state 1) switches to shrinking (0) if
+ * u < 1 - exp(-f_cat dt), a shrinking one to growing if u < 1 - exp(-f_res
+ * dt); a shrinking fiber that would pass below L_min grows instead, a growing
+ * one that would pass L_max (if L_max > 0) shrinks; then Ldot[i] = v_grow or
+ * -v_shrink (pass Ldot to fs_set_growth).  state is updated in place. */
+typedef struct {
+    double v_grow, v_shrink;   /* plus-end speeds (length / time) */
+    double f_cat, f_res;       /* catastrophe and rescue rates (1 / time) */
+    double L_min, L_max;       /* rescue length; capping length (<= 0: none) */
+} fs_kinetics;
+
+fs_status fs_dynamic_instability(int32_t n, const fs_kinetics *kinetics, double dt, const double *lengths,
+                                 const double *u, int32_t *state, double *Ldot);
+
 /* Device bytes a context for this problem allocates (fs_create with these
  * fibers, a boundary of n_surface_nodes nodes or 0, and these options) plus
  * the largest direct-sum scratch one step reserves.  An upper bound of what

@@ -24,9 +24,11 @@ Velocity expression at the nodes (Eq. main-sb-local):
 Rows (4N), rectangular collocation:
     velocity   (N-4 per component, first-kind points y):  -V(y) + [P_y w](y) = 0,
                with a growing or shrinking fiber (length rate Ldot, plus end
-               at alpha = 1): -V(y) + [P_y w](y) + (y + 1)(Ldot / L) X_alpha(y) = 0
-               (the nodes sit at fixed alpha = 2 s / L - 1, so they move with
-               the material velocity w plus the reparametrisation term)
+               at alpha = 1): -V(y) + [P_y w](y) + (y + 1) kappa X+_alpha(y) = 0,
+               kappa = Ldot / (L + dt Ldot), X+ = X + dt V (the nodes sit at
+               fixed alpha = 2 s / L - 1, so they move with the material
+               velocity w plus the reparametrisation term, taken at the new
+               time like every other term of the step)
     free ends  (Eq. bc-free, on X+):  V''(+-1) + X''(+-1)/dt = 0,
                                       V'''(+-1) + X'''(+-1)/dt = 0
     tension    (N-2 first-kind points z):  X_s(z) . [D_z w](z) = 0
@@ -61,6 +63,7 @@ class FiberOps:
         BT = cheb.basis_T(N)
         pm = np.array([1.0, -1.0])
         self.V_y = cheb.basis_matrix(BV, self.y)            # (N-4, N)
+        self.V1_y = cheb.basis_matrix(BV, self.y, 1)        # (N-4, N): alpha-derivative at y
         self.V_nodes = cheb.basis_matrix(BV, a)             # (N, N)
         self.V2_pm = cheb.basis_matrix(BV, pm, 2)           # (2, N)
         self.V3_pm = cheb.basis_matrix(BV, pm, 3)           # (2, N)
@@ -156,9 +159,12 @@ class Fiber:
             const[r0 + N - 2:r0 + N] = X3[:, a] / dt
             if Ldot != 0.0:
                 # growth (Sec. 2.4, kinetics): at fixed alpha the nodes move with
-                # the material velocity plus (alpha + 1)(Ldot / L) X_alpha, so the
-                # velocity rows -V + w = 0 become -V + w + R(y) = 0
-                const[r0:r0 + N - 4] = (op.y + 1.0) * (Ldot / L) * Xa_y[:, a]
+                # the material velocity plus (alpha + 1)(Ldot / L) X_alpha; taken
+                # at the new time (length L + dt Ldot, positions X + dt V):
+                # -V + w + (y + 1) kappa (X_alpha + dt V_alpha)(y) = 0
+                kappa = Ldot / (L + dt * Ldot)
+                const[r0:r0 + N - 4] = (op.y + 1.0) * kappa * Xa_y[:, a]
+                Rd[r0:r0 + N - 4, a * N:(a + 1) * N] += dt * kappa * (op.y + 1.0)[:, None] * op.V1_y
             Rw[3 * N:4 * N - 2, a * N:(a + 1) * N] = self.tz[:, a:a + 1] * op.D_z
         Rd[4 * N - 2:4 * N, 3 * N:4 * N] = op.T_pm
         self.F, self.S, self.Rw, self.Rd, self.const = F, S, Rw, Rd, const

@@ -22,6 +22,7 @@ __all__ = ["fs_options_default", "fs_create", "fs_create_batch", "fs_batch_info"
            "fs_step", "fs_sizes", "fs_last_error", "fs_kernel_stats", "fs_kernel_launches",
            "fs_probe_fma", "fs_estimate_bytes", "fs_device_bytes", "fs_server_create", "fs_submit",
            "fs_poll", "fs_server_wait", "fs_server_stats", "fs_server_destroy", "Server", "FsError",
+           "fs_set_growth", "fs_get_lengths", "fs_dynamic_instability",
            "FS_FP64", "FS_MIXED",
            "FS_SUM_FP32", "FS_SUM_FP64", "FS_SUM_FF", "FS_SUM_FP32_PLAIN"]
 
@@ -342,3 +343,34 @@ def fs_server_destroy(sv: Server):
         _native.load().fs_server_destroy(sv.ptr)
     sv.ptr = None
     sv.pending.clear()
+
+
+def fs_set_growth(h: Handle, Ldot):
+    """Per-fiber plus-end growth rates: a CUDA tensor or a numpy array."""
+    lib = _native.load()
+    if hasattr(Ldot, "is_cuda") and Ldot.is_cuda:
+        _check(lib.fs_set_growth(h.ptr, _dev_ptr(Ldot, "f64", "Ldot"), 1), "fs_set_growth")
+    else:
+        a, p = _host_ptr(Ldot, np.float64, "Ldot")
+        _check(lib.fs_set_growth(h.ptr, p, 0), "fs_set_growth")
+
+
+def fs_get_lengths(h: Handle, M: int):
+    out = np.zeros(int(M))
+    _check(_native.load().fs_get_lengths(h.ptr, out.ctypes.data_as(ctypes.c_void_p), 0), "fs_get_lengths")
+    return out
+
+
+def fs_dynamic_instability(state, lengths, u, dt: float, v_grow: float, v_shrink: float, f_cat: float,
+                           f_res: float, L_min: float, L_max: float = 0.0):
+    """One step of the two-state dynamic instability (host, no GPU): returns
+    (new_state int32, Ldot) for the given per-fiber uniform random numbers u."""
+    st = np.ascontiguousarray(state, dtype=np.int32).copy()
+    La, Lp = _host_ptr(lengths, np.float64, "lengths")
+    ua, up = _host_ptr(u, np.float64, "u")
+    Ld = np.zeros(st.shape[0])
+    k = _native.fs_kinetics(float(v_grow), float(v_shrink), float(f_cat), float(f_res), float(L_min), float(L_max))
+    _check(_native.load().fs_dynamic_instability(int(st.shape[0]), ctypes.byref(k), float(dt), Lp, up,
+                                                 st.ctypes.data_as(ctypes.c_void_p),
+                                                 Ld.ctypes.data_as(ctypes.c_void_p)), "fs_dynamic_instability")
+    return st, Ld

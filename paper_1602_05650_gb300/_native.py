@@ -53,6 +53,11 @@ class fs_request(ctypes.Structure):
                 ("out_X", P), ("out_V", P), ("out_T", P)]
 
 
+class fs_kinetics(ctypes.Structure):
+    _fields_ = [("v_grow", c_double), ("v_shrink", c_double), ("f_cat", c_double), ("f_res", c_double),
+                ("L_min", c_double), ("L_max", c_double)]
+
+
 # name -> (restype, argtypes)
 SIGNATURES = {
     "fs_options_default": (c_int32, [ctypes.POINTER(fs_options)]),
@@ -74,6 +79,9 @@ SIGNATURES = {
     "fs_kernel_stats": (c_int32, [P, ctypes.POINTER(fs_kernel_stat), c_int32]),
     "fs_kernel_launches": (ctypes.c_uint64, []),
     "fs_probe_fma": (c_int32, [c_int32, ctypes.POINTER(c_double)]),
+    "fs_set_growth": (c_int32, [P, P, c_int32]),
+    "fs_get_lengths": (c_int32, [P, P, c_int32]),
+    "fs_dynamic_instability": (c_int32, [c_int32, ctypes.POINTER(fs_kinetics), c_double, P, P, P, P]),
     "fs_estimate_bytes": (ctypes.c_size_t, [c_int32, P, c_int32, ctypes.POINTER(fs_options)]),
     "fs_device_bytes": (c_int32, [P, ctypes.POINTER(ctypes.c_size_t)]),
     "fs_server_create": (c_int32, [ctypes.POINTER(c_void_p), ctypes.c_size_t, c_int32, c_int32]),

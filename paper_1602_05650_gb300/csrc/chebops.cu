@@ -7,6 +7,7 @@
 //   * Clenshaw-Curtis weights as the integrals of the cardinal functions.
 // Matrix meanings (row-major):
 //   Vy  [(N-4) x N] : velocity basis at the first-kind points y_i
+//   Vgy [(N-4) x N] : (y_i + 1) x alpha-derivative of the velocity basis at y_i
 //   V2, V3 [2 x N]  : 2nd, 3rd alpha-derivative of the velocity basis at alpha = +1, -1
 //   Sig [N x N]     : 4th derivative of the velocity basis at the nodes (sigma)
 //   Tn  [N x N]     : tension basis at the nodes; Vn [N x N] velocity basis at the nodes
@@ -171,8 +172,10 @@ std::vector<double> build_ops(int N)
     for (int j = 0; j < N - 2; ++j) BT.push_back(integ_m(unit(j, j + 1), 2));
     for (int k = 0; k < 2; ++k) BT.push_back(unit(k, k + 1));
     for (int j = 0; j < N; ++j) {
-        for (int i = 0; i < N - 4; ++i)
+        for (int i = 0; i < N - 4; ++i) {
             A[lay.Vy + int64_t(i) * N + j] = static_cast<double>(clenshaw(BV[j], y[i]));
+            A[lay.Vgy + int64_t(i) * N + j] = static_cast<double>((y[i] + 1.0L) * eval_deriv(BV[j], 1, y[i]));
+        }
         for (int r = 0; r < 2; ++r) {
             const R x = r == 0 ? 1.0L : -1.0L;
             A[lay.V2 + int64_t(r) * N + j] = static_cast<double>(eval_deriv(BV[j], 2, x));

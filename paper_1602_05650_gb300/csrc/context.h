@@ -17,6 +17,7 @@ struct OpsLayout {
     // the nodes (G1) and at the tension points (Gz), 2nd / 3rd derivative at
     // alpha = +1, -1 (G2, G3), 4th derivative at the nodes (G4)
     int64_t G1h, G1l, Gzh, Gzl, G2h, G2l, G3h, G3l, G4h, G4l;
+    int64_t Vgy;   // (y_i + 1) x alpha-derivative of the velocity basis at y_i (growth)
     __host__ __device__ explicit OpsLayout(int n) : N(n)
     {
         int64_t o = 0;
@@ -44,6 +45,7 @@ struct OpsLayout {
         G3l = o; o += 2 * N;
         G4h = o; o += int64_t(N) * N;
         G4l = o; o += int64_t(N) * N;
+        Vgy = o; o += int64_t(N - 4) * N;
         total = (o + 3) & ~int64_t(3);
     }
 };
@@ -76,6 +78,7 @@ struct FiberTable {
     // block-build scratch (offsets from blk_ptr: 16 N^2 per fiber)
     double *ftau;    // [3 N^2] per fiber: force of each tension column, [a][l][j]
     double *wsc;     // [12 N^2] per fiber: w = (M + K_delta) f of each column, [col][b N + k]
+    const double *Ldot;  // [M] plus-end growth rates (nullptr: fixed lengths)
 };
 
 struct Surface {
@@ -124,6 +127,8 @@ struct fs_ctx {
     double *d_t = nullptr, *d_tz = nullptr, *d_fknown = nullptr, *d_W = nullptr, *d_mloc = nullptr,
            *d_bc = nullptr, *d_kp = nullptr;
     double *d_B = nullptr;        // column-major blocks, LU factors after build
+    double *d_Ldot = nullptr;     // [M] plus-end growth rates (fs_set_growth)
+    bool growth = false;          // some rate is non-zero
     double *d_ftau = nullptr;     // block-build scratch: tension-column forces (3 N^2 per fiber)
     double *d_wsc = nullptr;      // block-build scratch: w of every column (12 N^2 per fiber)
     int *d_piv = nullptr;

@@ -240,7 +240,7 @@ __device__ void dev_selfvel(const FiberTable &F, const Fib &fb, const double *f,
 
 // rows[c][r] for r < 4N; out[c * ostride + r] = sign * row (+ const when rhs)
 __device__ void dev_rows(const FiberTable &F, const Fib &fb, const double *us, const double *w,
-                         int nb, bool rhs, double *out, int64_t ostride)
+                         int nb, bool rhs, double *out, int64_t ostride, const double *wv = nullptr)
 {
     const int N = fb.N;
     const double *Vy = fb.M_(fb.lay.Vy), *V2 = fb.M_(fb.lay.V2), *V3 = fb.M_(fb.lay.V3),
@@ -258,6 +258,8 @@ __device__ void dev_rows(const FiberTable &F, const Fib &fb, const double *us, c
             if (i < N - 4) {
                 double s = 0.0;
                 for (int j = 0; j < N; ++j) s += Py[i * N + j] * wc[3 * j + a] - Vy[i * N + j] * ca[j];
+                if (wv)   // velocity-row-only nodal field (the growth term)
+                    for (int j = 0; j < N; ++j) s += Py[i * N + j] * wv[3 * j + a];
                 val = s;
             } else if (i < N - 2) {
                 const int rr = i - (N - 4);
@@ -338,8 +340,19 @@ __global__ void __launch_bounds__(128) k_rows(FiberTable F, const double *__rest
     extern __shared__ double rsm[];
     const Fib fb(F, blockIdx.x);
     const int N = fb.N;
-    double *us = rsm, *fs_ = us + 4 * N, *w = fs_ + 3 * N;
+    double *us = rsm, *fs_ = us + 4 * N, *w = fs_ + 3 * N, *wv = w + 3 * N;
     for (int i = threadIdx.x; i < 4 * N; i += blockDim.x) us[i] = (u && mode == 0) ? u[fb.u0 + i] : 0.0;
+    // growth (known part, right-hand side only): the nodes sit at fixed alpha,
+    // so the velocity rows carry (alpha + 1) kappa X+_alpha with kappa =
+    // Ldot / (L + dt Ldot); its known part (alpha + 1) kappa X_alpha =
+    // (alpha + 1) kappa (L / 2) X_s (the dt V_alpha part is in the self block)
+    const double ldot = (mode == 1 && F.Ldot) ? F.Ldot[fb.m] : 0.0;
+    if (ldot != 0.0) {
+        const double *al = fb.M_(fb.lay.alpha);
+        const double *t = F.t + 3 * fb.n0;
+        const double kl2 = ldot / (fb.L + F.dt * ldot) * 0.5 * fb.L;
+        for (int i = threadIdx.x; i < 3 * N; i += blockDim.x) wv[i] = (al[i / 3] + 1.0) * kl2 * t[i];
+    }
     if (mode == 2) {
         for (int i = threadIdx.x; i < 3 * N; i += blockDim.x) w[i] = ubar[3 * fb.n0 + i];
     } else {
@@ -348,7 +361,7 @@ __global__ void __launch_bounds__(128) k_rows(FiberTable F, const double *__rest
         dev_selfvel(F, fb, fs_, 1, ubar, w);
     }
     __syncthreads();
-    dev_rows(F, fb, us, w, 1, mode == 1, out + fb.u0, 0);
+    dev_rows(F, fb, us, w, 1, mode == 1, out + fb.u0, 0, ldot != 0.0 ? wv : nullptr);
 }
 
 // ------------------------------------------------------------- block build
@@ -537,6 +550,10 @@ __global__ void __launch_bounds__(256) k_build_rows(FiberTable F, double *__rest
     const int nrow = vel ? N - 4 : N - 2;
     const double *W = F.wsc + fb.blk0 / 4 * 3;
     const double *Py = fb.M_(fb.lay.Py), *Vy = fb.M_(fb.lay.Vy), *Dz = fb.M_(fb.lay.Dz);
+    const double *Vgy = fb.M_(fb.lay.Vgy);
+    // growth at the new time: (y + 1) kappa dt V_alpha(y), kappa = Ldot / (L + dt Ldot)
+    const double ldot = F.Ldot ? F.Ldot[fb.m] : 0.0;
+    const double gdt = ldot != 0.0 ? F.dt * ldot / (fb.L + F.dt * ldot) : 0.0;
     const double *tz = F.tz + 3 * fb.z0;
     double acc[4][4] = {};
     auto b_of_w = [&](int q, int cc) -> double {   // W[col][q], q component-major
@@ -571,7 +588,7 @@ __global__ void __launch_bounds__(256) k_build_rows(FiberTable F, double *__rest
             int row;
             if (vel) {
                 row = a * N + r;
-                if (col < 3 * N && col / N == a) v -= Vy[r * N + (col - a * N)];
+                if (col < 3 * N && col / N == a) v += gdt * Vgy[r * N + (col - a * N)] - Vy[r * N + (col - a * N)];
             } else {
                 row = 3 * N + r;
             }
@@ -877,9 +894,10 @@ __global__ void __launch_bounds__(256) k_lu_solve(FiberTable F, const double *__
     for (int i = tid; i < n; i += blockDim.x) out[fb.u0 + i] = y[i];
 }
 
+// V, T at the nodes; X <- X + dt V; L <- L + dt Ldot (growth)
 __global__ void __launch_bounds__(128) k_update(FiberTable F, const double *__restrict__ u,
                                                 double *__restrict__ X, double *__restrict__ V,
-                                                double *__restrict__ T)
+                                                double *__restrict__ T, double *__restrict__ L)
 {
     const Fib fb(F, blockIdx.x);
     const int N = fb.N;
@@ -896,6 +914,10 @@ __global__ void __launch_bounds__(128) k_update(FiberTable F, const double *__re
             for (int j = 0; j < N; ++j) s += Tn[k * N + j] * us[3 * N + j];
             T[fb.n0 + k] = s;
         }
+    }
+    if (F.Ldot) {
+        __syncthreads();   // every thread has read L (in fb) before it changes
+        if (threadIdx.x == 0) L[fb.m] += F.dt * F.Ldot[fb.m];
     }
 }
 
@@ -923,7 +945,7 @@ fs_status launch_rows(fs_ctx *c, const double *u, const double *f, const double 
                       int mode)
 {
     if (c->M == 0) return FS_OK;
-    const size_t sm = static_cast<size_t>(10 * c->max_N) * sizeof(double);
+    const size_t sm = static_cast<size_t>(13 * c->max_N) * sizeof(double);
     k_rows<<<c->M, 128, sm, c->stream>>>(c->table(), u, f, ubar, out, mode);
     FS_LAUNCH_CHECK();
     return FS_OK;
@@ -981,7 +1003,7 @@ fs_status launch_lu_solve(fs_ctx *c, const double *in, double *out)
 fs_status launch_update(fs_ctx *c, const double *u)
 {
     if (c->M == 0) return FS_OK;
-    k_update<<<c->M, 128, 0, c->stream>>>(c->table(), u, c->d_X, c->d_V, c->d_T);
+    k_update<<<c->M, 128, 0, c->stream>>>(c->table(), u, c->d_X, c->d_V, c->d_T, c->d_L);
     FS_LAUNCH_CHECK();
     return FS_OK;
 }

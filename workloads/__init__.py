@@ -105,15 +105,21 @@ def _curved_fiber(rng, centre, direction, length, alpha, amp, n_modes=4, n_gl=96
 
 def free_space(M: int, N, side: float, seed: int = 0, curved_amp: float = 0.0,
                L_range=(1.0, 3.0), mu=1.0, eps=1e-3, E=1.0, dt=1e-3,
-               centre_offset=None) -> Suspension:
-    """M fibers in the cube [0, side]^3 (N may be an int or a per-fiber array)."""
+               centre_offset=None, min_gap: float = 0.0) -> Suspension:
+    """M fibers in the cube [0, side]^3 (N may be an int or a per-fiber array).
+    min_gap > 0: straight chords at least min_gap x (mean length) apart
+    (random sequential addition)."""
     rng = np.random.default_rng(seed)
     n_per = np.full(M, N, dtype=np.int32) if np.isscalar(N) else np.asarray(N, np.int32)
-    centres = rng.uniform(0.0, side, size=(M, 3))
+    if min_gap > 0.0:
+        L = rng.uniform(L_range[0], L_range[1], size=M)
+        centres, dirs = _place_separated(rng, M, L, lambda: rng.uniform(0.0, side, size=3), min_gap)
+    else:
+        centres = rng.uniform(0.0, side, size=(M, 3))
+        dirs = _unit_vectors(rng, M)
+        L = rng.uniform(L_range[0], L_range[1], size=M)
     if centre_offset is not None:
         centres = centres + np.asarray(centre_offset)[None, :]
-    dirs = _unit_vectors(rng, M)
-    L = rng.uniform(L_range[0], L_range[1], size=M)
     return _assemble(rng, n_per, centres, dirs, L, curved_amp, mu, eps, E, dt, None)
 
 
@@ -186,9 +192,9 @@ def batched(n_systems: int, seed: int = 0, fibers_range=(8, 512),
     return out
 
 
-def _segment_distances(p, u, P, U, half):
-    """Closest distances between the segment p +- half u and the segments
-    P[k] +- half U[k] (u, U unit vectors)."""
+def _segment_distances(p, u, h, P, U, H):
+    """Closest distances between the segment p +- h u and the segments
+    P[k] +- H[k] U[k] (u, U unit vectors)."""
     w = p[None, :] - P
     b = U @ u
     d = w @ u
@@ -196,11 +202,32 @@ def _segment_distances(p, u, P, U, half):
     den = 1.0 - b * b
     with np.errstate(divide="ignore", invalid="ignore"):
         s = np.where(den > 1e-12, (b * e - d) / den, 0.0)
-    s = np.clip(s, -half, half)
-    t = np.clip(b * s + e, -half, half)
-    s = np.clip(b * t - d, -half, half)
+    s = np.clip(s, -h, h)
+    t = np.clip(b * s + e, -H, H)
+    s = np.clip(b * t - d, -h, h)
     diff = w + s[:, None] * u[None, :] - t[:, None] * U
     return np.linalg.norm(diff, axis=1)
+
+
+def _place_separated(rng, M, L, sample_centre, min_gap):
+    """Random sequential addition of M straight segments of lengths L with
+    centres from sample_centre() and uniform orientations, each at least
+    min_gap x (mean of the two lengths) from all earlier ones."""
+    centres = np.zeros((M, 3))
+    dirs = np.zeros((M, 3))
+    k = tries = 0
+    while k < M:
+        tries += 1
+        if tries > 1000 * M:
+            raise RuntimeError("could not place the fibers with this gap")
+        c = sample_centre()
+        u = _unit_vectors(rng, 1)[0]
+        if k and np.any(_segment_distances(c, u, L[k] / 2.0, centres[:k], dirs[:k], L[:k] / 2.0)
+                        < min_gap * 0.5 * (L[k] + L[:k])):
+            continue
+        centres[k], dirs[k] = c, u
+        k += 1
+    return centres, dirs
 
 
 def sedimenting_cloud(L_over_R: float, M: int = 1024, N: int = 16, seed: int = 0, R0: float = 1.0,
@@ -216,22 +243,9 @@ def sedimenting_cloud(L_over_R: float, M: int = 1024, N: int = 16, seed: int = 0
     (the cloud moves ~0.003 R0 per step)."""
     rng = np.random.default_rng(seed)
     n_per = np.full(M, N, dtype=np.int32)
-    Lf = L_over_R * R0
-    centres = np.zeros((M, 3))
-    dirs = np.zeros((M, 3))
-    k = 0
-    tries = 0
-    while k < M:
-        tries += 1
-        if tries > 1000 * M:
-            raise RuntimeError("sedimenting_cloud: could not place the fibers with this gap")
-        c = _unit_vectors(rng, 1)[0] * R0 * rng.uniform() ** (1.0 / 3.0)
-        u = _unit_vectors(rng, 1)[0]
-        if k and np.min(_segment_distances(c, u, centres[:k], dirs[:k], Lf / 2.0)) < min_gap * Lf:
-            continue
-        centres[k], dirs[k] = c, u
-        k += 1
-    L = np.full(M, Lf)
+    L = np.full(M, L_over_R * R0)
+    centres, dirs = _place_separated(rng, M, L, lambda: _unit_vectors(rng, 1)[0] * R0 * rng.uniform() ** (1.0 / 3.0),
+                                     min_gap)
     s = _assemble(rng, n_per, centres, dirs, L, 0.0, 1.0, 0.01, 3.2e-3 * f0 * R0 ** 3, dt, None)
     s.f_ext = np.tile([0.0, 0.0, -f0], (s.n_points, 1))
     return s
