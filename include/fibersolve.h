@@ -278,6 +278,14 @@ fs_status fs_probe_fma(int32_t precision, double *flops_per_s);
  * Synchronises the context's stream. */
 fs_status fs_set_growth(fs_ctx *ctx, const double *Ldot, int32_t ptr_is_device);
 
+/* The unknown vector of the last step's solve [n_unknowns] (fs_sizes): per
+ * fiber the coefficients [c_x, c_y, c_z, d] (N each) of V_a = sum_j c_a,j
+ * phi_j, phi = I^4 T_0 .. I^4 T_{N-5}, T_0 .. T_3, and T = sum_j d_j psi_j,
+ * psi = I^2 T_0 .. I^2 T_{N-3}, T_0, T_1 (Eq. cheb-basis, integrated form;
+ * I^m the m-fold integral from alpha = -1), then the periphery density
+ * [n_nodes][3].  Synchronises the context's stream. */
+fs_status fs_get_unknowns(fs_ctx *ctx, double *u, int32_t ptr_is_device);
+
 /* Current fiber lengths [n_fibers] (after growth).  Synchronises the stream. */
 fs_status fs_get_lengths(fs_ctx *ctx, double *lengths, int32_t ptr_is_device);
 

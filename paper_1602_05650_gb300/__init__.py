@@ -22,7 +22,7 @@ __all__ = ["fs_options_default", "fs_create", "fs_create_batch", "fs_batch_info"
            "fs_step", "fs_sizes", "fs_last_error", "fs_kernel_stats", "fs_kernel_launches",
            "fs_probe_fma", "fs_estimate_bytes", "fs_device_bytes", "fs_server_create", "fs_submit",
            "fs_poll", "fs_server_wait", "fs_server_stats", "fs_server_destroy", "Server", "FsError",
-           "fs_set_growth", "fs_get_lengths", "fs_dynamic_instability",
+           "fs_set_growth", "fs_get_lengths", "fs_get_unknowns", "fs_dynamic_instability",
            "FS_FP64", "FS_MIXED",
            "FS_SUM_FP32", "FS_SUM_FP64", "FS_SUM_FF", "FS_SUM_FP32_PLAIN"]
 
@@ -374,3 +374,10 @@ def fs_dynamic_instability(state, lengths, u, dt: float, v_grow: float, v_shrink
                                                  st.ctypes.data_as(ctypes.c_void_p),
                                                  Ld.ctypes.data_as(ctypes.c_void_p)), "fs_dynamic_instability")
     return st, Ld
+
+
+def fs_get_unknowns(h: Handle):
+    """The last solve's unknown vector (host numpy array of fs_sizes()[1])."""
+    out = np.zeros(int(h.n_unknowns))
+    _check(_native.load().fs_get_unknowns(h.ptr, out.ctypes.data_as(ctypes.c_void_p), 0), "fs_get_unknowns")
+    return out

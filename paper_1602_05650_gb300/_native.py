@@ -81,6 +81,7 @@ SIGNATURES = {
     "fs_probe_fma": (c_int32, [c_int32, ctypes.POINTER(c_double)]),
     "fs_set_growth": (c_int32, [P, P, c_int32]),
     "fs_get_lengths": (c_int32, [P, P, c_int32]),
+    "fs_get_unknowns": (c_int32, [P, P, c_int32]),
     "fs_dynamic_instability": (c_int32, [c_int32, ctypes.POINTER(fs_kinetics), c_double, P, P, P, P]),
     "fs_estimate_bytes": (ctypes.c_size_t, [c_int32, P, c_int32, ctypes.POINTER(fs_options)]),
     "fs_device_bytes": (c_int32, [P, ctypes.POINTER(ctypes.c_size_t)]),

@@ -1093,6 +1093,18 @@ fs_status fs_set_growth(fs_ctx *c, const double *Ldot, int32_t dev)
     return FS_OK;
 }
 
+fs_status fs_get_unknowns(fs_ctx *c, double *u, int32_t dev)
+{
+    if (!c || !u || c->n_unk == 0) {
+        set_error("fs_get_unknowns: NULL argument or empty context");
+        return FS_EINVAL;
+    }
+    FS_CUDA(cudaMemcpyAsync(u, c->d_x, static_cast<size_t>(c->n_unk) * sizeof(double),
+                            dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    FS_CUDA(cudaStreamSynchronize(c->stream));
+    return FS_OK;
+}
+
 fs_status fs_get_lengths(fs_ctx *c, double *L, int32_t dev)
 {
     if (!c || c->M == 0 || !L) {
