@@ -65,6 +65,8 @@ class FiberOps:
         self.V_y = cheb.basis_matrix(BV, self.y)            # (N-4, N)
         self.V1_y = cheb.basis_matrix(BV, self.y, 1)        # (N-4, N): alpha-derivative at y
         self.V_nodes = cheb.basis_matrix(BV, a)             # (N, N)
+        self.V0_pm = cheb.basis_matrix(BV, pm)              # (2, N): V at alpha = +1, -1
+        self.V1_pm = cheb.basis_matrix(BV, pm, 1)           # (2, N)
         self.V2_pm = cheb.basis_matrix(BV, pm, 2)           # (2, N)
         self.V3_pm = cheb.basis_matrix(BV, pm, 3)           # (2, N)
         self.sig_nodes = cheb.basis_matrix(BV, a, 4)        # (N, N): sigma at nodes
@@ -92,12 +94,16 @@ def stokeslet_tensor(r: np.ndarray, mu: float) -> np.ndarray:
     return (np.eye(3) + h[..., :, None] * h[..., None, :]) / (8.0 * math.pi * mu * rn[..., None, None])
 
 
+FREE, CLAMPED, HINGED = 0, 1, 2      # minus-end condition (Sec. 2.3)
+
+
 class Fiber:
     """Explicit geometry and operator matrices of one fiber (Sec. 3.2: geometry
     frozen at the current step, forces implicit)."""
 
     def __init__(self, X: np.ndarray, L: float, f_ext: np.ndarray, mu: float, eps: float,
-                 E: float, dt: float, delta: float, lsb: bool = False, Ldot: float = 0.0):
+                 E: float, dt: float, delta: float, lsb: bool = False, Ldot: float = 0.0,
+                 attach: int = FREE):
         N = X.shape[0]
         op = ops_for(N)
         self.N, self.op, self.L = N, op, L
@@ -167,6 +173,30 @@ class Fiber:
                 Rd[r0:r0 + N - 4, a * N:(a + 1) * N] += dt * kappa * (op.y + 1.0)[:, None] * op.V1_y
             Rw[3 * N:4 * N - 2, a * N:(a + 1) * N] = self.tz[:, a:a + 1] * op.D_z
         Rd[4 * N - 2:4 * N, 3 * N:4 * N] = op.T_pm
+        # minus end (alpha = -1, s = 0) attached to a rigid body (Sec. 2.3,
+        # Eqs. BC2-1, BC2-2, BC2-T); the body's U, Omega enter through
+        # rigid_rows.  The V_aaa(-1) rows become the position condition
+        # V(-1) = U + Omega x (X(-1) - X^P); clamped: the V_aa(-1) rows become
+        # g V_a(-1) = Omega x X_s(-1) (hinged keeps X+_aa(-1) = 0, torque
+        # free); the T(-1) = 0 row becomes the tangential projection of the
+        # velocity expression at the end, X_s . w(-1) = X_s . (U + Omega x r).
+        self.attach = attach
+        self.X_end = np.asarray(X[N - 1], float)
+        self.X2m = np.asarray(X2[1], dtype=float)          # X_aa(-1)
+        self.X3m = np.asarray(X3[1], dtype=float)          # X_aaa(-1)
+        if attach != FREE:
+            for a in range(3):
+                r0 = a * N
+                Rd[r0 + N - 1, :] = 0.0
+                Rd[r0 + N - 1, a * N:(a + 1) * N] = op.V0_pm[1]
+                const[r0 + N - 1] = 0.0
+                if attach == CLAMPED:
+                    Rd[r0 + N - 3, :] = 0.0
+                    Rd[r0 + N - 3, a * N:(a + 1) * N] = g * op.V1_pm[1]
+                    const[r0 + N - 3] = 0.0
+                Rw[4 * N - 1, a * N + N - 1] = self.t[N - 1, a]
+            Rd[4 * N - 1, :] = 0.0
+            const[4 * N - 1] = 0.0
         self.F, self.S, self.Rw, self.Rd, self.const = F, S, Rw, Rd, const
         self.B = Rd + Rw @ S @ F
 
@@ -194,6 +224,42 @@ class Fiber:
     def velocity_nodes(self, u: np.ndarray) -> np.ndarray:
         N = self.N
         return np.stack([self.op.V_nodes @ u[a * N:(a + 1) * N] for a in range(3)], axis=1)
+
+    def rigid_rows(self, U: np.ndarray, Om: np.ndarray, Xp: np.ndarray) -> np.ndarray:
+        """Terms of the attached-end rows in the body's U, Omega (zero for a
+        free fiber)."""
+        N = self.N
+        out = np.zeros(4 * N)
+        if self.attach == FREE:
+            return out
+        te = np.asarray(self.t[N - 1], float)
+        v = U + np.cross(Om, self.X_end - Xp)
+        for a in range(3):
+            out[a * N + N - 1] = -v[a]
+        if self.attach == CLAMPED:
+            w = np.cross(Om, te)
+            for a in range(3):
+                out[a * N + N - 3] = -w[a]
+        out[4 * N - 1] = -te @ v
+        return out
+
+    def end_load(self, u, Xp: np.ndarray, known: bool):
+        """(force, torque about Xp) that the attached end exerts on the body,
+        from the rod's force and moment balance: F^I(0) = -E X+_sss + T X_s and
+        (X(0) - X^P) x F^I(0) + E X_s x X+_ss at s = 0 (Sec. 2.3, Eqs. f-ext,
+        t-ext), X+ = X + dt V.  known: the part without unknowns (u ignored);
+        else the part linear in u."""
+        N, op, g, dt, E = self.N, self.op, 2.0 / self.L, self.dt, self.E
+        te = np.asarray(self.t[N - 1], float)
+        if known:
+            X3, X2, Tm = self.X3m, self.X2m, 0.0
+        else:
+            X3 = dt * np.array([op.V3_pm[1] @ u[a * N:(a + 1) * N] for a in range(3)])
+            X2 = dt * np.array([op.V2_pm[1] @ u[a * N:(a + 1) * N] for a in range(3)])
+            Tm = op.T_pm[1] @ u[3 * N:4 * N]
+        F = -E * g ** 3 * X3 + Tm * te
+        L = np.cross(self.X_end - Xp, F) + E * g ** 2 * np.cross(te, X2)
+        return F, L
 
     def tension_nodes(self, u: np.ndarray) -> np.ndarray:
         N = self.N

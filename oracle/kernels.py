@@ -37,6 +37,8 @@ def _load():
         lib.oracle_stresslet.argtypes = [I64, P, I64, P, P, P, P, P]
         lib.oracle_surface_self.argtypes = [I64, P, P, P, P, P]
         lib.oracle_surface_diag.argtypes = [I64, P, P, P, P]
+        lib.oracle_body_self.argtypes = [I64, P, P, P, P, P]
+        lib.oracle_body_diag.argtypes = [I64, P, P, P, P]
         lib.oracle_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -90,4 +92,21 @@ def surface_diag(y, normal, w) -> np.ndarray:
     y, normal, w = map(_f64, (y, normal, w))
     out = np.zeros((y.shape[0], 3))
     _load().oracle_surface_diag(y.shape[0], _p(y), _p(normal), _p(w), _p(out))
+    return out
+
+
+def body_self(y, normal, w, q) -> np.ndarray:
+    """-q/2 + T_pv[q] on a rigid body's surface nodes (fluid outside), by
+    singularity subtraction."""
+    y, normal, w, q = map(_f64, (y, normal, w, q))
+    out = np.zeros((y.shape[0], 3))
+    _load().oracle_body_self(y.shape[0], _p(y), _p(normal), _p(w), _p(q), _p(out))
+    return out
+
+
+def body_diag(y, normal, w) -> np.ndarray:
+    """Diagonal entries of body_self as a [n, 3] array."""
+    y, normal, w = map(_f64, (y, normal, w))
+    out = np.zeros((y.shape[0], 3))
+    _load().oracle_body_diag(y.shape[0], _p(y), _p(normal), _p(w), _p(out))
     return out

@@ -152,3 +152,63 @@ void oracle_surface_diag(int64_t n, const double *y, const double *normal, const
         }
     }
 }
+
+/* Rigid body surface, fluid OUTSIDE (Eq. main-nsb-second-kind): the limit of
+ * the double layer from the fluid side is -q/2 + T_pv[q]; with the Gauss
+ * identity (the double layer of a constant c is 0 outside, c/2 on the
+ * surface) it is the subtracted sum
+ *   out_i = sum_{j != i} w_j T(y_i - y_j) : ((q_j - q_i) n_j).
+ * No rank completion here: the body's Stokeslet, rotlet and rigid-motion
+ * unknowns are added by the caller. */
+void oracle_body_self(int64_t n, const double *y, const double *normal, const double *w,
+                      const double *q, double *out)
+{
+    const double c = -3.0 / (4.0 * M_PI);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        double u[3] = {0.0, 0.0, 0.0};
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double r[3], h[3], dq[3];
+            for (int a = 0; a < 3; ++a) r[a] = y[3 * i + a] - y[3 * j + a];
+            double rn = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+            for (int a = 0; a < 3; ++a) {
+                h[a] = r[a] / rn;
+                dq[a] = q[3 * j + a] - q[3 * i + a];
+            }
+            for (int a = 0; a < 3; ++a) {
+                double s = 0.0;
+                for (int b = 0; b < 3; ++b)
+                    for (int cc = 0; cc < 3; ++cc)
+                        s += c * h[a] * h[b] * h[cc] / (rn * rn) * dq[b] * normal[3 * j + cc];
+                u[a] += w[j] * s;
+            }
+        }
+        for (int a = 0; a < 3; ++a) out[3 * i + a] = u[a];
+    }
+}
+
+/* Diagonal of oracle_body_self: coefficient of q_{i,a} in row (i,a)
+ * (Jacobi entries of the body block, Eq. prec). */
+void oracle_body_diag(int64_t n, const double *y, const double *normal, const double *w,
+                      double *out)
+{
+    const double c = -3.0 / (4.0 * M_PI);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        for (int a = 0; a < 3; ++a) {
+            double s = 0.0;
+            for (int64_t j = 0; j < n; ++j) {
+                if (j == i) continue;
+                double r[3], h[3];
+                for (int b = 0; b < 3; ++b) r[b] = y[3 * i + b] - y[3 * j + b];
+                double rn = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+                for (int b = 0; b < 3; ++b) h[b] = r[b] / rn;
+                double t = 0.0;
+                for (int cc = 0; cc < 3; ++cc) t += c * h[a] * h[a] * h[cc] / (rn * rn) * normal[3 * j + cc];
+                s -= w[j] * t;
+            }
+            out[3 * i + a] = s;
+        }
+    }
+}

@@ -20,6 +20,9 @@ fibers with 31 points (Table 2), a sedimenting cloud of 1024 free fibers
   ball of radius R_c, with the sphere's 4x4 Gauss-Legendre patch nodes.
 * ``batched``: independent free-space systems with log-uniform fiber counts
   and mixed points per fiber.
+* ``aster``: a rigid sphere with fibers attached at their minus ends, pointing
+  outwards, inside a spherical periphery of six body radii (Table 2), driven
+  by a force on the sphere.
 """
 from __future__ import annotations
 
@@ -40,6 +43,24 @@ class Boundary:
 
 
 @dataclasses.dataclass
+class RigidBody:
+    """A rigid sphere: centre, radius, quadrature nodes on its surface
+    (absolute positions), outward normals, weights, and the external force
+    and torque applied to it."""
+    centre: np.ndarray    # [3]
+    radius: float
+    nodes: np.ndarray     # [n, 3]
+    normals: np.ndarray   # [n, 3]
+    weights: np.ndarray   # [n]
+    force: np.ndarray     # [3]
+    torque: np.ndarray    # [3]
+
+
+# minus-end conditions of a fiber (codes shared with the library's interface)
+FREE, CLAMPED, HINGED = 0, 1, 2
+
+
+@dataclasses.dataclass
 class Suspension:
     """One fiber suspension: all arrays fiber-major, nodes of fiber m at
     rows ptr[m]:ptr[m+1]."""
@@ -52,6 +73,8 @@ class Suspension:
     E: float = 1.0
     dt: float = 1e-3
     boundary: Optional[Boundary] = None
+    body: Optional[RigidBody] = None
+    attach: Optional[np.ndarray] = None   # [M] int32 minus-end condition (FREE/CLAMPED/HINGED)
 
     @property
     def ptr(self) -> np.ndarray:
@@ -278,3 +301,78 @@ def cfg_confined(seed: int = 0) -> Suspension:
 def cfg_large_matvec(seed: int = 0) -> Suspension:
     """8,192 fibers x 128 points in [0,80]^3 (1,048,576 points)."""
     return free_space(8192, 128, 80.0, seed=seed)
+
+
+def sphere_body(centre, radius: float, n_theta: int, n_phi: int, force=(0.0, 0.0, 0.0),
+                torque=(0.0, 0.0, 0.0), q: int = 4) -> RigidBody:
+    """A rigid sphere with the periphery's patch quadrature (q x q
+    Gauss-Legendre nodes on n_theta x n_phi (theta, phi) patches)."""
+    c = np.asarray(centre, dtype=np.float64)
+    b = sphere_quadrature(radius, n_theta, n_phi, q)
+    return RigidBody(centre=c, radius=float(radius), nodes=b.nodes + c[None, :], normals=b.normals,
+                     weights=b.weights, force=np.asarray(force, dtype=np.float64),
+                     torque=np.asarray(torque, dtype=np.float64))
+
+
+def _attachment_dirs(n: int, n_theta: int, n_phi: int) -> np.ndarray:
+    """n near-uniform unit vectors, each at the centre of a distinct cell of a
+    refined (theta, phi) patch grid, so that no attachment point falls on a
+    Gauss-Legendre node: Fibonacci-sphere directions, each moved to the
+    nearest unused cell centre (k x k cells per patch, k the smallest with
+    at least two cells per fiber)."""
+    k = 1
+    while n_theta * n_phi * k * k < 2 * n:
+        k += 1
+    th = (np.arange(n_theta * k) + 0.5) * math.pi / (n_theta * k)
+    ph = (np.arange(n_phi * k) + 0.5) * 2.0 * math.pi / (n_phi * k)
+    TH, PH = np.meshgrid(th, ph, indexing="ij")
+    cand = np.stack([np.sin(TH) * np.cos(PH), np.sin(TH) * np.sin(PH), np.cos(TH)], -1).reshape(-1, 3)
+    used = np.zeros(cand.shape[0], dtype=bool)
+    golden = math.pi * (3.0 - math.sqrt(5.0))
+    out = np.zeros((n, 3))
+    for i in range(n):
+        z = 1.0 - (2.0 * i + 1.0) / n
+        r = math.sqrt(max(0.0, 1.0 - z * z))
+        d = np.array([r * math.cos(golden * i), r * math.sin(golden * i), z])
+        score = cand @ d
+        score[used] = -np.inf
+        j = int(np.argmax(score))
+        used[j] = True
+        out[i] = cand[j]
+    return out
+
+
+def aster(n_fibers: int, N: int = 32, radius: float = 1.0, L: Optional[float] = None,
+          R_periphery: Optional[float] = 6.0, body_grid=(8, 16), periphery_grid=(12, 24),
+          attach: int = CLAMPED, force=None, torque=(0.0, 0.0, 0.0), fiber_force_std: float = 0.0,
+          tilt: float = 0.0, seed: int = 0, mu=1.0, eps=1e-3, E=1.0, dt=1e-2) -> Suspension:
+    """Fibers of length L (default 2 radius) attached at their minus ends
+    (alpha = -1, the last node) to a rigid sphere of the given radius centred
+    at the origin, pointing outwards (tilted from the normal by an angle
+    uniform in [0, tilt]); a spherical periphery of radius R_periphery x
+    radius (None: free space); a force on the sphere (default along z, of
+    size E / (32 L^2): 1/32 of the elastic force scale, Table 2) and
+    optional i.i.d. N(0, fiber_force_std^2) force per node on the fibers."""
+    rng = np.random.default_rng(seed)
+    L = 2.0 * radius if L is None else float(L)
+    d = _attachment_dirs(n_fibers, body_grid[0], body_grid[1])
+    dirs = d.copy()
+    if tilt > 0.0:
+        for m in range(n_fibers):
+            p = np.cross(d[m], rng.normal(size=3))
+            p /= np.linalg.norm(p)
+            a = rng.uniform(0.0, tilt)
+            dirs[m] = math.cos(a) * d[m] + math.sin(a) * p
+    alpha = collocation_alpha(N)
+    X = np.concatenate([radius * d[m][None, :] + ((alpha + 1.0) * L / 2.0)[:, None] * dirs[m][None, :]
+                        for m in range(n_fibers)]) if n_fibers else np.zeros((0, 3))
+    f_ext = fiber_force_std * rng.normal(size=X.shape) if fiber_force_std > 0.0 else np.zeros(X.shape)
+    if force is None:
+        force = (0.0, 0.0, E / (32.0 * L * L))
+    body = sphere_body((0.0, 0.0, 0.0), radius, body_grid[0], body_grid[1], force, torque)
+    bnd = None
+    if R_periphery is not None:
+        bnd = sphere_quadrature(R_periphery * radius, periphery_grid[0], periphery_grid[1])
+    return Suspension(n_per_fiber=np.full(n_fibers, N, dtype=np.int32), X=X,
+                      L=np.full(n_fibers, L), f_ext=f_ext, mu=mu, eps=eps, E=E, dt=dt, boundary=bnd,
+                      body=body, attach=np.full(n_fibers, attach, dtype=np.int32))
