@@ -73,6 +73,30 @@ typedef struct {
     const double *weights;  /* [n_nodes]    */
 } fs_boundary;
 
+/* A rigid sphere immersed in the suspension (Sec. 2.2, Eqs.
+ * main-nsb-second-kind, main-nsb-rgbt, main-nsb-rgbr): the fluid outside it
+ * sees its completed double layer T[q1] + G(x - center) F + R(x - center) L,
+ * its surface moves rigidly with the unknown velocities U, Omega, and F, L are
+ * the external force and torque below plus those of the attached fibers
+ * (Eqs. f-ext, t-ext).  Surface quadrature as for fs_boundary: node positions
+ * (absolute), outward unit normals, weights; host arrays, copied at creation. */
+typedef struct {
+    double center[3];
+    double radius;
+    int32_t n_nodes;
+    const double *nodes;    /* [n_nodes][3] */
+    const double *normals;  /* [n_nodes][3] */
+    const double *weights;  /* [n_nodes]    */
+    double force[3];        /* external force on the body */
+    double torque[3];       /* external torque on the body, about center */
+} fs_body;
+
+/* Minus-end (s = 0, alpha = -1) condition of a fiber (Sec. 2.3): free
+ * (Eq. bc-free), clamped to the body (Eqs. BC2-1, BC2-2, BC2-T: the end moves
+ * with the body and its tangent turns with it) or hinged (Eqs. BC2-1, BC2-T
+ * and X_ss = 0: the end moves with the body, no torque at the hinge). */
+enum { FS_END_FREE = 0, FS_END_CLAMPED = 1, FS_END_HINGED = 2 };
+
 typedef struct {
     int32_t prec;           /* fs_precision (default FS_MIXED) */
     double tol;             /* preconditioned relative residual target (default 1e-8):
@@ -148,6 +172,27 @@ fs_status fs_options_default(fs_options *opt);
 fs_status fs_create(fs_ctx **out, int32_t n_fibers, const int32_t *points_per_fiber,
                     double mu, double eps, double E, double dt,
                     const fs_boundary *boundary, const fs_options *opt, void *cuda_stream);
+
+/* fs_create with a rigid body (body != NULL) and per-fiber minus-end
+ * conditions minus_end[n_fibers] (FS_END_*; host array, copied; NULL = all
+ * free).  Fibers clamped or hinged to the body should start with their last
+ * node (alpha = -1) on its surface.  The unknown vector (fs_get_unknowns)
+ * then ends with the body's density [n_nodes][3], U [3] and Omega [3], after
+ * the periphery density.  Every fs_step moves the body's center and nodes by
+ * dt U.  Errors: FS_EINVAL for an incomplete body, a non-positive radius, an
+ * unknown end code, or an attached end without a body. */
+fs_status fs_create_with_body(fs_ctx **out, int32_t n_fibers, const int32_t *points_per_fiber,
+                              const int32_t *minus_end, double mu, double eps, double E, double dt,
+                              const fs_boundary *boundary, const fs_body *body, const fs_options *opt,
+                              void *cuda_stream);
+
+/* The body's current center, and U, Omega of the last step (host arrays of
+ * 3, any may be NULL).  Synchronises the context's stream.  FS_EINVAL
+ * without a body. */
+fs_status fs_get_body(fs_ctx *ctx, double *center, double *U, double *Omega);
+
+/* Replace the external force and torque on the body (host arrays of 3). */
+fs_status fs_set_body_load(fs_ctx *ctx, const double *force, const double *torque);
 
 /* A context holding n_systems independent free-space suspensions (fibers
  * 0..fibers_per_system[0]-1 form system 0, and so on; points_per_fiber lists all
@@ -237,7 +282,11 @@ fs_status fs_stresslet_apply(fs_ctx *ctx, const double *src_xyz, const double *s
  * main-cortex-density, fluid-side limit, singularity subtraction of Sec.
  * 3.1.2, rank completion N):
  *   out_i = sum_{j != i} w_j T(y_i - y_j):((q_j - q_i) n_j) + q_i + n_i sum_j w_j n_j.q_j
- * q, out: DEVICE [n_nodes][3].  FS_EINVAL if the context has no boundary. */
+ * q, out: DEVICE [n_nodes][3].  FS_EINVAL if the context has no boundary.
+ * With a rigid body (fs_create_with_body) q and out span all surface
+ * unknowns: the periphery's then the body's nodes [n][3], then U, Omega; body
+ * nodes give the rows of Eq. main-nsb-second-kind without the fibers' flow,
+ * followed by the six constraint rows (Eqs. main-nsb-rgbt, main-nsb-rgbr). */
 fs_status fs_surface_apply(fs_ctx *ctx, const double *q, double *out, int32_t sum_precision);
 
 /* Assemble the per-fiber self blocks (Eq. prec: fiber rows with the
@@ -283,7 +332,8 @@ fs_status fs_set_growth(fs_ctx *ctx, const double *Ldot, int32_t ptr_is_device);
  * phi_j, phi = I^4 T_0 .. I^4 T_{N-5}, T_0 .. T_3, and T = sum_j d_j psi_j,
  * psi = I^2 T_0 .. I^2 T_{N-3}, T_0, T_1 (Eq. cheb-basis, integrated form;
  * I^m the m-fold integral from alpha = -1), then the periphery density
- * [n_nodes][3].  Synchronises the context's stream. */
+ * [n_nodes][3], then (with a body) its density [n_nodes][3], U and Omega.
+ * Synchronises the context's stream. */
 fs_status fs_get_unknowns(fs_ctx *ctx, double *u, int32_t ptr_is_device);
 
 /* Current fiber lengths [n_fibers] (after growth).  Synchronises the stream. */

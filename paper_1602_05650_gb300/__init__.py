@@ -114,6 +114,66 @@ def fs_create(points_per_fiber, mu: float, eps: float, E: float, dt: float, boun
     return Handle(out, npts.value, nunk.value)
 
 
+FS_END_FREE, FS_END_CLAMPED, FS_END_HINGED = 0, 1, 2
+
+
+def fs_create_with_body(points_per_fiber, minus_end, mu: float, eps: float, E: float, dt: float, body,
+                        boundary=None, options: Optional[fs_options] = None, stream=None) -> Handle:
+    """A context with a rigid body (object with centre, radius, nodes,
+    normals, weights, force, torque) and per-fiber minus-end conditions
+    (FS_END_*; None = all free)."""
+    lib = _native.load()
+    ppf, ppf_p = _host_ptr(np.asarray(points_per_fiber), np.int32, "points_per_fiber")
+    M = 0 if ppf is None else int(ppf.shape[0])
+    keep = []
+    me_p = None
+    if minus_end is not None:
+        me, me_p = _host_ptr(np.asarray(minus_end), np.int32, "minus_end")
+        keep.append(me)
+    b = None
+    if boundary is not None:
+        nodes, pn = _host_ptr(boundary.nodes, np.float64, "nodes")
+        nrm, pm = _host_ptr(boundary.normals, np.float64, "normals")
+        w, pw = _host_ptr(boundary.weights, np.float64, "weights")
+        keep += [nodes, nrm, w]
+        b = fs_boundary(float(boundary.R), int(nodes.shape[0]), pn, pm, pw)
+    bn, bpn = _host_ptr(body.nodes, np.float64, "body nodes")
+    bm, bpm = _host_ptr(body.normals, np.float64, "body normals")
+    bw, bpw = _host_ptr(body.weights, np.float64, "body weights")
+    keep += [bn, bm, bw]
+    D3 = ctypes.c_double * 3
+    bd = _native.fs_body(D3(*[float(v) for v in body.centre]), float(body.radius), int(bn.shape[0]), bpn, bpm,
+                         bpw, D3(*[float(v) for v in body.force]), D3(*[float(v) for v in body.torque]))
+    st = None
+    if stream is not None:
+        st = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    out = ctypes.c_void_p()
+    _check(lib.fs_create_with_body(ctypes.byref(out), M, ppf_p, me_p, float(mu), float(eps), float(E), float(dt),
+                                   ctypes.byref(b) if b is not None else None, ctypes.byref(bd),
+                                   ctypes.byref(options) if options is not None else None, st),
+           "fs_create_with_body")
+    npts, nunk = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib.fs_sizes(out, ctypes.byref(npts), ctypes.byref(nunk)), "fs_sizes")
+    return Handle(out, npts.value, nunk.value)
+
+
+def fs_get_body(h: Handle):
+    """(centre, U, Omega) of the body, numpy arrays of 3."""
+    c, U, Om = (np.zeros(3) for _ in range(3))
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    _check(_native.load().fs_get_body(h.ptr, p(c), p(U), p(Om)), "fs_get_body")
+    return c, U, Om
+
+
+def fs_set_body_load(h: Handle, force, torque):
+    f = np.ascontiguousarray(force, dtype=np.float64)
+    t = np.ascontiguousarray(torque, dtype=np.float64)
+    if f.shape != (3,) or t.shape != (3,):
+        raise ValueError("force and torque must have 3 components")
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    _check(_native.load().fs_set_body_load(h.ptr, p(f), p(t)), "fs_set_body_load")
+
+
 def fs_create_batch(fibers_per_system, points_per_fiber, mu: float, eps: float, E: float, dt: float,
                     options: Optional[fs_options] = None, stream=None) -> Handle:
     """Independent free-space systems in one context (see include/fibersolve.h)."""

@@ -27,6 +27,11 @@ class fs_boundary(ctypes.Structure):
     _fields_ = [("R", c_double), ("n_nodes", c_int32), ("nodes", P), ("normals", P), ("weights", P)]
 
 
+class fs_body(ctypes.Structure):
+    _fields_ = [("center", c_double * 3), ("radius", c_double), ("n_nodes", c_int32), ("nodes", P),
+                ("normals", P), ("weights", P), ("force", c_double * 3), ("torque", c_double * 3)]
+
+
 class fs_options(ctypes.Structure):
     _fields_ = [("prec", c_int32), ("tol", c_double), ("max_iter", c_int32), ("restart", c_int32),
                 ("max_refine", c_int32), ("inner_tol", c_double), ("delta_over_L", c_double),
@@ -82,6 +87,10 @@ SIGNATURES = {
     "fs_set_growth": (c_int32, [P, P, c_int32]),
     "fs_get_lengths": (c_int32, [P, P, c_int32]),
     "fs_get_unknowns": (c_int32, [P, P, c_int32]),
+    "fs_create_with_body": (c_int32, [ctypes.POINTER(c_void_p), c_int32, P, P, c_double, c_double, c_double,
+                                      c_double, P, P, P, c_void_p]),
+    "fs_get_body": (c_int32, [P, P, P, P]),
+    "fs_set_body_load": (c_int32, [P, P, P]),
     "fs_dynamic_instability": (c_int32, [c_int32, ctypes.POINTER(fs_kinetics), c_double, P, P, P, P]),
     "fs_estimate_bytes": (ctypes.c_size_t, [c_int32, P, c_int32, ctypes.POINTER(fs_options)]),
     "fs_device_bytes": (c_int32, [P, ctypes.POINTER(ctypes.c_size_t)]),

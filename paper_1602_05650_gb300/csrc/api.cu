@@ -93,7 +93,8 @@ fs_status fs_options_default(fs_options *o)
 
 static fs_status create_impl(fs_ctx **out, int32_t n_systems, const int32_t *fps, int32_t n_fibers,
                              const int32_t *ppf, double mu, double eps, double E, double dt,
-                             const fs_boundary *boundary, const fs_options *opt, void *cuda_stream)
+                             const fs_boundary *boundary, const fs_options *opt, void *cuda_stream,
+                             const fs_body *body = nullptr, const int32_t *minus_end = nullptr)
 {
     if (!out) {
         set_error("fs_create: out is NULL");
@@ -118,6 +119,29 @@ static fs_status create_impl(fs_ctx **out, int32_t n_systems, const int32_t *fps
         set_error("fs_create: incomplete boundary description");
         return FS_EINVAL;
     }
+    if (body && (body->n_nodes <= 0 || !body->nodes || !body->normals || !body->weights ||
+                 !(body->radius > 0.0))) {
+        set_error("fs_create_with_body: incomplete body description");
+        return FS_EINVAL;
+    }
+    if (body)
+        for (int a = 0; a < 3; ++a)
+            if (!std::isfinite(body->center[a]) || !std::isfinite(body->force[a]) ||
+                !std::isfinite(body->torque[a])) {
+                set_error("fs_create_with_body: non-finite center or load");
+                return FS_EINVAL;
+            }
+    if (minus_end)
+        for (int m = 0; m < n_fibers; ++m) {
+            if (minus_end[m] != FS_END_FREE && minus_end[m] != FS_END_CLAMPED && minus_end[m] != FS_END_HINGED) {
+                set_error("fs_create_with_body: fiber %d has unknown end condition %d", m, minus_end[m]);
+                return FS_EINVAL;
+            }
+            if (minus_end[m] != FS_END_FREE && !body) {
+                set_error("fs_create_with_body: fiber %d is attached but there is no body", m);
+                return FS_EINVAL;
+            }
+        }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
         cudaGetLastError();
@@ -131,7 +155,7 @@ static fs_status create_impl(fs_ctx **out, int32_t n_systems, const int32_t *fps
     c->E = E;
     c->dt = dt;
     if (opt) c->opt = *opt; else fs_options_default(&c->opt);
-    fs_status s = context_init(c, n_systems, fps, n_fibers, ppf, boundary);
+    fs_status s = context_init(c, n_systems, fps, n_fibers, ppf, boundary, body, minus_end);
     if (s != FS_OK) {
         context_free(c);
         delete c;
@@ -146,6 +170,14 @@ fs_status fs_create(fs_ctx **out, int32_t n_fibers, const int32_t *ppf, double m
                     void *cuda_stream)
 {
     return create_impl(out, 1, nullptr, n_fibers, ppf, mu, eps, E, dt, boundary, opt, cuda_stream);
+}
+
+fs_status fs_create_with_body(fs_ctx **out, int32_t n_fibers, const int32_t *ppf, const int32_t *minus_end,
+                              double mu, double eps, double E, double dt, const fs_boundary *boundary,
+                              const fs_body *body, const fs_options *opt, void *cuda_stream)
+{
+    return create_impl(out, 1, nullptr, n_fibers, ppf, mu, eps, E, dt, boundary, opt, cuda_stream, body,
+                       minus_end);
 }
 
 fs_status fs_create_batch(fs_ctx **out, int32_t n_systems, const int32_t *fibers_per_system,

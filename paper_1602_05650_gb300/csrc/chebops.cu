@@ -9,6 +9,7 @@
 //   Vy  [(N-4) x N] : velocity basis at the first-kind points y_i
 //   Vgy [(N-4) x N] : (y_i + 1) x alpha-derivative of the velocity basis at y_i
 //   V2, V3 [2 x N]  : 2nd, 3rd alpha-derivative of the velocity basis at alpha = +1, -1
+//   V1 [2 x N]      : 1st alpha-derivative of the velocity basis at alpha = +1, -1
 //   Sig [N x N]     : 4th derivative of the velocity basis at the nodes (sigma)
 //   Tn  [N x N]     : tension basis at the nodes; Vn [N x N] velocity basis at the nodes
 //   Dm  [N x N]     : m-th derivative of the nodal interpolant at the nodes
@@ -180,6 +181,7 @@ std::vector<double> build_ops(int N)
             const R x = r == 0 ? 1.0L : -1.0L;
             A[lay.V2 + int64_t(r) * N + j] = static_cast<double>(eval_deriv(BV[j], 2, x));
             A[lay.V3 + int64_t(r) * N + j] = static_cast<double>(eval_deriv(BV[j], 3, x));
+            A[lay.V1 + int64_t(r) * N + j] = static_cast<double>(eval_deriv(BV[j], 1, x));
         }
         for (int k = 0; k < N; ++k) {
             // 4th derivative of I^4 T_j is T_j exactly; of T_0..T_3 it is 0

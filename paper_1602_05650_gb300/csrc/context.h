@@ -18,6 +18,7 @@ struct OpsLayout {
     // alpha = +1, -1 (G2, G3), 4th derivative at the nodes (G4)
     int64_t G1h, G1l, Gzh, Gzl, G2h, G2l, G3h, G3l, G4h, G4l;
     int64_t Vgy;   // (y_i + 1) x alpha-derivative of the velocity basis at y_i (growth)
+    int64_t V1;    // alpha-derivative of the velocity basis at alpha = +1, -1 (clamped end)
     __host__ __device__ explicit OpsLayout(int n) : N(n)
     {
         int64_t o = 0;
@@ -46,6 +47,7 @@ struct OpsLayout {
         G4h = o; o += int64_t(N) * N;
         G4l = o; o += int64_t(N) * N;
         Vgy = o; o += int64_t(N - 4) * N;
+        V1 = o; o += 2 * N;
         total = (o + 3) & ~int64_t(3);
     }
 };
@@ -79,16 +81,43 @@ struct FiberTable {
     double *ftau;    // [3 N^2] per fiber: force of each tension column, [a][l][j]
     double *wsc;     // [12 N^2] per fiber: w = (M + K_delta) f of each column, [col][b N + k]
     const double *Ldot;  // [M] plus-end growth rates (nullptr: fixed lengths)
+    const int *attach;   // [M] minus-end condition FS_END_* (nullptr: all free)
 };
 
+// Surface nodes of the periphery (first n_per) and of the rigid body (the
+// next n - n_per), one source set for the double-layer sums.
 struct Surface {
     int n = 0;
+    int n_per = 0;
     double *y = nullptr, *nrm = nullptr, *w = nullptr;  // [n][3], [n][3], [n]
     double *diag = nullptr;                             // [n][3] Jacobi entries
     double *A = nullptr;                                // [n][9] subtraction matrices
     double *tmp = nullptr;                              // [n][3] work
     double *flux = nullptr;                             // [1] sum w n.q
     int2 *excl = nullptr;                               // [n] own-node exclusion
+};
+
+// The rigid body (Sec. 2.2): device record rb[kRb*] and the attached fibers.
+enum : int {
+    kRbCenter = 0,   // [3] X^P
+    kRbF = 3,        // [3] Stokeslet strength F of the current evaluation
+    kRbL = 6,        // [3] rotlet strength L
+    kRbFext = 9,     // [3] external force
+    kRbLext = 12,    // [3] external torque
+    kRbArea = 15,    // surface area (sum of the weights)
+    kRbU = 16,       // [3] U of the last step
+    kRbOm = 19,      // [3] Omega of the last step
+    kRbSize = 24
+};
+
+struct Body {
+    bool on = false;
+    int n = 0;                    // surface nodes (inside Surface, after the periphery)
+    double radius = 0.0;
+    double *rb = nullptr;         // [kRbSize]
+    int *attach = nullptr;        // [M] FS_END_*
+    int *att_list = nullptr;      // [n_att] attached fiber indices
+    int n_att = 0;
 };
 
 }  // namespace fs
@@ -146,6 +175,8 @@ struct fs_ctx {
     double *d_obasis = nullptr, *d_oz = nullptr, *d_oh = nullptr, *d_opart = nullptr, *d_ow = nullptr,
            *d_or = nullptr, *oh_pinned = nullptr;
     fs::Surface surf;
+    fs::Body body;
+    int64_t n_surf_unk = 0;       // 3 x surface nodes (+ 6 rigid-body unknowns)
     double *d_usurf = nullptr;    // fiber Stokeslets at the surface nodes [n_s][3]
     bool have_state = false, precond_ok = false, geometry_ok = false;
     fs::Scratch scratch;          // far-field scratch (grown on demand)
@@ -158,7 +189,7 @@ struct fs_ctx {
 
 namespace fs {
 fs_status context_init(fs_ctx *c, int S, const int32_t *fibers_per_system, int M, const int32_t *ppf,
-                       const fs_boundary *b);
+                       const fs_boundary *b, const fs_body *body = nullptr, const int32_t *minus_end = nullptr);
 void context_free(fs_ctx *c);
 size_t estimate_bytes(int M, const int32_t *ppf, int n_surf, const fs_options &opt);
 
@@ -183,4 +214,19 @@ fs_status surface_rows(fs_ctx *c, const double *q, const double *usurf, double *
                        int sum_prec, bool hilo);
 fs_status surface_diag(fs_ctx *c);
 fs_status surface_precond(fs_ctx *c, const double *in, double *out);
+
+// body.cu
+// Stokeslet and rotlet strengths of the body from the attached ends: mode
+// LOAD_KNOWN (external load + ends' known part), LOAD_LIN (part linear in the
+// unknowns u), LOAD_BOTH (their sum).
+enum : int { LOAD_KNOWN = 0, LOAD_LIN = 1, LOAD_BOTH = 2 };
+fs_status body_load(fs_ctx *c, const double *u, int mode);
+// out[i] += G(x_i - X^P) F + R(x_i - X^P) L at n points
+fs_status body_point_flow(fs_ctx *c, const double *x, int64_t n, double *out);
+// fiber rows += sign x (terms of the attached-end rows in U, Omega of v)
+fs_status body_rigid_rows(fs_ctx *c, const double *v, double *rows, double sign);
+// out[0..6) = constraint rows: mean of w q1 - U, mean of w (y - X^P) x q1 - Omega
+fs_status body_constraints(fs_ctx *c, const double *q1, const double *rigid, double *out);
+// X^P, body nodes += dt U; record U, Omega
+fs_status body_update(fs_ctx *c, const double *rigid);
 }  // namespace fs

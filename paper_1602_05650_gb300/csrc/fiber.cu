@@ -20,7 +20,11 @@
 // with Phi_V = [I^4 T_0..I^4 T_{N-5}, T_0..T_3], T = Phi_T d with
 // Phi_T = [I^2 T_0..I^2 T_{N-3}, T_0, T_1].  Rows of fiber m at unk_ptr[m]:
 // for a = 0..2: N-4 velocity rows, V_a''(+1), V_a''(-1), V_a'''(+1), V_a'''(-1);
-// then N-2 tension rows, T(+1), T(-1).
+// then N-2 tension rows, T(+1), T(-1).  A minus end attached to the rigid body
+// (Sec. 2.3, Eqs. BC2-1, BC2-2, BC2-T) replaces V_a'''(-1) by V_a(-1) (its
+// value U + Omega x r enters through the coupling rows), for a clamped end
+// V_a''(-1) by g V_a'(-1) (= Omega x X_s), and T(-1) by X_s(-1) . w(-1), the
+// tangential velocity expression at the end node.
 #include <cmath>
 
 #include "context.h"
@@ -247,6 +251,8 @@ __device__ void dev_rows(const FiberTable &F, const Fib &fb, const double *us, c
                  *Py = fb.M_(fb.lay.Py), *Dz = fb.M_(fb.lay.Dz), *Tn = fb.M_(fb.lay.Tn);
     const double *tz = F.tz + 3 * fb.z0;
     const double *bc = F.bc + 12 * fb.m;
+    const int att = F.attach ? F.attach[fb.m] : FS_END_FREE;
+    const double *Vn = fb.M_(fb.lay.Vn), *V1 = fb.M_(fb.lay.V1);
     for (int idx = threadIdx.x; idx < nb * 4 * N; idx += blockDim.x) {
         const int c = idx / (4 * N), r = idx % (4 * N);
         const double *u = us + c * 4 * N;
@@ -264,13 +270,23 @@ __device__ void dev_rows(const FiberTable &F, const Fib &fb, const double *us, c
             } else if (i < N - 2) {
                 const int rr = i - (N - 4);
                 double s = 0.0;
-                for (int j = 0; j < N; ++j) s += V2[rr * N + j] * ca[j];
-                val = s + (rhs ? bc[rr * 3 + a] : 0.0);
+                if (rr == 1 && att == FS_END_CLAMPED) {   // g V_a'(-1)
+                    for (int j = 0; j < N; ++j) s += V1[N + j] * ca[j];
+                    val = fb.g * s;
+                } else {
+                    for (int j = 0; j < N; ++j) s += V2[rr * N + j] * ca[j];
+                    val = s + (rhs ? bc[rr * 3 + a] : 0.0);
+                }
             } else {
                 const int rr = i - (N - 2);
                 double s = 0.0;
-                for (int j = 0; j < N; ++j) s += V3[rr * N + j] * ca[j];
-                val = s + (rhs ? bc[(2 + rr) * 3 + a] : 0.0);
+                if (rr == 1 && att != FS_END_FREE) {      // V_a(-1)
+                    for (int j = 0; j < N; ++j) s += Vn[(N - 1) * N + j] * ca[j];
+                    val = s;
+                } else {
+                    for (int j = 0; j < N; ++j) s += V3[rr * N + j] * ca[j];
+                    val = s + (rhs ? bc[(2 + rr) * 3 + a] : 0.0);
+                }
             }
         } else {
             const int i = r - 3 * N;
@@ -283,6 +299,10 @@ __device__ void dev_rows(const FiberTable &F, const Fib &fb, const double *us, c
                     sz += d * wc[3 * j + 2];
                 }
                 val = tz[3 * i] * sx + tz[3 * i + 1] * sy + tz[3 * i + 2] * sz;
+            } else if (i == N - 1 && att != FS_END_FREE) {   // X_s(-1) . w(-1)
+                const double *te = F.t + 3 * (fb.n0 + N - 1);
+                const double *we = wc + 3 * (N - 1);
+                val = te[0] * we[0] + te[1] * we[1] + te[2] * we[2];
             } else {
                 const int node = (i == N - 2) ? 0 : N - 1;   // T(+1), T(-1)
                 const double *d = u + 3 * N;
@@ -596,13 +616,19 @@ __global__ void __launch_bounds__(256) k_build_rows(FiberTable F, double *__rest
         }
 }
 
-// Rows without w: the free-end rows (second and third derivative of V_a at
-// alpha = +1 and -1, Eq. bc-free) and T(+1), T(-1); grid M.
+// Rows without the velocity rows' w: the end rows (second and third
+// derivative of V_a at alpha = +1 and -1, Eq. bc-free, or the attached-end
+// rows) and T(+1), T(-1) (or X_s(-1) . w(-1) of an attached end, read from
+// the w columns k_build_w wrote); grid M.
 __global__ void __launch_bounds__(256) k_build_direct(FiberTable F, double *__restrict__ B)
 {
     const Fib fb(F, blockIdx.x);
     const int N = fb.N, n = 4 * N;
     const double *V2 = fb.M_(fb.lay.V2), *V3 = fb.M_(fb.lay.V3), *Tn = fb.M_(fb.lay.Tn);
+    const double *Vn = fb.M_(fb.lay.Vn), *V1 = fb.M_(fb.lay.V1);
+    const int att = F.attach ? F.attach[fb.m] : FS_END_FREE;
+    const double *W = F.wsc + fb.blk0 / 4 * 3;
+    const double *te = F.t + 3 * (fb.n0 + N - 1);
     double *Bm = B + fb.blk0;
     for (int idx = threadIdx.x; idx < 14 * n; idx += blockDim.x) {
         const int rr = idx / n, col = idx - rr * n;
@@ -613,8 +639,14 @@ __global__ void __launch_bounds__(256) k_build_direct(FiberTable F, double *__re
             row = a * N + N - 4 + q;
             if (col < 3 * N && col / N == a) {
                 const int j = col - a * N;
-                v = q < 2 ? V2[q * N + j] : V3[(q - 2) * N + j];
+                if (q == 3 && att != FS_END_FREE) v = Vn[(N - 1) * N + j];
+                else if (q == 1 && att == FS_END_CLAMPED) v = fb.g * V1[N + j];
+                else v = q < 2 ? V2[q * N + j] : V3[(q - 2) * N + j];
             }
+        } else if (rr == 13 && att != FS_END_FREE) {
+            row = 4 * N - 1;
+            const double *wc = W + static_cast<int64_t>(col) * 3 * N;
+            v = te[0] * wc[N - 1] + te[1] * wc[2 * N - 1] + te[2] * wc[3 * N - 1];
         } else {
             const int node = rr == 12 ? 0 : N - 1;
             row = 3 * N + N - 2 + (rr - 12);

@@ -265,22 +265,28 @@ fs_status far_field(fs_ctx *c, int sum_prec, bool hilo, const std::vector<int> *
 
 // Preconditioned operator of Eq. prec, out = P^-1 A v, evaluated as
 //   fibers : v + P^-1 (A - P) v  -- P is exactly the self block, so only the
-//            coupling rows Rw(ubar) pass through the block solves (the block's
-//            own rounding is never amplified by its inverse, cond ~1e9);
-//   surface: D^-1 (S q + fiber Stokeslets)  -- D the Jacobi diagonal.
+//            coupling rows Rw(ubar) (and an attached end's terms in the body's
+//            U, Omega) pass through the block solves (the block's own
+//            rounding is never amplified by its inverse, cond ~1e9);
+//   surface: D^-1 (S q + fiber Stokeslets)  -- D the Jacobi diagonal (with a
+//            body: its rows, Stokeslet and rotlet, and constraint rows).
 // sum_prec selects the far-field arithmetic; act restricts the far field to
 // those systems (results of other systems are not meaningful).
 fs_status apply_pa(fs_ctx *c, const double *v, double *out, int sum_prec, const std::vector<int> *act,
                    bool hilo = false)
 {
     FS_TRY(launch_force(c, v, c->d_f, c->d_wf));
+    FS_TRY(body_load(c, v, LOAD_LIN));
     FS_TRY(far_field(c, sum_prec, hilo, act));
     const double *q = c->surf.n ? v + c->n_fib_unk : nullptr;
     if (c->surf.n) FS_TRY(surface_couplings(c, q, c->d_ubar, sum_prec, hilo));
     FS_TRY(launch_rows(c, nullptr, c->d_f, c->d_ubar, c->d_e, ROWS_COUPLING));
+    FS_TRY(body_rigid_rows(c, v, c->d_e, 1.0));
     FS_TRY(launch_lu_solve(c, c->d_e, out));
-    k_add<<<blocks_for(c->n_fib_unk), 256, 0, c->stream>>>(out, v, c->n_fib_unk);
-    FS_LAUNCH_CHECK();
+    if (c->n_fib_unk) {
+        k_add<<<blocks_for(c->n_fib_unk), 256, 0, c->stream>>>(out, v, c->n_fib_unk);
+        FS_LAUNCH_CHECK();
+    }
     if (c->surf.n) {
         FS_TRY(surface_rows(c, q, c->d_usurf, c->d_e + c->n_fib_unk, false, sum_prec, hilo));
         FS_TRY(surface_precond(c, c->d_e + c->n_fib_unk, out + c->n_fib_unk));
@@ -306,6 +312,7 @@ fs_status rhs(fs_ctx *c, double *b, double *pb, int ap = -1, bool hilo = false)
 {
     if (ap < 0) ap = accurate_prec(c);
     FS_TRY(launch_force(c, nullptr, c->d_f, c->d_wf));
+    FS_TRY(body_load(c, nullptr, LOAD_KNOWN));
     FS_TRY(far_field(c, ap, hilo, &c->all_sys));
     if (c->surf.n) FS_TRY(surface_couplings(c, nullptr, c->d_ubar, ap, hilo));
     FS_TRY(launch_rows(c, nullptr, c->d_f, c->d_ubar, b, ROWS_RHS));
@@ -332,19 +339,25 @@ __global__ void k_negate(double *__restrict__ v, int64_t n)
 // the sum of the two densities (they are linear in the density), so
 //   fibers : r = P^-1 rows_rhs(f_known, ubar[W (f_known + f(x))] + T[q]) - x,
 //   surface: r = -D^-1 (S q + G[W (f_known + f(x))]),
-// q the periphery density part of x.
+// q the surface density part of x; the body's Stokeslet and rotlet carry the
+// known plus the linear end loads, and the attached ends' rigid terms of x
+// are subtracted from their rows.
 fs_status true_residual(fs_ctx *c, const double *x, double *r, int sum_prec)
 {
     FS_TRY(launch_force(c, x, c->d_f, c->d_wf, true));
+    FS_TRY(body_load(c, x, LOAD_BOTH));
     FS_TRY(far_field(c, sum_prec, false, &c->all_sys));
     const double *q = c->surf.n ? x + c->n_fib_unk : nullptr;
     if (c->surf.n) FS_TRY(surface_couplings(c, q, c->d_ubar, sum_prec, false));
     FS_TRY(launch_rows(c, nullptr, c->d_f, c->d_ubar, c->d_e, ROWS_RHS));
+    FS_TRY(body_rigid_rows(c, x, c->d_e, -1.0));
     FS_TRY(launch_lu_solve(c, c->d_e, r));
-    k_sub<<<blocks_for(c->n_fib_unk), 256, 0, c->stream>>>(r, x, c->n_fib_unk);
-    FS_LAUNCH_CHECK();
+    if (c->n_fib_unk) {
+        k_sub<<<blocks_for(c->n_fib_unk), 256, 0, c->stream>>>(r, x, c->n_fib_unk);
+        FS_LAUNCH_CHECK();
+    }
     if (c->surf.n) {
-        const int64_t n3 = 3 * int64_t(c->surf.n);
+        const int64_t n3 = c->n_surf_unk;
         FS_TRY(surface_rows(c, q, c->d_usurf, c->d_e + c->n_fib_unk, false, sum_prec, false));
         FS_TRY(surface_precond(c, c->d_e + c->n_fib_unk, r + c->n_fib_unk));
         k_negate<<<blocks_for(n3), 256, 0, c->stream>>>(r + c->n_fib_unk, n3);
@@ -549,8 +562,13 @@ double ms_since(std::chrono::steady_clock::time_point t0)
 
 }  // namespace
 
+fs_status fiber_arrays(fs_ctx *c, int M, const int32_t *ppf, const std::vector<int64_t> &kp,
+                       const std::vector<int64_t> &zp);
+fs_status krylov_arrays(fs_ctx *c);
+fs_status surface_arrays(fs_ctx *c, const fs_boundary *bd, const fs_body *body);
+
 fs_status context_init(fs_ctx *c, int S, const int32_t *fps, int M, const int32_t *ppf,
-                       const fs_boundary *bd)
+                       const fs_boundary *bd, const fs_body *body, const int32_t *minus_end)
 {
     c->M = M;
     c->Nm.assign(ppf, ppf + M);
@@ -572,8 +590,12 @@ fs_status context_init(fs_ctx *c, int S, const int32_t *fps, int M, const int32_
     c->n_blk = c->blk_ptr[M];
     c->n_kp = kp[M];
     c->n_z = zp[M];
-    c->surf.n = bd ? bd->n_nodes : 0;
-    c->n_unk = c->n_fib_unk + 3 * int64_t(c->surf.n);
+    c->surf.n_per = bd ? bd->n_nodes : 0;
+    c->body.on = body != nullptr;
+    c->body.n = body ? body->n_nodes : 0;
+    c->surf.n = c->surf.n_per + c->body.n;
+    c->n_surf_unk = 3 * int64_t(c->surf.n) + (c->body.on ? 6 : 0);
+    c->n_unk = c->n_fib_unk + c->n_surf_unk;
     if (c->n_tot >= (1LL << 31) - 1 || c->n_unk >= (1LL << 31) - 1) {
         set_error("fs_create: at most 2^31-2 points and unknowns");
         return FS_EINVAL;
@@ -609,8 +631,49 @@ fs_status context_init(fs_ctx *c, int S, const int32_t *fps, int M, const int32_
     FS_TRY(dalloc(c, &c->d_status, 1));
     FS_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
     FS_CUDA(cudaMallocHost(&c->h_pinned, 4096 * sizeof(double)));
-    if (M == 0) return FS_OK;
+    if (M == 0 && !c->body.on) return FS_OK;
+    if (M > 0) FS_TRY(fiber_arrays(c, M, ppf, kp, zp));
+    if (c->body.on) {
+        std::vector<int> att(M, FS_END_FREE), list;
+        for (int m = 0; m < M; ++m) {
+            att[m] = minus_end ? minus_end[m] : FS_END_FREE;
+            if (att[m] != FS_END_FREE) list.push_back(m);
+        }
+        c->body.n_att = static_cast<int>(list.size());
+        c->body.radius = body->radius;
+        double area = 0.0;
+        for (int i = 0; i < body->n_nodes; ++i) area += body->weights[i];
+        std::vector<double> rb(kRbSize, 0.0);
+        for (int a = 0; a < 3; ++a) {
+            rb[kRbCenter + a] = body->center[a];
+            rb[kRbFext + a] = body->force[a];
+            rb[kRbLext + a] = body->torque[a];
+        }
+        rb[kRbArea] = area;
+        FS_TRY(dalloc(c, &c->body.rb, kRbSize));
+        FS_TRY(dalloc(c, &c->body.attach, M));
+        FS_TRY(dalloc(c, &c->body.att_list, list.size()));
+        FS_CUDA(cudaMemcpyAsync(c->body.rb, rb.data(), kRbSize * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        if (M > 0)
+            FS_CUDA(cudaMemcpyAsync(c->body.attach, att.data(), M * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+        if (!list.empty())
+            FS_CUDA(cudaMemcpyAsync(c->body.att_list, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                    c->stream));
+        FS_CUDA(cudaStreamSynchronize(c->stream));   // host staging vectors
+        if (M == 0) c->have_state = true;   // a lone body needs no fiber state
+    }
+    FS_TRY(krylov_arrays(c));
+    FS_TRY(surface_arrays(c, bd, body));
+    // host staging vectors above go out of scope here; the context's stream
+    // may be a non-blocking one that other contexts share the device with
+    FS_CUDA(cudaStreamSynchronize(c->stream));
+    return FS_OK;
+}
 
+// Fiber arrays of context_init: op sets, pointers, geometry and block storage.
+fs_status fiber_arrays(fs_ctx *c, int M, const int32_t *ppf, const std::vector<int64_t> &kp,
+                       const std::vector<int64_t> &zp)
+{
     // op sets
     std::vector<double> ops;
     for (int m = 0; m < M; ++m) {
@@ -674,7 +737,13 @@ fs_status context_init(fs_ctx *c, int S, const int32_t *fps, int M, const int32_
     FS_CUDA(cudaMemsetAsync(c->d_kp, 0, 4 * c->n_kp * sizeof(double), c->stream));
     FS_CUDA(cudaMemsetAsync(c->d_V, 0, 3 * P * sizeof(double), c->stream));
     FS_CUDA(cudaMemsetAsync(c->d_T, 0, P * sizeof(double), c->stream));
+    FS_CUDA(cudaStreamSynchronize(c->stream));   // host staging vectors
+    return FS_OK;
+}
 
+// Krylov workspace of context_init.
+fs_status krylov_arrays(fs_ctx *c)
+{
     const int R = std::max(2, std::min(c->opt.restart, 250));   // k_finish_dots uses 256 threads
     c->kdim = R + 1;
     const int64_t n = c->n_unk;
@@ -713,26 +782,37 @@ fs_status context_init(fs_ctx *c, int S, const int32_t *fps, int M, const int32_
         FS_TRY(dalloc(c, &c->d_okk, static_cast<size_t>(c->S)));
         FS_CUDA(cudaMallocHost(&c->oh_pinned, c->S * SHo * sizeof(double)));
     }
-    if (c->surf.n) {
-        const int ns = c->surf.n;
-        FS_TRY(dalloc(c, &c->surf.y, 3 * ns));
-        FS_TRY(dalloc(c, &c->surf.nrm, 3 * ns));
-        FS_TRY(dalloc(c, &c->surf.w, ns));
-        FS_TRY(dalloc(c, &c->surf.diag, 3 * ns));
-        FS_TRY(dalloc(c, &c->d_usurf, 3 * ns));
-        FS_TRY(dalloc(c, &c->surf.A, 9 * ns));
-        FS_TRY(dalloc(c, &c->surf.tmp, 3 * ns));
-        FS_TRY(dalloc(c, &c->surf.flux, 1));
-        FS_TRY(dalloc(c, &c->surf.excl, ns));
-        FS_CUDA(cudaMemcpyAsync(c->surf.y, bd->nodes, 3 * ns * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-        FS_CUDA(cudaMemcpyAsync(c->surf.nrm, bd->normals, 3 * ns * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-        FS_CUDA(cudaMemcpyAsync(c->surf.w, bd->weights, ns * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-        FS_TRY(surface_diag(c));
-    }
-    // host staging vectors above go out of scope here; the context's stream
-    // may be a non-blocking one that other contexts share the device with
-    FS_CUDA(cudaStreamSynchronize(c->stream));
     return FS_OK;
+}
+
+// Surface arrays of context_init: periphery nodes, then the body's.
+fs_status surface_arrays(fs_ctx *c, const fs_boundary *bd, const fs_body *body)
+{
+    if (!c->surf.n) return FS_OK;
+    const int ns = c->surf.n, p = c->surf.n_per, nb = c->body.n;
+    FS_TRY(dalloc(c, &c->surf.y, 3 * ns));
+    FS_TRY(dalloc(c, &c->surf.nrm, 3 * ns));
+    FS_TRY(dalloc(c, &c->surf.w, ns));
+    FS_TRY(dalloc(c, &c->surf.diag, 3 * ns));
+    FS_TRY(dalloc(c, &c->d_usurf, 3 * ns));
+    FS_TRY(dalloc(c, &c->surf.A, 9 * ns));
+    FS_TRY(dalloc(c, &c->surf.tmp, 3 * ns));
+    FS_TRY(dalloc(c, &c->surf.flux, 1));
+    FS_TRY(dalloc(c, &c->surf.excl, ns));
+    FS_CUDA(cudaMemsetAsync(c->surf.flux, 0, sizeof(double), c->stream));
+    const size_t d = sizeof(double);
+    if (p > 0) {
+        FS_CUDA(cudaMemcpyAsync(c->surf.y, bd->nodes, 3 * p * d, cudaMemcpyHostToDevice, c->stream));
+        FS_CUDA(cudaMemcpyAsync(c->surf.nrm, bd->normals, 3 * p * d, cudaMemcpyHostToDevice, c->stream));
+        FS_CUDA(cudaMemcpyAsync(c->surf.w, bd->weights, p * d, cudaMemcpyHostToDevice, c->stream));
+    }
+    if (nb > 0) {
+        FS_CUDA(cudaMemcpyAsync(c->surf.y + 3 * int64_t(p), body->nodes, 3 * nb * d, cudaMemcpyHostToDevice, c->stream));
+        FS_CUDA(cudaMemcpyAsync(c->surf.nrm + 3 * int64_t(p), body->normals, 3 * nb * d, cudaMemcpyHostToDevice,
+                                c->stream));
+        FS_CUDA(cudaMemcpyAsync(c->surf.w + p, body->weights, nb * d, cudaMemcpyHostToDevice, c->stream));
+    }
+    return surface_diag(c);
 }
 
 // Upper bound of the CTAs one wave of a direct sum may hold (SMs x resident
@@ -774,7 +854,7 @@ size_t estimate_bytes(int M, const int32_t *ppf, int n_surf, const fs_options &o
     add(n_fib_unk * sizeof(int));
     add(n_fib_unk * sizeof(double));
     for (int64_t k : {3 * P, P, 3 * P, 3 * P, 3 * P}) add(k * d);
-    const int64_t n = n_fib_unk + 3 * int64_t(n_surf);
+    const int64_t n = n_fib_unk + 3 * int64_t(n_surf) + 6;   // + a rigid body's U, Omega
     const int R = std::max(2, std::min(opt.restart, 250));
     const int64_t kdim = R + 1;
     add(kdim * n * d);
@@ -802,6 +882,9 @@ size_t estimate_bytes(int M, const int32_t *ppf, int n_surf, const fs_options &o
         const int64_t ns = n_surf;
         for (int64_t k : {3 * ns, 3 * ns, ns, 3 * ns, 3 * ns, 9 * ns, 3 * ns, int64_t(1)}) add(k * d);
         add(ns * sizeof(int2));
+        add(kRbSize * d);                   // a rigid body's record and fiber lists
+        add(M * sizeof(int));
+        add(M * sizeof(int));
     }
     // the scratch grows to 5/4 of the largest sum it has served
     size_t sc = 0;
@@ -824,7 +907,8 @@ void context_free(fs_ctx *c)
                     c->d_t, c->d_tz, c->d_fknown, c->d_W, c->d_mloc, c->d_bc, c->d_kp, c->d_B, c->d_ftau, c->d_wsc,
                     c->d_piv, c->d_dinv, c->d_V, c->d_T, c->d_f, c->d_wf, c->d_ubar, c->d_basis, c->d_b,
                     c->d_x, c->d_r, c->d_w, c->d_e, c->d_pb, c->d_obasis, c->d_oz, c->d_oh, c->d_opart, c->d_ow, c->d_or, c->d_work, c->d_ich, c->d_isch, c->d_ikk, c->d_och, c->d_osch, c->d_okk, c->d_h, c->d_part, c->surf.y, c->surf.nrm,
-                    c->surf.w, c->surf.diag, c->d_usurf, c->surf.A, c->surf.tmp, c->surf.flux, c->surf.excl};
+                    c->surf.w, c->surf.diag, c->d_usurf, c->surf.A, c->surf.tmp, c->surf.flux, c->surf.excl,
+                    c->body.rb, c->body.attach, c->body.att_list};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -868,6 +952,7 @@ fs::FiberTable fs_ctx::table() const
     F.ftau = d_ftau;
     F.wsc = d_wsc;
     F.Ldot = growth ? d_Ldot : nullptr;
+    F.attach = body.on ? body.attach : nullptr;
     return F;
 }
 
@@ -937,7 +1022,7 @@ fs_status fs_build_precond(fs_ctx *c)
 
 fs_status fs_step(fs_ctx *c, fs_step_info *info)
 {
-    if (!c || !c->have_state || c->M == 0) {
+    if (!c || !c->have_state || (c->M == 0 && !c->body.on)) {
         set_error("fs_step: no state set");
         return FS_EINVAL;
     }
@@ -1055,6 +1140,7 @@ fs_status fs_step(fs_ctx *c, fs_step_info *info)
         return FS_ENOTCONV;
     }
     FS_TRY(launch_update(c, c->d_x));
+    FS_TRY(body_update(c, c->d_x + c->n_fib_unk + 3 * int64_t(c->surf.n)));
     c->geometry_ok = c->precond_ok = false;
     if (info) {
         FS_CUDA(cudaStreamSynchronize(c->stream));
