@@ -233,7 +233,12 @@ def run_workload(args, ws, rank, local, fs, torch):
               one batch, advanced --steps steps: steps/s and the settling
               speeds relative to V_c;
     kinetics  1,024 growing and shrinking microtubules (dynamic instability
-              with the paper's rates), advanced --steps steps."""
+              with the paper's rates), advanced --steps steps;
+    aster     the confined aster of Table 2 (32, 128, 512 and 2,048 fibers x
+              31 points clamped to a sphere inside a sphere six radii out,
+              force on the sphere, GMRES 1e-5): steps/s and GMRES iterations
+              per step, FP64 (up to 512 fibers) and mixed, advanced --steps
+              steps after --warmup steps."""
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     out = {"workload": args.workload, "data": "synthetic"}
@@ -365,6 +370,49 @@ def run_workload(args, ws, rank, local, fs, torch):
                     "timing": "host wall clock per step (state machine, rates upload and step)",
                     "iters": iters, "mean_length_um": [float(L0.mean()), float(L1.mean())],
                     "growing_fraction": float(state.mean())})
+    elif args.workload == "aster":
+        res = {}
+        for nf in (32, 128, 512, 2048):
+            s = wl.table2_aster(nf, seed=rank)
+            row = {}
+            variants = [("mixed", fs.FS_MIXED)]
+            if nf <= 512:   # the FP64 far field of 63,488 points costs ~0.1 s a matvec
+                variants = [("fp64", fs.FS_FP64)] + variants
+            for name, prec in variants:
+                opt = fs.fs_options_default()
+                opt.prec = prec
+                opt.tol = 1e-5
+                opt.max_iter = 600
+                opt.profile = 1
+                h = fs.fs_create_with_body(s.n_per_fiber, s.attach, s.mu, s.eps, s.E, s.dt, s.body,
+                                           boundary=s.boundary, options=opt, stream=stream)
+                fs.fs_set_state(h, torch.tensor(s.X, device=dev), torch.tensor(s.L, device=dev),
+                                torch.tensor(s.f_ext, device=dev))
+                for _ in range(args.warmup):
+                    fs.fs_step(h, info=False)
+                fs.fs_kernel_stats(h, reset=True)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                infos = [fs.fs_step(h, info=True) for _ in range(args.steps)]
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / args.steps
+                ks = fs.fs_kernel_stats(h)
+                _, U, _ = fs.fs_get_body(h)
+                fs.fs_destroy(h)
+                row[name] = {"ms_per_step": ms, "steps_per_s": 1e3 / ms,
+                             "avg_gmres_iters": float(np.mean([i.iters for i in infos])),
+                             "iters": [i.iters for i in infos],
+                             "outer": [i.refine_sweeps for i in infos], "U_z": float(U[2]),
+                             "kernels": {KS_NAMES[k]: [ks[k][0], round(ks[k][1], 2)] for k in range(7) if ks[k][0]}}
+            res[str(nf)] = row
+        s = wl.table2_aster(32)
+        out.update({"points_per_fiber": 31, "body_nodes": int(s.body.nodes.shape[0]),
+                    "periphery_nodes": int(s.boundary.nodes.shape[0]), "dt": s.dt, "tol": 1e-5,
+                    "steps": args.steps, "warmup": args.warmup, "result": res,
+                    "paper_avg_gmres_iters": {"32": 3, "128": 5, "512": 9, "2048": 16}})
     else:
         s = wl.cfg_large_matvec(seed=rank)
         opt = fs.fs_options_default()
@@ -483,7 +531,8 @@ def main():
     ap.add_argument("--tile", type=int, default=0,
                     help="far-field launch shape id (0 = default; 1..3 = targets per thread FP32 2/4/8, "
                          "float-float 1/2/4)")
-    ap.add_argument("--workload", choices=["confined", "batched", "large", "sediment", "kinetics"], default=None,
+    ap.add_argument("--workload", choices=["confined", "batched", "large", "sediment", "kinetics", "aster"],
+                    default=None,
                     help="a secondary workload instead of the headline step benchmark")
     ap.add_argument("--serve", type=int, default=0,
                     help="serving mode: number of independent requests (0 = the step benchmark)")

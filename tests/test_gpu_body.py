@@ -155,3 +155,4 @@ def test_aster_steps_follow_the_oracle():
         err, spread = rel(got[k], ref[k]), rel(loose[k], ref[k])
         print("%s %.2e (oracle at tol: %.2e)" % (k, err, spread))
         assert err <= 10.0 * max(spread, 1e-10), (k, err, spread)
+

@@ -376,3 +376,17 @@ def aster(n_fibers: int, N: int = 32, radius: float = 1.0, L: Optional[float] = 
     return Suspension(n_per_fiber=np.full(n_fibers, N, dtype=np.int32), X=X,
                       L=np.full(n_fibers, L), f_ext=f_ext, mu=mu, eps=eps, E=E, dt=dt, boundary=bnd,
                       body=body, attach=np.full(n_fibers, attach, dtype=np.int32))
+
+
+def table2_aster(n_fibers: int, seed: int = 0, N: int = 31, grid=(16, 32)) -> Suspension:
+    """The confined aster of Table 2: a sphere of radius r = 1 inside a
+    no-slip sphere of radius 6, n_fibers fibers of length 2r with N = 31
+    points clamped to it, a force of 1/32 of the elastic scale E / L^2 on the
+    sphere only; eps = 1e-3, E = mu = 1.  dt = 2.5e-4 tau_E, inside the
+    paper's stable range for every fiber count (tau_E = 8 pi mu L^4 / c,
+    c = -ln(eps^2 e), the caption's elastic relaxation time).  Surface grids
+    of 16 x 32 patches (8,192 nodes) on both spheres."""
+    eps, L, mu = 1e-3, 2.0, 1.0
+    tau_e = 8.0 * math.pi * mu * L ** 4 / (-math.log(eps * eps * math.e))
+    return aster(n_fibers, N=N, radius=1.0, L=L, R_periphery=6.0, body_grid=grid, periphery_grid=grid,
+                 attach=CLAMPED, seed=seed, mu=mu, eps=eps, E=1.0, dt=2.5e-4 * tau_e)
