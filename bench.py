@@ -226,9 +226,11 @@ def run_workload(args, ws, rank, local, fs, torch):
               mixed and FP64 steps/s;
     batched   256 independent systems (fibers log-uniform in [8, 512], N in
               {16, 32, 64}) in one context, mixed steps/s and systems/s;
-    large     the 1,048,576-point direct Stokeslet sum (8,192 x 128 fibers in
-              [0,80]^3, own-fiber exclusion): FP32 hi/lo, FP32 plain and
-              float-float over all targets, FP64 over 16,384 sampled targets;
+    large     the 1,048,576-point Stokeslet sum (8,192 x 128 fibers in
+              [0,80]^3, own-fiber exclusion): direct in FP32 hi/lo, FP32 plain
+              and float-float over all targets, FP64 over 16,384 sampled
+              targets; the treecode at orders 6 and 8 with its error on the
+              sampled targets;
     sediment  the four sedimenting clouds of Sec. 4.3 (1,024 x 16 each) in
               one batch, advanced --steps steps: steps/s and the settling
               speeds relative to V_c;
@@ -441,6 +443,27 @@ def run_workload(args, ws, rank, local, fs, torch):
             res[name] = {"targets": int(nt), "ms_per_launch": st[1] / st[0], "pairs_per_s": pairs_s,
                          "tflops": fpp * pairs_s / 1e12,
                          "full_matvec_s": s.n_points * s.n_points / pairs_s}
+        # treecode (fs_stokeslet_apply_tree) on all targets; its error on the
+        # FP64 sum's sampled targets
+        idx = torch.linspace(0, s.n_points - 1, 16384, device=dev).long()
+        u64 = torch.empty((16384, 3), dtype=torch.float64, device=dev)
+        fs.fs_stokeslet_apply(h, X, Wf, X[idx].contiguous(), u64, fid, fid[idx].contiguous(), fs.FS_SUM_FP64)
+        ut = torch.empty_like(X)
+        for order, theta in ((6, 0.5), (8, 0.5), (8, 0.4)):
+            fs.fs_stokeslet_apply_tree(h, X, Wf, X, ut, fid, fid, order=order, theta=theta)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fs.fs_stokeslet_apply_tree(h, X, Wf, X, ut, fid, fid, order=order, theta=theta)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            err = (torch.linalg.norm(ut[idx] - u64) / torch.linalg.norm(u64)).item()
+            res["tree_p%d_theta%.1f" % (order, theta)] = {
+                "ms_per_call": ms, "rel_error_sampled": err,
+                "speedup_vs_fp32_hilo": res["fp32_hilo"]["ms_per_launch"] / ms,
+                "speedup_vs_fp32_plain": res["fp32_plain"]["ms_per_launch"] / ms}
         fs.fs_destroy(h)
         out.update({"points": int(s.n_points), "pairs_full": float(s.n_points) ** 2, "result": res,
                     "fp32_vs_fp64_pairs_per_s": res["fp32_hilo"]["pairs_per_s"] / res["fp64_sampled"]["pairs_per_s"]})

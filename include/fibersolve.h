@@ -266,6 +266,24 @@ fs_status fs_stokeslet_apply_noalloc(const double *src_xyz, const double *src_wf
                                      const int32_t *tgt_fiber, int64_t n_tgt, double *out_u,
                                      double mu, int32_t sum_precision, void *cuda_stream);
 
+/* Fast summation of the sum of fs_stokeslet_apply (same arguments, same
+ * exclusion of same-fiber pairs when both id arrays are given): a Cartesian
+ * treecode (the paper evaluates this far field with a fast multipole method
+ * for large systems, Sec. 3.3).  The Stokeslet is split into four Laplace
+ * potentials; a source cell of radius rho (largest distance of its points
+ * from its centre) is replaced by its Taylor expansion of the given order
+ * (4, 6, 8 or 10) for a group of 32 targets whose box lies farther than
+ * rho / theta from the centre (theta in (0, 1)), nearer cells are opened and
+ * leaves summed directly.  FP32 arithmetic (hi/lo coordinates in the direct
+ * part), FP64 moments and totals; the error falls with order and theta (see
+ * the tests).  Pairs at zero distance (a point with itself) are skipped.
+ * Uses the context's scratch (grown as needed); synchronises
+ * the context's stream.  FS_EINVAL for a bad order or theta, FS_ENUMERIC if
+ * a traversal exceeded its stack (the output is then incomplete). */
+fs_status fs_stokeslet_apply_tree(fs_ctx *ctx, const double *src_xyz, const double *src_wf, int64_t n_src,
+                                  const int32_t *src_fiber, const double *tgt_xyz, const int32_t *tgt_fiber,
+                                  int64_t n_tgt, double *out_u, int32_t order, double theta);
+
 /* Direct double-layer (stresslet) sum (Eqs. stresslet, double-layer,
  * cortex-vel) at targets off the surface:
  *   out_u[i] = sum_j w_j T(tgt_i - y_j) : (q_j n_j),

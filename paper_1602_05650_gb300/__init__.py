@@ -256,6 +256,19 @@ def fs_stokeslet_apply(h: Handle, src_xyz, src_wf, tgt_xyz, out, src_fiber=None,
            "fs_stokeslet_apply")
 
 
+def fs_stokeslet_apply_tree(h: Handle, src_xyz, src_wf, tgt_xyz, out, src_fiber=None, tgt_fiber=None,
+                            order: int = 8, theta: float = 0.5):
+    """Treecode approximation of fs_stokeslet_apply (device tensors)."""
+    lib = _native.load()
+    _check(lib.fs_stokeslet_apply_tree(h.ptr, _dev_ptr(src_xyz, "f64", "src_xyz"),
+                                       _dev_ptr(src_wf, "f64", "src_wf"), int(src_xyz.shape[0]),
+                                       _dev_ptr(src_fiber, "i32", "src_fiber"),
+                                       _dev_ptr(tgt_xyz, "f64", "tgt_xyz"),
+                                       _dev_ptr(tgt_fiber, "i32", "tgt_fiber"), int(tgt_xyz.shape[0]),
+                                       _dev_ptr(out, "f64", "out"), int(order), float(theta)),
+           "fs_stokeslet_apply_tree")
+
+
 def fs_stresslet_apply(h: Handle, src_xyz, src_nrm, src_w, src_q, tgt_xyz, out,
                        sum_precision: int = FS_SUM_FP32):
     lib = _native.load()

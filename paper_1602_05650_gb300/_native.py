@@ -76,6 +76,7 @@ SIGNATURES = {
     "fs_get_state": (c_int32, [P, P, P, P, c_int32]),
     "fs_stokeslet_apply": (c_int32, [P, P, P, c_int64, P, P, P, c_int64, P, c_int32]),
     "fs_stresslet_apply": (c_int32, [P, P, P, P, P, c_int64, P, c_int64, P, c_int32]),
+    "fs_stokeslet_apply_tree": (c_int32, [P, P, P, c_int64, P, P, P, c_int64, P, c_int32, c_double]),
     "fs_stokeslet_apply_noalloc": (c_int32, [P, P, c_int64, P, P, P, c_int64, P, c_double, c_int32, P]),
     "fs_surface_apply": (c_int32, [P, P, P, c_int32]),
     "fs_build_precond": (c_int32, [P]),
