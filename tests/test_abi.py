@@ -50,3 +50,33 @@ def test_options_default_and_errors_without_gpu(lib):
     bad = (ctypes.c_int32 * 1)(3)
     assert lib.fs_create(ctypes.byref(out), 1, bad, 1.0, 1e-3, 1.0, 1e-3, None, None, None) == _native.FS_EINVAL
     assert lib.fs_status_str(4) == b"FS_ENOTCONV"
+
+
+def test_body_arguments_are_validated_without_gpu(lib):
+    """fs_create_with_body rejects an incomplete body, unknown end codes and
+    attached ends without a body before any device call."""
+    out = ctypes.c_void_p()
+    ppf = (ctypes.c_int32 * 2)(16, 16)
+    nodes = (ctypes.c_double * 12)(*([1.0, 0.0, 0.0] * 4))
+    w = (ctypes.c_double * 4)(1.0, 1.0, 1.0, 1.0)
+    D3 = ctypes.c_double * 3
+
+    def body(n=4, radius=1.0, nod=nodes, force=(0.0, 0.0, 1.0)):
+        return _native.fs_body(D3(0.0, 0.0, 0.0), radius, n, ctypes.cast(nod, ctypes.c_void_p) if nod else None,
+                               ctypes.cast(nodes, ctypes.c_void_p), ctypes.cast(w, ctypes.c_void_p), D3(*force),
+                               D3(0.0, 0.0, 0.0))
+
+    def create(ends, b):
+        e = (ctypes.c_int32 * 2)(*ends) if ends is not None else None
+        return lib.fs_create_with_body(ctypes.byref(out), 2, ppf, e, 1.0, 1e-3, 1.0, 1e-3, None,
+                                       ctypes.byref(b) if b is not None else None, None, None)
+
+    assert create((1, 7), body()) == _native.FS_EINVAL                       # unknown end code
+    assert b"end condition" in lib.fs_last_error()
+    assert create((1, 0), None) == _native.FS_EINVAL                         # attached, no body
+    assert b"no body" in lib.fs_last_error()
+    assert create((0, 0), body(n=0)) == _native.FS_EINVAL                    # no surface nodes
+    assert create((0, 0), body(radius=0.0)) == _native.FS_EINVAL             # no radius
+    assert create((0, 0), body(nod=None)) == _native.FS_EINVAL               # missing nodes
+    assert create((0, 0), body(force=(0.0, float("nan"), 0.0))) == _native.FS_EINVAL
+    assert b"non-finite" in lib.fs_last_error()
