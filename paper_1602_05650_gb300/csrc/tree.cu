@@ -14,7 +14,9 @@
 //   |k| |r|^2 a_k = (2|k| - 1) sum_i r_i a_{k - e_i} - (|k| - 1) sum_i a_{k - 2 e_i}
 // (the recurrence of Cartesian treecodes, Li, Johnston and Krasny, J. Comput.
 // Phys. 228, 2009).  With the moments M_k = sum_n q_n (y_n - c)^k of a charge q,
-//   phi = sum_{|k| <= p} a_k M_k,   d_i phi = -sum_{|m| <= p+1, m_i >= 1} m_i a_m M_{m - e_i}.
+//   phi = sum_{|k| <= p} a_k M_k,   d_i phi = -sum_{|m| <= p+1, m_i >= 1} m_i a_m M_{m - e_i},
+// evaluated on the (p + 2)^2 coefficients with kz <= 1 against moment tables
+// folded by the harmonic trace relation (see ridx).
 //
 // Tree.  Sources sorted by 30-bit Morton key in the bounding cube of sources
 // and targets; cells level by level from the key prefixes: a cell with more
@@ -48,7 +50,6 @@ constexpr int kLeafCap = 64;
 constexpr int kGroup = 32;
 constexpr int kWarps = 4;          // warps (target groups) per CTA
 constexpr int kStack = 192;        // traversal stack entries per warp
-constexpr int kMaxOrder = 10;
 
 __host__ __device__ constexpr int nterms(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
 
@@ -56,6 +57,19 @@ __host__ __device__ constexpr int nterms(int p) { return (p + 1) * (p + 2) * (p 
 __host__ __device__ constexpr int tidx(int a, int b, int c)
 {
     return nterms(a + b + c - 1) + (b + c) * (b + c + 1) / 2 + c;
+}
+
+// Harmonic reduction.  The Taylor coefficients of 1/r obey the trace
+// relation (kx+2)(kx+1) a_{k+2ex} + (ky+2)(ky+1) a_{k+2ey} + (kz+2)(kz+1) a_{k+2ez} = 0
+// (Laplace's equation), so each degree d has 2d + 1 independent coefficients,
+// those with kz <= 1, and the recurrence closes on them (it never needs
+// a_{k-2ez}).  A contraction sum_k a_k T_k then equals sum over kz <= 1 of
+// a_k T'_k with T' the tensor "folded" by the relation (entries with kz >= 2
+// moved onto kz - 2); the folding is done once per cell in FP64.
+// Reduced index: degree-major (offset d^2), kz = 0 first (kx descending), then kz = 1.
+__host__ __device__ constexpr int ridx(int a, int b, int c)
+{
+    return (a + b + c) * (a + b + c) + (c == 0 ? (b + c) : (a + b + c) + 1 + (b + c - 1));
 }
 
 __device__ __forceinline__ unsigned spread10(unsigned v)
@@ -382,16 +396,64 @@ __global__ void __launch_bounds__(128) k_m2m(Cells C, const int *__restrict__ ce
     if (threadIdx.x == 0) C.rad[c] = rmax;
 }
 
-// FP32 moments for the evaluation, one float4 (four charges) per term:
-// out[c][t] = (M[c][0][t], .., M[c][3][t])
-__global__ void k_moments_f4(const double *__restrict__ M, int ncells, int T, float4 *__restrict__ out)
+// Folded FP32 tables of one cell, float4 (four charges) per entry:
+//   [0, (P+1)^2)                     potentials, M_k folded, degrees 0..P
+//   then for i = x, y, z: (P+2)^2-1  gradient tensors T^i_m = -m_i M_{m-e_i}, degrees 1..P+1
+// One thread per (charge, table, degree); FP64.
+__host__ __device__ constexpr int nfold(int P) { return (P + 1) * (P + 1) + 3 * ((P + 2) * (P + 2) - 1); }
+
+template <int P>
+__global__ void __launch_bounds__(128) k_fold(const double *__restrict__ M, int ncells, float4 *__restrict__ out)
 {
-    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-    if (i >= int64_t(ncells) * T) return;
-    const int64_t c = i / T, t = i - c * T;
-    const double *m = M + c * 4 * T + t;
-    out[i] = make_float4(static_cast<float>(m[0]), static_cast<float>(m[T]), static_cast<float>(m[2 * T]),
-                         static_cast<float>(m[3 * T]));
+    constexpr int T = nterms(P);
+    constexpr int NF = nfold(P);
+    constexpr int ntask = 4 * 4 * (P + 2);   // charge x table x degree
+    const int64_t gid = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    const int64_t cell = gid / ntask;
+    if (cell >= ncells) return;
+    const int task = static_cast<int>(gid - cell * ntask);
+    const int q = task / (4 * (P + 2)), tab = (task / (P + 2)) % 4, d = task % (P + 2);
+    if (tab == 0 && d > P) return;      // potentials: degrees 0..P
+    if (tab > 0 && d == 0) return;      // gradients: degrees 1..P+1
+    const double *Mq = M + (cell * 4 + q) * T;
+    double v[(P + 2) * (P + 3) / 2];     // degree-d tensor, index (b + c)(b + c + 1)/2 + c
+    for (int a = d; a >= 0; --a)
+        for (int b = d - a; b >= 0; --b) {
+            const int c = d - a - b, j = (b + c) * (b + c + 1) / 2 + c;
+            double t;
+            if (tab == 0) {
+                t = Mq[tidx(a, b, c)];
+            } else {
+                const int k[3] = {a, b, c}, i = tab - 1;
+                if (k[i] == 0) {
+                    t = 0.0;
+                } else {
+                    int km[3] = {a, b, c};
+                    --km[i];
+                    t = -double(k[i]) * Mq[tidx(km[0], km[1], km[2])];
+                }
+            }
+            v[j] = t;
+        }
+    // fold entries with c >= 2 (highest c first) onto c - 2
+    for (int c = d; c >= 2; --c)
+        for (int b = d - c; b >= 0; --b) {
+            const int a = d - b - c;
+            const double x = v[(b + c) * (b + c + 1) / 2 + c];
+            const int bz = c - 2;
+            const double w = double((bz + 2) * (bz + 1));
+            // (a + 2, b, c - 2) and (a, b + 2, c - 2)
+            v[(b + bz) * (b + bz + 1) / 2 + bz] -= x * double(a + 2) * double(a + 1) / w;
+            v[(b + 2 + bz) * (b + 2 + bz + 1) / 2 + bz] -= x * double(b + 2) * double(b + 1) / w;
+        }
+    const int base = tab == 0 ? 0 : (P + 1) * (P + 1) + (tab - 1) * ((P + 2) * (P + 2) - 1) - 1;
+    float *o = reinterpret_cast<float *>(out + cell * NF);
+    for (int a = d; a >= 0; --a)
+        for (int b = d - a; b >= 0; --b) {
+            const int c = d - a - b;
+            if (c > 1) continue;
+            o[4 * (base + ridx(a, b, c)) + q] = static_cast<float>(v[(b + c) * (b + c + 1) / 2 + c]);
+        }
 }
 
 // evaluation records: centre relative to the cube centre as hi (with the
@@ -461,56 +523,71 @@ __global__ void k_groups(const double *__restrict__ x, const int *__restrict__ t
 }
 
 // ------------------------------------------------------------ evaluation
-// 8 pi mu u += phi_i - r_j d_i phi_j + d_i phi_4 for one cell's moments sM
-// (one float4 of the four charges per term, in shared memory), r = x - c.
-// Degree n + 1 coefficients are generated before the degree-n moments are
-// contracted, so each moment is read once (potentials with a_k, gradients
-// with a_{k + e_i}) and only three degrees of coefficients are live.
+// 8 pi mu u += phi_i - r_j d_i phi_j + d_i phi_4 for one cell's folded tables
+// sF (shared memory), r = x - c: the coefficients with kz <= 1 of degree n + 1
+// are generated before the degree-n potential table and the degree-(n + 1)
+// gradient tables are contracted, so only two degrees are live.
 template <int P>
-__device__ __forceinline__ void m2p(const float4 *sM, float rx, float ry, float rz, float (&u)[3])
+__device__ __forceinline__ void m2p(const float4 *sF, float rx, float ry, float rz, float (&u)[3])
 {
-    float a[nterms(P + 1)];
+    constexpr int G0 = (P + 1) * (P + 1), GN = (P + 2) * (P + 2) - 1;
+    float a[(P + 2) * (P + 2)];
     const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
     const float ir2 = 1.0f / r2;
     a[0] = rsqrtf(r2);
-    float phi[4] = {0.0f, 0.0f, 0.0f, 0.0f}, gx[4] = {0.0f, 0.0f, 0.0f, 0.0f}, gy[4] = {0.0f, 0.0f, 0.0f, 0.0f},
+    float phi[3] = {0.0f, 0.0f, 0.0f}, gx[4] = {0.0f, 0.0f, 0.0f, 0.0f}, gy[4] = {0.0f, 0.0f, 0.0f, 0.0f},
           gz[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
     for (int n = 0; n <= P; ++n) {
         const int m = n + 1;
         const float c1 = float(2 * m - 1) / float(m), c2 = float(m - 1) / float(m);
 #pragma unroll
-        for (int aa = m; aa >= 0; --aa)
+        for (int cc = 0; cc <= 1; ++cc)
 #pragma unroll
-            for (int bb = m - aa; bb >= 0; --bb) {
-                const int cc = m - aa - bb;
+            for (int aa = m - cc; aa >= 0; --aa) {
+                const int bb = m - cc - aa;
                 float s1 = 0.0f, s2 = 0.0f;
-                if (aa >= 1) s1 = fmaf(rx, a[tidx(aa - 1, bb, cc)], s1);
-                if (bb >= 1) s1 = fmaf(ry, a[tidx(aa, bb - 1, cc)], s1);
-                if (cc >= 1) s1 = fmaf(rz, a[tidx(aa, bb, cc - 1)], s1);
-                if (aa >= 2) s2 += a[tidx(aa - 2, bb, cc)];
-                if (bb >= 2) s2 += a[tidx(aa, bb - 2, cc)];
-                if (cc >= 2) s2 += a[tidx(aa, bb, cc - 2)];
-                a[tidx(aa, bb, cc)] = (c1 * s1 - c2 * s2) * ir2;
+                if (aa >= 1) s1 = fmaf(rx, a[ridx(aa - 1, bb, cc)], s1);
+                if (bb >= 1) s1 = fmaf(ry, a[ridx(aa, bb - 1, cc)], s1);
+                if (cc >= 1) s1 = fmaf(rz, a[ridx(aa, bb, cc - 1)], s1);
+                if (aa >= 2) s2 += a[ridx(aa - 2, bb, cc)];
+                if (bb >= 2) s2 += a[ridx(aa, bb - 2, cc)];
+                a[ridx(aa, bb, cc)] = (c1 * s1 - c2 * s2) * ir2;
             }
+        // potentials of degree n (the fourth charge's potential is not needed)
 #pragma unroll
-        for (int aa = n; aa >= 0; --aa)
+        for (int cc = 0; cc <= 1; ++cc)
 #pragma unroll
-            for (int bb = n - aa; bb >= 0; --bb) {
-                const int cc = n - aa - bb;
-                const float4 mk = sM[tidx(aa, bb, cc)];
-                const float ak = a[tidx(aa, bb, cc)];
-                const float ax = -float(aa + 1) * a[tidx(aa + 1, bb, cc)];
-                const float ay = -float(bb + 1) * a[tidx(aa, bb + 1, cc)];
-                const float az = -float(cc + 1) * a[tidx(aa, bb, cc + 1)];
-                const float mq[4] = {mk.x, mk.y, mk.z, mk.w};
+            for (int aa = n - cc; aa >= 0; --aa) {
+                const int bb = n - cc - aa;
+                if (bb < 0) continue;
+                const float ak = a[ridx(aa, bb, cc)];
+                const float4 t = sF[ridx(aa, bb, cc)];
+                phi[0] = fmaf(ak, t.x, phi[0]);
+                phi[1] = fmaf(ak, t.y, phi[1]);
+                phi[2] = fmaf(ak, t.z, phi[2]);
+            }
+        // gradients: tables of degree m
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    phi[q] = fmaf(ak, mq[q], phi[q]);
-                    gx[q] = fmaf(ax, mq[q], gx[q]);
-                    gy[q] = fmaf(ay, mq[q], gy[q]);
-                    gz[q] = fmaf(az, mq[q], gz[q]);
-                }
+        for (int cc = 0; cc <= 1; ++cc)
+#pragma unroll
+            for (int aa = m - cc; aa >= 0; --aa) {
+                const int bb = m - cc - aa;
+                const int j = ridx(aa, bb, cc) - 1;
+                const float am = a[ridx(aa, bb, cc)];
+                const float4 tx = sF[G0 + j], ty = sF[G0 + GN + j], tz = sF[G0 + 2 * GN + j];
+                gx[0] = fmaf(am, tx.x, gx[0]);
+                gx[1] = fmaf(am, tx.y, gx[1]);
+                gx[2] = fmaf(am, tx.z, gx[2]);
+                gx[3] = fmaf(am, tx.w, gx[3]);
+                gy[0] = fmaf(am, ty.x, gy[0]);
+                gy[1] = fmaf(am, ty.y, gy[1]);
+                gy[2] = fmaf(am, ty.z, gy[2]);
+                gy[3] = fmaf(am, ty.w, gy[3]);
+                gz[0] = fmaf(am, tz.x, gz[0]);
+                gz[1] = fmaf(am, tz.y, gz[1]);
+                gz[2] = fmaf(am, tz.z, gz[2]);
+                gz[3] = fmaf(am, tz.w, gz[3]);
             }
     }
     u[0] += phi[0] - (rx * gx[0] + ry * gx[1] + rz * gx[2]) + gx[3];
@@ -547,7 +624,7 @@ __device__ __forceinline__ void acc2(float &s, float &e, float v)
 struct EvalArgs {
     const float4 *ch, *cl;           // cell centres (hi + radius, lo)
     const int4 *ci;                  // cell (beg, end, cb, ce)
-    const float4 *Mf;                // [cells][T] FP32 moments of the four charges
+    const float4 *Mf;                // [cells][nfold(P)] folded FP32 tables of the four charges
     const float4 *yh, *yl, *yf;      // sorted sources
     const float4 *xh, *xl;           // sorted targets
     const float4 *gctr;              // group centres (hi + half-diagonal, lo)
@@ -589,7 +666,8 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_tree_eval(EvalArgs A)
 {
     constexpr int T = nterms(P);
     __shared__ int stack[kWarps][kStack];
-    __shared__ float4 smom[kWarps][T];
+    constexpr int NF = nfold(P);
+    __shared__ float4 smom[kWarps][NF];
     __shared__ float4 sy[kWarps][3][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = blockIdx.x * kWarps + warp;
@@ -623,7 +701,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_tree_eval(EvalArgs A)
         const bool far = dist > 0.0f && chc.w < A.theta * dist;
         float u[3] = {0.0f, 0.0f, 0.0f};
         if (far && e - b > A.direct_max) {
-            for (int k = lane; k < T; k += 32) smom[warp][k] = __ldg(A.Mf + int64_t(c) * T + k);
+            for (int k = lane; k < NF; k += 32) smom[warp][k] = __ldg(A.Mf + int64_t(c) * NF + k);
             __syncwarp();
             if (ok) m2p<P>(smom[warp], xg[0] + dx, xg[1] + dy, xg[2] + dz, u);   // r = x - c
             __syncwarp();
@@ -712,8 +790,8 @@ fs_status launch_eval_and_moments(const Cells &C, const std::vector<int> &leaves
         FS_LAUNCH_CHECK();
         FS_CUDA(cudaStreamSynchronize(st));
     }
-    const int64_t nm = int64_t(ncells) * T;
-    k_moments_f4<<<static_cast<unsigned>((nm + 255) / 256), 256, 0, st>>>(Md, ncells, T, Mf);
+    const int64_t ntask = int64_t(ncells) * 16 * (P + 2);
+    k_fold<P><<<static_cast<unsigned>((ntask + 127) / 128), 128, 0, st>>>(Md, ncells, Mf);
     FS_LAUNCH_CHECK();
     k_pack_cells<<<(ncells + 255) / 256, 256, 0, st>>>(C, ncells, cube, pch, pcl, pci);
     FS_LAUNCH_CHECK();
@@ -783,7 +861,8 @@ fs_status fs_stokeslet_apply_tree(fs_ctx *c, const double *src_xyz, const double
     acct(size_t(cap) * 4);                                  // list
     acct(size_t(ns) * 6 * d);                               // xs, fs
     acct(size_t(ns) * 3 * 16);                              // yh, yl, yf
-    acct(size_t(cap) * 4 * T * (d + 4));                    // moments
+    acct(size_t(cap) * 4 * T * d);                          // FP64 moments
+    acct(size_t(cap) * nfold(order) * 16);                  // folded FP32 tables
     acct(size_t(ngroups) * 32);
     acct(size_t(cap) * 48);
     acct(size_t(nt) * 2 * 16);
@@ -814,7 +893,7 @@ fs_status fs_stokeslet_apply_tree(fs_ctx *c, const double *src_xyz, const double
     double *xs = cv.take<double>(3 * size_t(ns)), *fsrc = cv.take<double>(3 * size_t(ns));
     float4 *yh = cv.take<float4>(ns), *yl = cv.take<float4>(ns), *yf = cv.take<float4>(ns);
     double *Md = cv.take<double>(size_t(cap) * 4 * T);
-    float4 *Mf = cv.take<float4>(size_t(cap) * T);
+    float4 *Mf = cv.take<float4>(size_t(cap) * nfold(order));
     float4 *gctr = cv.take<float4>(2 * size_t(ngroups));
     float4 *pch = cv.take<float4>(cap), *pcl = cv.take<float4>(cap);
     int4 *pci = cv.take<int4>(cap);
