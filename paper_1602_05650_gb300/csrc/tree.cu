@@ -49,7 +49,9 @@ constexpr int kMaxLevel = 10;
 constexpr int kLeafCap = 64;
 constexpr int kGroup = 32;
 constexpr int kWarps = 4;          // warps (target groups) per CTA
-constexpr int kStack = 192;        // traversal stack entries per warp
+// traversal stack entries per warp (order 10 keeps the CTA's static shared
+// memory under 48 KB)
+__host__ __device__ constexpr int stack_size(int P) { return P >= 10 ? 320 : 1024; }
 
 __host__ __device__ constexpr int nterms(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
 
@@ -252,21 +254,42 @@ __global__ void k_gather_src(const double *__restrict__ x, const double *__restr
 }
 
 // ------------------------------------------------------------ moments (FP64)
-// P2M at the leaves: one CTA per leaf, threads over the terms, points staged
-// in shared memory; rad from the points.
+// multi-index (a, b, c) of term t (degree-major order of tidx)
+__device__ __forceinline__ void term_of(int t, int &a, int &b, int &c)
+{
+    int n = 0;
+    while (nterms(n) <= t) ++n;
+    const int r = t - nterms(n - 1);
+    int bc = 0;
+    while ((bc + 1) * (bc + 2) / 2 <= r) ++bc;
+    c = r - bc * (bc + 1) / 2;
+    b = bc - c;
+    a = n - bc;
+}
+
+// P2M at the leaves: one CTA per leaf, threads over the terms; points staged
+// in shared memory with their powers (y - c)_i^e, so a monomial is two
+// products; rad from the points.
 template <int P>
 __global__ void __launch_bounds__(128) k_p2m(Cells C, const int *__restrict__ leaves, int nleaves,
                                              const double *__restrict__ xs, const double *__restrict__ fs,
                                              double *__restrict__ M)
 {
     constexpr int T = nterms(P);
-    __shared__ double sd[32][3], sq[32][4];
+    constexpr int S = (T + 127) / 128;
+    __shared__ double pw[32][3][P + 1], sq[32][4];
     __shared__ float srad[128];
     const int li = blockIdx.x;
     if (li >= nleaves) return;
     const int c = leaves[li];
     const double *ctr = C.ctr + 3 * int64_t(c);
-    double acc[(T + 127) / 128][4] = {};
+    int ta[S], tb[S], tc[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int t = threadIdx.x + 128 * s;
+        if (t < T) term_of(t, ta[s], tb[s], tc[s]);
+    }
+    double acc[S][4] = {};
     float rmax = 0.0f;
     for (int b0 = C.beg[c]; b0 < C.end[c]; b0 += 32) {
         const int nb = min(32, C.end[c] - b0);
@@ -276,7 +299,11 @@ __global__ void __launch_bounds__(128) k_p2m(Cells C, const int *__restrict__ le
             double d[3];
             for (int a = 0; a < 3; ++a) {
                 d[a] = xs[3 * int64_t(i) + a] - ctr[a];
-                sd[threadIdx.x][a] = d[a];
+                double v = 1.0;
+                for (int e = 0; e <= P; ++e) {
+                    pw[threadIdx.x][a][e] = v;
+                    v *= d[a];
+                }
             }
             const double *f = fs + 3 * int64_t(i);
             sq[threadIdx.x][0] = f[0];
@@ -287,27 +314,16 @@ __global__ void __launch_bounds__(128) k_p2m(Cells C, const int *__restrict__ le
         }
         __syncthreads();
 #pragma unroll
-        for (int s = 0; s < (T + 127) / 128; ++s) {
-            const int t = threadIdx.x + 128 * s;
-            if (t >= T) break;
-            // decode t -> (a, b, c)
-            int n = 0;
-            while (nterms(n) <= t) ++n;
-            const int r = t - nterms(n - 1);
-            int bc = 0;
-            while ((bc + 1) * (bc + 2) / 2 <= r) ++bc;
-            const int cc = r - bc * (bc + 1) / 2, bb = bc - cc, aa = n - bc;
+        for (int s = 0; s < S; ++s) {
+            if (threadIdx.x + 128 * s >= T) break;
             for (int j = 0; j < nb; ++j) {
-                double m = 1.0;
-                for (int e = 0; e < aa; ++e) m *= sd[j][0];
-                for (int e = 0; e < bb; ++e) m *= sd[j][1];
-                for (int e = 0; e < cc; ++e) m *= sd[j][2];
-                for (int q = 0; q < 4; ++q) acc[s][q] += m * sq[j][q];
+                const double m = pw[j][0][ta[s]] * pw[j][1][tb[s]] * pw[j][2][tc[s]];
+                for (int q = 0; q < 4; ++q) acc[s][q] = fma(m, sq[j][q], acc[s][q]);
             }
         }
     }
 #pragma unroll
-    for (int s = 0; s < (T + 127) / 128; ++s) {
+    for (int s = 0; s < S; ++s) {
         const int t = threadIdx.x + 128 * s;
         if (t < T)
             for (int q = 0; q < 4; ++q) M[(int64_t(c) * 4 + q) * T + t] = acc[s][q];
@@ -322,7 +338,8 @@ __global__ void __launch_bounds__(128) k_p2m(Cells C, const int *__restrict__ le
 }
 
 // M2M for the split cells of one level: M_k(parent) = sum_children sum_{j <= k}
-// binom(k, j) d^{k - j} M_j(child), d = c_child - c_parent; the charge
+// binom(k, j) d^{k - j} M_j(child), d = c_child - c_parent, applied as three
+// one-dimensional shifts (the binomial kernel is separable); the charge
 // (y - c).f moves with the centre, so its parent moments add d . (the shifted
 // force moments).
 template <int P>
@@ -330,8 +347,10 @@ __global__ void __launch_bounds__(128) k_m2m(Cells C, const int *__restrict__ ce
                                              double *__restrict__ M)
 {
     constexpr int T = nterms(P);
+    constexpr int S = (4 * T + 127) / 128;   // (charge, term) entries per thread
     __shared__ double pw[3][P + 1];
     __shared__ double binom[P + 1][P + 1];
+    __shared__ double t1[4 * T], t2[4 * T];
     const int ci = blockIdx.x;
     if (ci >= ncells) return;
     const int c = cells[ci];
@@ -344,7 +363,14 @@ __global__ void __launch_bounds__(128) k_m2m(Cells C, const int *__restrict__ ce
         }
         binom[n][k] = b;
     }
-    double acc[(T + 127) / 128][4] = {};
+    int ta[S], tb[S], tc[S], tq[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int e = threadIdx.x + 128 * s;
+        tq[s] = e / T;
+        if (e < 4 * T) term_of(e % T, ta[s], tb[s], tc[s]);
+    }
+    double acc[S] = {};
     float rmax = 0.0f;
     for (int ch = C.cb[c]; ch < C.ce[c]; ++ch) {
         __syncthreads();
@@ -360,38 +386,49 @@ __global__ void __launch_bounds__(128) k_m2m(Cells C, const int *__restrict__ ce
         const double dx = pw[0][1], dy = pw[1][1], dz = pw[2][1];
         rmax = fmaxf(rmax, C.rad[ch] + static_cast<float>(sqrt(dx * dx + dy * dy + dz * dz)));
         const double *Mc = M + int64_t(ch) * 4 * T;
+        // x pass: t1[a,b,c] = sum_{j <= a} binom(a, j) dx^(a-j) M[j,b,c]
 #pragma unroll
-        for (int s = 0; s < (T + 127) / 128; ++s) {
-            const int t = threadIdx.x + 128 * s;
-            if (t >= T) break;
-            int n = 0;
-            while (nterms(n) <= t) ++n;
-            const int r = t - nterms(n - 1);
-            int bc = 0;
-            while ((bc + 1) * (bc + 2) / 2 <= r) ++bc;
-            const int kc = r - bc * (bc + 1) / 2, kb = bc - kc, ka = n - bc;
-            double sh[4] = {0.0, 0.0, 0.0, 0.0};
-            for (int ja = 0; ja <= ka; ++ja)
-                for (int jb = 0; jb <= kb; ++jb)
-                    for (int jc = 0; jc <= kc; ++jc) {
-                        const double w = binom[ka][ja] * binom[kb][jb] * binom[kc][jc] * pw[0][ka - ja] *
-                                         pw[1][kb - jb] * pw[2][kc - jc];
-                        const int j = tidx(ja, jb, jc);
-                        for (int q = 0; q < 4; ++q) sh[q] += w * Mc[q * T + j];
-                    }
-            // the fourth charge is relative to the cell centre:
-            // (y - c_parent).f = (y - c_child).f + d.f
-            acc[s][0] += sh[0];
-            acc[s][1] += sh[1];
-            acc[s][2] += sh[2];
-            acc[s][3] += sh[3] + dx * sh[0] + dy * sh[1] + dz * sh[2];
+        for (int s = 0; s < S; ++s) {
+            const int e = threadIdx.x + 128 * s;
+            if (e >= 4 * T) break;
+            double v = 0.0;
+            for (int j = 0; j <= ta[s]; ++j) v = fma(binom[ta[s]][j] * pw[0][ta[s] - j], Mc[tq[s] * T + tidx(j, tb[s], tc[s])], v);
+            t1[e] = v;
+        }
+        __syncthreads();
+        // y pass
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int e = threadIdx.x + 128 * s;
+            if (e >= 4 * T) break;
+            double v = 0.0;
+            for (int j = 0; j <= tb[s]; ++j) v = fma(binom[tb[s]][j] * pw[1][tb[s] - j], t1[tq[s] * T + tidx(ta[s], j, tc[s])], v);
+            t2[e] = v;
+        }
+        __syncthreads();
+        // z pass into t1, then accumulate with the charge shift
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int e = threadIdx.x + 128 * s;
+            if (e >= 4 * T) break;
+            double v = 0.0;
+            for (int j = 0; j <= tc[s]; ++j) v = fma(binom[tc[s]][j] * pw[2][tc[s] - j], t2[tq[s] * T + tidx(ta[s], tb[s], j)], v);
+            t1[e] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int e = threadIdx.x + 128 * s;
+            if (e >= 4 * T) break;
+            const int t = e % T;
+            acc[s] += t1[e];
+            if (tq[s] == 3) acc[s] += dx * t1[t] + dy * t1[T + t] + dz * t1[2 * T + t];
         }
     }
 #pragma unroll
-    for (int s = 0; s < (T + 127) / 128; ++s) {
-        const int t = threadIdx.x + 128 * s;
-        if (t < T)
-            for (int q = 0; q < 4; ++q) M[(int64_t(c) * 4 + q) * T + t] = acc[s][q];
+    for (int s = 0; s < S; ++s) {
+        const int e = threadIdx.x + 128 * s;
+        if (e < 4 * T) M[int64_t(c) * 4 * T + e] = acc[s];
     }
     if (threadIdx.x == 0) C.rad[c] = rmax;
 }
@@ -399,55 +436,56 @@ __global__ void __launch_bounds__(128) k_m2m(Cells C, const int *__restrict__ ce
 // Folded FP32 tables of one cell, float4 (four charges) per entry:
 //   [0, (P+1)^2)                     potentials, M_k folded, degrees 0..P
 //   then for i = x, y, z: (P+2)^2-1  gradient tensors T^i_m = -m_i M_{m-e_i}, degrees 1..P+1
-// One thread per (charge, table, degree); FP64.
+// One CTA per cell, the tensors in shared memory, one thread per (charge,
+// table, degree); FP64.
 __host__ __device__ constexpr int nfold(int P) { return (P + 1) * (P + 1) + 3 * ((P + 2) * (P + 2) - 1); }
 
 template <int P>
-__global__ void __launch_bounds__(128) k_fold(const double *__restrict__ M, int ncells, float4 *__restrict__ out)
+__global__ void __launch_bounds__(16 * (P + 2)) k_fold(const double *__restrict__ M, int ncells,
+                                                      float4 *__restrict__ out)
 {
-    constexpr int T = nterms(P);
-    constexpr int NF = nfold(P);
-    constexpr int ntask = 4 * 4 * (P + 2);   // charge x table x degree
-    const int64_t gid = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-    const int64_t cell = gid / ntask;
+    constexpr int T = nterms(P), T1 = nterms(P + 1), NF = nfold(P);
+    // the 16 tensors of the cell (charge q x table: potential, gradient x, y, z)
+    // over degrees 0..P+1, degree-major as tidx
+    __shared__ double sv[16][T1];
+    const int cell = blockIdx.x;
     if (cell >= ncells) return;
-    const int task = static_cast<int>(gid - cell * ntask);
-    const int q = task / (4 * (P + 2)), tab = (task / (P + 2)) % 4, d = task % (P + 2);
-    if (tab == 0 && d > P) return;      // potentials: degrees 0..P
-    if (tab > 0 && d == 0) return;      // gradients: degrees 1..P+1
-    const double *Mq = M + (cell * 4 + q) * T;
-    double v[(P + 2) * (P + 3) / 2];     // degree-d tensor, index (b + c)(b + c + 1)/2 + c
-    for (int a = d; a >= 0; --a)
-        for (int b = d - a; b >= 0; --b) {
-            const int c = d - a - b, j = (b + c) * (b + c + 1) / 2 + c;
-            double t;
-            if (tab == 0) {
-                t = Mq[tidx(a, b, c)];
-            } else {
-                const int k[3] = {a, b, c}, i = tab - 1;
-                if (k[i] == 0) {
-                    t = 0.0;
-                } else {
-                    int km[3] = {a, b, c};
-                    --km[i];
-                    t = -double(k[i]) * Mq[tidx(km[0], km[1], km[2])];
-                }
+    const double *Mc = M + int64_t(cell) * 4 * T;
+    for (int idx = threadIdx.x; idx < 16 * T1; idx += blockDim.x) {
+        const int tq = idx / T1, t = idx - tq * T1, q = tq >> 2, tab = tq & 3;
+        int k[3];
+        term_of(t, k[0], k[1], k[2]);
+        const int n = k[0] + k[1] + k[2];
+        double v = 0.0;
+        if (tab == 0) {
+            if (n <= P) v = Mc[q * T + t];
+        } else {
+            const int i = tab - 1;
+            if (k[i] >= 1) {
+                int km[3] = {k[0], k[1], k[2]};
+                --km[i];
+                v = -double(k[i]) * Mc[q * T + tidx(km[0], km[1], km[2])];
             }
-            v[j] = t;
         }
-    // fold entries with c >= 2 (highest c first) onto c - 2
+        sv[tq][t] = v;
+    }
+    __syncthreads();
+    // one thread per (tensor, degree): fold the entries with c >= 2 (highest
+    // c first) onto c - 2, then write the entries with c <= 1
+    const int tq = threadIdx.x / (P + 2), d = threadIdx.x % (P + 2);
+    const int q = tq >> 2, tab = tq & 3;
+    if ((tab == 0 && d > P) || (tab > 0 && d == 0)) return;
+    double *v = sv[tq] + nterms(d - 1);
     for (int c = d; c >= 2; --c)
         for (int b = d - c; b >= 0; --b) {
-            const int a = d - b - c;
+            const int a = d - b - c, bz = c - 2;
             const double x = v[(b + c) * (b + c + 1) / 2 + c];
-            const int bz = c - 2;
             const double w = double((bz + 2) * (bz + 1));
-            // (a + 2, b, c - 2) and (a, b + 2, c - 2)
             v[(b + bz) * (b + bz + 1) / 2 + bz] -= x * double(a + 2) * double(a + 1) / w;
             v[(b + 2 + bz) * (b + 2 + bz + 1) / 2 + bz] -= x * double(b + 2) * double(b + 1) / w;
         }
     const int base = tab == 0 ? 0 : (P + 1) * (P + 1) + (tab - 1) * ((P + 2) * (P + 2) - 1) - 1;
-    float *o = reinterpret_cast<float *>(out + cell * NF);
+    float *o = reinterpret_cast<float *>(out + int64_t(cell) * NF);
     for (int a = d; a >= 0; --a)
         for (int b = d - a; b >= 0; --b) {
             const int c = d - a - b;
@@ -665,6 +703,7 @@ template <int P>
 __global__ void __launch_bounds__(kWarps * 32, 4) k_tree_eval(EvalArgs A)
 {
     constexpr int T = nterms(P);
+    constexpr int kStack = stack_size(P);
     __shared__ int stack[kWarps][kStack];
     constexpr int NF = nfold(P);
     __shared__ float4 smom[kWarps][NF];
@@ -683,42 +722,73 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_tree_eval(EvalArgs A)
     const float xg[3] = {(xh.x - gh4.x) + (xl.x - gl4.x), (xh.y - gh4.y) + (xl.y - gl4.y),
                          (xh.z - gh4.z) + (xl.z - gl4.z)};
     float acc[3] = {0.0f, 0.0f, 0.0f}, err[3] = {0.0f, 0.0f, 0.0f};
-    int top = 0;
+    // warp-parallel walk: up to 32 cells popped at once, one per lane, each
+    // loaded and classified by its lane; children pushed with a warp prefix
+    // sum; then the batch's expansions and direct cells are evaluated by the
+    // whole warp, one cell at a time, in lane order
+    int top = 1;
     if (lane == 0) stack[warp][0] = 0;
-    top = 1;
     __syncwarp();
     while (top > 0) {
-        const int c = stack[warp][top - 1];
-        --top;
+        // batch size shrinks as the stack fills (an opened cell pushes at most
+        // 8 children), down to one cell at a time (depth first)
+        const int nb = min(min(32, top), max(1, (kStack - top) / 8));
+        top -= nb;
+        const bool mine = lane < nb;
+        const int c = mine ? stack[warp][top + lane] : 0;
         __syncwarp();
-        const float4 chc = __ldg(A.ch + c), clc = __ldg(A.cl + c);
-        const int4 cic = __ldg(A.ci + c);
-        // group centre - cell centre, from hi/lo parts
-        const float dx = (gh4.x - chc.x) + (gl4.x - clc.x), dy = (gh4.y - chc.y) + (gl4.y - clc.y),
-                    dz = (gh4.z - chc.z) + (gl4.z - clc.z);
-        const float dist = sqrtf(dx * dx + dy * dy + dz * dz) - gh;
-        const int b = cic.x, e = cic.y, cb = cic.z;
-        const bool far = dist > 0.0f && chc.w < A.theta * dist;
-        float u[3] = {0.0f, 0.0f, 0.0f};
-        if (far && e - b > A.direct_max) {
-            for (int k = lane; k < NF; k += 32) smom[warp][k] = __ldg(A.Mf + int64_t(c) * NF + k);
+        int kind = 0;   // 1: expand, 2: direct, 3: open
+        float dx = 0.0f, dy = 0.0f, dz = 0.0f;
+        int4 cic = make_int4(0, 0, 0, 0);
+        if (mine) {
+            const float4 chc = __ldg(A.ch + c), clc = __ldg(A.cl + c);
+            cic = __ldg(A.ci + c);
+            // group centre - cell centre, from hi/lo parts
+            dx = (gh4.x - chc.x) + (gl4.x - clc.x);
+            dy = (gh4.y - chc.y) + (gl4.y - clc.y);
+            dz = (gh4.z - chc.z) + (gl4.z - clc.z);
+            const float dist = sqrtf(dx * dx + dy * dy + dz * dz) - gh;
+            const bool far = dist > 0.0f && chc.w < A.theta * dist;
+            kind = (far && cic.y - cic.x > A.direct_max) ? 1 : ((far || cic.z < 0) ? 2 : 3);
+        }
+        const int nch = kind == 3 ? cic.w - cic.z : 0;
+        int inc = nch;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += v;
+        }
+        const int total = __shfl_sync(0xffffffffu, inc, 31);
+        if (top + total > kStack) {
+            if (lane == 0) atomicOr(A.status, DEV_ERR_NUMERIC);
+            break;
+        }
+        for (int j = 0; j < nch; ++j) stack[warp][top + inc - nch + j] = cic.z + j;
+        top += total;
+        unsigned mm = __ballot_sync(0xffffffffu, kind == 1);
+        while (mm) {
+            const int src = __ffs(mm) - 1;
+            mm &= mm - 1;
+            const int cc = __shfl_sync(0xffffffffu, c, src);
+            const float ex = __shfl_sync(0xffffffffu, dx, src), ey = __shfl_sync(0xffffffffu, dy, src),
+                        ez = __shfl_sync(0xffffffffu, dz, src);
+            for (int k = lane; k < NF; k += 32) smom[warp][k] = __ldg(A.Mf + int64_t(cc) * NF + k);
             __syncwarp();
-            if (ok) m2p<P>(smom[warp], xg[0] + dx, xg[1] + dy, xg[2] + dz, u);   // r = x - c
+            float u[3] = {0.0f, 0.0f, 0.0f};
+            if (ok) m2p<P>(smom[warp], xg[0] + ex, xg[1] + ey, xg[2] + ez, u);   // r = x - c
             __syncwarp();
             for (int a = 0; a < 3; ++a) acc2(acc[a], err[a], u[a]);
-        } else if (far || cb < 0) {
+        }
+        unsigned pm = __ballot_sync(0xffffffffu, kind == 2);
+        while (pm) {
+            const int src = __ffs(pm) - 1;
+            pm &= pm - 1;
+            const int b = __shfl_sync(0xffffffffu, cic.x, src), e = __shfl_sync(0xffffffffu, cic.y, src);
+            float u[3] = {0.0f, 0.0f, 0.0f};
             p2p_range(A, b, e, t, ok, xh, xl, sy[warp], lane, u);
             for (int a = 0; a < 3; ++a) acc2(acc[a], err[a], u[a]);
-        } else {
-            const int nch = cic.w - cb;
-            if (top + nch > kStack) {
-                if (lane == 0) atomicOr(A.status, DEV_ERR_NUMERIC);
-                break;
-            }
-            if (lane < nch) stack[warp][top + lane] = cb + lane;
-            top += nch;
-            __syncwarp();
         }
+        __syncwarp();
     }
     if (ok) {
         const int j = A.tperm[t];
@@ -742,9 +812,22 @@ __device__ __forceinline__ void hilo4(const double *x, const double *cube, float
     l = make_float4(ll[0], ll[1], ll[2], 0.0f);
 }
 
-__global__ void k_sub_own(const double *__restrict__ xs, const double *__restrict__ wf, const double *__restrict__ xt,
-                          const int2 *__restrict__ excl, int n, const double *__restrict__ cube, double scale,
-                          double *__restrict__ out)
+// the sorted source records back in the sources' original order
+__global__ void k_unsort_src(const int *__restrict__ perm, int n, const float4 *__restrict__ yh,
+                             const float4 *__restrict__ yl, const float4 *__restrict__ yf, float4 *__restrict__ oh,
+                             float4 *__restrict__ ol, float4 *__restrict__ of)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int j = perm[i];
+    oh[j] = yh[i];
+    ol[j] = yl[i];
+    of[j] = yf[i];
+}
+
+__global__ void k_sub_own(const float4 *__restrict__ oh, const float4 *__restrict__ ol, const float4 *__restrict__ of,
+                          const double *__restrict__ xt, const int2 *__restrict__ excl, int n,
+                          const double *__restrict__ cube, double scale, double *__restrict__ out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -753,12 +836,8 @@ __global__ void k_sub_own(const double *__restrict__ xs, const double *__restric
     hilo4(xt + 3 * int64_t(i), cube, xh, xl);
     float acc[3] = {0.0f, 0.0f, 0.0f}, err[3] = {0.0f, 0.0f, 0.0f};
     for (int j = r.x; j < r.y; ++j) {
-        float4 h, l;
-        hilo4(xs + 3 * int64_t(j), cube, h, l);
-        const double *f = wf + 3 * int64_t(j);
-        const float4 f4 = make_float4(static_cast<float>(f[0]), static_cast<float>(f[1]), static_cast<float>(f[2]), 0.0f);
         float u[3] = {0.0f, 0.0f, 0.0f};
-        pair_stokes(xh, xl, h, l, f4, u);
+        pair_stokes(xh, xl, __ldg(oh + j), __ldg(ol + j), __ldg(of + j), u);
         for (int a = 0; a < 3; ++a) acc2(acc[a], err[a], u[a]);
     }
     for (int a = 0; a < 3; ++a)
@@ -790,8 +869,7 @@ fs_status launch_eval_and_moments(const Cells &C, const std::vector<int> &leaves
         FS_LAUNCH_CHECK();
         FS_CUDA(cudaStreamSynchronize(st));
     }
-    const int64_t ntask = int64_t(ncells) * 16 * (P + 2);
-    k_fold<P><<<static_cast<unsigned>((ntask + 127) / 128), 128, 0, st>>>(Md, ncells, Mf);
+    k_fold<P><<<static_cast<unsigned>(ncells), 16 * (P + 2), 0, st>>>(Md, ncells, Mf);
     FS_LAUNCH_CHECK();
     k_pack_cells<<<(ncells + 255) / 256, 256, 0, st>>>(C, ncells, cube, pch, pcl, pci);
     FS_LAUNCH_CHECK();
@@ -866,7 +944,10 @@ fs_status fs_stokeslet_apply_tree(fs_ctx *c, const double *src_xyz, const double
     acct(size_t(ngroups) * 32);
     acct(size_t(cap) * 48);
     acct(size_t(nt) * 2 * 16);
-    if (ids) acct(size_t(nt) * sizeof(int2));
+    if (ids) {
+        acct(size_t(nt) * sizeof(int2));
+        for (int k = 0; k < 3; ++k) acct(size_t(ns) * 16);
+    }
     need += 64 * 256;   // alignment of the individual arrays
     FS_TRY(c->scratch.reserve(need, st));
     Carve cv(c->scratch.ptr, c->scratch.bytes);
@@ -899,6 +980,8 @@ fs_status fs_stokeslet_apply_tree(fs_ctx *c, const double *src_xyz, const double
     int4 *pci = cv.take<int4>(cap);
     float4 *xh = cv.take<float4>(nt), *xl = cv.take<float4>(nt);
     int2 *excl = ids ? cv.take<int2>(nt) : nullptr;
+    float4 *oh = ids ? cv.take<float4>(ns) : nullptr, *ol = ids ? cv.take<float4>(ns) : nullptr,
+           *of = ids ? cv.take<float4>(ns) : nullptr;
     if (cv.used > cv.cap) {
         set_error("fs_stokeslet_apply_tree: workspace accounting");
         return FS_EINVAL;
@@ -997,7 +1080,10 @@ fs_status fs_stokeslet_apply_tree(fs_ctx *c, const double *src_xyz, const double
     }
     if (ids) {
         FS_TRY(exclusion_from_ids(src_fiber, n_src, tgt_fiber, n_tgt, excl, st));
-        k_sub_own<<<(nt + 127) / 128, 128, 0, st>>>(src_xyz, src_wf, tgt_xyz, excl, nt, cube, A.scale, out_u);
+        // the pair records of the near field, in the sources' original order
+        k_unsort_src<<<(ns + 255) / 256, 256, 0, st>>>(sperm, ns, yh, yl, yf, oh, ol, of);
+        FS_LAUNCH_CHECK();
+        k_sub_own<<<(nt + 127) / 128, 128, 0, st>>>(oh, ol, of, tgt_xyz, excl, nt, cube, A.scale, out_u);
         FS_LAUNCH_CHECK();
     }
     int h_status = 0;
