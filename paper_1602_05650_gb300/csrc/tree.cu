@@ -448,13 +448,21 @@ __global__ void __launch_bounds__(16 * (P + 2)) k_fold(const double *__restrict_
     // the 16 tensors of the cell (charge q x table: potential, gradient x, y, z)
     // over degrees 0..P+1, degree-major as tidx
     __shared__ double sv[16][T1];
+    __shared__ unsigned char sk[T1][3];   // multi-index of each term
     const int cell = blockIdx.x;
     if (cell >= ncells) return;
     const double *Mc = M + int64_t(cell) * 4 * T;
+    for (int t = threadIdx.x; t < T1; t += blockDim.x) {
+        int a, b, c;
+        term_of(t, a, b, c);
+        sk[t][0] = static_cast<unsigned char>(a);
+        sk[t][1] = static_cast<unsigned char>(b);
+        sk[t][2] = static_cast<unsigned char>(c);
+    }
+    __syncthreads();
     for (int idx = threadIdx.x; idx < 16 * T1; idx += blockDim.x) {
         const int tq = idx / T1, t = idx - tq * T1, q = tq >> 2, tab = tq & 3;
-        int k[3];
-        term_of(t, k[0], k[1], k[2]);
+        const int k[3] = {sk[t][0], sk[t][1], sk[t][2]};
         const int n = k[0] + k[1] + k[2];
         double v = 0.0;
         if (tab == 0) {
@@ -476,14 +484,16 @@ __global__ void __launch_bounds__(16 * (P + 2)) k_fold(const double *__restrict_
     const int q = tq >> 2, tab = tq & 3;
     if ((tab == 0 && d > P) || (tab > 0 && d == 0)) return;
     double *v = sv[tq] + nterms(d - 1);
-    for (int c = d; c >= 2; --c)
+    for (int c = d; c >= 2; --c) {
+        const int bz = c - 2;
+        const double rw = 1.0 / double((bz + 2) * (bz + 1));
         for (int b = d - c; b >= 0; --b) {
-            const int a = d - b - c, bz = c - 2;
-            const double x = v[(b + c) * (b + c + 1) / 2 + c];
-            const double w = double((bz + 2) * (bz + 1));
-            v[(b + bz) * (b + bz + 1) / 2 + bz] -= x * double(a + 2) * double(a + 1) / w;
-            v[(b + 2 + bz) * (b + 2 + bz + 1) / 2 + bz] -= x * double(b + 2) * double(b + 1) / w;
+            const int a = d - b - c;
+            const double x = v[(b + c) * (b + c + 1) / 2 + c] * rw;
+            v[(b + bz) * (b + bz + 1) / 2 + bz] -= x * double((a + 2) * (a + 1));
+            v[(b + 2 + bz) * (b + 2 + bz + 1) / 2 + bz] -= x * double((b + 2) * (b + 1));
         }
+    }
     const int base = tab == 0 ? 0 : (P + 1) * (P + 1) + (tab - 1) * ((P + 2) * (P + 2) - 1) - 1;
     float *o = reinterpret_cast<float *>(out + int64_t(cell) * NF);
     for (int a = d; a >= 0; --a)
