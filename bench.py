@@ -236,6 +236,8 @@ def run_workload(args, ws, rank, local, fs, torch):
               speeds relative to V_c;
     kinetics  1,024 growing and shrinking microtubules (dynamic instability
               with the paper's rates), advanced --steps steps;
+    tree-step one implicit step of 1,048,576 points (32,768 fibers x 32) with
+              the treecode far field and with the direct one;
     aster     the confined aster of Table 2 (32, 128, 512 and 2,048 fibers x
               31 points clamped to a sphere inside a sphere six radii out,
               force on the sphere, GMRES 1e-5): steps/s and GMRES iterations
@@ -372,6 +374,35 @@ def run_workload(args, ws, rank, local, fs, torch):
                     "timing": "host wall clock per step (state machine, rates upload and step)",
                     "iters": iters, "mean_length_um": [float(L0.mean()), float(L1.mean())],
                     "growing_fraction": float(state.mean())})
+    elif args.workload == "tree-step":
+        # 1,048,576 points (32,768 straight fibers x 32 points in [0,100]^3,
+        # the cloud's density; N(0,1) force per node), one mixed step at tol
+        # 1e-5 with the treecode far field (order 8, theta 0.5) and one with
+        # the direct far field, from the same state; velocity difference
+        s = wl.free_space(32768, 32, 100.0, seed=rank)
+        X = torch.tensor(s.X, device=dev)
+        L = torch.tensor(s.L, device=dev)
+        F = torch.tensor(s.f_ext, device=dev)
+        res, V = {}, {}
+        for name, order in (("tree_p8_theta0.5", 8), ("direct", 0)):
+            opt = fs.fs_options_default()
+            opt.prec = fs.FS_MIXED
+            opt.tol = 1e-5
+            opt.tree_order = order
+            opt.tree_theta = 0.5
+            h = fs.fs_create(s.n_per_fiber, s.mu, s.eps, s.E, s.dt, options=opt, stream=stream)
+            steps = 1 if order == 0 else max(1, min(args.steps, 3))
+            ms, infos = _timed_steps(fs, torch, h, stream, X, L, F, steps, 1 if order else 0)
+            V[name] = torch.empty_like(X)
+            fs.fs_get_state(h, V=V[name])
+            fs.fs_destroy(h)
+            res[name] = {"ms_per_step": ms, "steps_per_s": 1e3 / ms, "iters": [i.iters for i in infos],
+                         "outer": [i.refine_sweeps for i in infos], "resid": [i.resid for i in infos],
+                         "t_ms_rhs_build_solve": [round(x, 1) for x in infos[0].t_ms[:3]]}
+        dv = (torch.linalg.norm(V["tree_p8_theta0.5"] - V["direct"]) / torch.linalg.norm(V["direct"])).item()
+        out.update({"points": int(s.n_points), "fibers": s.n_fibers, "points_per_fiber": 32, "tol": 1e-5,
+                    "result": res, "velocity_rel_difference_tree_vs_direct": dv,
+                    "speedup_tree_vs_direct": res["direct"]["ms_per_step"] / res["tree_p8_theta0.5"]["ms_per_step"]})
     elif args.workload == "aster":
         res = {}
         for nf in (32, 128, 512, 2048):
@@ -554,7 +585,8 @@ def main():
     ap.add_argument("--tile", type=int, default=0,
                     help="far-field launch shape id (0 = default; 1..3 = targets per thread FP32 2/4/8, "
                          "float-float 1/2/4)")
-    ap.add_argument("--workload", choices=["confined", "batched", "large", "sediment", "kinetics", "aster"],
+    ap.add_argument("--workload", choices=["confined", "batched", "large", "sediment", "kinetics", "aster",
+                                           "tree-step"],
                     default=None,
                     help="a secondary workload instead of the headline step benchmark")
     ap.add_argument("--serve", type=int, default=0,

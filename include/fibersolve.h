@@ -126,6 +126,12 @@ typedef struct {
                                reduced 1e3-fold before the next true residual.
                                0 = flexible GMRES with every outer direction in float-float,
                                each preconditioned by an FP32-far-field GMRES solve */
+    int32_t tree_order;     /* 0 = direct far field (default); 4, 6, 8 or 10 = every
+                               fiber-fiber far field of the step (every precision) is the
+                               treecode of fs_stokeslet_apply_tree at this order: the
+                               operator is then the treecode's, and tol applies to it (as
+                               with the paper's fast summation); single-system contexts */
+    double tree_theta;      /* opening angle of the treecode (default 0.5) */
 } fs_options;
 
 /* Direct-sum kernel classes reported by fs_kernel_stats. */

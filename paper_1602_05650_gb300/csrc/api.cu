@@ -88,6 +88,8 @@ fs_status fs_options_default(fs_options *o)
     o->tile_override = 0;
     o->profile = 0;
     o->relax = 1;
+    o->tree_order = 0;
+    o->tree_theta = 0.5;
     return FS_OK;
 }
 
@@ -142,6 +144,21 @@ static fs_status create_impl(fs_ctx **out, int32_t n_systems, const int32_t *fps
                 return FS_EINVAL;
             }
         }
+    if (opt) {
+        const int t = opt->tree_order;
+        if (t != 0 && t != 4 && t != 6 && t != 8 && t != 10) {
+            set_error("fs_create: tree_order must be 0, 4, 6, 8 or 10 (got %d)", t);
+            return FS_EINVAL;
+        }
+        if (t && !(opt->tree_theta > 0.0 && opt->tree_theta < 1.0)) {
+            set_error("fs_create: tree_theta must lie in (0, 1)");
+            return FS_EINVAL;
+        }
+        if (t && n_systems > 1) {
+            set_error("fs_create_batch: the treecode far field serves single-system contexts");
+            return FS_EINVAL;
+        }
+    }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
         cudaGetLastError();

@@ -215,6 +215,12 @@ fs_status surface_rows(fs_ctx *c, const double *q, const double *usurf, double *
 fs_status surface_diag(fs_ctx *c);
 fs_status surface_precond(fs_ctx *c, const double *in, double *out);
 
+// tree.cu: the treecode sum (fs_stokeslet_apply_tree), exclusion from ids or
+// from per-target source ranges excl_given
+fs_status tree_sum(fs_ctx *c, const double *src_xyz, const double *src_wf, int64_t n_src, const int32_t *src_fiber,
+                   const double *tgt_xyz, const int32_t *tgt_fiber, int64_t n_tgt, double *out_u, int32_t order,
+                   double theta, const int2 *excl_given);
+
 // body.cu
 // Stokeslet and rotlet strengths of the body from the attached ends: mode
 // LOAD_KNOWN (external load + ends' known part), LOAD_LIN (part linear in the

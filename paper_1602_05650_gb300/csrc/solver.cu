@@ -225,6 +225,12 @@ fs_status fetch_h(fs_ctx *c, const Space &sp)
 // its own system's sources only): ubar = (1/8 pi mu) sum_{other fibers} G0 W f
 fs_status far_field(fs_ctx *c, int sum_prec, bool hilo, const std::vector<int> *act)
 {
+    if (c->opt.tree_order > 0) {
+        // fast summation: the treecode at the chosen order, whatever the precision
+        c->pairs_last += c->n_tot * c->n_tot;
+        return tree_sum(c, c->d_X, c->d_wf, c->n_tot, nullptr, c->d_X, nullptr, c->n_tot, c->d_ubar,
+                        c->opt.tree_order, c->opt.tree_theta, c->d_excl);
+    }
     PairSumArgs a;
     a.kind = PAIR_STOKESLET;
     a.src_xyz = c->d_X;

@@ -892,13 +892,13 @@ fs_status launch_eval_and_moments(const Cells &C, const std::vector<int> &leaves
 }  // namespace
 }  // namespace fs
 
-using namespace fs;
+namespace fs {
 
-extern "C" {
-
-fs_status fs_stokeslet_apply_tree(fs_ctx *c, const double *src_xyz, const double *src_wf, int64_t n_src,
-                                  const int32_t *src_fiber, const double *tgt_xyz, const int32_t *tgt_fiber,
-                                  int64_t n_tgt, double *out_u, int32_t order, double theta)
+// The treecode sum; exclusion from fiber ids, or from per-target source
+// ranges (excl_given, as exclusion_from_ids writes them) when not NULL.
+fs_status tree_sum(fs_ctx *c, const double *src_xyz, const double *src_wf, int64_t n_src, const int32_t *src_fiber,
+                   const double *tgt_xyz, const int32_t *tgt_fiber, int64_t n_tgt, double *out_u, int32_t order,
+                   double theta, const int2 *excl_given)
 {
     if (!c || n_src < 0 || n_tgt < 0 || (n_src > 0 && (!src_xyz || !src_wf)) || (n_tgt > 0 && (!tgt_xyz || !out_u))) {
         set_error("fs_stokeslet_apply_tree: bad sizes or NULL arrays");
@@ -924,7 +924,7 @@ fs_status fs_stokeslet_apply_tree(fs_ctx *c, const double *src_xyz, const double
     }
     const int ns = static_cast<int>(n_src), nt = static_cast<int>(n_tgt);
     const bool self = src_xyz == tgt_xyz && n_src == n_tgt;
-    const bool ids = src_fiber && tgt_fiber;
+    const bool ids = (src_fiber && tgt_fiber) || excl_given;
     const int T = nterms(order);
     const int cap = 2 * ns + 64;   // cells: a split cell holds > kLeafCap points
     const int ngroups = (nt + kGroup - 1) / kGroup;
@@ -954,6 +954,7 @@ fs_status fs_stokeslet_apply_tree(fs_ctx *c, const double *src_xyz, const double
     acct(size_t(ngroups) * 32);
     acct(size_t(cap) * 48);
     acct(size_t(nt) * 2 * 16);
+    acct(sizeof(int));
     if (ids) {
         acct(size_t(nt) * sizeof(int2));
         for (int k = 0; k < 3; ++k) acct(size_t(ns) * 16);
@@ -989,13 +990,15 @@ fs_status fs_stokeslet_apply_tree(fs_ctx *c, const double *src_xyz, const double
     float4 *pch = cv.take<float4>(cap), *pcl = cv.take<float4>(cap);
     int4 *pci = cv.take<int4>(cap);
     float4 *xh = cv.take<float4>(nt), *xl = cv.take<float4>(nt);
-    int2 *excl = ids ? cv.take<int2>(nt) : nullptr;
+    int2 *excl = (ids && !excl_given) ? cv.take<int2>(nt) : nullptr;
     float4 *oh = ids ? cv.take<float4>(ns) : nullptr, *ol = ids ? cv.take<float4>(ns) : nullptr,
            *of = ids ? cv.take<float4>(ns) : nullptr;
+    int *tstat = cv.take<int>(1);   // traversal status (own word: the context's may carry other flags)
     if (cv.used > cv.cap) {
         set_error("fs_stokeslet_apply_tree: workspace accounting");
         return FS_EINVAL;
     }
+    FS_CUDA(cudaMemsetAsync(tstat, 0, sizeof(int), st));
 
     // bounding cube of sources and targets
     k_minmax<<<nparts / 2, 256, 0, st>>>(src_xyz, n_src, part);
@@ -1081,7 +1084,7 @@ fs_status fs_stokeslet_apply_tree(fs_ctx *c, const double *src_xyz, const double
     A.theta = static_cast<float>(theta);
     A.scale = 1.0 / (8.0 * M_PI * c->mu);
     A.out = out_u;
-    A.status = c->d_status;
+    A.status = tstat;
     switch (order) {
     case 4: FS_TRY(launch_eval_and_moments<4>(C, leaves, split, ncells, d_list, xs, fsrc, Md, Mf, cube, pch, pcl, pci, A, st)); break;
     case 6: FS_TRY(launch_eval_and_moments<6>(C, leaves, split, ncells, d_list, xs, fsrc, Md, Mf, cube, pch, pcl, pci, A, st)); break;
@@ -1089,7 +1092,8 @@ fs_status fs_stokeslet_apply_tree(fs_ctx *c, const double *src_xyz, const double
     default: FS_TRY(launch_eval_and_moments<10>(C, leaves, split, ncells, d_list, xs, fsrc, Md, Mf, cube, pch, pcl, pci, A, st)); break;
     }
     if (ids) {
-        FS_TRY(exclusion_from_ids(src_fiber, n_src, tgt_fiber, n_tgt, excl, st));
+        if (excl_given) excl = const_cast<int2 *>(excl_given);
+        else FS_TRY(exclusion_from_ids(src_fiber, n_src, tgt_fiber, n_tgt, excl, st));
         // the pair records of the near field, in the sources' original order
         k_unsort_src<<<(ns + 255) / 256, 256, 0, st>>>(sperm, ns, yh, yl, yf, oh, ol, of);
         FS_LAUNCH_CHECK();
@@ -1097,14 +1101,26 @@ fs_status fs_stokeslet_apply_tree(fs_ctx *c, const double *src_xyz, const double
         FS_LAUNCH_CHECK();
     }
     int h_status = 0;
-    FS_CUDA(cudaMemcpyAsync(&h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    FS_CUDA(cudaMemcpyAsync(&h_status, tstat, sizeof(int), cudaMemcpyDeviceToHost, st));
     FS_CUDA(cudaStreamSynchronize(st));
     if (h_status) {
-        FS_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(int), st));
         set_error("fs_stokeslet_apply_tree: traversal stack overflow");
         return FS_ENUMERIC;
     }
     return FS_OK;
+}
+
+}  // namespace fs
+
+using namespace fs;
+
+extern "C" {
+
+fs_status fs_stokeslet_apply_tree(fs_ctx *c, const double *src_xyz, const double *src_wf, int64_t n_src,
+                                  const int32_t *src_fiber, const double *tgt_xyz, const int32_t *tgt_fiber,
+                                  int64_t n_tgt, double *out_u, int32_t order, double theta)
+{
+    return tree_sum(c, src_xyz, src_wf, n_src, src_fiber, tgt_xyz, tgt_fiber, n_tgt, out_u, order, theta, nullptr);
 }
 
 }  // extern "C"

@@ -80,3 +80,16 @@ def test_body_arguments_are_validated_without_gpu(lib):
     assert create((0, 0), body(nod=None)) == _native.FS_EINVAL               # missing nodes
     assert create((0, 0), body(force=(0.0, float("nan"), 0.0))) == _native.FS_EINVAL
     assert b"non-finite" in lib.fs_last_error()
+
+
+def test_treecode_options_are_validated_without_gpu(lib):
+    o = _native.fs_options()
+    lib.fs_options_default(ctypes.byref(o))
+    assert o.tree_order == 0 and o.tree_theta == 0.5
+    out = ctypes.c_void_p()
+    ppf = (ctypes.c_int32 * 1)(16)
+    for order, theta in ((5, 0.5), (8, 1.0), (8, 0.0)):
+        o.tree_order, o.tree_theta = order, theta
+        assert lib.fs_create(ctypes.byref(out), 1, ppf, 1.0, 1e-3, 1.0, 1e-3, None, ctypes.byref(o),
+                             None) == _native.FS_EINVAL
+        assert b"tree" in lib.fs_last_error()

@@ -122,3 +122,27 @@ def test_full_size_sampled_against_the_oracle(ctx):
     e = rel(out[idx], ref)
     print("1,048,576 points, order 8 theta 0.4: sampled error %.3e" % e)
     assert e <= 1e-5
+
+
+@pytest.mark.parametrize("prec,tol", [(fs.FS_FP64, 1e-8), (fs.FS_MIXED, 1e-8)])
+def test_step_with_the_treecode_far_field(prec, tol):
+    """fs_step with tree_order set: every fiber-fiber far field is the
+    treecode, so the step solves the treecode's system; its velocities differ
+    from the direct step's by the treecode's error (here 6,400 points, order
+    8, theta 0.4)."""
+    from tests.gpu_helpers import gpu_step
+    s = wl.free_space(200, 32, 15.0, seed=4, curved_amp=0.05)
+    V_ref, _, _, _ = gpu_step(s, torch, prec=fs.FS_FP64, tol=1e-11)
+    opt = fs.fs_options_default()
+    opt.prec, opt.tol, opt.tree_order, opt.tree_theta = prec, tol, 8, 0.4
+    h = fs.fs_create(s.n_per_fiber, s.mu, s.eps, s.E, s.dt, options=opt)
+    X = dev(s.X)
+    fs.fs_set_state(h, X, dev(s.L), dev(s.f_ext))
+    info = fs.fs_step(h)
+    V = torch.empty_like(X)
+    fs.fs_get_state(h, V=V)
+    fs.fs_destroy(h)
+    e = rel(V.cpu().numpy(), V_ref)
+    print("tree step (prec %d): velocity difference %.3e, %d iterations" % (prec, e, info.iters))
+    assert info.resid <= tol
+    assert e <= 1e-4
