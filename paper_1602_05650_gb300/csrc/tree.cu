@@ -565,8 +565,12 @@ __global__ void k_groups(const double *__restrict__ x, const int *__restrict__ t
             gl[a] = static_cast<float>(d - static_cast<double>(gh[a]));
             h2 += 0.25 * (hi[a] - lo[a]) * (hi[a] - lo[a]);
         }
-        gctr[2 * int64_t(g)] = make_float4(gh[0], gh[1], gh[2], static_cast<float>(sqrt(h2)) * (1.0f + 1e-6f) + 1e-30f);
-        gctr[2 * int64_t(g) + 1] = make_float4(gl[0], gl[1], gl[2], 0.0f);
+        gctr[3 * int64_t(g)] = make_float4(gh[0], gh[1], gh[2], static_cast<float>(sqrt(h2)) * (1.0f + 1e-6f) + 1e-30f);
+        gctr[3 * int64_t(g) + 1] = make_float4(gl[0], gl[1], gl[2], 0.0f);
+        // half-extents of the group's box (rounded up)
+        gctr[3 * int64_t(g) + 2] = make_float4(static_cast<float>(0.5 * (hi[0] - lo[0])) * (1.0f + 1e-6f) + 1e-30f,
+                                               static_cast<float>(0.5 * (hi[1] - lo[1])) * (1.0f + 1e-6f) + 1e-30f,
+                                               static_cast<float>(0.5 * (hi[2] - lo[2])) * (1.0f + 1e-6f) + 1e-30f, 0.0f);
     }
 }
 
@@ -675,7 +679,7 @@ struct EvalArgs {
     const float4 *Mf;                // [cells][nfold(P)] folded FP32 tables of the four charges
     const float4 *yh, *yl, *yf;      // sorted sources
     const float4 *xh, *xl;           // sorted targets
-    const float4 *gctr;              // group centres (hi + half-diagonal, lo)
+    const float4 *gctr;              // per group: centre hi (+ half-diagonal), lo, box half-extents
     const int *tperm;                // sorted target -> original index
     int n_tgt, ngroups;
     float theta;
@@ -725,8 +729,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_tree_eval(EvalArgs A)
     const bool ok = t < A.n_tgt;
     const float4 xh = ok ? A.xh[t] : make_float4(0.f, 0.f, 0.f, 0.f);
     const float4 xl = ok ? A.xl[t] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 gh4 = A.gctr[2 * int64_t(g)], gl4 = A.gctr[2 * int64_t(g) + 1];
-    const float gh = gh4.w;
+    const float4 gh4 = A.gctr[3 * int64_t(g)], gl4 = A.gctr[3 * int64_t(g) + 1], ge4 = A.gctr[3 * int64_t(g) + 2];
     // target relative to the group centre, from hi/lo parts (both offsets
     // from the cube centre can be large; their difference is small)
     const float xg[3] = {(xh.x - gh4.x) + (xl.x - gl4.x), (xh.y - gh4.y) + (xl.y - gl4.y),
@@ -757,7 +760,11 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_tree_eval(EvalArgs A)
             dx = (gh4.x - chc.x) + (gl4.x - clc.x);
             dy = (gh4.y - chc.y) + (gl4.y - clc.y);
             dz = (gh4.z - chc.z) + (gl4.z - clc.z);
-            const float dist = sqrtf(dx * dx + dy * dy + dz * dz) - gh;
+            // distance from the cell centre to the group's box: a cell whose
+            // radius is below theta times it is expanded for every target
+            const float px = fmaxf(fabsf(dx) - ge4.x, 0.0f), py = fmaxf(fabsf(dy) - ge4.y, 0.0f),
+                        pz = fmaxf(fabsf(dz) - ge4.z, 0.0f);
+            const float dist = sqrtf(px * px + py * py + pz * pz);
             const bool far = dist > 0.0f && chc.w < A.theta * dist;
             kind = (far && cic.y - cic.x > A.direct_max) ? 1 : ((far || cic.z < 0) ? 2 : 3);
         }
@@ -951,7 +958,7 @@ fs_status tree_sum(fs_ctx *c, const double *src_xyz, const double *src_wf, int64
     acct(size_t(ns) * 3 * 16);                              // yh, yl, yf
     acct(size_t(cap) * 4 * T * d);                          // FP64 moments
     acct(size_t(cap) * nfold(order) * 16);                  // folded FP32 tables
-    acct(size_t(ngroups) * 32);
+    acct(size_t(ngroups) * 48);
     acct(size_t(cap) * 48);
     acct(size_t(nt) * 2 * 16);
     acct(sizeof(int));
@@ -986,7 +993,7 @@ fs_status tree_sum(fs_ctx *c, const double *src_xyz, const double *src_wf, int64
     float4 *yh = cv.take<float4>(ns), *yl = cv.take<float4>(ns), *yf = cv.take<float4>(ns);
     double *Md = cv.take<double>(size_t(cap) * 4 * T);
     float4 *Mf = cv.take<float4>(size_t(cap) * nfold(order));
-    float4 *gctr = cv.take<float4>(2 * size_t(ngroups));
+    float4 *gctr = cv.take<float4>(3 * size_t(ngroups));
     float4 *pch = cv.take<float4>(cap), *pcl = cv.take<float4>(cap);
     int4 *pci = cv.take<int4>(cap);
     float4 *xh = cv.take<float4>(nt), *xl = cv.take<float4>(nt);
