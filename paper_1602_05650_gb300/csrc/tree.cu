@@ -21,8 +21,9 @@
 // Tree.  Sources sorted by 30-bit Morton key in the bounding cube of sources
 // and targets; cells level by level from the key prefixes: a cell with more
 // than kLeafCap points is split into its non-empty octants (10 levels at
-// most).  Moments in FP64: P2M at the leaves, then a binomial shift (M2M) up
-// the tree; the cell radius rho is the largest distance of its points from c.
+// most).  A cell's expansion centre c is the centre of its points' box.
+// Moments in FP64: P2M at the leaves, then a binomial shift (M2M) up the
+// tree; the cell radius rho is the largest distance of its points from c.
 //
 // Evaluation.  One warp per group of 32 consecutive sorted targets with a
 // traversal stack in shared memory.  A cell with rho < theta x (distance
@@ -152,12 +153,13 @@ __global__ void k_keys(const double *__restrict__ x, int64_t n, const double *__
 
 // ------------------------------------------------------------ tree cells
 struct Cells {
-    double *ctr;      // [cap][3] geometric centre
+    double *ctr;      // [cap][3] expansion centre: the centre of the box of the cell's points
     float *rad;       // [cap] largest distance of a point from ctr
     int *beg, *end;   // sorted point range
     int *cb, *ce;     // child range (cb = -1: leaf)
     int *par;         // parent (-1: root)
     int *lvl;
+    double *box;      // [cap][6] box of the cell's points (lo xyz, hi xyz)
 };
 
 __device__ void cell_centre(unsigned prefix, int level, const double *cube, double *c)
@@ -254,6 +256,52 @@ __global__ void k_gather_src(const double *__restrict__ x, const double *__restr
 }
 
 // ------------------------------------------------------------ moments (FP64)
+// Boxes of the cells' points (FP64), leaves from the points, split cells
+// from their children, and the expansion centres at the boxes' centres (a
+// cell's points often fill only part of its octant: fibers).
+__global__ void k_leaf_box(Cells C, const int *__restrict__ leaves, int nleaves, const double *__restrict__ xs)
+{
+    const int li = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (li >= nleaves) return;
+    const int c = leaves[li];
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i = C.beg[c] + lane; i < C.end[c]; i += 32)
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = fmin(lo[a], xs[3 * int64_t(i) + a]);
+            hi[a] = fmax(hi[a], xs[3 * int64_t(i) + a]);
+        }
+    for (int a = 0; a < 3; ++a)
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[a] = fmin(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+            hi[a] = fmax(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+        }
+    if (lane == 0)
+        for (int a = 0; a < 3; ++a) {
+            C.box[6 * int64_t(c) + a] = lo[a];
+            C.box[6 * int64_t(c) + 3 + a] = hi[a];
+            C.ctr[3 * int64_t(c) + a] = 0.5 * (lo[a] + hi[a]);
+        }
+}
+
+__global__ void k_split_box(Cells C, const int *__restrict__ cells, int ncells)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ncells) return;
+    const int c = cells[k];
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int ch = C.cb[c]; ch < C.ce[c]; ++ch)
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = fmin(lo[a], C.box[6 * int64_t(ch) + a]);
+            hi[a] = fmax(hi[a], C.box[6 * int64_t(ch) + 3 + a]);
+        }
+    for (int a = 0; a < 3; ++a) {
+        C.box[6 * int64_t(c) + a] = lo[a];
+        C.box[6 * int64_t(c) + 3 + a] = hi[a];
+        C.ctr[3 * int64_t(c) + a] = 0.5 * (lo[a] + hi[a]);
+    }
+}
+
 // multi-index (a, b, c) of term t (degree-major order of tidx)
 __device__ __forceinline__ void term_of(int t, int &a, int &b, int &c)
 {
@@ -871,6 +919,22 @@ fs_status launch_eval_and_moments(const Cells &C, const std::vector<int> &leaves
                                   float4 *pch, float4 *pcl, int4 *pci, EvalArgs A, cudaStream_t st)
 {
     constexpr int T = nterms(P);
+    // point boxes and expansion centres, leaves then split cells bottom-up
+    if (!leaves_h.empty()) {
+        FS_CUDA(cudaMemcpyAsync(d_list, leaves_h.data(), leaves_h.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        k_leaf_box<<<static_cast<unsigned>((leaves_h.size() + 3) / 4), 128, 0, st>>>(C, d_list,
+                                                                                  static_cast<int>(leaves_h.size()), xs);
+        FS_LAUNCH_CHECK();
+        FS_CUDA(cudaStreamSynchronize(st));   // d_list is reused below
+    }
+    for (int lv = kMaxLevel; lv >= 0; --lv) {
+        const std::vector<int> &v = split_by_level[lv];
+        if (v.empty()) continue;
+        FS_CUDA(cudaMemcpyAsync(d_list, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        k_split_box<<<static_cast<unsigned>((v.size() + 127) / 128), 128, 0, st>>>(C, d_list, static_cast<int>(v.size()));
+        FS_LAUNCH_CHECK();
+        FS_CUDA(cudaStreamSynchronize(st));
+    }
     if (!leaves_h.empty()) {
         FS_CUDA(cudaMemcpyAsync(d_list, leaves_h.data(), leaves_h.size() * sizeof(int), cudaMemcpyHostToDevice, st));
         k_p2m<P><<<static_cast<unsigned>(leaves_h.size()), 128, 0, st>>>(C, d_list, static_cast<int>(leaves_h.size()),
@@ -953,6 +1017,7 @@ fs_status tree_sum(fs_ctx *c, const double *src_xyz, const double *src_wf, int64
     acct(size_t(ns) * 4 * 3);                               // pcell, flag, pos
     acct(sizeof(int));
     acct(size_t(cap) * (3 * d + 4 + 6 * 4));                // cells
+    acct(size_t(cap) * 6 * d);                              // cell point boxes
     acct(size_t(cap) * 4);                                  // list
     acct(size_t(ns) * 6 * d);                               // xs, fs
     acct(size_t(ns) * 3 * 16);                              // yh, yl, yf
@@ -988,6 +1053,7 @@ fs_status tree_sum(fs_ctx *c, const double *src_xyz, const double *src_wf, int64
     C.ce = cv.take<int>(cap);
     C.par = cv.take<int>(cap);
     C.lvl = cv.take<int>(cap);
+    C.box = cv.take<double>(6 * size_t(cap));
     int *d_list = cv.take<int>(cap);
     double *xs = cv.take<double>(3 * size_t(ns)), *fsrc = cv.take<double>(3 * size_t(ns));
     float4 *yh = cv.take<float4>(ns), *yl = cv.take<float4>(ns), *yf = cv.take<float4>(ns);

@@ -4,12 +4,12 @@ truncation error that falls with its order and with the opening angle).
 
 Measured on GB300 (relative 2-norm error over all targets, 19,200 points on
 300 curved fibers, own-fiber pairs excluded): at theta = 0.5, orders 4, 6, 8
-and 10 give 1.2e-3, 1.5e-4, 2.3e-5 and 4.7e-6; at order 8, theta = 0.7,
-0.5 and 0.35 give 4.6e-4, 2.3e-5 and 2.1e-6.  The gates allow up to about
-twice those numbers, and the error must fall with the order and with theta
+and 10 give 1.3e-3, 1.7e-4, 2.6e-5 and 4.6e-6; at order 8, theta = 0.7,
+0.5 and 0.35 give 5.1e-4, 2.6e-5 and 2.2e-6.  The gates allow up to 1.5 to
+2.3 times those numbers, and the error must fall with the order and with theta
 (a wrong expansion coefficient or moment shift stalls the convergence:
 before a missing charge-shift term was fixed, all orders sat at 3e-2).  Full
-size: 1,048,576 points, order 8, theta 0.4: 5.5e-6 on 256 sampled targets."""
+size: 1,048,576 points, order 8, theta 0.4: 5.7e-6 on 256 sampled targets."""
 import numpy as np
 import pytest
 
