@@ -40,6 +40,23 @@ KS_NAMES = ["stokeslet_fp32", "stokeslet_fp64", "stresslet_fp32", "stresslet_fp6
 WORKLOAD = "cloud-1024x64: 1,024 curved fibers x 64 Chebyshev points (65,536 points), [0,40]^3"
 
 
+def job_time(x: float, dist, device) -> float:
+    """A per-rank time as the job's: the maximum over ranks (the job ends
+    with its slowest rank); unchanged on one process."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, ws: int, seconds: float) -> float:
+    """Whole-job throughput: the units every rank processed (replicas, weak
+    scaling) over the job's time."""
+    return units_per_rank * ws / seconds
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -665,10 +682,7 @@ def main():
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
     stats = fs.fs_kernel_stats(h, reset=True)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = job_time(ms, dist, dev)
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     pinned = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
@@ -682,10 +696,7 @@ def main():
         fs.fs_step(h, info=False)
         fs.fs_get_state(h, V=Vh)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = job_time(e2e_s, dist, dev)
     h2d = Xh.nbytes + Lh.nbytes + Fh.nbytes
     d2h = Vh.nbytes
     fs.fs_destroy(h)
@@ -742,7 +753,7 @@ def main():
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         cpu = oracle_baseline(s, fp64["iters"] if fp64 else args.ref_iters)
-    value = ws * 1e3 / ms
+    value = job_rate(1.0, ws, ms * 1e-3)
     line = {
         "metric": "implicit steps/s (%s; mixed FP32/FP64, GMRES 1e-8)" % WORKLOAD,
         "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
@@ -756,7 +767,7 @@ def main():
         "roofline": roofline,
         "cpu_baseline": ({"value": cpu["value"], "unit": "steps/s", "cores": cpu["cores"],
                           "kind": "oracle", "sample": cpu["sample"]} if cpu else None),
-        "e2e": {"value": ws / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": job_rate(1.0, ws, e2e_s), "unit": "steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
         "clocks": clk,
