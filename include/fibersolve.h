@@ -119,11 +119,12 @@ typedef struct {
                                FP32-far-field operator with an FP32 right-hand side to
                                inner_tol, ONE float-float true residual r (one set of far
                                fields of the known force plus the solution's force and of
-                               the periphery density), then GMRES on the FP32 hi/lo operator
+                               the periphery density), then GMRES on the plain FP32 operator
                                for the correction until |r - P^-1 A d| <= tol |P^-1 b| (its
-                               operator error, relative ~1e-7, acts on a correction of size
-                               |r|); a residual with 1e-6 |r| > tol |P^-1 b| / 20 is only
-                               reduced 1e3-fold before the next true residual.
+                               operator error, relative ~3e-6 and at most 1e-4, acts on a
+                               correction of size |r|); a residual with 1e-4 |r| > tol
+                               |P^-1 b| / 20 is only reduced 1e3-fold before the next true
+                               residual.
                                0 = flexible GMRES with every outer direction in float-float,
                                each preconditioned by an FP32-far-field GMRES solve */
     int32_t tree_order;     /* 0 = direct far field (default); 4, 6, 8 or 10 = every
