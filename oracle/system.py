@@ -1,4 +1,6 @@
-"""Global linear system of one implicit step and its GMRES solve (oracle).
+"""Global linear system of one implicit step and its GMRES solve (oracle;
+test infrastructure -- only the tests, the smoke check and the benchmark's
+CPU-baseline legs use it).
 
 Sec. 3.2-3.3: the linearised backward-Euler step gives A u = b
 (Eq. sche-linear-eq) with fiber blocks (4N_m unknowns each) and, under
