@@ -156,3 +156,27 @@ def test_aster_steps_follow_the_oracle():
         print("%s %.2e (oracle at tol: %.2e)" % (k, err, spread))
         assert err <= 10.0 * max(spread, 1e-10), (k, err, spread)
 
+
+
+def test_aster_with_the_treecode_far_field():
+    """A body context with tree_order set: the fiber-fiber far field is the
+    treecode, the body's and periphery's sums stay direct; the step agrees
+    with the direct one to the treecode's accuracy."""
+    s = wl.aster(24, N=16, body_grid=(6, 12), R_periphery=4.0, periphery_grid=(6, 12), fiber_force_std=1.0,
+                 tilt=0.3, torque=(0.1, 0.0, 0.2), seed=6)
+    ref = gpu_body_step(s, prec=fs.FS_FP64, tol=1e-11)
+    opt = fs.fs_options_default()
+    opt.prec, opt.tol, opt.tree_order, opt.tree_theta = fs.FS_FP64, 1e-11, 8, 0.4
+    opt.restart, opt.max_iter = 100, 400
+    h = fs.fs_create_with_body(s.n_per_fiber, s.attach, s.mu, s.eps, s.E, s.dt, s.body, boundary=s.boundary,
+                               options=opt)
+    fs.fs_set_state(h, dev(s.X, torch), dev(s.L, torch), dev(s.f_ext, torch))
+    fs.fs_step(h)
+    _, U, Om = fs.fs_get_body(h)
+    V = torch.empty(s.X.shape, dtype=torch.float64, device="cuda:0")
+    fs.fs_get_state(h, V=V)
+    fs.fs_destroy(h)
+    print("tree vs direct: U %.2e Omega %.2e V %.2e" % (rel(U, ref["U"]), rel(Om, ref["Omega"]),
+                                                        rel(V.cpu().numpy(), ref["V"])))
+    assert rel(U, ref["U"]) <= 1e-4 and rel(Om, ref["Omega"]) <= 1e-4
+    assert rel(V.cpu().numpy(), ref["V"]) <= 1e-4

@@ -179,3 +179,21 @@ def test_aster_gmres_equals_dense_solve():
     u = np.linalg.solve(A, b)
     r = sy.step(tol=1e-13)
     assert np.linalg.norm(r.u - u) <= 1e-9 * np.linalg.norm(u)
+
+
+def test_table2_aster_inputs():
+    """The Table 2 configuration: fibers attached at distinct points on the
+    sphere, pointing outwards, inside the periphery, with the paper's load."""
+    s = wl.table2_aster(64, grid=(8, 16))
+    N = 31
+    ends = s.X[N - 1::N]                       # minus ends (alpha = -1, last node)
+    assert np.allclose(np.linalg.norm(ends, axis=1), 1.0)
+    d = np.linalg.norm(ends[:, None, :] - ends[None, :, :], axis=-1) + np.eye(64) * 10
+    assert d.min() > 0.05                       # distinct attachment points
+    plus = s.X[0::N]
+    assert np.allclose(np.linalg.norm(plus, axis=1), 3.0)          # length 2, radial
+    assert np.all(np.linalg.norm(s.boundary.nodes, axis=1) <= 6.0 + 1e-12)
+    assert np.allclose(s.body.force, (0.0, 0.0, 1.0 / (32 * 4.0)))
+    # no attachment point sits on a surface quadrature node
+    dn = np.linalg.norm(ends[:, None, :] - s.body.nodes[None, :, :], axis=-1)
+    assert dn.min() > 1e-3
