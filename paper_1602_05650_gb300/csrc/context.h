@@ -180,6 +180,7 @@ struct fs_ctx {
     double *d_usurf = nullptr;    // fiber Stokeslets at the surface nodes [n_s][3]
     bool have_state = false, precond_ok = false, geometry_ok = false;
     fs::Scratch scratch;          // far-field scratch (grown on demand)
+    fs::Scratch tree_scratch;     // treecode per-cell tables (grown on demand)
     fs::Profiler prof;            // CUDA-event records (opt.profile)
     int64_t pairs_last = 0;
     size_t dev_bytes = 0;         // device memory allocated by the context (without scratch)

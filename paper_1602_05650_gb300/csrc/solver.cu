@@ -928,6 +928,7 @@ void context_free(fs_ctx *c)
     c->prof.pool.clear();
     c->h_pinned = nullptr;
     c->scratch.release();
+    c->tree_scratch.release();
 }
 
 }  // namespace fs

@@ -1021,10 +1021,7 @@ fs_status tree_sum(fs_ctx *c, const double *src_xyz, const double *src_wf, int64
     acct(size_t(cap) * 4);                                  // list
     acct(size_t(ns) * 6 * d);                               // xs, fs
     acct(size_t(ns) * 3 * 16);                              // yh, yl, yf
-    acct(size_t(cap) * 4 * T * d);                          // FP64 moments
-    acct(size_t(cap) * nfold(order) * 16);                  // folded FP32 tables
     acct(size_t(ngroups) * 48);
-    acct(size_t(cap) * 48);
     acct(size_t(nt) * 2 * 16);
     acct(sizeof(int));
     if (ids) {
@@ -1057,11 +1054,7 @@ fs_status tree_sum(fs_ctx *c, const double *src_xyz, const double *src_wf, int64
     int *d_list = cv.take<int>(cap);
     double *xs = cv.take<double>(3 * size_t(ns)), *fsrc = cv.take<double>(3 * size_t(ns));
     float4 *yh = cv.take<float4>(ns), *yl = cv.take<float4>(ns), *yf = cv.take<float4>(ns);
-    double *Md = cv.take<double>(size_t(cap) * 4 * T);
-    float4 *Mf = cv.take<float4>(size_t(cap) * nfold(order));
     float4 *gctr = cv.take<float4>(3 * size_t(ngroups));
-    float4 *pch = cv.take<float4>(cap), *pcl = cv.take<float4>(cap);
-    int4 *pci = cv.take<int4>(cap);
     float4 *xh = cv.take<float4>(nt), *xl = cv.take<float4>(nt);
     int2 *excl = (ids && !excl_given) ? cv.take<int2>(nt) : nullptr;
     float4 *oh = ids ? cv.take<float4>(ns) : nullptr, *ol = ids ? cv.take<float4>(ns) : nullptr,
@@ -1136,6 +1129,25 @@ fs_status tree_sum(fs_ctx *c, const double *src_xyz, const double *src_wf, int64
     for (int k = 0; k < ncells; ++k) {
         if (cbh[k] < 0) leaves.push_back(k);
         else split[lvh[k]].push_back(k);
+    }
+    // per-cell tables, sized by the cells the tree has (the bound cap is far
+    // larger: a split cell holds more than kLeafCap points), in the
+    // context's second workspace
+    size_t need2 = 0;
+    auto acct2 = [&](size_t bytes) { need2 += (bytes + 255) & ~size_t(255); };
+    acct2(size_t(ncells) * 4 * T * d);                      // FP64 moments
+    acct2(size_t(ncells) * nfold(order) * 16);              // folded FP32 tables
+    acct2(size_t(ncells) * 48);                             // evaluation records
+    need2 += 4 * 256;
+    FS_TRY(c->tree_scratch.reserve(need2, st));
+    Carve cv2(c->tree_scratch.ptr, c->tree_scratch.bytes);
+    double *Md = cv2.take<double>(size_t(ncells) * 4 * T);
+    float4 *Mf = cv2.take<float4>(size_t(ncells) * nfold(order));
+    float4 *pch = cv2.take<float4>(ncells), *pcl = cv2.take<float4>(ncells);
+    int4 *pci = cv2.take<int4>(ncells);
+    if (cv2.used > cv2.cap) {
+        set_error("fs_stokeslet_apply_tree: workspace accounting");
+        return FS_EINVAL;
     }
     k_groups<<<(nt + 127) / 128, 128, 0, st>>>(tgt_xyz, tperm, nt, cube, gctr, xh, xl);
     FS_LAUNCH_CHECK();
