@@ -93,3 +93,54 @@ def test_treecode_options_are_validated_without_gpu(lib):
         assert lib.fs_create(ctypes.byref(out), 1, ppf, 1.0, 1e-3, 1.0, 1e-3, None, ctypes.byref(o),
                              None) == _native.FS_EINVAL
         assert b"tree" in lib.fs_last_error()
+
+
+def _header_structs():
+    """name -> [(field, C type, array length)] for every typedef struct of
+    the header, in declaration order."""
+    text = open(os.path.join(ROOT, "include", "fibersolve.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for body, name in re.findall(r"typedef struct\s*\{(.*?)\}\s*(fs_\w+)\s*;", text, flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = " ".join(decl.split())
+            if not decl:
+                continue
+            m = re.match(r"((?:const )?[\w ]+?)\s*(\*?)\s*(\w+(?:\[\d+\])?(?:\s*,\s*\*?\s*\w+(?:\[\d+\])?)*)$", decl)
+            assert m, decl
+            ctype = m.group(1).strip() + (" *" if m.group(2) else "")
+            for item in m.group(3).split(","):
+                item = item.strip()
+                ptr = item.startswith("*")
+                item = item.lstrip("*").strip()
+                n = 1
+                am = re.match(r"(\w+)\[(\d+)\]", item)
+                if am:
+                    item, n = am.group(1), int(am.group(2))
+                fields.append((item, ctype + (" *" if ptr else ""), n))
+        out[name] = fields
+    return out
+
+
+def test_binding_struct_layouts_match_the_header():
+    """Every struct the binding passes by reference has the header's fields,
+    in order, with matching sizes (a silent layout mismatch would corrupt
+    every call)."""
+    sizes = {"double": 8, "int32_t": 4, "int64_t": 8, "size_t": 8}
+    structs = _header_structs()
+    checked = 0
+    for name, fields in structs.items():
+        cls = getattr(_native, name, None)
+        if cls is None:
+            continue
+        py = cls._fields_
+        assert [f[0] for f in py] == [f[0] for f in fields], name
+        for (fname, ctype, n), (_, pytype) in zip(fields, py):
+            if "*" in ctype:
+                assert ctypes.sizeof(pytype) == ctypes.sizeof(ctypes.c_void_p), (name, fname)
+            else:
+                base = ctype.replace("const ", "").strip()
+                assert ctypes.sizeof(pytype) == sizes[base] * n, (name, fname)
+        checked += 1
+    assert checked >= 6
