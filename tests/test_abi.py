@@ -101,7 +101,7 @@ def _header_structs():
     text = open(os.path.join(ROOT, "include", "fibersolve.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     out = {}
-    for body, name in re.findall(r"typedef struct\s*\{(.*?)\}\s*(fs_\w+)\s*;", text, flags=re.S):
+    for body, name in re.findall(r"typedef struct\s*(?:fs_\w+\s*)?\{(.*?)\}\s*(fs_\w+)\s*;", text, flags=re.S):
         fields = []
         for decl in body.split(";"):
             decl = " ".join(decl.split())
@@ -143,4 +143,4 @@ def test_binding_struct_layouts_match_the_header():
                 base = ctype.replace("const ", "").strip()
                 assert ctypes.sizeof(pytype) == sizes[base] * n, (name, fname)
         checked += 1
-    assert checked >= 6
+    assert checked >= 7 and "fs_request" in structs
