@@ -102,7 +102,7 @@ typedef struct {
     double tol;             /* preconditioned relative residual target (default 1e-8):
                                ||P^-1 (b - A u)|| <= tol ||P^-1 b|| */
     int32_t max_iter;       /* GMRES iterations per solve (default 200) */
-    int32_t restart;        /* GMRES restart length (default 60, at most 250) */
+    int32_t restart;        /* GMRES restart length (default 60; 1..250, 1 acts as 2) */
     int32_t max_refine;     /* FS_MIXED, free space, relax = 1: at most this many float-float
                                true residuals per step (default 6; normally one is used) */
     double inner_tol;       /* FS_MIXED: relative tolerance of the FP32-far-field GMRES
@@ -110,8 +110,12 @@ typedef struct {
                                solves of the flexible GMRES) (default 1e-6) */
     double delta_over_L;    /* regularisation delta of K_delta as a fraction of L (default 0.01) */
     int32_t lsb;            /* 1 = local slender-body theory: drop K_delta (default 0) */
-    int32_t use_graph;      /* reserved: capture the inner iteration in a CUDA graph */
-    int32_t tile_override;  /* 0 = autotuned far-field launch shape, else a shape id */
+    int32_t use_graph;      /* reserved, must be 0: CUDA graph capture is not implemented */
+    int32_t tile_override;  /* direct-sum launch shape: 0 = the shape measured fastest on
+                               GB300 for each precision (targets per thread: FP32 8,
+                               float-float 4, FP64 2; grid from the occupancy
+                               calculator); 1, 2, 3 = 2, 4, 8 targets per thread in FP32
+                               and 1, 2, 4 in float-float and FP64 (default 0) */
     int32_t profile;        /* 1 = bracket every direct-sum kernel with CUDA events on the
                                context's stream (read with fs_kernel_stats) (default 0) */
     int32_t relax;          /* FS_MIXED: 1 = evaluate the far fields in float-float only
@@ -175,7 +179,12 @@ fs_status fs_options_default(fs_options *opt);
  * Chebyshev points each (host array, copied), viscosity mu, slenderness eps,
  * bending modulus E and time step dt (Sec. 2.3-2.4, 3.2).  n_fibers = 0 gives a
  * context usable only for the direct-sum entry points.  cuda_stream is a
- * cudaStream_t or NULL.  Allocates the context's device memory. */
+ * cudaStream_t or NULL.  Allocates the context's device memory.  opt NULL =
+ * the defaults; FS_EINVAL (before any CUDA call) when a size or parameter is
+ * out of range or a field of opt is outside its documented values (prec not
+ * FS_FP64/FS_MIXED, tol or inner_tol outside (0, 1), max_iter or max_refine
+ * < 1, restart outside 1..250, delta_over_L negative, lsb/relax/profile not
+ * 0 or 1, use_graph not 0, tile_override outside 0..3, bad tree options). */
 fs_status fs_create(fs_ctx **out, int32_t n_fibers, const int32_t *points_per_fiber,
                     double mu, double eps, double E, double dt,
                     const fs_boundary *boundary, const fs_options *opt, void *cuda_stream);

@@ -45,6 +45,54 @@ void Scratch::release()
     bytes = 0;
 }
 
+fs_status check_options(const fs_options &o, const char *who, int n_systems)
+{
+    // the step dispatches on prec: any other value would reach the flexible
+    // GMRES without its outer Krylov arrays (allocated for FS_MIXED only)
+    if (o.prec != FS_FP64 && o.prec != FS_MIXED) {
+        set_error("%s: prec must be FS_FP64 or FS_MIXED (got %d)", who, o.prec);
+        return FS_EINVAL;
+    }
+    if (!(o.tol > 0.0 && o.tol < 1.0) || !(o.inner_tol > 0.0 && o.inner_tol < 1.0)) {
+        set_error("%s: tol and inner_tol must lie in (0, 1)", who);
+        return FS_EINVAL;
+    }
+    if (o.max_iter < 1 || o.restart < 1 || o.restart > 250 || o.max_refine < 1) {
+        set_error("%s: need max_iter >= 1, 1 <= restart <= 250, max_refine >= 1", who);
+        return FS_EINVAL;
+    }
+    if (!(o.delta_over_L >= 0.0) || !std::isfinite(o.delta_over_L)) {
+        set_error("%s: delta_over_L must be finite and >= 0", who);
+        return FS_EINVAL;
+    }
+    if ((o.lsb | o.relax | o.profile) & ~1) {
+        set_error("%s: lsb, relax and profile are 0 or 1", who);
+        return FS_EINVAL;
+    }
+    if (o.use_graph != 0) {
+        set_error("%s: use_graph is reserved and must be 0", who);
+        return FS_EINVAL;
+    }
+    if (o.tile_override < 0 || o.tile_override > 3) {
+        set_error("%s: tile_override must be 0 (measured default) or a shape id 1..3", who);
+        return FS_EINVAL;
+    }
+    const int t = o.tree_order;
+    if (t != 0 && t != 4 && t != 6 && t != 8 && t != 10) {
+        set_error("%s: tree_order must be 0, 4, 6, 8 or 10 (got %d)", who, t);
+        return FS_EINVAL;
+    }
+    if (t && !(o.tree_theta > 0.0 && o.tree_theta < 1.0)) {
+        set_error("%s: tree_theta must lie in (0, 1)", who);
+        return FS_EINVAL;
+    }
+    if (t && n_systems > 1) {
+        set_error("%s: the treecode far field serves single-system contexts", who);
+        return FS_EINVAL;
+    }
+    return FS_OK;
+}
+
 }  // namespace fs
 
 using namespace fs;
@@ -144,21 +192,7 @@ static fs_status create_impl(fs_ctx **out, int32_t n_systems, const int32_t *fps
                 return FS_EINVAL;
             }
         }
-    if (opt) {
-        const int t = opt->tree_order;
-        if (t != 0 && t != 4 && t != 6 && t != 8 && t != 10) {
-            set_error("fs_create: tree_order must be 0, 4, 6, 8 or 10 (got %d)", t);
-            return FS_EINVAL;
-        }
-        if (t && !(opt->tree_theta > 0.0 && opt->tree_theta < 1.0)) {
-            set_error("fs_create: tree_theta must lie in (0, 1)");
-            return FS_EINVAL;
-        }
-        if (t && n_systems > 1) {
-            set_error("fs_create_batch: the treecode far field serves single-system contexts");
-            return FS_EINVAL;
-        }
-    }
+    if (opt) FS_TRY(check_options(*opt, n_systems > 1 ? "fs_create_batch" : "fs_create", n_systems));
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
         cudaGetLastError();

@@ -193,6 +193,9 @@ fs_status context_init(fs_ctx *c, int S, const int32_t *fibers_per_system, int M
                        const fs_boundary *b, const fs_body *body = nullptr, const int32_t *minus_end = nullptr);
 void context_free(fs_ctx *c);
 size_t estimate_bytes(int M, const int32_t *ppf, int n_surf, const fs_options &opt);
+// FS_EINVAL (with the message prefixed by `who`) unless every field of the
+// options is in its documented range
+fs_status check_options(const fs_options &o, const char *who, int n_systems);
 
 // fiber.cu
 fs_status launch_geometry(fs_ctx *c);

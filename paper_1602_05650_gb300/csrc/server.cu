@@ -159,6 +159,10 @@ fs_status fs_submit(fs_server *sv, const fs_request *rq, uint64_t *ticket)
         set_error("fs_submit: bad request");
         return FS_EINVAL;
     }
+    if (!(rq->mu > 0.0) || !(rq->eps > 0.0 && rq->eps < 1.0) || !(rq->E >= 0.0) || !(rq->dt > 0.0)) {
+        set_error("fs_submit: need mu > 0, 0 < eps < 1, E >= 0, dt > 0");
+        return FS_EINVAL;
+    }
     Req *r = new Req();
     r->ppf.assign(rq->points_per_fiber, rq->points_per_fiber + rq->n_fibers);
     int64_t ntot = 0;
@@ -194,6 +198,10 @@ fs_status fs_submit(fs_server *sv, const fs_request *rq, uint64_t *ticket)
     fs_options_default(&r->opt);
     r->opt.prec = rq->prec;
     r->opt.tol = rq->tol > 0.0 ? rq->tol : r->opt.tol;
+    if (check_options(r->opt, "fs_submit", 1) != FS_OK) {
+        delete r;
+        return FS_EINVAL;
+    }
     r->out_X = rq->out_X;
     r->out_V = rq->out_V;
     r->out_T = rq->out_T;

@@ -95,6 +95,37 @@ def test_treecode_options_are_validated_without_gpu(lib):
         assert b"tree" in lib.fs_last_error()
 
 
+def test_step_options_are_validated_without_gpu(lib):
+    """Every option outside its documented values is refused by fs_create
+    before any CUDA call (an unknown precision would otherwise reach the
+    flexible GMRES, whose outer Krylov space only FS_MIXED allocates)."""
+    out = ctypes.c_void_p()
+    ppf = (ctypes.c_int32 * 1)(16)
+    bad = [("prec", 2), ("prec", -1), ("tol", 0.0), ("tol", 1.0), ("tol", float("nan")),
+           ("inner_tol", 0.0), ("max_iter", 0), ("restart", 0), ("restart", 251),
+           ("max_refine", 0), ("delta_over_L", -0.01), ("delta_over_L", float("inf")),
+           ("lsb", 2), ("relax", -1), ("profile", 3), ("use_graph", 1),
+           ("tile_override", 4), ("tile_override", -1)]
+    for field, value in bad:
+        o = _native.fs_options()
+        lib.fs_options_default(ctypes.byref(o))
+        setattr(o, field, value)
+        assert lib.fs_create(ctypes.byref(out), 1, ppf, 1.0, 1e-3, 1.0, 1e-3, None, ctypes.byref(o),
+                             None) == _native.FS_EINVAL, (field, value)
+        assert not out.value
+        msg = lib.fs_last_error()
+        assert msg.startswith(b"fs_create:") and field.split("_")[0].encode() in msg, (field, msg)
+    # the same checks guard the batch constructor
+    o = _native.fs_options()
+    lib.fs_options_default(ctypes.byref(o))
+    o.prec = 5
+    fps = (ctypes.c_int32 * 2)(1, 1)
+    pp = (ctypes.c_int32 * 2)(16, 16)
+    assert lib.fs_create_batch(ctypes.byref(out), 2, fps, pp, 1.0, 1e-3, 1.0, 1e-3, ctypes.byref(o),
+                               None) == _native.FS_EINVAL
+    assert lib.fs_last_error().startswith(b"fs_create_batch: prec")
+
+
 def _header_structs():
     """name -> [(field, C type, array length)] for every typedef struct of
     the header, in declaration order."""

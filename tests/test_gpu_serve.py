@@ -89,6 +89,23 @@ def test_budget_admits_one_at_a_time_and_rejects_oversize():
         assert np.array_equal(done[t]["V"], V)
 
 
+def test_bad_request_is_refused_at_submit():
+    """Options and physical parameters are checked when the request is
+    queued, so a bad request never takes a slot."""
+    s = wl.free_space(2, 16, 3.0, seed=6)
+    sv = fs.fs_server_create(1 << 30, max_slots=1)
+    try:
+        for kw in ({"prec": 7}, {"tol": 2.0}):
+            with pytest.raises(fs.FsError) as e:
+                fs.fs_submit(sv, s.n_per_fiber, s.X, s.L, s.mu, s.eps, s.E, s.dt, f_ext=s.f_ext, **kw)
+            assert e.value.status == 1             # FS_EINVAL
+        with pytest.raises(fs.FsError) as e:
+            fs.fs_submit(sv, s.n_per_fiber, s.X, s.L, -1.0, s.eps, s.E, s.dt)
+        assert "mu > 0" in str(e.value)
+    finally:
+        fs.fs_server_destroy(sv)
+
+
 def test_poll_before_done_and_failed_request():
     s_big = wl.free_space(256, 32, 14.0, seed=5)
     s_bad = wl.free_space(2, 16, 3.0, seed=6)
