@@ -380,7 +380,9 @@ fs_status fs_get_lengths(fs_ctx *ctx, double *lengths, int32_t ptr_is_device);
  * u < 1 - exp(-f_cat dt), a shrinking one to growing if u < 1 - exp(-f_res
  * dt); a shrinking fiber that would pass below L_min grows instead, a growing
  * one that would pass L_max (if L_max > 0) shrinks; then Ldot[i] = v_grow or
- * -v_shrink (pass Ldot to fs_set_growth).  state is updated in place. */
+ * -v_shrink (pass Ldot to fs_set_growth).  state is updated in place.
+ * FS_EINVAL: NULL arrays, dt not finite and > 0, a speed or rate negative or
+ * not finite, L_min or L_max not finite. */
 typedef struct {
     double v_grow, v_shrink;   /* plus-end speeds (length / time) */
     double f_cat, f_res;       /* catastrophe and rescue rates (1 / time) */

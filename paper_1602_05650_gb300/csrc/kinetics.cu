@@ -12,9 +12,19 @@ extern "C" {
 fs_status fs_dynamic_instability(int32_t n, const fs_kinetics *k, double dt, const double *L, const double *u,
                                  int32_t *state, double *Ldot)
 {
-    if (n < 0 || !k || (n > 0 && (!L || !u || !state || !Ldot)) || !(dt > 0.0) || k->v_grow < 0.0 ||
-        k->v_shrink < 0.0 || k->f_cat < 0.0 || k->f_res < 0.0) {
-        set_error("fs_dynamic_instability: bad arguments");
+    if (n < 0 || !k || (n > 0 && (!L || !u || !state || !Ldot)) || !(dt > 0.0) || !std::isfinite(dt)) {
+        set_error("fs_dynamic_instability: bad sizes, NULL arrays or dt not in (0, inf)");
+        return FS_EINVAL;
+    }
+    // written so that NaN fails: speeds and rates finite and >= 0, lengths finite
+    const double rates[4] = {k->v_grow, k->v_shrink, k->f_cat, k->f_res};
+    for (double r : rates)
+        if (!(r >= 0.0) || !std::isfinite(r)) {
+            set_error("fs_dynamic_instability: speeds and rates must be finite and >= 0");
+            return FS_EINVAL;
+        }
+    if (!std::isfinite(k->L_min) || !std::isfinite(k->L_max)) {
+        set_error("fs_dynamic_instability: L_min and L_max must be finite");
         return FS_EINVAL;
     }
     const double p_cat = -std::expm1(-k->f_cat * dt);

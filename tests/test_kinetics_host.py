@@ -39,3 +39,11 @@ def test_rejects_bad_arguments(fs):
         fs.fs_dynamic_instability([1], [1.0], [0.5], -1.0, 1.0, 1.0, 1.0, 1.0, 0.1)
     with pytest.raises(fs.FsError):
         fs.fs_dynamic_instability([1], [1.0], [0.5], 0.1, -1.0, 1.0, 1.0, 1.0, 0.1)
+    nan, inf = float("nan"), float("inf")
+    for dt, vg, vs, fc, fr, lmin, lmax in ((0.1, nan, 1.0, 1.0, 1.0, 0.1, 0.0),
+                                           (0.1, 1.0, 1.0, nan, 1.0, 0.1, 0.0),
+                                           (0.1, 1.0, inf, 1.0, 1.0, 0.1, 0.0),
+                                           (nan, 1.0, 1.0, 1.0, 1.0, 0.1, 0.0),
+                                           (0.1, 1.0, 1.0, 1.0, 1.0, nan, 0.0)):
+        with pytest.raises(fs.FsError):
+            fs.fs_dynamic_instability([1], [1.0], [0.5], dt, vg, vs, fc, fr, lmin, lmax)
