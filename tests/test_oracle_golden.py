@@ -1,5 +1,9 @@
-"""Oracle against values the paper prints for a worked example (fixtures in
+"""Oracle and input recipes against values the paper prints (fixtures in
 tests/golden/, each citing its source).
+
+sedimenting_cloud.txt and table2_aster.txt (Sec. 4.3, Table 2): the
+synthetic workloads that stand in for the paper's cloud and confined aster
+have the sizes, parameters and layout the paper prints.
 
 kdelta_regularisation.txt (Sec. 3.5, regularisation of K_delta): a sphere
 with 32 hinged fibers of length 5r in free space, pulled by a force.  The
@@ -74,3 +78,45 @@ def test_kdelta_regularisation_matches_the_printed_values():
     assert order / 10 <= step1 <= order * 10
     # and the change shrinks as delta decreases
     assert step2 < step1
+
+
+def test_sedimenting_cloud_follows_the_printed_setup():
+    """The synthetic cloud (workloads.sedimenting_cloud) has the sizes,
+    parameters and layout Sec. 4.3 prints, and its four lengths give the
+    quoted effective volume fractions (to their rounding, 5 %)."""
+    g = read_golden("sedimenting_cloud.txt")
+    R0 = g["R0"]
+    for i in range(1, 5):
+        L = g["L_%d" % i]
+        s = wl.sedimenting_cloud(L, R0=R0)
+        assert s.n_fibers == int(g["n_fibers"])
+        assert s.eps == g["eps"] and s.E == pytest.approx(g["E_over_f0_R0_cubed"] * R0 ** 3)
+        assert np.all(s.L == L * R0)
+        phi = s.n_fibers * (L * R0 / 2) ** 3 / (4.0 / 3.0 * np.pi * R0 ** 3)
+        assert phi == pytest.approx(g["phi_%d" % i], rel=0.05)
+        X = s.X.reshape(s.n_fibers, -1, 3)
+        assert np.linalg.norm(X.mean(axis=1), axis=1).max() <= R0      # centres in the ball
+        assert np.all(s.f_ext[:, :2] == 0.0) and np.all(s.f_ext[:, 2] < 0.0)   # downward load
+
+
+def test_table2_aster_follows_the_printed_setup():
+    """workloads.table2_aster is the Table 2 configuration, and its time step
+    is below the paper's largest stable step for every fiber count."""
+    g = read_golden("table2_aster.txt")
+    from oracle.fiber import CLAMPED
+    r = g["r"]
+    for i in range(1, 5):
+        n = int(g["n_fibers_%d" % i])
+        s = wl.table2_aster(n, grid=(4, 8))
+        L = g["L_over_r"] * r
+        assert s.n_fibers == n and np.all(s.n_per_fiber == int(g["points_per_fiber"]))
+        assert np.all(s.L == L) and np.all(s.attach == CLAMPED)
+        assert s.body.radius == r and s.boundary.R == pytest.approx(g["R_outer_over_r"] * r)
+        assert np.linalg.norm(s.body.force) == pytest.approx(g["force_over_E_per_L2"] * s.E / L ** 2)
+        assert not np.any(s.f_ext)                                      # load on the sphere only
+        # minus ends on the sphere, fibers pointing outwards to radius r + L
+        X = s.X.reshape(n, -1, 3)
+        assert np.allclose(np.linalg.norm(X[:, -1], axis=1), r)
+        assert np.allclose(np.linalg.norm(X[:, 0], axis=1), r + L)
+        tau_e = 8.0 * np.pi * s.mu * L ** 4 / (-np.log(s.eps ** 2 * np.e))
+        assert s.dt <= 1e-3 * g["dt_max_%d" % i] * tau_e
