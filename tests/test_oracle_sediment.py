@@ -9,8 +9,6 @@ value comes from the implementation; the random sample makes the agreement
 statistical (~1 %), gate 3 %."""
 import math
 
-import numpy as np
-
 import workloads as wl
 from oracle import kernels as ok
 from oracle import system
