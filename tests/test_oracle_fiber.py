@@ -195,3 +195,60 @@ def test_confined_no_slip_on_wall():
     # at the quadrature nodes themselves the discrete equation holds exactly
     us = kernels.surface_self(b.nodes, b.normals, b.weights, r.q)[::97]
     assert np.allclose(us + uf_w, 0.0, atol=1e-7 * np.abs(uf_w).max())
+
+
+def _compatible_curve(alpha, L, k0, frame, centre):
+    """Planar centreline with curvature k0 sin^4(pi s / L): zero, with its
+    first derivatives, at both ends, so it meets the free-end conditions
+    X_ss = X_sss = 0 (Eq. bc-free).  Arclength-parametrised by integrating the
+    tangent angle with Gauss-Legendre quadrature."""
+    gx, gw = np.polynomial.legendre.leggauss(80)
+    kappa = lambda u: k0 * np.sin(np.pi * u / L) ** 4
+
+    def theta(u):
+        return 0.5 * u * np.sum(gw * kappa(0.5 * u * (gx + 1.0)))
+
+    pts = []
+    for s in (alpha + 1.0) * L / 2.0:
+        th = np.array([theta(x) for x in 0.5 * s * (gx + 1.0)])
+        pts.append([0.5 * s * np.sum(gw * np.cos(th)), 0.5 * s * np.sum(gw * np.sin(th)), 0.0])
+    return np.asarray(centre) + np.array(pts) @ frame
+
+
+def test_spectral_convergence_in_N():
+    """Two interacting curved fibers whose initial shape meets the free-end
+    conditions, under a uniform load, local slender-body theory: the step's
+    velocity and tension, interpolated to common points, converge
+    geometrically in N (measured against N = 48: V 4e-4, 6e-7, 1e-9 and T
+    2e-2, 1e-4, 6e-7 at N = 16, 24, 32).  A curve with curvature at a free
+    end breaks those conditions: its tension then carries a mode that grows
+    like N^2 and V converges only algebraically, so the input must be
+    compatible.  With K_delta the node quadrature resolves the kernel's
+    width delta = 0.01 L only near N ~ 160, and V converges algebraically
+    (1e-3, 4e-4, 1.5e-4)."""
+    from numpy.polynomial import chebyshev as C
+    L = 2.0
+    frames = [np.eye(3), np.array([[0, 0, 1], [1, 0, 0], [0, 1, 0]], float)]
+    centres = [np.zeros(3), np.array([0.5, 1.2, -0.6])]
+    probe = np.linspace(-1.0, 1.0, 11)
+
+    def run(N):
+        a = cheb.nodes(N)
+        X = np.concatenate([_compatible_curve(a, L, 0.8, fr, c) for fr, c in zip(frames, centres)])
+        f = np.tile([0.3, -0.2, -1.0], (X.shape[0], 1))
+        r = system.System(X, np.full(2, L), np.full(2, N, np.int32), f, 1.0, 1e-3, 1.0, 1e-2, 0.01,
+                          True).step(tol=1e-14)
+        V, T = r.V.reshape(2, N, 3), r.T.reshape(2, N)
+        Vi = np.concatenate([np.stack([C.chebval(probe, C.chebfit(a, V[m, :, k], N - 1)) for k in range(3)], -1)
+                             for m in range(2)])
+        Ti = np.concatenate([C.chebval(probe, C.chebfit(a, T[m], N - 1)) for m in range(2)])
+        return Vi, Ti
+
+    Vr, Tr = run(48)
+    eV, eT = [], []
+    for N in (16, 24, 32):
+        V, T = run(N)
+        eV.append(np.linalg.norm(V - Vr) / np.linalg.norm(Vr))
+        eT.append(np.linalg.norm(T - Tr) / np.linalg.norm(Tr))
+    assert eV[1] < eV[0] / 100 and eV[2] < eV[1] / 100 and eV[2] < 1e-8, eV
+    assert eT[1] < eT[0] / 30 and eT[2] < eT[1] / 30 and eT[2] < 1e-5, eT
