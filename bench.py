@@ -40,6 +40,22 @@ KS_NAMES = ["stokeslet_fp32", "stokeslet_fp64", "stresslet_fp32", "stresslet_fp6
 WORKLOAD = "cloud-1024x64: 1,024 curved fibers x 64 Chebyshev points (65,536 points), [0,40]^3"
 
 
+# the library's default inner tolerance of the mixed solve (fs_options_default);
+# both arms name it in their config
+DEFAULT_INNER_TOL = 1e-6
+
+
+def workload_config(s, ws: int, inner_tol: float, relax: int) -> dict:
+    """The headline workload as both arms report it: the cloud, its physical
+    parameters, the solve's tolerances and how it is run."""
+    return {"workload": WORKLOAD, "fibers": s.n_fibers, "points_per_fiber": 64,
+            "precision": "mixed", "tol": 1e-8, "inner_tol": inner_tol, "relax": relax,
+            "eps": s.eps, "mu": s.mu, "E": s.E, "dt": s.dt,
+            "state": "every step from the initial cloud (device-to-device reset timed)",
+            "l2": "inputs larger than L2 (per-step fiber blocks 537 MB, Krylov basis 128 MB)",
+            "parallelism": "replicas" if ws > 1 else "1 GPU"}
+
+
 def job_time(x: float, dist, device) -> float:
     """A per-rank time as the job's: the maximum over ranks (the job ends
     with its slowest rank); unchanged on one process."""
@@ -178,7 +194,8 @@ def run_reference(args, ws, rank):
             "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "fibers": s.n_fibers, "points_per_fiber": 64},
+            "config": workload_config(s, ws, args.inner_tol if args.inner_tol > 0 else DEFAULT_INNER_TOL,
+                                      0 if args.no_relax else 1),
             "cpu_baseline": {"kind": "oracle", "cores": base["cores"], "sample": base["sample"],
                              "value": 1.0 / t, "unit": "steps/s"},
             "e2e": {"value": 1.0 / t, "unit": "steps/s", "h2d_bytes_per_step": 0,
@@ -759,11 +776,7 @@ def main():
         "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 far field + f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "fibers": s.n_fibers, "points_per_fiber": 64,
-                   "precision": "mixed", "tol": 1e-8, "inner_tol": opt.inner_tol, "relax": opt.relax, "eps": s.eps, "mu": s.mu, "E": s.E, "dt": s.dt,
-                   "state": "every step from the initial cloud (device-to-device reset timed)",
-                   "l2": "inputs larger than L2 (per-step fiber blocks 537 MB, Krylov basis 128 MB)",
-                   "parallelism": "replicas" if ws > 1 else "1 GPU"},
+        "config": workload_config(s, ws, opt.inner_tol, opt.relax),
         "roofline": roofline,
         "cpu_baseline": ({"value": cpu["value"], "unit": "steps/s", "cores": cpu["cores"],
                           "kind": "oracle", "sample": cpu["sample"]} if cpu else None),
