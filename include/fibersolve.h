@@ -227,6 +227,9 @@ fs_status fs_create_batch(fs_ctx **out, int32_t n_systems, const int32_t *fibers
 fs_status fs_batch_info(const fs_ctx *ctx, int32_t *iters, int32_t *outer, double *resid,
                         int32_t *converged);
 
+/* Synchronise the context's stream, then free everything the context holds
+ * (device arrays, scratch, pinned host buffers).  NULL is a no-op; the caller's
+ * stream itself is not destroyed. */
 void fs_destroy(fs_ctx *ctx);
 
 /* Set the fiber state: node positions X [N_tot][3] (fiber-major, node k of
@@ -463,7 +466,10 @@ void fs_server_destroy(fs_server *sv);
 /* Number of points N_tot and unknowns of the context. */
 fs_status fs_sizes(const fs_ctx *ctx, int64_t *n_points, int64_t *n_unknowns);
 
+/* Message of the last failed call on this thread (thread-local, static storage;
+ * empty if none failed). */
 const char *fs_last_error(void);
+/* Name of a status code ("FS_OK", "FS_EINVAL", ...; "FS_UNKNOWN" otherwise). */
 const char *fs_status_str(int32_t status);
 
 #ifdef __cplusplus
