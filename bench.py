@@ -373,9 +373,11 @@ def run_workload(args, ws, rank, local, fs, torch):
         # dynamic instability with the rates of the paper's parameter table
         # (V_g 0.12, V_s 0.288 um/s, f_cat = f_res = 0.014 / s), rescue at
         # 2 um, dt = 0.1 s
-        s = wl.free_space(1024, 32, 60.0, seed=rank, L_range=(5.0, 10.0), E=10.0, dt=0.1, min_gap=0.1)
+        mt = wl.MICROTUBULE
+        s = wl.free_space(1024, 32, 60.0, seed=rank, L_range=(5.0, 10.0), mu=mt["mu"], E=mt["E"], dt=0.1,
+                          min_gap=0.1)
         s.f_ext = np.tile([0.0, 0.0, -0.05], (s.n_points, 1))
-        kin_args = (s.dt, 0.12, 0.288, 0.014, 0.014, 2.0)
+        kin_args = (s.dt, mt["v_grow"], mt["v_shrink"], mt["f_cat"], mt["f_res"], 2.0)
         opt = fs.fs_options_default()
         opt.prec = fs.FS_MIXED
         opt.tol = 1e-8

@@ -5,6 +5,10 @@ sedimenting_cloud.txt and table2_aster.txt (Sec. 4.3, Table 2): the
 synthetic workloads that stand in for the paper's cloud and confined aster
 have the sizes, parameters and layout the paper prints.
 
+microtubule_parameters.txt (Sec. 4, table of simulation parameters): the
+dynamic-instability rates, bending modulus and viscosity of the kinetics
+workload.
+
 kdelta_regularisation.txt (Sec. 3.5, regularisation of K_delta): a sphere
 with 32 hinged fibers of length 5r in free space, pulled by a force.  The
 paper reports three things:
@@ -120,3 +124,8 @@ def test_table2_aster_follows_the_printed_setup():
         assert np.allclose(np.linalg.norm(X[:, 0], axis=1), r + L)
         tau_e = 8.0 * np.pi * s.mu * L ** 4 / (-np.log(s.eps ** 2 * np.e))
         assert s.dt <= 1e-3 * g["dt_max_%d" % i] * tau_e
+
+
+def test_microtubule_parameters_are_the_printed_table():
+    g = read_golden("microtubule_parameters.txt")
+    assert wl.MICROTUBULE == g

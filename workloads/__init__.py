@@ -3,9 +3,9 @@
 This module is shared by the CPU oracle, the tests and the benchmark.  It
 holds no arithmetic of the numerical method (no Chebyshev transforms, no
 quadrature rules of the method, no kernels): it only places fibers in space,
-draws external forces and lays out the spherical boundary's quadrature nodes,
-which the paper treats as precomputed inputs (Sec. 3.1.1, Eq. patch-gl-quad:
-"Jacobian and normal ... are inputs").
+draws external forces and lays out the spherical boundary's quadrature nodes.
+The paper computes the surface's Jacobian and normals in a preprocessing step
+outside the solver (Sec. 3.1.1, Eq. patch-gl-quad), so they are inputs here too.
 
 Every generator takes a seed and returns plain numpy float64/int32 arrays.
 
@@ -58,6 +58,12 @@ class RigidBody:
 
 # minus-end conditions of a fiber (codes shared with the library's interface)
 FREE, CLAMPED, HINGED = 0, 1, 2
+
+# Microtubule parameters of the paper's simulation table (Sec. 4, taken there
+# from Kimura and Onami 2005), in um, s and pN: plus-end growth and shrinkage
+# speeds (um/s), catastrophe and rescue rates (1/s), bending modulus
+# (pN um^2) and cytoplasm viscosity (pN s / um^2 = Pa s).
+MICROTUBULE = {"v_grow": 0.12, "v_shrink": 0.288, "f_cat": 0.014, "f_res": 0.014, "E": 10.0, "mu": 1.0}
 
 
 @dataclasses.dataclass
