@@ -460,7 +460,9 @@ fs_status fs_server_stats(fs_server *sv, int32_t *pending, int32_t *running, siz
                           int64_t *completed);
 
 /* Finish the running requests, drop the queued ones (their tickets become
- * invalid) and join the workers. */
+ * invalid) and join the workers.  Running requests still write their output
+ * arrays before this returns.  No other call on sv may be in progress or
+ * follow it (a thread blocked in fs_server_wait on sv must return first). */
 void fs_server_destroy(fs_server *sv);
 
 /* Number of points N_tot and unknowns of the context. */
