@@ -125,7 +125,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_baseline(s, gpu_fp64_iters: int, budget_fibers: int = 256, budget_targets: int = 32768):
+def oracle_baseline(s, gpu_fp64_iters: int, budget_fibers: int = 512, budget_targets: int = 32768):
     """Time the CPU oracle on a bounded sample of the workload and scale to one
     step: per-fiber setup (geometry, self block, LU) for `budget_fibers` fibers
     scaled to all fibers, plus (1 + iters) far-field sums, each timed on
@@ -185,7 +185,7 @@ def run_reference(args, ws, rank):
     vals = []
     base = None
     for k in range(args.warmup + args.steps):
-        base = oracle_baseline(s, gpu_fp64_iters=args.ref_iters, budget_fibers=32, budget_targets=2048)
+        base = oracle_baseline(s, gpu_fp64_iters=args.ref_iters, budget_fibers=128, budget_targets=8192)
         if k >= args.warmup:
             vals.append(base["seconds_per_step_extrapolated"])
     t = float(np.mean(vals))
