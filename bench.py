@@ -272,6 +272,10 @@ def run_workload(args, ws, rank, local, fs, torch):
               with the paper's rates), advanced --steps steps;
     tree-step one implicit step of 1,048,576 points (32,768 fibers x 32) with
               the treecode far field and with the direct one;
+    tree-case one treecode sum of 262,144 points (4,096 fibers x 64 in
+              [0,50]^3, own-fiber exclusion) at --tree-order / --tree-theta,
+              timed after one untimed call: the small case for profiling the
+              treecode's kernels;
     aster     the confined aster of Table 2 (32, 128, 512 and 2,048 fibers x
               31 points clamped to a sphere inside a sphere six radii out,
               force on the sphere, GMRES 1e-5): steps/s and GMRES iterations
@@ -439,6 +443,25 @@ def run_workload(args, ws, rank, local, fs, torch):
         out.update({"points": int(s.n_points), "fibers": s.n_fibers, "points_per_fiber": 32, "tol": 1e-5,
                     "result": res, "velocity_rel_difference_tree_vs_direct": dv,
                     "speedup_tree_vs_direct": res["direct"]["ms_per_step"] / res["tree_p8_theta0.5"]["ms_per_step"]})
+    elif args.workload == "tree-case":
+        s = wl.free_space(4096, 64, 50.0, seed=rank)
+        h = fs.fs_create([], s.mu, s.eps, s.E, s.dt, stream=stream)
+        X = torch.tensor(s.X, device=dev)
+        Wf = torch.tensor(s.f_ext * 0.01, device=dev)
+        fid = torch.tensor(s.fiber_id(), dtype=torch.int32, device=dev)
+        ut = torch.empty_like(X)
+        order, theta = args.tree_order, args.tree_theta
+        fs.fs_stokeslet_apply_tree(h, X, Wf, X, ut, fid, fid, order=order, theta=theta)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fs.fs_stokeslet_apply_tree(h, X, Wf, X, ut, fid, fid, order=order, theta=theta)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fs.fs_destroy(h)
+        out.update({"points": int(s.n_points), "order": order, "theta": theta,
+                    "ms_per_call": e0.elapsed_time(e1)})
     elif args.workload == "aster":
         res = {}
         for nf in (32, 128, 512, 2048):
@@ -622,9 +645,11 @@ def main():
                     help="far-field launch shape id (0 = default; 1..3 = targets per thread FP32 2/4/8, "
                          "float-float 1/2/4)")
     ap.add_argument("--workload", choices=["confined", "batched", "large", "sediment", "kinetics", "aster",
-                                           "tree-step"],
+                                           "tree-step", "tree-case"],
                     default=None,
                     help="a secondary workload instead of the headline step benchmark")
+    ap.add_argument("--tree-order", type=int, default=8, help="--workload tree-case: expansion order")
+    ap.add_argument("--tree-theta", type=float, default=0.4, help="--workload tree-case: opening angle")
     ap.add_argument("--serve", type=int, default=0,
                     help="serving mode: number of independent requests (0 = the step benchmark)")
     ap.add_argument("--rate", type=float, default=0.0, help="--serve: Poisson arrival rate per s (0 = burst)")
