@@ -175,3 +175,15 @@ def test_binding_struct_layouts_match_the_header():
                 assert ctypes.sizeof(pytype) == sizes[base] * n, (name, fname)
         checked += 1
     assert checked >= 7 and "fs_request" in structs
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the built library every call raises ImportError: there is no
+    CPU fallback behind the binding."""
+    import paper_1602_05650_gb300 as fs
+    monkeypatch.setattr(_native, "_lib", None)
+    monkeypatch.setattr(_native, "LIB_PATH", str(tmp_path / "libfibersolve.so"))
+    with pytest.raises(ImportError, match="no CPU fallback"):
+        fs.fs_options_default()
+    with pytest.raises(ImportError):
+        fs.fs_estimate_bytes([16, 16])
