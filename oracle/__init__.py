@@ -1,7 +1,7 @@
 """CPU oracle of the implicit fiber step -- TEST INFRASTRUCTURE ONLY.
 
-Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
-leg may import this package.  The library (``paper_1602_05650_gb300``) never
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU legs (its
+``cpu_baseline`` and its ``--impl reference`` arm) may import this package.  The library (``paper_1602_05650_gb300``) never
 imports, links or runs it, and the two share no code: the only shared module
 is ``workloads``, which generates seeded inputs and holds none of the
 method's arithmetic.
@@ -15,11 +15,17 @@ Modules and the passages they follow:
   pairsum.c   Eqs. oseen, stresslet, single-layer, double-layer,
               main-cortex-density with Sec. 3.1.2 singularity subtraction
   fiber.py    Eqs. main-sb-local, sb-stokes-reg, force-balance,
-              main-elastic-force, main-inextensibility, bc-free; Sec. 3.2
-  system.py   Eqs. complementary-uc/uf, sche-linear-eq, prec; Sec. 3.3 GMRES
+              main-elastic-force, main-inextensibility, bc-free; Sec. 3.2;
+              attached minus ends (Eqs. BC2-1, BC2-2, BC2-T) and growth
+              (Sec. 2.4)
+  system.py   Eqs. complementary-uc/uf, sche-linear-eq, prec; Sec. 3.3 GMRES;
+              the rigid body (Eqs. main-nsb-second-kind, main-nsb-rgbt,
+              main-nsb-rgbr, f-ext, t-ext)
+  kinetics.py Sec. 2.4 / Sec. 5 two-state dynamic instability
 
 Pinning (tests/test_oracle_*.py, all `-m "not gpu"`): every function above
-is pinned against closed forms, invariants or brute force; see the test
-docstrings for which pin covers which function.
+is pinned against closed forms, invariants, brute force, convergence in N
+or values the paper prints (tests/golden/); the test docstrings say which
+pin covers which function.
 """
 from . import cheb, kernels, fiber, system  # noqa: F401
