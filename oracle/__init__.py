@@ -1,10 +1,10 @@
 """CPU oracle of the implicit fiber step -- TEST INFRASTRUCTURE ONLY.
 
 Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU legs (its
-``cpu_baseline`` and its ``--impl reference`` arm) may import this package.  The library (``paper_1602_05650_gb300``) never
-imports, links or runs it, and the two share no code: the only shared module
-is ``workloads``, which generates seeded inputs and holds none of the
-method's arithmetic.
+``cpu_baseline`` and its ``--impl reference`` arm) may import this package.
+The library (``paper_1602_05650_gb300``) never imports, links or runs it, and
+the two share no code: the only shared module is ``workloads``, which
+generates seeded inputs and holds none of the method's arithmetic.
 
 Plain FP64 throughout: numpy / scipy for the Chebyshev algebra, dense
 per-fiber matrices, LU and GMRES; plain C double loops (pairsum.c) for the
