@@ -125,6 +125,30 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), with the
+    architecture."""
+    import platform
+    name = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                name = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not name:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    name = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return "%s (%s)" % (name or "unknown model", platform.machine())
+
+
 def oracle_baseline(s, gpu_fp64_iters: int, budget_fibers: int = 512, budget_targets: int = 32768):
     """Time the CPU oracle on a bounded sample of the workload and scale to one
     step: per-fiber setup (geometry, self block, LU) for `budget_fibers` fibers
@@ -153,8 +177,8 @@ def oracle_baseline(s, gpu_fp64_iters: int, budget_fibers: int = 512, budget_tar
                   budget_fibers, M, M / budget_fibers, budget_targets, s.n_points,
                   s.n_points / budget_targets, n_ff, gpu_fp64_iters,
                   t_setup * budget_fibers / M + t_ff * budget_targets / s.n_points))
-    return {"value": 1.0 / t_step, "unit": "steps/s", "cores": ok.threads(), "kind": "oracle",
-            "sample": sample, "seconds_per_step_extrapolated": t_step}
+    return {"value": 1.0 / t_step, "unit": "steps/s", "cores": ok.threads(), "cpu": cpu_model(),
+            "kind": "oracle", "sample": sample, "seconds_per_step_extrapolated": t_step}
 
 
 def traffic_for(kernel_class: str):
@@ -196,8 +220,8 @@ def run_reference(args, ws, rank):
             "impl": "reference",
             "config": workload_config(s, ws, args.inner_tol if args.inner_tol > 0 else DEFAULT_INNER_TOL,
                                       0 if args.no_relax else 1),
-            "cpu_baseline": {"kind": "oracle", "cores": base["cores"], "sample": base["sample"],
-                             "value": 1.0 / t, "unit": "steps/s"},
+            "cpu_baseline": {"kind": "oracle", "cores": base["cores"], "cpu": base["cpu"],
+                             "sample": base["sample"], "value": 1.0 / t, "unit": "steps/s"},
             "e2e": {"value": 1.0 / t, "unit": "steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -805,7 +829,7 @@ def main():
         "vs_baseline": None, "dtype": "f32 far field + f64", "data": "synthetic",
         "config": workload_config(s, ws, opt.inner_tol, opt.relax),
         "roofline": roofline,
-        "cpu_baseline": ({"value": cpu["value"], "unit": "steps/s", "cores": cpu["cores"],
+        "cpu_baseline": ({"value": cpu["value"], "unit": "steps/s", "cores": cpu["cores"], "cpu": cpu["cpu"],
                           "kind": "oracle", "sample": cpu["sample"]} if cpu else None),
         "e2e": {"value": job_rate(1.0, ws, e2e_s), "unit": "steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},

@@ -40,7 +40,7 @@ def test_reference_arm_prints_one_contract_line():
     # the same workload description as the native arm at its defaults
     assert d["config"] == bench.workload_config(wl.cfg_cloud_mixed(0), 1, bench.DEFAULT_INNER_TOL, 1)
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["cpu"]
     assert cb["value"] == d["value"] and cb["unit"] == d["unit"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
