@@ -59,6 +59,25 @@ def _dev_ptr(t, dtype_name: str, name: str):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _count(t) -> int:
+    return int(t.numel()) if hasattr(t, "numel") else int(np.asarray(t).size)
+
+
+def _need(t, count: int, name: str):
+    """The library reads or writes exactly `count` elements of t: refuse any
+    other size here (a short array would be overrun)."""
+    if t is not None and _count(t) != count:
+        raise ValueError("%s has %d elements, %d expected" % (name, _count(t), count))
+
+
+def _points(t, name: str) -> int:
+    """Number of points of an [n, 3] array."""
+    shape = tuple(t.shape)
+    if len(shape) != 2 or shape[1] != 3:
+        raise ValueError("%s must have shape [n, 3] (got %s)" % (name, shape))
+    return int(shape[0])
+
+
 def _host_ptr(a, dtype, name: str):
     if a is None:
         return None, None
@@ -69,10 +88,11 @@ def _host_ptr(a, dtype, name: str):
 class Handle:
     """Owns an fs_ctx*; destroyed by fs_destroy (or when collected)."""
 
-    def __init__(self, ptr: ctypes.c_void_p, n_points: int, n_unknowns: int):
+    def __init__(self, ptr: ctypes.c_void_p, n_points: int, n_unknowns: int, n_fibers: int):
         self.ptr = ptr
         self.n_points = n_points
         self.n_unknowns = n_unknowns
+        self.n_fibers = n_fibers
 
     def __del__(self):
         try:
@@ -111,7 +131,7 @@ def fs_create(points_per_fiber, mu: float, eps: float, E: float, dt: float, boun
                          ctypes.byref(options) if options is not None else None, st), "fs_create")
     npts, nunk = ctypes.c_int64(), ctypes.c_int64()
     _check(lib.fs_sizes(out, ctypes.byref(npts), ctypes.byref(nunk)), "fs_sizes")
-    return Handle(out, npts.value, nunk.value)
+    return Handle(out, npts.value, nunk.value, M)
 
 
 FS_END_FREE, FS_END_CLAMPED, FS_END_HINGED = 0, 1, 2
@@ -154,7 +174,7 @@ def fs_create_with_body(points_per_fiber, minus_end, mu: float, eps: float, E: f
            "fs_create_with_body")
     npts, nunk = ctypes.c_int64(), ctypes.c_int64()
     _check(lib.fs_sizes(out, ctypes.byref(npts), ctypes.byref(nunk)), "fs_sizes")
-    return Handle(out, npts.value, nunk.value)
+    return Handle(out, npts.value, nunk.value, M)
 
 
 def fs_get_body(h: Handle):
@@ -189,7 +209,7 @@ def fs_create_batch(fibers_per_system, points_per_fiber, mu: float, eps: float, 
                                st), "fs_create_batch")
     npts, nunk = ctypes.c_int64(), ctypes.c_int64()
     _check(lib.fs_sizes(out, ctypes.byref(npts), ctypes.byref(nunk)), "fs_sizes")
-    h = Handle(out, npts.value, nunk.value)
+    h = Handle(out, npts.value, nunk.value, int(ppf.shape[0]))
     h.n_systems = int(fps.shape[0])
     return h
 
@@ -219,6 +239,9 @@ def fs_sizes(h: Handle):
 def fs_set_state(h: Handle, X, lengths, f_ext=None):
     """X [N_tot,3], lengths [M], f_ext [N_tot,3]: all CUDA tensors or all numpy arrays."""
     lib = _native.load()
+    _need(X, 3 * h.n_points, "X")
+    _need(lengths, h.n_fibers, "lengths")
+    _need(f_ext, 3 * h.n_points, "f_ext")
     if hasattr(X, "is_cuda") and X.is_cuda:
         _check(lib.fs_set_state(h.ptr, _dev_ptr(X, "f64", "X"), _dev_ptr(lengths, "f64", "lengths"),
                                 _dev_ptr(f_ext, "f64", "f_ext"), 1), "fs_set_state")
@@ -232,6 +255,9 @@ def fs_set_state(h: Handle, X, lengths, f_ext=None):
 def fs_get_state(h: Handle, X=None, T=None, V=None):
     """Fill the given output arrays (CUDA tensors or numpy arrays, same kind)."""
     lib = _native.load()
+    _need(X, 3 * h.n_points, "X")
+    _need(T, h.n_points, "T")
+    _need(V, 3 * h.n_points, "V")
     arrs = [a for a in (X, T, V) if a is not None]
     if arrs and hasattr(arrs[0], "is_cuda") and arrs[0].is_cuda:
         _check(lib.fs_get_state(h.ptr, _dev_ptr(X, "f64", "X"), _dev_ptr(T, "f64", "T"),
@@ -244,9 +270,18 @@ def fs_get_state(h: Handle, X=None, T=None, V=None):
         _check(lib.fs_get_state(h.ptr, p(X), p(T), p(V), 0), "fs_get_state")
 
 
+def _check_pair_args(src_xyz, src_wf, tgt_xyz, out, src_fiber, tgt_fiber):
+    ns, nt = _points(src_xyz, "src_xyz"), _points(tgt_xyz, "tgt_xyz")
+    _need(src_wf, 3 * ns, "src_wf")
+    _need(out, 3 * nt, "out")
+    _need(src_fiber, ns, "src_fiber")
+    _need(tgt_fiber, nt, "tgt_fiber")
+
+
 def fs_stokeslet_apply(h: Handle, src_xyz, src_wf, tgt_xyz, out, src_fiber=None, tgt_fiber=None,
                        sum_precision: int = FS_SUM_FP32):
     lib = _native.load()
+    _check_pair_args(src_xyz, src_wf, tgt_xyz, out, src_fiber, tgt_fiber)
     _check(lib.fs_stokeslet_apply(h.ptr, _dev_ptr(src_xyz, "f64", "src_xyz"),
                                   _dev_ptr(src_wf, "f64", "src_wf"), int(src_xyz.shape[0]),
                                   _dev_ptr(src_fiber, "i32", "src_fiber"),
@@ -260,6 +295,7 @@ def fs_stokeslet_apply_tree(h: Handle, src_xyz, src_wf, tgt_xyz, out, src_fiber=
                             order: int = 8, theta: float = 0.5):
     """Treecode approximation of fs_stokeslet_apply (device tensors)."""
     lib = _native.load()
+    _check_pair_args(src_xyz, src_wf, tgt_xyz, out, src_fiber, tgt_fiber)
     _check(lib.fs_stokeslet_apply_tree(h.ptr, _dev_ptr(src_xyz, "f64", "src_xyz"),
                                        _dev_ptr(src_wf, "f64", "src_wf"), int(src_xyz.shape[0]),
                                        _dev_ptr(src_fiber, "i32", "src_fiber"),
@@ -272,6 +308,11 @@ def fs_stokeslet_apply_tree(h: Handle, src_xyz, src_wf, tgt_xyz, out, src_fiber=
 def fs_stresslet_apply(h: Handle, src_xyz, src_nrm, src_w, src_q, tgt_xyz, out,
                        sum_precision: int = FS_SUM_FP32):
     lib = _native.load()
+    ns, nt = _points(src_xyz, "src_xyz"), _points(tgt_xyz, "tgt_xyz")
+    _need(src_nrm, 3 * ns, "src_nrm")
+    _need(src_w, ns, "src_w")
+    _need(src_q, 3 * ns, "src_q")
+    _need(out, 3 * nt, "out")
     _check(lib.fs_stresslet_apply(h.ptr, _dev_ptr(src_xyz, "f64", "src_xyz"),
                                   _dev_ptr(src_nrm, "f64", "src_nrm"), _dev_ptr(src_w, "f64", "src_w"),
                                   _dev_ptr(src_q, "f64", "src_q"), int(src_xyz.shape[0]),
@@ -281,6 +322,10 @@ def fs_stresslet_apply(h: Handle, src_xyz, src_nrm, src_w, src_q, tgt_xyz, out,
 
 
 def fs_surface_apply(h: Handle, q, out, sum_precision: int = FS_SUM_FP64):
+    # every unknown after the fibers' 4 per node: densities, then the body's U, Omega
+    n_surf = h.n_unknowns - 4 * h.n_points
+    _need(q, n_surf, "q")
+    _need(out, n_surf, "out")
     _check(_native.load().fs_surface_apply(h.ptr, _dev_ptr(q, "f64", "q"), _dev_ptr(out, "f64", "out"),
                                            int(sum_precision)), "fs_surface_apply")
 
@@ -421,6 +466,7 @@ def fs_server_destroy(sv: Server):
 def fs_set_growth(h: Handle, Ldot):
     """Per-fiber plus-end growth rates: a CUDA tensor or a numpy array."""
     lib = _native.load()
+    _need(Ldot, h.n_fibers, "Ldot")
     if hasattr(Ldot, "is_cuda") and Ldot.is_cuda:
         _check(lib.fs_set_growth(h.ptr, _dev_ptr(Ldot, "f64", "Ldot"), 1), "fs_set_growth")
     else:
@@ -429,6 +475,8 @@ def fs_set_growth(h: Handle, Ldot):
 
 
 def fs_get_lengths(h: Handle, M: int):
+    if int(M) != h.n_fibers:
+        raise ValueError("the context has %d fibers, not %d" % (h.n_fibers, int(M)))
     out = np.zeros(int(M))
     _check(_native.load().fs_get_lengths(h.ptr, out.ctypes.data_as(ctypes.c_void_p), 0), "fs_get_lengths")
     return out
@@ -439,6 +487,8 @@ def fs_dynamic_instability(state, lengths, u, dt: float, v_grow: float, v_shrink
     """One step of the two-state dynamic instability (host, no GPU): returns
     (new_state int32, Ldot) for the given per-fiber uniform random numbers u."""
     st = np.ascontiguousarray(state, dtype=np.int32).copy()
+    _need(lengths, st.size, "lengths")
+    _need(u, st.size, "u")
     La, Lp = _host_ptr(lengths, np.float64, "lengths")
     ua, up = _host_ptr(u, np.float64, "u")
     Ld = np.zeros(st.shape[0])
