@@ -78,6 +78,25 @@ def _points(t, name: str) -> int:
     return int(shape[0])
 
 
+def _checked3(v, name: str):
+    a = np.asarray(v, dtype=np.float64).ravel()
+    if a.size != 3:
+        raise ValueError("%s must have 3 components" % name)
+    return a
+
+
+def _surface_ptrs(obj, what: str):
+    """Contiguous float64 nodes [n, 3], normals [n, 3] and weights [n] of a
+    boundary or body, sizes checked; returns the arrays and their pointers."""
+    nodes, pn = _host_ptr(obj.nodes, np.float64, what + " nodes")
+    n = _points(nodes, what + " nodes")
+    nrm, pm = _host_ptr(obj.normals, np.float64, what + " normals")
+    w, pw = _host_ptr(obj.weights, np.float64, what + " weights")
+    _need(nrm, 3 * n, what + " normals")
+    _need(w, n, what + " weights")
+    return (nodes, nrm, w), (pn, pm, pw), n
+
+
 def _host_ptr(a, dtype, name: str):
     if a is None:
         return None, None
@@ -117,11 +136,9 @@ def fs_create(points_per_fiber, mu: float, eps: float, E: float, dt: float, boun
     b = None
     keep = []
     if boundary is not None:
-        nodes, pn = _host_ptr(boundary.nodes, np.float64, "nodes")
-        nrm, pm = _host_ptr(boundary.normals, np.float64, "normals")
-        w, pw = _host_ptr(boundary.weights, np.float64, "weights")
-        keep += [nodes, nrm, w]
-        b = fs_boundary(float(boundary.R), int(nodes.shape[0]), pn, pm, pw)
+        arrs, (pn, pm, pw), n = _surface_ptrs(boundary, "boundary")
+        keep += list(arrs)
+        b = fs_boundary(float(boundary.R), n, pn, pm, pw)
     st = None
     if stream is not None:
         st = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
@@ -149,21 +166,19 @@ def fs_create_with_body(points_per_fiber, minus_end, mu: float, eps: float, E: f
     me_p = None
     if minus_end is not None:
         me, me_p = _host_ptr(np.asarray(minus_end), np.int32, "minus_end")
+        _need(me, M, "minus_end")
         keep.append(me)
     b = None
     if boundary is not None:
-        nodes, pn = _host_ptr(boundary.nodes, np.float64, "nodes")
-        nrm, pm = _host_ptr(boundary.normals, np.float64, "normals")
-        w, pw = _host_ptr(boundary.weights, np.float64, "weights")
-        keep += [nodes, nrm, w]
-        b = fs_boundary(float(boundary.R), int(nodes.shape[0]), pn, pm, pw)
-    bn, bpn = _host_ptr(body.nodes, np.float64, "body nodes")
-    bm, bpm = _host_ptr(body.normals, np.float64, "body normals")
-    bw, bpw = _host_ptr(body.weights, np.float64, "body weights")
-    keep += [bn, bm, bw]
+        arrs, (pn, pm, pw), n = _surface_ptrs(boundary, "boundary")
+        keep += list(arrs)
+        b = fs_boundary(float(boundary.R), n, pn, pm, pw)
+    arrs, (bpn, bpm, bpw), nb = _surface_ptrs(body, "body")
+    keep += list(arrs)
     D3 = ctypes.c_double * 3
-    bd = _native.fs_body(D3(*[float(v) for v in body.centre]), float(body.radius), int(bn.shape[0]), bpn, bpm,
-                         bpw, D3(*[float(v) for v in body.force]), D3(*[float(v) for v in body.torque]))
+    vec3 = lambda v, name: D3(*[float(x) for x in _checked3(v, name)])
+    bd = _native.fs_body(vec3(body.centre, "body centre"), float(body.radius), nb, bpn, bpm, bpw,
+                         vec3(body.force, "body force"), vec3(body.torque, "body torque"))
     st = None
     if stream is not None:
         st = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
@@ -400,19 +415,20 @@ def fs_submit(sv: Server, points_per_fiber, X, lengths, mu: float, eps: float, E
     """Queue one step request (host numpy inputs).  Returns the ticket; the
     outputs (X, V, T numpy arrays) are returned by fs_poll / fs_server_wait."""
     ppf, ppf_p = _host_ptr(np.asarray(points_per_fiber), np.int32, "points_per_fiber")
+    n_tot = int(ppf.sum())
+    _need(X, 3 * n_tot, "X")
+    _need(lengths, int(ppf.shape[0]), "lengths")
+    _need(f_ext, 3 * n_tot, "f_ext")
     xa, xp = _host_ptr(X, np.float64, "X")
     la, lp = _host_ptr(lengths, np.float64, "lengths")
     fa, fp = _host_ptr(f_ext, np.float64, "f_ext")
-    n_tot = int(ppf.sum())
     outs = (np.zeros((n_tot, 3)), np.zeros((n_tot, 3)), np.zeros(n_tot))
     keep = [ppf, xa, la, fa, outs]
     bptr = None
     if boundary is not None:
-        nodes, pn = _host_ptr(boundary.nodes, np.float64, "nodes")
-        nrm, pm = _host_ptr(boundary.normals, np.float64, "normals")
-        w, pw = _host_ptr(boundary.weights, np.float64, "weights")
-        b = fs_boundary(float(boundary.R), int(nodes.shape[0]), pn, pm, pw)
-        keep += [nodes, nrm, w, b]
+        arrs, (pn, pm, pw), n = _surface_ptrs(boundary, "boundary")
+        b = fs_boundary(float(boundary.R), n, pn, pm, pw)
+        keep += list(arrs) + [b]
         bptr = ctypes.pointer(b)
     p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
     rq = _native.fs_request(int(ppf.shape[0]), ppf_p, xp, lp, fp, bptr, float(mu), float(eps), float(E),

@@ -95,3 +95,32 @@ def test_dynamic_instability_inputs():
         fs.fs_dynamic_instability([1, 1], [1.0], [0.5, 0.5], 0.1, 1.0, 1.0, 1.0, 1.0, 0.1)
     with pytest.raises(ValueError, match="u has"):
         fs.fs_dynamic_instability([1, 1], [1.0, 1.0], [0.5], 0.1, 1.0, 1.0, 1.0, 1.0, 0.1)
+
+
+def test_constructors_and_submit():
+    import workloads as wl
+    b = wl.sphere_quadrature(6.0, 2, 4)
+    short = wl.Boundary(b.R, b.nodes, b.normals, b.weights[:-1])
+    with pytest.raises(ValueError, match="boundary weights"):
+        fs.fs_create([8, 8], 1.0, 1e-3, 1.0, 1e-3, boundary=short)
+    if not torch.cuda.is_available():
+        with pytest.raises(fs.FsError):                  # right sizes: no CUDA device here
+            fs.fs_create([8, 8], 1.0, 1e-3, 1.0, 1e-3, boundary=b)
+    body = wl.sphere_body((0.0, 0.0, 0.0), 1.0, 2, 4)
+    with pytest.raises(ValueError, match="minus_end"):
+        fs.fs_create_with_body([8, 8], [1], 1.0, 1e-3, 1.0, 1e-3, body)
+    bad_body = wl.RigidBody(body.centre, body.radius, body.nodes, body.normals[:-1], body.weights,
+                            body.force, body.torque)
+    with pytest.raises(ValueError, match="body normals"):
+        fs.fs_create_with_body([8, 8], [1, 1], 1.0, 1e-3, 1.0, 1e-3, bad_body)
+    bad_load = wl.RigidBody(body.centre, body.radius, body.nodes, body.normals, body.weights,
+                            np.zeros(2), body.torque)
+    with pytest.raises(ValueError, match="body force"):
+        fs.fs_create_with_body([8, 8], [1, 1], 1.0, 1e-3, 1.0, 1e-3, bad_load)
+    sv = fs.Server(ctypes.c_void_p(0))
+    with pytest.raises(ValueError, match="X has"):
+        fs.fs_submit(sv, [8, 8], np.zeros((15, 3)), [1.0, 1.0], 1.0, 1e-3, 1.0, 1e-3)
+    with pytest.raises(ValueError, match="lengths"):
+        fs.fs_submit(sv, [8, 8], np.zeros((16, 3)), [1.0], 1.0, 1e-3, 1.0, 1e-3)
+    with pytest.raises(fs.FsError):                      # right sizes: the NULL server is refused
+        fs.fs_submit(sv, [8, 8], np.zeros((16, 3)), [1.0, 1.0], 1.0, 1e-3, 1.0, 1e-3)
