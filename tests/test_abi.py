@@ -187,3 +187,40 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         fs.fs_options_default()
     with pytest.raises(ImportError):
         fs.fs_estimate_bytes([16, 16])
+
+
+def test_header_is_plain_c_and_links(tmp_path):
+    """A C99 program (no C++, no torch) includes the header, links the
+    library and calls it: option defaults, a validation error with its
+    message, the memory estimate."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not found")
+    build.build()
+    src = tmp_path / "client.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "fibersolve.h"
+int main(void) {
+    fs_options o;
+    if (fs_options_default(&o) != FS_OK || o.prec != FS_MIXED) return 1;
+    int32_t ppf[2] = {16, 5};
+    fs_ctx *c = NULL;
+    fs_status s = fs_create(&c, 2, ppf, 1.0, 1e-3, 1.0, 1e-3, NULL, &o, NULL);
+    if (s != FS_EINVAL || c != NULL || strstr(fs_last_error(), "fiber 1") == NULL) return 2;
+    if (strcmp(fs_status_str(s), "FS_EINVAL") != 0) return 3;
+    if (fs_estimate_bytes(1, ppf, 0, &o) == 0 || fs_estimate_bytes(2, ppf, 0, &o) != 0) return 4;
+    printf("ok\n");
+    return 0;
+}
+''')
+    lib_dir = os.path.dirname(_native.LIB_PATH)
+    exe = tmp_path / "client"
+    cc = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                         "-I", os.path.join(ROOT, "include"), str(src), "-L", lib_dir, "-lfibersolve",
+                         "-Wl,-rpath," + lib_dir, "-o", str(exe)], capture_output=True, text=True)
+    assert cc.returncode == 0, cc.stderr
+    run = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert run.returncode == 0 and run.stdout.strip() == "ok", (run.returncode, run.stdout, run.stderr)
