@@ -398,7 +398,8 @@ fs_status fs_dynamic_instability(int32_t n, const fs_kinetics *kinetics, double 
 /* Device bytes a context for this problem allocates (fs_create with these
  * fibers, a boundary of n_surface_nodes nodes or 0, and these options) plus
  * the largest direct-sum scratch one step reserves.  An upper bound of what
- * fs_device_bytes reports after a step; 0 for invalid arguments.  Host-only:
+ * fs_device_bytes reports after a step; 0 for invalid arguments (including
+ * options fs_create would refuse).  Host-only:
  * no CUDA call.  (No counterpart in the paper: sizing for admission control.) */
 size_t fs_estimate_bytes(int32_t n_fibers, const int32_t *points_per_fiber, int32_t n_surface_nodes,
                          const fs_options *options);

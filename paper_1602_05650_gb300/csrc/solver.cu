@@ -1222,6 +1222,8 @@ size_t fs_estimate_bytes(int32_t n_fibers, const int32_t *points_per_fiber, int3
         if (points_per_fiber[m] < 6 || points_per_fiber[m] > 256) return 0;
     fs_options o;
     if (options) o = *options; else fs_options_default(&o);
+    // options fs_create would refuse (an unknown precision, restart > 250, ...) estimate nothing
+    if (check_options(o, "fs_estimate_bytes", 1) != FS_OK) return 0;
     return estimate_bytes(n_fibers, points_per_fiber, n_surface_nodes, o);
 }
 

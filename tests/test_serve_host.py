@@ -46,6 +46,8 @@ def test_estimate_rejects_invalid(lib):
     assert est(lib, [257]) == 0
     assert lib.fs_estimate_bytes(-1, None, 0, None) == 0
     assert lib.fs_estimate_bytes(0, None, 0, None) > 0   # an empty context still holds its status word
+    assert est(lib, [32] * 4, prec=7) == 0                 # options fs_create would refuse
+    assert est(lib, [32] * 4, restart=251) == 0
 
 
 def test_server_argument_checks(lib):
