@@ -215,6 +215,7 @@ def fs_create_batch(fibers_per_system, points_per_fiber, mu: float, eps: float, 
     lib = _native.load()
     fps, fps_p = _host_ptr(np.asarray(fibers_per_system), np.int32, "fibers_per_system")
     ppf, ppf_p = _host_ptr(np.asarray(points_per_fiber), np.int32, "points_per_fiber")
+    _need(ppf, int(fps.astype(np.int64).sum()), "points_per_fiber")   # one entry per fiber of all systems
     st = None
     if stream is not None:
         st = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))

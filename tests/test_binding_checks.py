@@ -124,3 +124,5 @@ def test_constructors_and_submit():
         fs.fs_submit(sv, [8, 8], np.zeros((16, 3)), [1.0], 1.0, 1e-3, 1.0, 1e-3)
     with pytest.raises(fs.FsError):                      # right sizes: the NULL server is refused
         fs.fs_submit(sv, [8, 8], np.zeros((16, 3)), [1.0, 1.0], 1.0, 1e-3, 1.0, 1e-3)
+    with pytest.raises(ValueError, match="points_per_fiber"):
+        fs.fs_create_batch([2, 3], [8] * 4, 1.0, 1e-3, 1.0, 1e-3)
