@@ -143,14 +143,17 @@ def test_surface_diag_matches_operator():
             assert abs(col[i, a] - d[i, a]) < 1e-13
 
 
-def test_confined_point_force_at_centre():
+@pytest.mark.parametrize("mu", [1.0, 2.5])
+def test_confined_point_force_at_centre(mu):
     """A point force F at the centre of a no-slip sphere of radius R: the
     periphery equation (Eq. main-cortex-density) must give the interior image
     flow u^c = (1/8 pi mu)[-(3/R) I + (2 r^2 I - x x)/R^3] F (the Stokes flow
     that cancels G F on |x| = R), to quadrature accuracy, converging with
-    refinement."""
+    refinement.  At mu != 1 this also fixes the stresslet's scaling: the
+    equation's identity term q/2 does not scale with 1/mu, so a stresslet
+    carrying 1/mu would miss the closed form."""
     import scipy.sparse.linalg as sla
-    R, mu = 2.0, 1.0
+    R = 2.0
     F = np.array([0.4, -0.3, 1.0])
     pts = np.array([[0.0, 0.0, 0.0], [0.5, 0.2, -0.3], [-0.8, 0.4, 0.6]])
 
