@@ -38,10 +38,11 @@ def _build():
     ok.build()
 
 
-def bare_sphere(grid, force=(0.0, 0.0, 0.0), torque=(0.0, 0.0, 0.0), periphery=None, centre=(0.0, 0.0, 0.0)):
+def bare_sphere(grid, force=(0.0, 0.0, 0.0), torque=(0.0, 0.0, 0.0), periphery=None, centre=(0.0, 0.0, 0.0),
+                mu=MU):
     b = wl.sphere_body(centre, 1.0, *grid, force=force, torque=torque)
     return wl.Suspension(n_per_fiber=np.zeros(0, np.int32), X=np.zeros((0, 3)), L=np.zeros(0),
-                         f_ext=np.zeros((0, 3)), mu=MU, body=b, attach=np.zeros(0, np.int32),
+                         f_ext=np.zeros((0, 3)), mu=mu, body=b, attach=np.zeros(0, np.int32),
                          boundary=periphery)
 
 
@@ -54,20 +55,22 @@ def cross_aster(attach, force, N=16, E=1.0, grid=(6, 12)):
                          E=E, dt=1e-2, body=b, attach=np.full(6, attach, np.int32))
 
 
-def test_isolated_sphere_stokes_drag_converges():
+@pytest.mark.parametrize("mu", [MU, 2.5])
+def test_isolated_sphere_stokes_drag_converges(mu):
     F = np.array([0.2, -0.5, 1.0])
     errs = []
     for grid in ((4, 8), (6, 12)):
-        r = system.from_suspension(bare_sphere(grid, force=F, centre=(0.3, -0.2, 0.1))).step(tol=1e-12)
-        errs.append(np.linalg.norm(r.U - F / (6 * np.pi * MU)) / np.linalg.norm(F / (6 * np.pi * MU)))
+        r = system.from_suspension(bare_sphere(grid, force=F, centre=(0.3, -0.2, 0.1), mu=mu)).step(tol=1e-12)
+        errs.append(np.linalg.norm(r.U - F / (6 * np.pi * mu)) / np.linalg.norm(F / (6 * np.pi * mu)))
         assert np.linalg.norm(r.Omega) <= 1e-12 * np.linalg.norm(r.U)
     assert errs[1] < errs[0] / 10 and errs[1] <= 5e-9, errs
 
 
-def test_isolated_sphere_rotational_drag():
+@pytest.mark.parametrize("mu", [MU, 2.5])
+def test_isolated_sphere_rotational_drag(mu):
     Lt = np.array([0.3, 0.1, -0.7])
-    r = system.from_suspension(bare_sphere((4, 8), torque=Lt)).step(tol=1e-12)
-    assert np.linalg.norm(r.Omega - Lt / (8 * np.pi * MU)) <= 1e-10 * np.linalg.norm(Lt / (8 * np.pi * MU))
+    r = system.from_suspension(bare_sphere((4, 8), torque=Lt, mu=mu)).step(tol=1e-12)
+    assert np.linalg.norm(r.Omega - Lt / (8 * np.pi * mu)) <= 1e-10 * np.linalg.norm(Lt / (8 * np.pi * mu))
     assert np.linalg.norm(r.U) <= 1e-12
 
 
