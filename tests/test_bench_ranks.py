@@ -45,3 +45,22 @@ def test_job_time_is_the_slowest_rank_and_the_rate_counts_every_rank():
 def test_single_process_is_unchanged():
     assert bench.job_time(0.3, None, None) == 0.3
     assert bench.job_rate(1.0, 1, 0.5) == 2.0
+
+
+def test_reference_arm_under_torchrun_prints_one_line():
+    """`bench.py --impl reference` launched as the driver launches it for
+    N = 2 (torchrun, two ranks, gloo): rank 0 alone runs the oracle and prints
+    one JSON line, the other rank exits 0 without work."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
+           "bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "1"]
+    p = subprocess.run(cmd, cwd=root, capture_output=True, text=True, timeout=900)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [ln for ln in p.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, p.stdout
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
