@@ -23,18 +23,18 @@ def nodes(N: int) -> np.ndarray:
 def first_kind(M: int) -> np.ndarray:
     """M Chebyshev points of the first kind, cos((2j+1) pi / (2M)); the
     rectangular-collocation row points (velocity rows: M = N-4, tension rows:
-    M = N-2)."""
+    M = N-2) (Sec. 3.1.3)."""
     return np.cos(np.pi * (2.0 * np.arange(M) + 1.0) / (2.0 * M))
 
 
 def vander(x: np.ndarray, n: int) -> np.ndarray:
-    """V[i, j] = T_j(x_i), j < n."""
+    """V[i, j] = T_j(x_i), j < n (Sec. 3.1.3, Eq. cheb-basis)."""
     return C.chebvander(np.asarray(x, float), n - 1)
 
 
 def values_to_coeffs(values: np.ndarray) -> np.ndarray:
     """Chebyshev coefficients of the degree N-1 interpolant of nodal values
-    (rows = nodes), by solving the Chebyshev-Vandermonde system exactly."""
+    (rows = nodes), by solving the Chebyshev-Vandermonde system exactly (Sec. 3.1.3)."""
     N = values.shape[0]
     return np.linalg.solve(vander(nodes(N), N), values)
 
@@ -50,7 +50,7 @@ def cc_weights(N: int) -> np.ndarray:
 
 
 def series_at(coef: np.ndarray, x, m: int = 0) -> np.ndarray:
-    """m-th alpha-derivative of the series `coef` [n, 3] at the points x -> [len(x), 3]."""
+    """m-th alpha-derivative of the series `coef` [n, 3] at the points x -> [len(x), 3] (Sec. 3.1.3)."""
     x = np.atleast_1d(np.asarray(x, float))
     c = C.chebder(coef, m, axis=0) if m > 0 else coef
     if c.shape[0] == 0:
@@ -60,7 +60,7 @@ def series_at(coef: np.ndarray, x, m: int = 0) -> np.ndarray:
 
 def nodal_deriv_matrix(N: int, x: np.ndarray, m: int) -> np.ndarray:
     """Matrix mapping nodal values at the N nodes to the m-th derivative of
-    their interpolant at the points x."""
+    their interpolant at the points x (Sec. 3.1.3; D_s = (2/L) D_alpha, Sec. 3.2)."""
     cols = []
     Vinv = np.linalg.inv(vander(nodes(N), N))
     for j in range(N):
@@ -74,7 +74,7 @@ def nodal_deriv_matrix(N: int, x: np.ndarray, m: int) -> np.ndarray:
 
 def integrated_T(j: int, m: int) -> np.ndarray:
     """Coefficients of I^m T_j: m-fold integral of T_j from alpha = -1 (each
-    antiderivative vanishes at -1)."""
+    antiderivative vanishes at -1) (Sec. 3.1.3, Eq. cheb-basis)."""
     e = np.zeros(j + 1)
     e[j] = 1.0
     return C.chebint(e, m, lbnd=-1.0)
@@ -86,15 +86,18 @@ PI_LD = LD("3.141592653589793238462643383279502884197")
 
 
 def nodes_ld(N: int) -> np.ndarray:
+    """The N collocation nodes cos(k pi/(N-1)) in numpy.longdouble (Sec. 3.1.3)."""
     return np.cos(PI_LD * np.arange(N, dtype=LD) / LD(N - 1))
 
 
 def first_kind_ld(M: int) -> np.ndarray:
+    """The M first-kind points in numpy.longdouble (Sec. 3.1.3)."""
     return np.cos(PI_LD * (LD(2) * np.arange(M, dtype=LD) + LD(1)) / LD(2 * M))
 
 
 def solve_ld(A: np.ndarray, B: np.ndarray) -> np.ndarray:
-    """Gaussian elimination with partial pivoting in numpy.longdouble."""
+    """Gaussian elimination with partial pivoting in numpy.longdouble, for the
+    extended-precision geometry of Sec. 3.1.3."""
     A = np.array(A, dtype=LD)
     B = np.array(B, dtype=LD)
     n = A.shape[0]
@@ -117,7 +120,7 @@ def interp_derivs_ext(values: np.ndarray, pts: np.ndarray, m: int) -> np.ndarray
     [N, 3], computed in extended precision (numpy.longdouble): values are taken
     relative to the first node, the Chebyshev-Vandermonde system is solved by
     Gaussian elimination, then differentiated and evaluated with
-    numpy.polynomial.chebyshev.  Returns float64 [len(pts), 3]."""
+    numpy.polynomial.chebyshev.  Returns float64 [len(pts), 3] (Sec. 3.1.3, in extended precision)."""
     N = values.shape[0]
     v = np.asarray(values, dtype=LD)
     v = v - v[0][None, :]
@@ -139,12 +142,12 @@ def basis_V(N: int):
 
 
 def basis_T(N: int):
-    """Unknown basis for the tension: I^2 T_0 .. I^2 T_{N-3}, then T_0, T_1."""
+    """Unknown basis for the tension: I^2 T_0 .. I^2 T_{N-3}, then T_0, T_1 (Sec. 3.1.3, Eq. cheb-basis)."""
     return [integrated_T(j, 2) for j in range(N - 2)] + [integrated_T(k, 0) for k in range(2)]
 
 
 def basis_matrix(basis, x: np.ndarray, m: int = 0) -> np.ndarray:
-    """[len(x), len(basis)]: m-th derivative of each basis function at x."""
+    """[len(x), len(basis)]: m-th derivative of each basis function at x (Sec. 3.1.3, Eq. cheb-basis)."""
     x = np.atleast_1d(np.asarray(x, float))
     out = np.zeros((x.shape[0], len(basis)))
     for j, c in enumerate(basis):

@@ -49,7 +49,7 @@ from . import cheb
 
 
 class FiberOps:
-    """Matrices that depend only on the number of points N."""
+    """Matrices that depend only on the number of points N (Sec. 3.1.3-3.2)."""
 
     def __init__(self, N: int):
         if N < 6:
@@ -82,6 +82,7 @@ _OPS = {}
 
 
 def ops_for(N: int) -> FiberOps:
+    """The FiberOps of N points, built once per N (Sec. 3.1.3-3.2)."""
     if N not in _OPS:
         _OPS[N] = FiberOps(N)
     return _OPS[N]
@@ -211,23 +212,26 @@ class Fiber:
         return v.reshape(3, -1).T
 
     def f_lin(self, u: np.ndarray) -> np.ndarray:
+        """Nodal force of the unknowns u, -E dt D_s^4 V + D_s(T X_s) (Eq.
+        main-elastic-force, Sec. 3.2)."""
         return self.from_cm(self.F @ u)
 
     def rows_from_ubar(self, ubar: np.ndarray) -> np.ndarray:
-        """Rw applied to a nodal velocity field [N, 3]."""
+        """Rw applied to a nodal velocity field [N, 3] (Sec. 3.2, Eq. sche-linear-eq)."""
         return self.Rw @ self.to_cm(ubar)
 
     def rows_known(self) -> np.ndarray:
-        """Constant rows from the known force and the free-end data."""
+        """Constant rows from the known force and the free-end data (Sec. 3.2, Eq. bc-free)."""
         return self.Rw @ (self.S @ self.to_cm(self.f_known)) + self.const
 
     def velocity_nodes(self, u: np.ndarray) -> np.ndarray:
+        """V at the nodes from the unknowns u (Eq. cheb-basis)."""
         N = self.N
         return np.stack([self.op.V_nodes @ u[a * N:(a + 1) * N] for a in range(3)], axis=1)
 
     def rigid_rows(self, U: np.ndarray, Om: np.ndarray, Xp: np.ndarray) -> np.ndarray:
         """Terms of the attached-end rows in the body's U, Omega (zero for a
-        free fiber)."""
+        free fiber) (Eqs. BC2-1, BC2-2, BC2-T)."""
         N = self.N
         out = np.zeros(4 * N)
         if self.attach == FREE:
@@ -262,5 +266,6 @@ class Fiber:
         return F, L
 
     def tension_nodes(self, u: np.ndarray) -> np.ndarray:
+        """T at the nodes from the unknowns u (Eq. cheb-basis)."""
         N = self.N
         return self.op.T_nodes @ u[3 * N:4 * N]

@@ -61,7 +61,8 @@ def threads() -> int:
 
 
 def stokeslet(tgt, src, wf, mu=1.0, tgt_fiber=None, src_fiber=None) -> np.ndarray:
-    """u_i = sum_j G(x_i - y_j) wf_j, skipping same-fiber pairs when ids are given."""
+    """u_i = sum_j G(x_i - y_j) wf_j, skipping same-fiber pairs when ids are
+    given (Eqs. oseen, complementary-uf)."""
     tgt, src, wf = _f64(tgt), _f64(src), _f64(wf)
     tf, sf = _i32(tgt_fiber), _i32(src_fiber)
     out = np.zeros((tgt.shape[0], 3))
@@ -71,7 +72,7 @@ def stokeslet(tgt, src, wf, mu=1.0, tgt_fiber=None, src_fiber=None) -> np.ndarra
 
 
 def stresslet(tgt, src, normal, w, q) -> np.ndarray:
-    """u_i = sum_j w_j T(x_i - y_j):(q_j n_j) at off-surface targets."""
+    """u_i = sum_j w_j T(x_i - y_j):(q_j n_j) at off-surface targets (Eqs. stresslet, double-layer)."""
     tgt, src, normal, w, q = map(_f64, (tgt, src, normal, w, q))
     out = np.zeros((tgt.shape[0], 3))
     _load().oracle_stresslet(tgt.shape[0], _p(tgt), src.shape[0], _p(src), _p(normal), _p(w),
@@ -80,7 +81,8 @@ def stresslet(tgt, src, normal, w, q) -> np.ndarray:
 
 
 def surface_self(y, normal, w, q) -> np.ndarray:
-    """q/2 + T_pv[q] + N[q] on the surface nodes (fluid-side limit), by singularity subtraction."""
+    """q/2 + T_pv[q] + N[q] on the surface nodes (fluid-side limit), by singularity
+    subtraction (Eq. main-cortex-density, Sec. 3.1.2)."""
     y, normal, w, q = map(_f64, (y, normal, w, q))
     out = np.zeros((y.shape[0], 3))
     _load().oracle_surface_self(y.shape[0], _p(y), _p(normal), _p(w), _p(q), _p(out))
@@ -88,7 +90,7 @@ def surface_self(y, normal, w, q) -> np.ndarray:
 
 
 def surface_diag(y, normal, w) -> np.ndarray:
-    """Diagonal entries of surface_self as a [n, 3] array."""
+    """Diagonal entries of surface_self as a [n, 3] array (Eq. prec)."""
     y, normal, w = map(_f64, (y, normal, w))
     out = np.zeros((y.shape[0], 3))
     _load().oracle_surface_diag(y.shape[0], _p(y), _p(normal), _p(w), _p(out))
@@ -97,7 +99,7 @@ def surface_diag(y, normal, w) -> np.ndarray:
 
 def body_self(y, normal, w, q) -> np.ndarray:
     """-q/2 + T_pv[q] on a rigid body's surface nodes (fluid outside), by
-    singularity subtraction."""
+    singularity subtraction (Eq. main-nsb-second-kind, Sec. 3.1.2)."""
     y, normal, w, q = map(_f64, (y, normal, w, q))
     out = np.zeros((y.shape[0], 3))
     _load().oracle_body_self(y.shape[0], _p(y), _p(normal), _p(w), _p(q), _p(out))
@@ -105,7 +107,7 @@ def body_self(y, normal, w, q) -> np.ndarray:
 
 
 def body_diag(y, normal, w) -> np.ndarray:
-    """Diagonal entries of body_self as a [n, 3] array."""
+    """Diagonal entries of body_self as a [n, 3] array (Eq. prec)."""
     y, normal, w = map(_f64, (y, normal, w))
     out = np.zeros((y.shape[0], 3))
     _load().oracle_body_diag(y.shape[0], _p(y), _p(normal), _p(w), _p(out))

@@ -26,7 +26,7 @@ import numpy as np
 def dynamic_instability(state, L, u, dt, v_grow, v_shrink, f_cat, f_res, L_min, L_max=0.0):
     """Advance the per-fiber states (1 growing, 0 shrinking) by one step;
     returns (new_state, Ldot).  The rules above, applied to all fibers at
-    once: the switch, then the rescue at L_min, else the cap at L_max."""
+    once: the switch, then the rescue at L_min, else the cap at L_max (Sec. 2.4, Sec. 5)."""
     state = np.asarray(state, dtype=np.int32)
     L = np.asarray(L, dtype=float)
     u = np.asarray(u, dtype=float)

@@ -75,6 +75,9 @@ class StepResult:
 
 
 class System:
+    """The coupled implicit system of all fibers, the periphery and the body
+    (Eqs. sche-linear-eq, complementary-uf, complementary-uc)."""
+
     def __init__(self, X, L, n_per_fiber, f_ext, mu=1.0, eps=1e-3, E=1.0, dt=1e-3,
                  delta_over_L=0.01, lsb=False, boundary=None, Ldot=None, body=None, attach=None):
         self.mu = mu
@@ -172,6 +175,8 @@ class System:
         return ub, us
 
     def matvec(self, u: np.ndarray) -> np.ndarray:
+        """A u: each fiber's rows with the far field of the others, and the
+        surface rows (Eq. sche-linear-eq)."""
         us, q = self._split(u)
         f = np.concatenate([fb.f_lin(um) for fb, um in zip(self.fibers, us)]) if self.fibers \
             else np.zeros((0, 3))
@@ -204,6 +209,8 @@ class System:
         return out
 
     def rhs(self) -> np.ndarray:
+        """Right-hand side b from the known force, the free-end data and the
+        body's load (Sec. 3.2, Eq. sche-linear-eq)."""
         f = np.concatenate([fb.f_known for fb in self.fibers]) if self.fibers else np.zeros((0, 3))
         F = Lt = None
         if self.body is not None:
@@ -220,6 +227,8 @@ class System:
         return b
 
     def precond(self, v: np.ndarray) -> np.ndarray:
+        """P^-1 v: per-fiber block solves and Jacobi on the surface unknowns
+        (Eq. prec)."""
         out = np.empty_like(v)
         for m in range(len(self.fibers)):
             sl = slice(self.uptr[m], self.uptr[m + 1])
@@ -233,6 +242,7 @@ class System:
 
     # ---------------------------------------------------------------- GMRES
     def gmres(self, b: np.ndarray, tol: float, max_iter: int = 300, matvec=None):
+        """GMRES on the preconditioned system (Sec. 3.3)."""
         A = matvec or self.matvec
         r0 = self.precond(b)
         beta = np.linalg.norm(r0)
@@ -273,6 +283,7 @@ class System:
         return x, k, abs(g[k]) / beta
 
     def step(self, tol: float = 1e-10, max_iter: int = 300) -> StepResult:
+        """One implicit step: assemble, solve, read V and T (Sec. 3.2-3.3)."""
         b = self.rhs()
         u, its, res = self.gmres(b, tol, max_iter)
         us, q = self._split(u)
