@@ -1,6 +1,7 @@
-// Two-state dynamic instability of the fibers' plus ends (host code): the
-// growth rates fs_set_growth takes, drawn from the per-fiber state with the
-// caller's uniform random numbers.
+// Two-state dynamic instability of the fibers' plus ends (Sec. 2.4 growth,
+// Sec. 5 catastrophe and rescue; host code): the growth rates fs_set_growth
+// takes, drawn from the per-fiber state with the caller's uniform random
+// numbers.
 #include <cmath>
 
 #include "internal.h"
