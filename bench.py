@@ -805,14 +805,18 @@ def main():
     is64 = dom in (1, 3)
     ach = FLOPS_PER_PAIR[kind] * pairs / (total_ms * 1e-3) / 1e12 if total_ms > 0 else 0.0
     sm_max = clk.get("sm_max_mhz") or 2070.0
-    derived_fp32 = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    derived_fp32 = n_sm * 128 * 2 * sm_max * 1e6 / 1e12
     peak = (fp64_peak / 1e12) if is64 else derived_fp32
     roofline = {"bound": "alu", "kernel": "k_pairsum " + KS_NAMES[dom],
                 "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak if peak else None,
                 "traffic": traffic_for(KS_NAMES[dom]),
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, from "
+                                  "profiles/traffic.txt, used only when it was captured on the current "
+                                  "source of csrc/pairsum.cu (sha1 match), else null",
                 "flops_per_pair": FLOPS_PER_PAIR[kind],
                 "peak_source": ("measured FP64 FMA loop (fs_probe_fma)" if is64 else
-                                "152 SMs x 128 FP32 lanes x 2 x max SM clock"),
+                                "%d SMs (queried) x 128 FP32 lanes x 2 x max SM clock" % n_sm),
                 "launch_ms_avg": total_ms / launches_d if launches_d else None,
                 "measured_fp32_fma_tflops": fp32_peak / 1e12,
                 "measured_fp64_fma_tflops": fp64_peak / 1e12}

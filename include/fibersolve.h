@@ -255,7 +255,11 @@ fs_status fs_get_state(fs_ctx *ctx, double *X, double *T, double *V, int32_t ptr
  * src_xyz [n_src][3], src_wf [n_src][3] (force times quadrature weight),
  * tgt_xyz [n_tgt][3], out_u [n_tgt][3]: DEVICE arrays of double; ids int32.
  * mu comes from the context.  Enqueued on the context's stream; uses the
- * context's scratch memory (grown on demand). */
+ * context's scratch memory (grown on demand).  Returns without synchronising,
+ * so a bounded device-side wait that gives up (not expected in normal
+ * operation) shows in the result: every out_u entry is NaN, in this and
+ * every later sum of the context, until the context's next fs_step returns
+ * FS_ETIMEOUT and clears the flag. */
 fs_status fs_stokeslet_apply(fs_ctx *ctx, const double *src_xyz, const double *src_wf,
                              int64_t n_src, const int32_t *src_fiber,
                              const double *tgt_xyz, const int32_t *tgt_fiber, int64_t n_tgt,
@@ -272,14 +276,19 @@ fs_status fs_stokeslet_apply(fs_ctx *ctx, const double *src_xyz, const double *s
  *    optional and then non-decreasing over the sources).
  *  - Allocates nothing: its scratch is a fixed 16 MiB array in device memory
  *    that every GPU which loads this library holds until the process exits.
- *    Requests needing more scratch (roughly beyond 65,536 sources and
- *    targets in FP32) return FS_EINVAL with the size in fs_last_error().
+ *    A call needs the packed sources (32-64 bytes each), one partial sum per
+ *    target per resident CTA wave ((SMs x resident CTAs + target blocks) x
+ *    targets per block x 24 bytes) and, with ids, 8 bytes per target; on a
+ *    152-SM GB300 that admits 65,536 sources and targets in every precision.
+ *    Larger requests return FS_EINVAL with the size in fs_last_error().
  *  - The first call on a device looks up that array's device address (no
  *    allocation); make that first call before any stream capture.
  *  - All calls share the one array and it keeps the previous call's
  *    contents; calls that overlap on the GPU (different streams or threads
  *    without ordering between them) race on it and give wrong results.
- *  - Enqueued on `cuda_stream`; returns without synchronising. */
+ *  - Enqueued on `cuda_stream`; returns without synchronising.  A bounded
+ *    device-side wait that gives up (not expected in normal operation) is
+ *    reported only in the result: every out_u entry is NaN. */
 fs_status fs_stokeslet_apply_noalloc(const double *src_xyz, const double *src_wf, int64_t n_src,
                                      const int32_t *src_fiber, const double *tgt_xyz,
                                      const int32_t *tgt_fiber, int64_t n_tgt, double *out_u,

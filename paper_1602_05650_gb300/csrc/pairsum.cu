@@ -880,11 +880,21 @@ __global__ void k_pack(const double *__restrict__ xyz, const double *__restrict_
 // between), in ascending order (deterministic).  CTA c holds tiles
 // [floor(c W / G), floor((c + 1) W / G)); the largest c with floor(c W / G) <= t
 // is ceil((t + 1) G / W) - 1.
+// A CTA whose bounded wait gave up leaves its partial slots unwritten (they
+// hold whatever an earlier sum left there), so when the status word carries
+// DEV_ERR_TIMEOUT every output is set to NaN instead: the failure is visible
+// in the result without a host synchronisation.
 __global__ void k_reduce_streamk(const double *__restrict__ part, int64_t n_tgt, int tb, int64_t nt,
-                                 int64_t W, int G, double scale, int acc, double *__restrict__ out)
+                                 int64_t W, int G, double scale, int acc, double *__restrict__ out,
+                                 const int *__restrict__ status)
 {
     const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
     if (i >= n_tgt) return;
+    if (status && (*status & DEV_ERR_TIMEOUT)) {
+        double *o = out + 3 * i;
+        o[0] = o[1] = o[2] = __longlong_as_double(0x7ff8000000000000LL);
+        return;
+    }
     const int64_t b = i / tb, l = i - b * tb;
     const int64_t t0 = b * nt, t1 = (b + 1) * nt - 1;
     const int64_t c_lo = ((t0 + 1) * G + W - 1) / W - 1;
@@ -1148,7 +1158,7 @@ fs_status pairsum(const PairSumArgs &a, void *scratch, size_t scratch_bytes, int
     }
     if (!work) {
         k_reduce_streamk<<<static_cast<unsigned>((a.n_tgt + 255) / 256), 256, 0, st>>>(
-            part, a.n_tgt, p.tb, p.nt, p.W, p.grid, a.scale, acc, a.out);
+            part, a.n_tgt, p.tb, p.nt, p.W, p.grid, a.scale, acc, a.out, d_status);
         FS_LAUNCH_CHECK();
     }
     return FS_OK;

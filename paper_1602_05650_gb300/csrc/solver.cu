@@ -1,11 +1,20 @@
 // Context setup, Krylov kernels and the implicit step driver.
 //
 // One step (Sec. 3.2-3.3): geometry, per-fiber self blocks + LU (Eq. prec),
-// right-hand side with an FP64 far field, then
-//   FS_FP64 : left-preconditioned GMRES on A u = b with the FP64 far field;
-//   FS_MIXED: iterative refinement -- r = b - A u with the FP64 far field,
-//             GMRES on A e = r with the FP32 far field to inner_tol, u += e --
-//             until ||P^-1 r|| <= tol ||P^-1 b||.
+// right-hand side, then one of
+//   FS_FP64            : left-preconditioned GMRES on A u = b, every far field
+//                        in FP64;
+//   FS_MIXED, relax = 1: GMRES on the operator with the plain FP32 far field and
+//                        an FP32 hi/lo right-hand side to inner_tol; ONE true
+//                        preconditioned residual r = P^-1 b - P^-1 A u whose far
+//                        fields are float-float (FP64-grade, on the FP32 pipe);
+//                        GMRES on the plain FP32 operator for the correction d
+//                        until |r - P^-1 A d| <= tol |P^-1 b|, u += d (a residual
+//                        too large for the FP32 operator's accuracy is reduced
+//                        1e3-fold and r taken again, at most max_refine times);
+//   FS_MIXED, relax = 0: flexible GMRES whose outer operator has float-float far
+//                        fields, each direction preconditioned by a GMRES solve
+//                        on the FP32-far-field operator to inner_tol.
 // GMRES: x0 = 0, classical Gram-Schmidt with one re-orthogonalisation (CGS2),
 // Givens rotations on the host (one small device->host copy per iteration).
 #include <algorithm>
