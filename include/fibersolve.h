@@ -137,6 +137,15 @@ typedef struct {
                                operator is then the treecode's, and tol applies to it (as
                                with the paper's fast summation); single-system contexts */
     double tree_theta;      /* opening angle of the treecode (default 0.5) */
+    int32_t growth_implicit;/* growing or shrinking fibers (fs_set_growth): 0 = the
+                               reparametrisation term (alpha + 1)(Ldot / L) X_alpha at the
+                               current time, on the right-hand side (Sec. 3.2, Eq.
+                               discrete-rhs) (default); 1 = the same term at the new time,
+                               (alpha + 1) kappa X+_alpha with kappa = Ldot / (L + dt Ldot):
+                               its dt V_alpha part enters the self block.  The explicit
+                               term is forward Euler on an advection in alpha and goes
+                               unstable for fast-shrinking fibers (dt |Ldot| / L of a few
+                               percent); the implicit one stays stable there */
 } fs_options;
 
 /* Direct-sum kernel classes reported by fs_kernel_stats. */
@@ -365,10 +374,12 @@ fs_status fs_probe_fma(int32_t precision, double *flops_per_s);
 /* Plus-end growth rates dL/dt per fiber [n_fibers] for the following steps
  * (fiber (de)polymerization, Sec. 2.4 kinetics; 0 = fixed length, the
  * default).  The nodes stay at alpha_k in alpha = 2 s / L - 1 (minus end at
- * alpha = -1 fixed), so each step moves them by dt (w + (alpha + 1) kappa
- * X+_alpha) -- w the material velocity of Eq. main-sb-local, X+ = X + dt V,
- * kappa = Ldot / (L + dt Ldot), the reparametrisation term taken at the new
- * time -- and sets L <- L + dt Ldot.  fs_get_state's V is then (X+ - X)/dt,
+ * alpha = -1 fixed), so each step moves them by dt (w + R) -- w the material
+ * velocity of Eq. main-sb-local, R the reparametrisation term of Eq.
+ * chain-rule with the sign that advances the plus end: R = (alpha + 1)
+ * (Ldot / L) X_alpha at the current time (Eq. discrete-rhs; the default) or,
+ * with fs_options.growth_implicit = 1, R = (alpha + 1) kappa X+_alpha, X+ =
+ * X + dt V, kappa = Ldot / (L + dt Ldot) -- and sets L <- L + dt Ldot.  fs_get_state's V is then (X+ - X)/dt,
  * the nodes' rate.  FS_EINVAL if some L + dt Ldot would not stay positive.
  * Synchronises the context's stream. */
 fs_status fs_set_growth(fs_ctx *ctx, const double *Ldot, int32_t ptr_is_device);

@@ -24,11 +24,15 @@ Velocity expression at the nodes (Eq. main-sb-local):
 Rows (4N), rectangular collocation:
     velocity   (N-4 per component, first-kind points y):  -V(y) + [P_y w](y) = 0,
                with a growing or shrinking fiber (length rate Ldot, plus end
-               at alpha = 1): -V(y) + [P_y w](y) + (y + 1) kappa X+_alpha(y) = 0,
-               kappa = Ldot / (L + dt Ldot), X+ = X + dt V (the nodes sit at
-               fixed alpha = 2 s / L - 1, so they move with the material
-               velocity w plus the reparametrisation term, taken at the new
-               time like every other term of the step)
+               at alpha = 1) the nodes sit at fixed alpha = 2 s / L - 1, so
+               they move with the material velocity w plus the
+               reparametrisation term R (Sec. 2.4, Eq. chain-rule, with the
+               sign that advances the plus end):
+               growth="explicit" (default; Eq. discrete-rhs, R at the current
+               time):  -V(y) + [P_y w](y) + (y + 1)(Ldot / L) X_alpha(y) = 0;
+               growth="implicit" (named variant, R at the new time):
+                 -V(y) + [P_y w](y) + (y + 1) kappa X+_alpha(y) = 0,
+                 kappa = Ldot / (L + dt Ldot), X+ = X + dt V
     free ends  (Eq. bc-free, on X+):  V''(+-1) + X''(+-1)/dt = 0,
                                       V'''(+-1) + X'''(+-1)/dt = 0
     tension    (N-2 first-kind points z):  X_s(z) . [D_z w](z) = 0
@@ -104,7 +108,9 @@ class Fiber:
 
     def __init__(self, X: np.ndarray, L: float, f_ext: np.ndarray, mu: float, eps: float,
                  E: float, dt: float, delta: float, lsb: bool = False, Ldot: float = 0.0,
-                 attach: int = FREE):
+                 attach: int = FREE, growth: str = "explicit"):
+        if growth not in ("explicit", "implicit"):
+            raise ValueError("growth must be 'explicit' or 'implicit'")
         N = X.shape[0]
         op = ops_for(N)
         self.N, self.op, self.L = N, op, L
@@ -164,11 +170,15 @@ class Fiber:
             Rd[r0 + N - 2:r0 + N, a * N:(a + 1) * N] = op.V3_pm
             const[r0 + N - 4:r0 + N - 2] = X2[:, a] / dt
             const[r0 + N - 2:r0 + N] = X3[:, a] / dt
-            if Ldot != 0.0:
-                # growth (Sec. 2.4, kinetics): at fixed alpha the nodes move with
-                # the material velocity plus (alpha + 1)(Ldot / L) X_alpha; taken
-                # at the new time (length L + dt Ldot, positions X + dt V):
-                # -V + w + (y + 1) kappa (X_alpha + dt V_alpha)(y) = 0
+            if Ldot != 0.0 and growth == "explicit":
+                # growth (Sec. 2.4, Eq. chain-rule; Sec. 3.2, Eq. discrete-rhs):
+                # at fixed alpha the nodes move with the material velocity plus
+                # (alpha + 1)(Ldot / L) X_alpha, taken at the current time:
+                # -V + w + (y + 1)(Ldot / L) X_alpha(y) = 0
+                const[r0:r0 + N - 4] = (op.y + 1.0) * (Ldot / L) * Xa_y[:, a]
+            elif Ldot != 0.0:
+                # the same term at the new time (length L + dt Ldot, positions
+                # X + dt V): -V + w + (y + 1) kappa (X_alpha + dt V_alpha)(y) = 0
                 kappa = Ldot / (L + dt * Ldot)
                 const[r0:r0 + N - 4] = (op.y + 1.0) * kappa * Xa_y[:, a]
                 Rd[r0:r0 + N - 4, a * N:(a + 1) * N] += dt * kappa * (op.y + 1.0)[:, None] * op.V1_y

@@ -79,7 +79,8 @@ class System:
     (Eqs. sche-linear-eq, complementary-uf, complementary-uc)."""
 
     def __init__(self, X, L, n_per_fiber, f_ext, mu=1.0, eps=1e-3, E=1.0, dt=1e-3,
-                 delta_over_L=0.01, lsb=False, boundary=None, Ldot=None, body=None, attach=None):
+                 delta_over_L=0.01, lsb=False, boundary=None, Ldot=None, body=None, attach=None,
+                 growth="explicit"):
         self.mu = mu
         self.dt = dt
         self.n_per = np.asarray(n_per_fiber, dtype=np.int64)
@@ -91,7 +92,7 @@ class System:
             self.fibers.append(Fiber(self.X[a:b], float(L[m]), np.asarray(f_ext[a:b], float), mu,
                                      eps, E, dt, delta_over_L * float(L[m]), lsb,
                                      0.0 if Ldot is None else float(Ldot[m]),
-                                     FREE if attach is None else int(attach[m])))
+                                     FREE if attach is None else int(attach[m]), growth))
         self.L = np.asarray(L, float)
         self.Ldot = np.zeros(len(self.n_per)) if Ldot is None else np.asarray(Ldot, float)
         self.uptr = np.concatenate([[0], np.cumsum(4 * self.n_per)])
@@ -301,9 +302,11 @@ class System:
         return res_
 
 
-def from_suspension(s, delta_over_L=0.01, lsb=False, Ldot=None) -> System:
+def from_suspension(s, delta_over_L=0.01, lsb=False, Ldot=None, growth="explicit") -> System:
     """Build the system from a workloads.Suspension (Ldot: per-fiber length
-    rates, None = fixed lengths; a rigid body and the fibers' minus-end
-    conditions when the suspension has them)."""
+    rates, None = fixed lengths; growth: "explicit" = the growth term at the
+    current time as in Eq. discrete-rhs, "implicit" = at the new time; a
+    rigid body and the fibers' minus-end conditions when the suspension has
+    them)."""
     return System(s.X, s.L, s.n_per_fiber, s.f_ext, s.mu, s.eps, s.E, s.dt, delta_over_L, lsb,
-                  s.boundary, Ldot, getattr(s, "body", None), getattr(s, "attach", None))
+                  s.boundary, Ldot, getattr(s, "body", None), getattr(s, "attach", None), growth)

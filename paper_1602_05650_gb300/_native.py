@@ -36,7 +36,8 @@ class fs_options(ctypes.Structure):
     _fields_ = [("prec", c_int32), ("tol", c_double), ("max_iter", c_int32), ("restart", c_int32),
                 ("max_refine", c_int32), ("inner_tol", c_double), ("delta_over_L", c_double),
                 ("lsb", c_int32), ("use_graph", c_int32), ("tile_override", c_int32),
-                ("profile", c_int32), ("relax", c_int32), ("tree_order", c_int32), ("tree_theta", c_double)]
+                ("profile", c_int32), ("relax", c_int32), ("tree_order", c_int32), ("tree_theta", c_double),
+                ("growth_implicit", c_int32)]
 
 
 class fs_kernel_stat(ctypes.Structure):

@@ -65,8 +65,8 @@ fs_status check_options(const fs_options &o, const char *who, int n_systems)
         set_error("%s: delta_over_L must be finite and >= 0", who);
         return FS_EINVAL;
     }
-    if ((o.lsb | o.relax | o.profile) & ~1) {
-        set_error("%s: lsb, relax and profile are 0 or 1", who);
+    if ((o.lsb | o.relax | o.profile | o.growth_implicit) & ~1) {
+        set_error("%s: lsb, relax, profile and growth_implicit are 0 or 1", who);
         return FS_EINVAL;
     }
     if (o.use_graph != 0) {
@@ -138,6 +138,7 @@ fs_status fs_options_default(fs_options *o)
     o->relax = 1;
     o->tree_order = 0;
     o->tree_theta = 0.5;
+    o->growth_implicit = 0;
     return FS_OK;
 }
 

@@ -81,6 +81,7 @@ struct FiberTable {
     double *ftau;    // [3 N^2] per fiber: force of each tension column, [a][l][j]
     double *wsc;     // [12 N^2] per fiber: w = (M + K_delta) f of each column, [col][b N + k]
     const double *Ldot;  // [M] plus-end growth rates (nullptr: fixed lengths)
+    int growth_implicit; // 0: growth term at the current time (Eq. discrete-rhs); 1: at the new time
     const int *attach;   // [M] minus-end condition FS_END_* (nullptr: all free)
 };
 

@@ -362,15 +362,17 @@ __global__ void __launch_bounds__(128) k_rows(FiberTable F, const double *__rest
     const int N = fb.N;
     double *us = rsm, *fs_ = us + 4 * N, *w = fs_ + 3 * N, *wv = w + 3 * N;
     for (int i = threadIdx.x; i < 4 * N; i += blockDim.x) us[i] = (u && mode == 0) ? u[fb.u0 + i] : 0.0;
-    // growth (known part, right-hand side only): the nodes sit at fixed alpha,
-    // so the velocity rows carry (alpha + 1) kappa X+_alpha with kappa =
-    // Ldot / (L + dt Ldot); its known part (alpha + 1) kappa X_alpha =
-    // (alpha + 1) kappa (L / 2) X_s (the dt V_alpha part is in the self block)
+    // growth (Sec. 2.4, Eq. chain-rule): the nodes sit at fixed alpha, so the
+    // velocity rows carry the reparametrisation term R = (alpha + 1) k X_alpha
+    // = (alpha + 1) k (L / 2) X_s.  Explicit (Eq. discrete-rhs): k = Ldot / L,
+    // all of it on the right-hand side.  Implicit: k = kappa = Ldot / (L + dt
+    // Ldot) on X+_alpha; its known part is this one, its dt V_alpha part sits
+    // in the self block.
     const double ldot = (mode == 1 && F.Ldot) ? F.Ldot[fb.m] : 0.0;
     if (ldot != 0.0) {
         const double *al = fb.M_(fb.lay.alpha);
         const double *t = F.t + 3 * fb.n0;
-        const double kl2 = ldot / (fb.L + F.dt * ldot) * 0.5 * fb.L;
+        const double kl2 = (F.growth_implicit ? ldot / (fb.L + F.dt * ldot) : ldot / fb.L) * 0.5 * fb.L;
         for (int i = threadIdx.x; i < 3 * N; i += blockDim.x) wv[i] = (al[i / 3] + 1.0) * kl2 * t[i];
     }
     if (mode == 2) {
@@ -571,8 +573,9 @@ __global__ void __launch_bounds__(256) k_build_rows(FiberTable F, double *__rest
     const double *W = F.wsc + fb.blk0 / 4 * 3;
     const double *Py = fb.M_(fb.lay.Py), *Vy = fb.M_(fb.lay.Vy), *Dz = fb.M_(fb.lay.Dz);
     const double *Vgy = fb.M_(fb.lay.Vgy);
-    // growth at the new time: (y + 1) kappa dt V_alpha(y), kappa = Ldot / (L + dt Ldot)
-    const double ldot = F.Ldot ? F.Ldot[fb.m] : 0.0;
+    // growth at the new time (implicit variant only): (y + 1) kappa dt V_alpha(y),
+    // kappa = Ldot / (L + dt Ldot); the explicit term has no part in the block
+    const double ldot = (F.Ldot && F.growth_implicit) ? F.Ldot[fb.m] : 0.0;
     const double gdt = ldot != 0.0 ? F.dt * ldot / (fb.L + F.dt * ldot) : 0.0;
     const double *tz = F.tz + 3 * fb.z0;
     double acc[4][4] = {};

@@ -971,6 +971,7 @@ fs::FiberTable fs_ctx::table() const
     F.ftau = d_ftau;
     F.wsc = d_wsc;
     F.Ldot = growth ? d_Ldot : nullptr;
+    F.growth_implicit = opt.growth_implicit;
     F.attach = body.on ? body.attach : nullptr;
     return F;
 }

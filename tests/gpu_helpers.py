@@ -15,8 +15,9 @@ def dev(a, torch, dtype=None):
 
 
 def make_ctx(s, prec=fs.FS_FP64, tol=1e-12, lsb=False, delta_over_L=0.01, restart=60, max_iter=300,
-             relax=None, profile=False):
+             relax=None, profile=False, growth_implicit=False):
     opt = fs.fs_options_default()
+    opt.growth_implicit = 1 if growth_implicit else 0
     if relax is not None:
         opt.relax = 1 if relax else 0
     opt.profile = 1 if profile else 0

@@ -1,6 +1,8 @@
 """Growing and shrinking fibers on the GPU (fs_set_growth): parity of the step
-with the oracle, the exact extension of a force-free straight fiber, lengths
-updated by dt Ldot, and steps driven by the dynamic instability."""
+with the oracle for both growth schemes (the paper's explicit term of Eq.
+discrete-rhs, the default, and the implicit variant), the exact extension of
+a force-free straight fiber, lengths updated by dt Ldot, and steps driven by
+the dynamic instability."""
 import copy
 
 import numpy as np
@@ -18,8 +20,11 @@ pytestmark = pytest.mark.gpu
 import paper_1602_05650_gb300 as fs  # noqa: E402
 
 
-def step_with_growth(s, Ldot, prec=fs.FS_FP64, tol=1e-12):
-    h = make_ctx(s, prec=prec, tol=tol)
+GROWTH = {"explicit": False, "implicit": True}
+
+
+def step_with_growth(s, Ldot, prec=fs.FS_FP64, tol=1e-12, growth="explicit"):
+    h = make_ctx(s, prec=prec, tol=tol, growth_implicit=GROWTH[growth])
     X = dev(s.X, torch)
     fs.fs_set_state(h, X, dev(s.L, torch), dev(s.f_ext, torch))
     fs.fs_set_growth(h, np.asarray(Ldot, float))
@@ -32,23 +37,25 @@ def step_with_growth(s, Ldot, prec=fs.FS_FP64, tol=1e-12):
     return V.cpu().numpy(), Xn.cpu().numpy(), L
 
 
+@pytest.mark.parametrize("growth", ["explicit", "implicit"])
 @pytest.mark.parametrize("prec,tol,gate", [(fs.FS_FP64, 1e-12, 1e-10), (fs.FS_MIXED, 1e-10, 1e-8)])
-def test_growth_step_matches_oracle(prec, tol, gate):
+def test_growth_step_matches_oracle(prec, tol, gate, growth):
     s = wl.free_space(12, 24, 6.0, seed=7, curved_amp=0.05)
     s.f_ext = np.tile([0.0, 0.0, -1.0], (s.n_points, 1))
     Ldot = np.random.default_rng(1).uniform(-2.0, 2.0, 12)
-    ref = system.from_suspension(s, Ldot=Ldot).step(tol=1e-13)
-    V, Xn, L = step_with_growth(s, Ldot, prec, tol)
+    ref = system.from_suspension(s, Ldot=Ldot, growth=growth).step(tol=1e-13)
+    V, Xn, L = step_with_growth(s, Ldot, prec, tol, growth)
     assert rel(V, ref.V) <= gate
     assert rel(Xn, ref.X_new) <= gate
     assert np.allclose(L, s.L + s.dt * Ldot, rtol=1e-15, atol=0.0)
 
 
-def test_force_free_straight_fiber_extends_exactly():
+@pytest.mark.parametrize("growth", ["explicit", "implicit"])
+def test_force_free_straight_fiber_extends_exactly(growth):
     s = wl.free_space(3, 16, 20.0, seed=1)
     s.f_ext[:] = 0.0
     Ldot = np.array([0.7, -0.4, 2.0])
-    _, Xn, L = step_with_growth(s, Ldot)
+    _, Xn, L = step_with_growth(s, Ldot, growth=growth)
     a = cheb.nodes(16)
     for m in range(3):
         X = s.X[m * 16:(m + 1) * 16]
@@ -66,13 +73,14 @@ def test_rejects_a_rate_that_would_empty_a_fiber():
     fs.fs_destroy(h)
 
 
-def test_dynamic_instability_steps_match_oracle():
+@pytest.mark.parametrize("growth", ["explicit", "implicit"])
+def test_dynamic_instability_steps_match_oracle(growth):
     """Three steps; each step the library's host state machine sets the rates
     (the oracle's gives the same, bit for bit) and both sides step from the
     GPU's current state."""
     s = wl.free_space(10, 16, 5.0, seed=9, curved_amp=0.05)
     s.f_ext = np.tile([0.1, 0.0, -1.0], (s.n_points, 1))
-    h = make_ctx(s, tol=1e-12)
+    h = make_ctx(s, tol=1e-12, growth_implicit=GROWTH[growth])
     X = dev(s.X, torch)
     fs.fs_set_state(h, X, dev(s.L, torch), dev(s.f_ext, torch))
     rng = np.random.default_rng(3)
@@ -89,7 +97,7 @@ def test_dynamic_instability_steps_match_oracle():
         assert np.array_equal(state, state_o) and np.array_equal(Ld, Ld_o)
         fs.fs_set_growth(h, Ld)
         cur.L = L
-        ref = system.from_suspension(cur, Ldot=Ld).step(tol=1e-13)
+        ref = system.from_suspension(cur, Ldot=Ld, growth=growth).step(tol=1e-13)
         fs.fs_step(h)
         fs.fs_get_state(h, X=Xn, V=V)
         assert rel(V.cpu().numpy(), ref.V) <= 1e-10
