@@ -56,9 +56,14 @@ typedef enum {
                         compensated (TwoSum) accumulation across tiles, FP64 output */
     FS_SUM_FF = 2,   /* float-float ("double-single") arithmetic on the FP32 pipe,
                         ~2^-44 relative rounding per pair */
-    FS_SUM_FP32_PLAIN = 3 /* FS_SUM_FP32 without the lo parts of the coordinates:
-                        ~15% faster, coordinate rounding ~2^-24 of the extent of
-                        the sources (relative to their bounding-box centre) */
+    FS_SUM_FP32_PLAIN = 3 /* Stokeslet: FP32 in packed two-target instructions,
+                        each thread's consecutive targets in a frame at its middle
+                        target (sources moved into it from their hi/lo parts): on
+                        fiber nodes the pair differences round relative to the
+                        fiber's extent (hi/lo accuracy) at ~20% less cost; targets
+                        that are not spatially grouped round like coordinates
+                        centred on the sources' bounding box (2^-24 of its extent);
+                        Stokeslet sums only */
 } fs_sum_precision;
 
 /* Spherical no-slip periphery (Sec. 2.1, Eq. main-cortex-density) discretised
@@ -283,7 +288,7 @@ fs_status fs_stokeslet_apply(fs_ctx *ctx, const double *src_xyz, const double *s
  *  - Needs no context: mu and the CUDA stream (cudaStream_t or NULL) are
  *    arguments; arrays as in fs_stokeslet_apply (DEVICE arrays, fiber ids
  *    optional and then non-decreasing over the sources).
- *  - Allocates nothing: its scratch is a fixed 16 MiB array in device memory
+ *  - Allocates nothing: its scratch is a fixed 32 MiB array in device memory
  *    that every GPU which loads this library holds until the process exits.
  *    A call needs the packed sources (32-64 bytes each), one partial sum per
  *    target per resident CTA wave ((SMs x resident CTAs + target blocks) x

@@ -15,7 +15,7 @@
 namespace fs {
 namespace {
 
-constexpr size_t kNoAllocBytes = size_t(16) << 20;   // 16 MiB, held by every GPU that loads the library
+constexpr size_t kNoAllocBytes = size_t(32) << 20;   // 32 MiB, held by every GPU that loads the library
 
 // [0, 256): status word; [256, kNoAllocBytes): exclusion ranges and the direct-sum scratch
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];

@@ -395,6 +395,281 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+// ------------------------------------------------- FP32 Stokeslet, packed pairs
+// The FP32 Stokeslet sum in Blackwell's packed two-lane FP32 instructions
+// (__fadd2_rn / __fmul2_rn / __ffma2_rn: one instruction evaluates the same
+// source against two targets), so that the 17 FP32 operations of a pair take
+// 8.5 issue slots and the kernel is bound by the FMA pipe, not by issue.
+//
+// Per pair: 16 FP32 operations (3 differences, 3 for |r|^2, 3 for r.(W f),
+// one for (r.(W f))/|r|^2, 3 + 3 for the accumulation) plus two MUFU
+// operations (rsqrt, rcp).
+//
+// Coordinates in a per-thread frame.  Each thread holds T consecutive
+// targets (normally nodes of one fiber) and a frame origin g = (float) of its
+// middle target's coordinates relative to the sources' bounding-box centre
+// (exactly representable in FP32).  Targets are stored as t - g rounded once
+// from FP64; a source arrives as hi + lo floats of s - centre and is moved
+// into the frame once per thread as (g - s_hi) - s_lo.  For the sources near
+// a thread's targets, g - s_hi is exact (Sterbenz), so the rounding of the
+// pair difference is relative to the pair's own distance and the fiber's
+// extent, not to the extent of the whole point set (the accuracy of the hi/lo
+// kernel at the cost of 6 FP32 operations per source per thread, 0.75 per
+// pair at T = 8).
+// Approximate reciprocal on the MUFU unit (PTX rcp.approx.ftz.f32, about
+// 1 ulp); used for 1/|r|^2 beside rsqrt's 1/|r|.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+template <int T, bool MASK>
+__device__ __forceinline__ void tile_x2(const float4 *__restrict__ sp, const float4 *__restrict__ sw,
+                                        const float4 *__restrict__ sl, int cnt, int j0, float gx, float gy,
+                                        float gz, const float2 (&tx)[T / 2], const float2 (&ty)[T / 2],
+                                        const float2 (&tz)[T / 2], const int2 *__restrict__ ex,
+                                        float2 (&ax)[T / 2], float2 (&ay)[T / 2], float2 (&az)[T / 2])
+{
+    // masked tiles (those that overlap some target's own fiber): the
+    // targets' excluded source ranges, [lo, lo + cnt)
+    int elo[MASK ? T : 1], ecnt[MASK ? T : 1];
+    if constexpr (MASK) {
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int2 e = ex[t];
+            elo[t] = e.x;
+            ecnt[t] = e.y > e.x ? e.y - e.x : 0;
+        }
+    }
+#pragma unroll 8
+    for (int j = 0; j < cnt; ++j) {
+        const float4 p = sp[j], f = sw[j], l = sl[j];
+        // minus the source in the thread's frame
+        const float nx = (gx - p.x) - l.x, ny = (gy - p.y) - l.y, nz = (gz - p.z) - l.z;
+        const float2 NX = make_float2(nx, nx), NY = make_float2(ny, ny), NZ = make_float2(nz, nz);
+        const float2 FX = make_float2(f.x, f.x), FY = make_float2(f.y, f.y), FZ = make_float2(f.z, f.z);
+#pragma unroll
+        for (int q = 0; q < T / 2; ++q) {
+            const float2 dx = __fadd2_rn(tx[q], NX);
+            const float2 dy = __fadd2_rn(ty[q], NY);
+            const float2 dz = __fadd2_rn(tz[q], NZ);
+            float2 r2 = __fmul2_rn(dx, dx);
+            r2 = __ffma2_rn(dy, dy, r2);
+            r2 = __ffma2_rn(dz, dz, r2);
+            // 1/|r| and 1/|r|^2 both on the MUFU unit (the FMA pipe is the bound)
+            float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+            float2 ri2 = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
+            if constexpr (MASK) {
+                if (static_cast<unsigned>(j0 + j - elo[2 * q]) < static_cast<unsigned>(ecnt[2 * q]))
+                    ri.x = ri2.x = 0.0f;
+                if (static_cast<unsigned>(j0 + j - elo[2 * q + 1]) < static_cast<unsigned>(ecnt[2 * q + 1]))
+                    ri.y = ri2.y = 0.0f;
+            }
+            float2 rf = __fmul2_rn(dx, FX);
+            rf = __ffma2_rn(dy, FY, rf);
+            rf = __ffma2_rn(dz, FZ, rf);
+            const float2 s = __fmul2_rn(rf, ri2);
+            ax[q] = __ffma2_rn(ri, __ffma2_rn(s, dx, FX), ax[q]);
+            ay[q] = __ffma2_rn(ri, __ffma2_rn(s, dy, FY), ay[q]);
+            az[q] = __ffma2_rn(ri, __ffma2_rn(s, dz, FZ), az[q]);
+        }
+    }
+}
+
+// Resident CTAs per SM the packed kernel is compiled for: 4 at 8 targets per
+// thread (16 warps per SM; at 3 the FMA pipe idled for want of eligible warps).
+template <int T>
+struct X2Occ {
+    static constexpr int value = T >= 8 ? 4 : 6;
+};
+
+// Shared memory of the packed kernel beyond its source stages: the
+// compensated cross-tile sums (s, c) of x, y, z for T targets per thread.
+__host__ __device__ constexpr size_t x2_sum_bytes(int T) { return size_t(6) * T * kThreads * sizeof(float); }
+
+// Same schedule and outputs as k_pairsum (stream-K partials or work-list
+// items); sources packed as [0] position hi, [1] W f, [2] position lo.
+// Target i of a piece is tbase + tid T + t.  The cross-tile sums live in
+// shared memory ([value][target][thread], conflict-free) to keep the
+// registers within four CTAs per SM.
+template <int T>
+__global__ void __launch_bounds__(kThreads, X2Occ<T>::value)
+    k_stokeslet_x2(const float4 *__restrict__ src, int64_t n_src, int64_t nt, int64_t W, int G,
+                   const double *__restrict__ tgt, const int2 *__restrict__ excl, int64_t n_tgt,
+                   const double *__restrict__ center, double *__restrict__ out, double *__restrict__ part,
+                   double scale, int acc, int *__restrict__ status, const int4 *__restrict__ work)
+{
+    static_assert(T % 2 == 0, "targets per thread come in pairs");
+    constexpr int NARR = 3, TILE = kTile32, TB = T * kThreads, NP = T / 2;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float4 *smem = reinterpret_cast<float4 *>(smem_raw);   // [stage][array][TILE]
+    float *sums = reinterpret_cast<float *>(smem + 2 * NARR * TILE);   // [6][T][kThreads]
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ int s_lo, s_hi;
+
+    const int tid = threadIdx.x;
+    const Run run(work, nt, W, G, n_src, TILE, TB);
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    auto stage_ptr = [&](int stage, int arr) -> float4 * { return smem + (stage * NARR + arr) * TILE; };
+    auto issue = [&](int64_t it) {
+        int64_t j0;
+        int cnt;
+        run.src(it, j0, cnt);
+        const int stage = static_cast<int>(it & 1);
+        const uint32_t bytes = static_cast<uint32_t>(cnt) * 16u;
+        mbar_expect_tx(&bars[stage], bytes * NARR);
+#pragma unroll
+        for (int a = 0; a < NARR; ++a) bulk_g2s(stage_ptr(stage, a), src + a * n_src + j0, bytes, &bars[stage]);
+    };
+    if (tid == 0) {
+        if (run.n_run > 0) issue(0);
+        if (run.n_run > 1) issue(1);
+    }
+    auto sum_at = [&](int v, int t) -> float & { return sums[(v * T + t) * kThreads + tid]; };
+    const double c0 = center[0], c1 = center[1], c2 = center[2];
+    bool failed = false;
+    int64_t it = 0;
+    do {
+        int64_t tbase, t_end, len, blk;
+        run.piece(it, n_tgt, tbase, t_end, len, blk);
+        if (tid == 0) {
+            s_lo = INT_MAX;
+            s_hi = INT_MIN;
+        }
+        const int64_t i0 = tbase + static_cast<int64_t>(tid) * T;
+        // frame origin: the middle target (else the first valid one), rounded
+        // to FP32 -- unless the thread's targets spread farther from it than
+        // it lies from the centre (targets that are not nodes of one fiber),
+        // where the centre itself rounds no worse
+        const int64_t im = i0 + T / 2 < t_end ? i0 + T / 2 : i0;
+        float gx = 0.0f, gy = 0.0f, gz = 0.0f;
+        if (im < t_end) {
+            const double mx = tgt[3 * im + 0] - c0, my = tgt[3 * im + 1] - c1, mz = tgt[3 * im + 2] - c2;
+            double spread = 0.0;
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                const int64_t i = i0 + t;
+                if (i < t_end)
+                    spread = fmax(spread, fmax(fabs(tgt[3 * i] - c0 - mx),
+                                               fmax(fabs(tgt[3 * i + 1] - c1 - my), fabs(tgt[3 * i + 2] - c2 - mz))));
+            }
+            if (spread < fmax(fabs(mx), fmax(fabs(my), fabs(mz)))) {
+                gx = static_cast<float>(mx);
+                gy = static_cast<float>(my);
+                gz = static_cast<float>(mz);
+            }
+        }
+        float2 tx[NP], ty[NP], tz[NP];
+        int my_lo = INT_MAX, my_hi = INT_MIN;
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int64_t i = i0 + t;
+            double x = 0.0, y = 0.0, z = 0.0;
+            if (i < t_end) {
+                x = (tgt[3 * i + 0] - c0) - static_cast<double>(gx);
+                y = (tgt[3 * i + 1] - c1) - static_cast<double>(gy);
+                z = (tgt[3 * i + 2] - c2) - static_cast<double>(gz);
+                if (excl) {
+                    const int2 e = excl[i];
+                    if (e.y > e.x) {
+                        my_lo = min(my_lo, e.x);
+                        my_hi = max(my_hi, e.y);
+                    }
+                }
+            }
+            float *px = reinterpret_cast<float *>(&tx[t / 2]) + (t & 1);
+            float *py = reinterpret_cast<float *>(&ty[t / 2]) + (t & 1);
+            float *pz = reinterpret_cast<float *>(&tz[t / 2]) + (t & 1);
+            *px = static_cast<float>(x);
+            *py = static_cast<float>(y);
+            *pz = static_cast<float>(z);
+#pragma unroll
+            for (int v = 0; v < 6; ++v) sum_at(v, t) = 0.0f;
+        }
+        __syncthreads();
+        if (my_hi > my_lo) {
+            atomicMin(&s_lo, my_lo);
+            atomicMax(&s_hi, my_hi);
+        }
+        __syncthreads();
+        const int blo = s_lo, bhi = s_hi;
+
+        for (int64_t q = 0; q < len; ++q, ++it) {
+            const int stage = static_cast<int>(it & 1);
+            const bool ok = mbar_wait(&bars[stage], static_cast<uint32_t>((it >> 1) & 1));
+            if (!__syncthreads_and(ok)) {
+                failed = true;
+                break;
+            }
+            if (tid == 0 && it >= 1 && it + 1 < run.n_run) issue(it + 1);
+            int64_t j0;
+            int cnt;
+            run.src(it, j0, cnt);
+            const bool masked = bhi > blo && j0 < bhi && j0 + cnt > blo;
+            float2 ax[NP], ay[NP], az[NP];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) ax[p] = ay[p] = az[p] = make_float2(0.0f, 0.0f);
+            if (masked) {
+                // targets past the end (a ragged last block) carry an empty range
+                int2 ex[T];
+#pragma unroll
+                for (int t = 0; t < T; ++t) ex[t] = (excl && i0 + t < t_end) ? excl[i0 + t] : make_int2(0, 0);
+                tile_x2<T, true>(stage_ptr(stage, 0), stage_ptr(stage, 1), stage_ptr(stage, 2), cnt,
+                                 static_cast<int>(j0), gx, gy, gz, tx, ty, tz, ex, ax, ay, az);
+            } else {
+                tile_x2<T, false>(stage_ptr(stage, 0), stage_ptr(stage, 1), stage_ptr(stage, 2), cnt,
+                                  static_cast<int>(j0), gx, gy, gz, tx, ty, tz, nullptr, ax, ay, az);
+            }
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const float v[6] = {ax[p].x, ax[p].y, ay[p].x, ay[p].y, az[p].x, az[p].y};
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    const int t = 2 * p + (k & 1), comp = k >> 1;
+                    float sv = sum_at(comp, t), cv = sum_at(3 + comp, t);
+                    two_sum(sv, cv, v[k]);
+                    sum_at(comp, t) = sv;
+                    sum_at(3 + comp, t) = cv;
+                }
+            }
+        }
+        if (failed) break;
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int64_t i = i0 + t;
+            if (i >= t_end) continue;
+            const double ux = static_cast<double>(sum_at(0, t)) + static_cast<double>(sum_at(3, t));
+            const double uy = static_cast<double>(sum_at(1, t)) + static_cast<double>(sum_at(4, t));
+            const double uz = static_cast<double>(sum_at(2, t)) + static_cast<double>(sum_at(5, t));
+            if (work) {
+                double *o = out + 3 * i;
+                o[0] = (acc ? o[0] : 0.0) + scale * ux;
+                o[1] = (acc ? o[1] : 0.0) + scale * uy;
+                o[2] = (acc ? o[2] : 0.0) + scale * uz;
+            } else {
+                double *o = part + ((static_cast<int64_t>(blockIdx.x) + blk) * TB + tid * T + t) * 3;
+                o[0] = ux;
+                o[1] = uy;
+                o[2] = uz;
+            }
+        }
+    } while (it < run.n_run);
+    if (failed) {
+        if (tid == 0) {
+            atomicOr(status, DEV_ERR_TIMEOUT);
+            mbar_wait(&bars[0], 0);
+            mbar_wait(&bars[1], 0);
+        }
+    }
+}
+
 // ------------------------------------------------------------ float-float
 // Stokeslet sum in float-float ("double-single") arithmetic on the FP32 pipe:
 // every quantity is an unevaluated sum hi + lo of two floats, built from
@@ -950,9 +1225,20 @@ int num_sms()
 
 namespace {
 
+// The FP32 Stokeslet without hi/lo targets runs in packed pairs with
+// per-thread frames (k_stokeslet_x2); its sources carry the lo parts.
+bool packed_x2(int kind, int prec, bool hilo)
+{
+    return kind == PAIR_STOKESLET && prec == FS_SUM_FP32 && !hilo;
+}
+
 // Kernel instantiation for (kind, precision, hi/lo, targets per thread).
 const void *kernel_of(int kind, int prec, bool hilo, int tpt)
 {
+    if (packed_x2(kind, prec, hilo))
+        return tpt == 2 ? reinterpret_cast<const void *>(&k_stokeslet_x2<2>)
+                        : tpt == 4 ? reinterpret_cast<const void *>(&k_stokeslet_x2<4>)
+                                   : reinterpret_cast<const void *>(&k_stokeslet_x2<8>);
 #define FS_K(R, TT, K, HL) reinterpret_cast<const void *>(&k_pairsum<R, TT, K, HL>)
 #define FS_K_T(R, K, HL) (tpt == 2 ? FS_K(R, 2, K, HL) : tpt == 8 ? FS_K(R, 8, K, HL) : FS_K(R, 4, K, HL))
 #define FS_K_T64(K) (tpt == 1 ? FS_K(double, 1, K, false) : tpt == 4 ? FS_K(double, 4, K, false) \
@@ -974,10 +1260,29 @@ const void *kernel_of(int kind, int prec, bool hilo, int tpt)
 #undef FS_K
 }
 
+// Allow a kernel `smem` bytes of dynamic shared memory: beyond 48 KB per
+// CTA (static included) a launch needs the opt-in attribute.  Cached per
+// kernel at the largest size set so far.
+bool allow_smem(const void *k, size_t smem)
+{
+    static std::mutex mu;
+    static std::map<const void *, size_t> set;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = set.find(k);
+    if (it != set.end() && it->second >= smem) return true;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    set[k] = smem;
+    return true;
+}
+
 // Resident CTAs per SM of a kernel at kThreads threads and `smem` dynamic
 // shared memory (occupancy calculator, cached per kernel and size).
 int resident_ctas(const void *k, size_t smem)
 {
+    allow_smem(k, smem);
     static std::mutex mu;
     static std::map<std::pair<const void *, size_t>, int> cache;
     std::lock_guard<std::mutex> lk(mu);
@@ -1013,9 +1318,11 @@ SumPlan plan_pairsum(int kind, int64_t n_src, int64_t n_tgt, int sum_prec, bool 
     }
     p.threads = kThreads;
     p.tb = p.tpt * kThreads;
-    p.n_arr = ff ? (kind == PAIR_STRESSLET ? 6 : 4) : (kind == PAIR_STRESSLET ? 3 : 2) + (hilo ? 1 : 0);
+    p.n_arr = ff ? (kind == PAIR_STRESSLET ? 6 : 4)
+                 : (kind == PAIR_STRESSLET ? 3 : 2) + ((hilo || packed_x2(kind, sum_prec, hilo)) ? 1 : 0);
     p.v4 = (f32 || ff) ? sizeof(float4) : sizeof(double4_32a);
     p.smem = static_cast<size_t>(p.n_arr) * 2 * p.tile * p.v4;
+    if (packed_x2(kind, sum_prec, hilo)) p.smem += x2_sum_bytes(p.tpt);
     p.nb = (n_tgt + p.tb - 1) / p.tb;
     p.nt = (n_src + p.tile - 1) / p.tile;
     p.W = p.nb * p.nt;
@@ -1105,7 +1412,8 @@ fs_status pairsum(const PairSumArgs &a, void *scratch, size_t scratch_bytes, int
     k_bbox_center<<<1, 32, 0, st>>>(box, kBoxParts, a.n_src, center);
     FS_LAUNCH_CHECK();
     const unsigned pb = static_cast<unsigned>((a.n_src + 255) / 256);
-    const int lo_slot = hilo ? p.n_arr - 1 : 0;
+    const bool x2 = packed_x2(a.kind, prec, hilo);
+    const int lo_slot = (hilo || x2) ? p.n_arr - 1 : 0;
     if (ff)
         k_pack_ff<<<pb, 256, 0, st>>>(a.src_xyz, a.src_dens, a.kind == PAIR_STRESSLET ? a.src_w : nullptr,
                                       a.kind == PAIR_STRESSLET ? a.src_nrm : nullptr, a.n_src, center,
@@ -1140,8 +1448,12 @@ fs_status pairsum(const PairSumArgs &a, void *scratch, size_t scratch_bytes, int
         int *status = d_status;
         void *args[] = {&src, &n_src, &nt, &W, &G, &tgt, &excl, &n_tgt, &center, &out, &part, &scale, &accv,
                         &status, &work};
-        const cudaError_t e = cudaLaunchKernel(kernel_of(a.kind, prec, hilo, p.tpt), dim3(grid), dim3(kThreads),
-                                               args, p.smem, st);
+        const void *kern = kernel_of(a.kind, prec, hilo, p.tpt);
+        if (!allow_smem(kern, p.smem)) {
+            set_error("pairsum: cannot allow %zu bytes of shared memory", p.smem);
+            return FS_ECUDA;
+        }
+        const cudaError_t e = cudaLaunchKernel(kern, dim3(grid), dim3(kThreads), args, p.smem, st);
         if (e != cudaSuccess) {
             cudaGetLastError();
             set_error("pairsum: launch failed: %s", cudaGetErrorString(e));

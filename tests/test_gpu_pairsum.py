@@ -20,10 +20,16 @@ pytestmark = pytest.mark.gpu
 import paper_1602_05650_gb300 as fs  # noqa: E402
 
 FS_SUM_FF = 2
-# FS_SUM_FP32_PLAIN rounds the centred coordinates to FP32: |dr| <= 2^-24 |x|
-# per coordinate (|x| <= side / 2 = 5), i.e. ~5e-7 absolute, against pair
-# distances of ~0.05 and more for these point clouds: 1e-5 relative.
-TOL = {fs.FS_SUM_FP64: 1e-12, fs.FS_SUM_FP32: 1e-6, FS_SUM_FF: 5e-11, fs.FS_SUM_FP32_PLAIN: 1e-5}
+# FS_SUM_FP32_PLAIN keeps the coordinates of each thread's consecutive targets
+# in a frame at its middle target: on fiber nodes (the sums of the step) the
+# pair differences round relative to the fiber's extent, the accuracy of the
+# hi/lo sum (1e-6).  Uniformly random points are not spatially grouped, so
+# there the frame is the centre of the sources and the coordinates round to
+# 2^-24 |x| (|x| <= side / 2 = 5), ~5e-7 absolute against pair distances of
+# ~0.05 and more: 1e-5 relative.
+TOL = {fs.FS_SUM_FP64: 1e-12, fs.FS_SUM_FP32: 1e-6, FS_SUM_FF: 5e-11, fs.FS_SUM_FP32_PLAIN: 1e-6}
+TOL_RANDOM = dict(TOL)
+TOL_RANDOM[fs.FS_SUM_FP32_PLAIN] = 1e-5
 
 
 @pytest.fixture(scope="module")
@@ -55,7 +61,7 @@ def test_stokeslet_random_points(ctx, prec, n_src, n_tgt):
     tgt, _ = random_points(n_tgt, 2)
     got = gpu_stokeslet(ctx, src, wf, tgt, prec)
     ref = ok.stokeslet(tgt, src, wf, 1.3)
-    assert rel(got, ref) <= TOL[prec]
+    assert rel(got, ref) <= TOL_RANDOM[prec]
 
 
 @pytest.mark.parametrize("prec", [fs.FS_SUM_FP64, fs.FS_SUM_FP32, FS_SUM_FF, fs.FS_SUM_FP32_PLAIN])
@@ -77,7 +83,7 @@ def test_every_launch_shape_agrees(shape):
     h = fs.fs_create([], 1.0, 1e-3, 1.0, 1e-3, options=opt)
     s = wl.free_space(40, 32, 10.0, seed=4)
     fid = s.fiber_id()
-    for prec in (fs.FS_SUM_FP64, fs.FS_SUM_FP32, FS_SUM_FF):
+    for prec in (fs.FS_SUM_FP64, fs.FS_SUM_FP32, FS_SUM_FF, fs.FS_SUM_FP32_PLAIN):
         got = gpu_stokeslet(h, s.X, s.f_ext, s.X, prec, fid, fid)
         ref = ok.stokeslet(s.X, s.X, s.f_ext, 1.0, fid, fid)
         assert rel(got, ref) <= TOL[prec]
@@ -112,9 +118,11 @@ def test_cloud_size_sampled(ctx):
     rng = np.random.default_rng(0)
     idx = np.sort(rng.choice(s.n_points, 512, replace=False))
     ref = ok.stokeslet(s.X[idx], s.X, wf, 1.3, fid[idx], fid)
-    for prec in (fs.FS_SUM_FP32, fs.FS_SUM_FP64, FS_SUM_FF):
+    for prec in (fs.FS_SUM_FP32, fs.FS_SUM_FP64, FS_SUM_FF, fs.FS_SUM_FP32_PLAIN):
         got = gpu_stokeslet(ctx, s.X, wf, s.X, prec, fid, fid)
-        assert rel(got[idx], ref) <= TOL[prec]
+        err = rel(got[idx], ref)
+        print("cloud 65,536 sampled: precision %d rel err %.3e" % (prec, err))
+        assert err <= TOL[prec]
 
 
 @pytest.mark.parametrize("prec", [fs.FS_SUM_FP64, fs.FS_SUM_FP32, FS_SUM_FF])
