@@ -287,6 +287,19 @@ class System:
         """One implicit step: assemble, solve, read V and T (Sec. 3.2-3.3)."""
         b = self.rhs()
         u, its, res = self.gmres(b, tol, max_iter)
+        return self.result(u, its, res)
+
+    def exact_step(self) -> StepResult:
+        """The step with the exact solution of the assembled FP64 system
+        (oracle.exact: dense assembly, LU and refinement with double-double
+        residuals) instead of GMRES; small systems only."""
+        from . import exact
+        A, b = exact.assemble(self)
+        u, _ = exact.solve_refined(A, b)
+        return self.result(u, 0, 0.0)
+
+    def result(self, u: np.ndarray, its: int = 0, res: float = 0.0) -> StepResult:
+        """V, T, X+ (and the body's motion) from the unknowns u."""
         us, q = self._split(u)
         V = np.concatenate([fb.velocity_nodes(um) for fb, um in zip(self.fibers, us)]) \
             if self.fibers else np.zeros((0, 3))

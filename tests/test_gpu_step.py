@@ -194,3 +194,33 @@ def test_not_converged_reports_and_keeps_state():
     fs.fs_get_state(h, X=Xn)
     assert torch.equal(Xn, X)
     fs.fs_destroy(h)
+
+
+@pytest.mark.parametrize("prec,tol,gate_v,gate_x", [(fs.FS_FP64, 1e-12, 5e-8, 3e-11),
+                                                     (fs.FS_MIXED, 1e-10, 3e-7, 1.5e-10)])
+def test_trajectory_of_five_steps(prec, tol, gate_v, gate_x):
+    """Five consecutive steps, each side advancing its own state (the library
+    from its X+, the oracle from its X+): 24 curved fibers, 32 points, a
+    smooth load.  The two trajectories separate step by step: a difference
+    dX of the positions enters the next step's free-end rows as ~N^6 dX / dt
+    (measured gaps, FP64 path: V 4e-11, 1e-9, 6e-9, 8e-9, 2e-8 with X at
+    4e-14 .. 1e-11; mixed path: V up to 1e-7, X up to 5e-11).  Gates, held
+    at every step: FP64 V 5e-8, X 3e-11; mixed V 3e-7, X 1.5e-10."""
+    import copy
+    from tests.gpu_helpers import dev, make_ctx
+    s = gravity(wl.free_space(24, 32, 6.0, seed=8, curved_amp=0.05), (0.2, -0.1, -1.0))
+    h = make_ctx(s, prec=prec, tol=tol)
+    X = dev(s.X, torch)
+    fs.fs_set_state(h, X, dev(s.L, torch), dev(s.f_ext, torch))
+    V = torch.empty_like(X)
+    state = copy.deepcopy(s)
+    gaps = []
+    for step in range(5):
+        fs.fs_step(h)
+        fs.fs_get_state(h, V=V, X=X)
+        ref = system.from_suspension(state).step(tol=1e-13)
+        state.X = ref.X_new
+        gaps.append((rel(V.cpu().numpy(), ref.V), rel(X.cpu().numpy(), ref.X_new)))
+    fs.fs_destroy(h)
+    print("trajectory prec %d: " % prec + " ".join("V %.1e X %.1e" % g for g in gaps))
+    assert all(g[0] <= gate_v and g[1] <= gate_x for g in gaps)
