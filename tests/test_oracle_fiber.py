@@ -252,3 +252,24 @@ def test_spectral_convergence_in_N():
         eT.append(np.linalg.norm(T - Tr) / np.linalg.norm(Tr))
     assert eV[1] < eV[0] / 100 and eV[2] < eV[1] / 100 and eV[2] < 1e-8, eV
     assert eT[1] < eT[0] / 30 and eT[2] < eT[1] / 30 and eT[2] < 1e-5, eT
+
+
+def test_multistep_growth_of_a_curved_end_fiber_at_64_points():
+    """The divergence of multi-step runs belongs to the discrete method, not
+    to an implementation: one free curved fiber (the workloads' recipe, whose
+    ends carry curvature against Eq. bc-free), a uniform load, dt = 1e-3,
+    stepped by the oracle alone.  At N = 64 its tension grows about 600-fold
+    in seven steps (17 -> 1e4); the same fiber at N = 32 keeps it within 10 % (it relaxes, 2.8 -> 2.7)."""
+    def run(N):
+        s = wl.free_space(1, N, 5.0, seed=0, curved_amp=0.05, L_range=(2.5, 3.0))
+        s.f_ext = np.tile(np.random.default_rng(0).normal(size=3), (N, 1))
+        X, T = s.X.copy(), []
+        for _ in range(7):
+            sub = wl.Suspension(s.n_per_fiber, X, s.L, s.f_ext, s.mu, s.eps, s.E, s.dt)
+            r = system.from_suspension(sub).step(tol=1e-12)
+            X = r.X_new
+            T.append(np.abs(r.T).max())
+        return T
+    T64, T32 = run(64), run(32)
+    assert T64[-1] > 100.0 * T64[0]
+    assert max(T32) < 1.1 * min(T32)
