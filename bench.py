@@ -588,22 +588,22 @@ def run_workload(args, ws, rank, local, fs, torch):
         print(json.dumps(out), flush=True)
 
 
-def run_serve(args, ws, rank, local, fs, torch):
-    """Serving: independent systems (8..512 fibers, 16/32/64 points, mixed
-    precision, tol 1e-8) submitted with Poisson arrivals to an fs_server;
-    reports throughput and latency percentiles, and the same systems stepped
-    together in one batched context for comparison."""
-    systems = wl.batched(args.serve, seed=100 + rank)
-    rng = np.random.default_rng(rank)
-    gaps = rng.exponential(1.0 / args.rate, size=len(systems)) if args.rate > 0 else np.zeros(len(systems))
-    sv = fs.fs_server_create(int(args.budget_gb * (1 << 30)), max_slots=args.slots, device=local)
+def serve_once(fs, systems, rate: float, slots: int, budget_gb: float, device: int, seed: int):
+    """Submit `systems` (mixed precision, tol 1e-8) to a fresh fs_server with
+    Poisson arrivals at `rate` per second (0: all at once); returns the wall
+    time, per-request latency and queue times (ms), and the server's batch
+    count.  Three warm-up requests first (kernels loaded, tables built)."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, size=len(systems)) if rate > 0 else np.zeros(len(systems))
+    sv = fs.fs_server_create(int(budget_gb * (1 << 30)), max_slots=slots, device=device)
 
     def submit(s):
         return fs.fs_submit(sv, s.n_per_fiber, s.X, s.L, s.mu, s.eps, s.E, s.dt, f_ext=s.f_ext,
                             prec=fs.FS_MIXED, tol=1e-8)
 
-    for s in systems[:3]:   # warm-up: kernels loaded, op tables built once
+    for s in systems[:3]:
         fs.fs_server_wait(sv, submit(s))
+    b0 = fs.fs_server_batches(sv)
     t0 = time.perf_counter()
     tickets, due = [], t0
     for s, g in zip(systems, gaps):
@@ -613,9 +613,42 @@ def run_serve(args, ws, rank, local, fs, torch):
         tickets.append(submit(s))
     res = [fs.fs_server_wait(sv, t) for t in tickets]
     wall = time.perf_counter() - t0
+    batches = fs.fs_server_batches(sv) - b0
     fs.fs_server_destroy(sv)
     lat = np.array([r["info"].t_ms[6] for r in res])
     que = np.array([r["info"].t_ms[5] for r in res])
+    per_batch = np.array([r["info"].t_ms[7] for r in res])
+    return {"wall_s": wall, "req_per_s": len(systems) / wall, "batches": int(batches),
+            "requests_per_batch_mean": float(per_batch.mean()),
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
+                           "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
+            "queue_ms": {"p50": float(np.percentile(que, 50)), "p99": float(np.percentile(que, 99))}}
+
+
+def serving_leg(fs, local, rank, n_req: int = 48, slots: int = 64, budget_gb: float = 64.0):
+    """The headline line's serving figures: n_req independent requests drawn
+    from the batched distribution (8..512 fibers, 16/32/64 points); a burst
+    gives the saturated rate, then Poisson arrivals at 0.7 x that rate give
+    p50 / p99 latency."""
+    systems = wl.batched(n_req, seed=200 + rank)
+    burst = serve_once(fs, systems, 0.0, slots, budget_gb, local, seed=rank)
+    rate = 0.7 * burst["req_per_s"]
+    pois = serve_once(fs, systems, rate, slots, budget_gb, local, seed=rank + 1)
+    return {"requests": n_req, "points_total": int(sum(x.n_points for x in systems)),
+            "distribution": "fibers log-uniform in [8, 512], N in {16, 32, 64}, mixed, tol 1e-8",
+            "saturated_req_per_s": burst["req_per_s"], "arrival_rate_per_s": rate,
+            "req_per_s": pois["req_per_s"], "p50_ms": pois["latency_ms"]["p50"],
+            "p99_ms": pois["latency_ms"]["p99"], "batches": pois["batches"],
+            "requests_per_batch_mean": pois["requests_per_batch_mean"], "burst": burst}
+
+
+def run_serve(args, ws, rank, local, fs, torch):
+    """Serving: independent systems (8..512 fibers, 16/32/64 points, mixed
+    precision, tol 1e-8) submitted with Poisson arrivals to an fs_server;
+    reports throughput and latency percentiles, and the same systems stepped
+    together in one batched context for comparison."""
+    systems = wl.batched(args.serve, seed=100 + rank)
+    out = serve_once(fs, systems, args.rate, args.slots, args.budget_gb, local, seed=rank)
 
     # the same systems in one batched context (fs_create_batch): one step for all
     opt = fs.fs_options_default()
@@ -638,15 +671,13 @@ def run_serve(args, ws, rank, local, fs, torch):
     fs.fs_destroy(h)
     if rank == 0:
         pts = sum(x.n_points for x in systems)
-        print(json.dumps({
+        out.update({
             "mode": "serve", "requests": len(systems), "points_total": int(pts),
             "fibers": [int(min(x.n_fibers for x in systems)), int(max(x.n_fibers for x in systems))],
             "slots": args.slots, "budget_gb": args.budget_gb, "arrival_rate_per_s": args.rate,
-            "throughput_req_per_s": len(systems) / wall, "wall_s": wall,
-            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
-                           "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
-            "queue_ms": {"p50": float(np.percentile(que, 50)), "p99": float(np.percentile(que, 99))},
-            "batched_one_context": {"step_s": min(bt), "req_per_s": len(systems) / min(bt)}}), flush=True)
+            "throughput_req_per_s": out["req_per_s"],
+            "batched_one_context": {"step_s": min(bt), "req_per_s": len(systems) / min(bt)}})
+        print(json.dumps(out), flush=True)
 
 
 def main():
@@ -659,6 +690,7 @@ def main():
                     help="GMRES iterations assumed for the reference arm's extrapolation")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg of the headline line")
     ap.add_argument("--kernel", choices=["stokeslet_fp32", "stokeslet_fp64", "stokeslet_ff", "stokeslet_fp32_plain"],
                     default=None,
                     help="time only the direct-sum kernel on the cloud (fs_stokeslet_apply)")
@@ -792,6 +824,9 @@ def main():
         fp64 = {"ms_per_step": a0.elapsed_time(a1), "iters": inf64.iters, "resid": inf64.resid}
         fs.fs_destroy(h64)
 
+    # serving: continuous batching under Poisson arrivals (p50 / p99 latency)
+    serve = None if args.no_serve else serving_leg(fs, local, rank)
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -823,7 +858,8 @@ def main():
                 "launch_ms_avg": total_ms / launches_d if launches_d else None,
                 "measured_fp32_fma_tflops": fp32_peak / 1e12,
                 "measured_fp64_fma_tflops": fp64_peak / 1e12}
-    st32 = per_class["stokeslet_fp32"]
+    # the Stokeslet pair rate of the step's FP32 sum (the dominant kernel)
+    st32 = per_class["stokeslet_fp32_plain"]
     pairs_per_s = st32["pairs"] / (st32["ms"] * 1e-3) if st32["ms"] > 0 else None
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
@@ -851,7 +887,10 @@ def main():
                                           for i in infos]},
         "fp64_path": fp64,
         "mixed_speedup_vs_fp64": (fp64["ms_per_step"] / ms) if fp64 else None,
+        "serving": serve,
     }
+    if serve:
+        line.update({"p50_ms": serve["p50_ms"], "p99_ms": serve["p99_ms"], "req_per_s": serve["req_per_s"]})
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

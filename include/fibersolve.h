@@ -180,7 +180,8 @@ typedef struct {
                                (outer) GMRES recurrence, accurate operator */
     double t_ms[8];         /* host wall-clock ms: [0] right-hand side [1] geometry and
                                preconditioner build [2] solve [3] update [4] total;
-                               others reserved (filled when info is requested) */
+                               serving only: [5] queued [6] submit to done [7] requests
+                               in the batch; (filled when info is requested) */
     int64_t pairs;          /* Stokeslet pairs evaluated */
 } fs_step_info;
 
@@ -432,16 +433,22 @@ size_t fs_estimate_bytes(int32_t n_fibers, const int32_t *points_per_fiber, int3
 /* Device bytes the context holds now (its arrays and its scratch). */
 fs_status fs_device_bytes(const fs_ctx *ctx, size_t *bytes);
 
-/* ------------------------------------------------------------------ serving
- * Independent step requests admitted continuously.  (No counterpart in the
- * paper: a serving front end over fs_create / fs_step.)  A server owns
- * max_slots worker threads on one device, each with its own CUDA stream;
- * submitted requests wait in a FIFO and the head is admitted when a worker
- * is free and fs_estimate_bytes of the request fits what the HBM budget has
- * left.  An admitted request gets its own context, runs one fs_step and
- * writes the result to the caller's host arrays; its arithmetic is that of
- * fs_step on the same input alone.  Requests running at the same time
- * overlap on the GPU. */
+/* Serving (continuous batching): independent step requests submitted at any
+ * time.  The server allocates its HBM budget ONCE at creation and runs two
+ * engines, each with its own CUDA stream.  A free engine takes the queue head
+ * and every queued request that can share a step with it -- same mu, eps, E,
+ * dt, precision and tolerance, free space, at most max_slots requests, as long
+ * as the batch's memory estimate fits the largest free piece of the budget --
+ * and runs ONE batched implicit step for them (every launch covers all of the
+ * batch's systems, each system with its own GMRES; fs_create_batch).
+ * Requests that arrive meanwhile join the next batch, so the two engines'
+ * batches overlap on the GPU.  No request allocates device memory: its batch
+ * context carves its buffers from the budget, and the piece goes back when
+ * the step ends.  A request with a boundary runs in a batch of its own.  A
+ * request's arithmetic does not depend on its batch (far fields per system,
+ * per-system reductions), so it gives the same bits alone and in any mix;
+ * they agree with fs_step on the same input within the solve tolerance
+ * (fs_step sums one system's far field in another order). */
 typedef struct fs_server fs_server;
 
 typedef struct fs_request {
@@ -459,8 +466,9 @@ typedef struct fs_request {
     double *out_T;                     /* [N_tot] tension, or NULL */
 } fs_request;
 
-/* Start a server on `device` with max_slots in [1, 256] workers and a budget
- * of hbm_budget_bytes of device memory for the requests' contexts. */
+/* Start a server on `device`: allocates hbm_budget_bytes of device memory
+ * (FS_ENOMEM if it cannot) and starts two engine threads; max_slots in
+ * [1, 4096] is the largest number of requests one batched step admits. */
 fs_status fs_server_create(fs_server **out, size_t hbm_budget_bytes, int32_t max_slots, int32_t device);
 
 /* Queue a request.  All its input arrays are copied before the call returns;
@@ -472,8 +480,12 @@ fs_status fs_submit(fs_server *sv, const fs_request *request, uint64_t *ticket);
 /* Non-blocking completion check: FS_EAGAIN while queued or running;
  * otherwise the request's own status (FS_OK, or the error of fs_create /
  * fs_step with its message in fs_last_error()) and the ticket is released.
- * info (may be NULL) receives fs_step's info with t_ms[5] = time queued and
- * t_ms[6] = submit-to-done latency, in milliseconds. */
+ * info (may be NULL) receives the batch step's info with the request's own
+ * iterations, sweeps and residual, t_ms[5] = time queued and t_ms[6] =
+ * submit-to-done latency in milliseconds, t_ms[7] = requests in its batch.
+ * A request whose system did not converge reports FS_ENOTCONV (its outputs
+ * still hold the last iterate's step); the others of its batch are not
+ * affected. */
 fs_status fs_poll(fs_server *sv, uint64_t ticket, fs_step_info *info);
 
 /* Blocking form of fs_poll: waits up to timeout_s seconds; FS_ETIMEOUT if the
@@ -485,8 +497,11 @@ fs_status fs_server_wait(fs_server *sv, uint64_t ticket, fs_step_info *info, dou
 fs_status fs_server_stats(fs_server *sv, int32_t *pending, int32_t *running, size_t *bytes_in_use,
                           int64_t *completed);
 
-/* Finish the running requests, drop the queued ones (their tickets become
- * invalid) and join the workers.  Running requests still write their output
+/* Batched steps the server has started since creation. */
+fs_status fs_server_batches(fs_server *sv, int64_t *batches);
+
+/* Finish the running batches, drop the queued requests (their tickets
+ * become invalid), join the engines and free the budget's memory.  Running requests still write their output
  * arrays before this returns.  No other call on sv may be in progress or
  * follow it (a thread blocked in fs_server_wait on sv must return first). */
 void fs_server_destroy(fs_server *sv);

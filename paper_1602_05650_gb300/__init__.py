@@ -21,7 +21,8 @@ __all__ = ["fs_options_default", "fs_create", "fs_create_batch", "fs_batch_info"
            "fs_stokeslet_apply", "fs_stresslet_apply", "fs_surface_apply", "fs_build_precond",
            "fs_step", "fs_sizes", "fs_last_error", "fs_kernel_stats", "fs_kernel_launches",
            "fs_probe_fma", "fs_estimate_bytes", "fs_device_bytes", "fs_server_create", "fs_submit",
-           "fs_poll", "fs_server_wait", "fs_server_stats", "fs_server_destroy", "Server", "FsError",
+           "fs_poll", "fs_server_wait", "fs_server_stats", "fs_server_batches", "fs_server_destroy", "Server",
+           "FsError",
            "fs_set_growth", "fs_get_lengths", "fs_get_unknowns", "fs_dynamic_instability",
            "FS_FP64", "FS_MIXED",
            "FS_SUM_FP32", "FS_SUM_FP64", "FS_SUM_FF", "FS_SUM_FP32_PLAIN"]
@@ -471,6 +472,12 @@ def fs_server_stats(sv: Server):
     _check(_native.load().fs_server_stats(sv.ptr, ctypes.byref(pe), ctypes.byref(ru), ctypes.byref(by),
                                           ctypes.byref(co)), "fs_server_stats")
     return {"pending": pe.value, "running": ru.value, "bytes_in_use": int(by.value), "completed": co.value}
+
+
+def fs_server_batches(sv: Server) -> int:
+    n = ctypes.c_int64()
+    _check(_native.load().fs_server_batches(sv.ptr, ctypes.byref(n)), "fs_server_batches")
+    return int(n.value)
 
 
 def fs_server_destroy(sv: Server):

@@ -103,6 +103,7 @@ SIGNATURES = {
     "fs_server_stats": (c_int32, [P, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32),
                                   ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(c_int64)]),
     "fs_server_destroy": (None, [P]),
+    "fs_server_batches": (c_int32, [P, ctypes.POINTER(c_int64)]),
     "fs_last_error": (ctypes.c_char_p, []),
     "fs_status_str": (ctypes.c_char_p, [c_int32]),
 }

@@ -18,9 +18,37 @@ void set_error(const char *fmt, ...)
     va_end(ap);
 }
 
+void *Pool::take_dev(size_t bytes)
+{
+    const size_t at = (dev_used + 255) & ~size_t(255);
+    if (at + bytes > dev_cap) return nullptr;
+    dev_used = at + bytes;
+    return dev + at;
+}
+
+void *Pool::take_host(size_t bytes)
+{
+    const size_t at = (host_used + 255) & ~size_t(255);
+    if (at + bytes > host_cap) return nullptr;
+    host_used = at + bytes;
+    return host + at;
+}
+
 fs_status Scratch::reserve(size_t need, cudaStream_t st)
 {
     if (need <= bytes) return FS_OK;
+    if (pool) {
+        // the region was sized for the largest sum; an earlier, smaller piece
+        // stays unused until the region is given back
+        void *p = pool->take_dev(need);
+        if (!p) {
+            set_error("scratch: %zu bytes exceed the preallocated region", need);
+            return FS_ENOMEM;
+        }
+        ptr = p;
+        bytes = need;
+        return FS_OK;
+    }
     if (ptr) {
         FS_CUDA(cudaStreamSynchronize(st));
         FS_CUDA(cudaFree(ptr));
@@ -40,7 +68,7 @@ fs_status Scratch::reserve(size_t need, cudaStream_t st)
 
 void Scratch::release()
 {
-    if (ptr) cudaFree(ptr);
+    if (ptr && !pool) cudaFree(ptr);
     ptr = nullptr;
     bytes = 0;
 }
@@ -145,7 +173,8 @@ fs_status fs_options_default(fs_options *o)
 static fs_status create_impl(fs_ctx **out, int32_t n_systems, const int32_t *fps, int32_t n_fibers,
                              const int32_t *ppf, double mu, double eps, double E, double dt,
                              const fs_boundary *boundary, const fs_options *opt, void *cuda_stream,
-                             const fs_body *body = nullptr, const int32_t *minus_end = nullptr)
+                             const fs_body *body = nullptr, const int32_t *minus_end = nullptr,
+                             Pool *pool = nullptr, bool serving = false)
 {
     if (!out) {
         set_error("fs_create: out is NULL");
@@ -207,6 +236,9 @@ static fs_status create_impl(fs_ctx **out, int32_t n_systems, const int32_t *fps
     c->E = E;
     c->dt = dt;
     if (opt) c->opt = *opt; else fs_options_default(&c->opt);
+    c->pool = pool;
+    c->scratch.pool = c->tree_scratch.pool = pool;
+    c->worklist = c->partial_ok = serving;
     fs_status s = context_init(c, n_systems, fps, n_fibers, ppf, boundary, body, minus_end);
     if (s != FS_OK) {
         context_free(c);
@@ -216,6 +248,20 @@ static fs_status create_impl(fs_ctx **out, int32_t n_systems, const int32_t *fps
     *out = c;
     return FS_OK;
 }
+
+}  // extern "C"
+
+namespace fs {
+fs_status create_serving(fs_ctx **out, int32_t n_systems, const int32_t *fps, int32_t n_fibers, const int32_t *ppf,
+                         double mu, double eps, double E, double dt, const fs_boundary *boundary,
+                         const fs_options *opt, void *cuda_stream, Pool *pool)
+{
+    return create_impl(out, n_systems, fps, n_fibers, ppf, mu, eps, E, dt, boundary, opt, cuda_stream, nullptr,
+                       nullptr, pool, true);
+}
+}  // namespace fs
+
+extern "C" {
 
 fs_status fs_create(fs_ctx **out, int32_t n_fibers, const int32_t *ppf, double mu, double eps,
                     double E, double dt, const fs_boundary *boundary, const fs_options *opt,

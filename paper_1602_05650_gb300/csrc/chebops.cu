@@ -20,6 +20,9 @@
 // Velocity basis: I^4 T_0 .. I^4 T_{N-5}, T_0..T_3; tension basis: I^2 T_0 ..
 // I^2 T_{N-3}, T_0, T_1 (I^m: m-fold integral from alpha = -1).
 #include <cmath>
+#include <map>
+#include <memory>
+#include <mutex>
 
 #include "context.h"
 
@@ -88,9 +91,33 @@ Vec integ_m(Vec c, int m)
     return c;
 }
 
+std::vector<double> compute_ops(int N);
+
 }  // namespace
 
+// The tables depend on N only and take long-double work to build: built once
+// per N per process (every context, batch and serving request reuses them).
 std::vector<double> build_ops(int N)
+{
+    static std::mutex mu;
+    static std::map<int, std::shared_ptr<const std::vector<double>>> cache;
+    std::shared_ptr<const std::vector<double>> t;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(N);
+        if (it != cache.end()) t = it->second;
+    }
+    if (!t) {
+        auto built = std::make_shared<const std::vector<double>>(compute_ops(N));
+        std::lock_guard<std::mutex> lk(mu);
+        t = cache.emplace(N, built).first->second;
+    }
+    return *t;
+}
+
+namespace {
+
+std::vector<double> compute_ops(int N)
 {
     const OpsLayout lay(N);
     std::vector<double> A(lay.total, 0.0);
@@ -193,5 +220,7 @@ std::vector<double> build_ops(int N)
     }
     return A;
 }
+
+}  // namespace
 
 }  // namespace fs

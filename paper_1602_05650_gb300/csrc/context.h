@@ -185,6 +185,9 @@ struct fs_ctx {
     fs::Profiler prof;            // CUDA-event records (opt.profile)
     int64_t pairs_last = 0;
     size_t dev_bytes = 0;         // device memory allocated by the context (without scratch)
+    fs::Pool *pool = nullptr;     // preallocated region for every buffer (serving), or nullptr
+    bool worklist = false;        // far fields always per system (work-list mode), also for one system
+    bool partial_ok = false;      // batch step: update every system, report convergence per system
 
     fs::FiberTable table() const;
 };
@@ -193,6 +196,13 @@ namespace fs {
 fs_status context_init(fs_ctx *c, int S, const int32_t *fibers_per_system, int M, const int32_t *ppf,
                        const fs_boundary *b, const fs_body *body = nullptr, const int32_t *minus_end = nullptr);
 void context_free(fs_ctx *c);
+// A context for a serving batch: n_systems independent systems (or one with a
+// boundary), every buffer carved from `pool`, far fields per system even for
+// one system (a request's arithmetic does not depend on the batch it runs
+// in), and a step that updates every system whatever the others do.
+fs_status create_serving(fs_ctx **out, int32_t n_systems, const int32_t *fps, int32_t n_fibers, const int32_t *ppf,
+                         double mu, double eps, double E, double dt, const fs_boundary *boundary,
+                         const fs_options *opt, void *cuda_stream, Pool *pool);
 size_t estimate_bytes(int M, const int32_t *ppf, int n_surf, const fs_options &opt);
 // FS_EINVAL (with the message prefixed by `who`) unless every field of the
 // options is in its documented range

@@ -45,9 +45,23 @@ enum : int {
 
 // ---------------------------------------------------------------- scratch
 // Grow-only device buffer owned by a context.
+// A region of preallocated memory a context draws all of its buffers from
+// instead of cudaMalloc / cudaMallocHost (serving: the server owns the
+// memory, contexts only carve it).  Bump allocation, 256-byte pieces; the
+// region is given back as a whole by its owner.
+struct Pool {
+    char *dev = nullptr;
+    size_t dev_cap = 0, dev_used = 0;
+    char *host = nullptr;   // pinned host memory
+    size_t host_cap = 0, host_used = 0;
+    void *take_dev(size_t bytes);    // nullptr when the region is exhausted
+    void *take_host(size_t bytes);
+};
+
 struct Scratch {
     void *ptr = nullptr;
     size_t bytes = 0;
+    Pool *pool = nullptr;   // draw from this region instead of cudaMalloc
     fs_status reserve(size_t need, cudaStream_t st);
     void release();
 };

@@ -1407,10 +1407,17 @@ fs_status pairsum(const PairSumArgs &a, void *scratch, size_t scratch_bytes, int
         set_error("pairsum: scratch too small (%zu > %zu bytes)", cv.used, scratch_bytes);
         return FS_EINVAL;
     }
-    k_bbox_part<<<kBoxParts, 256, 0, st>>>(a.src_xyz, a.n_src, box);
-    FS_LAUNCH_CHECK();
-    k_bbox_center<<<1, 32, 0, st>>>(box, kBoxParts, a.n_src, center);
-    FS_LAUNCH_CHECK();
+    if (work) {
+        // independent systems: the coordinates are not centred on a box of
+        // all of them, so that each system's sums do not depend on the
+        // others (the kernels' frames and lo parts keep the accuracy)
+        FS_CUDA(cudaMemsetAsync(center, 0, 3 * sizeof(double), st));
+    } else {
+        k_bbox_part<<<kBoxParts, 256, 0, st>>>(a.src_xyz, a.n_src, box);
+        FS_LAUNCH_CHECK();
+        k_bbox_center<<<1, 32, 0, st>>>(box, kBoxParts, a.n_src, center);
+        FS_LAUNCH_CHECK();
+    }
     const unsigned pb = static_cast<unsigned>((a.n_src + 255) / 256);
     const bool x2 = packed_x2(a.kind, prec, hilo);
     const int lo_slot = (hilo || x2) ? p.n_arr - 1 : 0;

@@ -36,11 +36,35 @@ __global__ void k_add(double *__restrict__ x, const double *__restrict__ e, int6
 
 unsigned blocks_for(int64_t n) { return static_cast<unsigned>((n + 255) / 256); }
 
+// Pinned host buffer: from the context's region when it has one.
+fs_status pinned_alloc(fs_ctx *c, double **p, size_t n)
+{
+    if (c->pool) {
+        *p = static_cast<double *>(c->pool->take_host(n * sizeof(double)));
+        if (!*p) {
+            set_error("pinned host buffer of %zu bytes exceeds the preallocated region", n * sizeof(double));
+            return FS_ENOMEM;
+        }
+        return FS_OK;
+    }
+    FS_CUDA(cudaMallocHost(p, n * sizeof(double)));
+    return FS_OK;
+}
+
 template <class T>
 fs_status dalloc(fs_ctx *c, T **p, size_t n)
 {
     *p = nullptr;
     if (n == 0) return FS_OK;
+    if (c->pool) {
+        *p = static_cast<T *>(c->pool->take_dev(n * sizeof(T)));
+        if (!*p) {
+            set_error("device allocation of %zu bytes exceeds the preallocated region", n * sizeof(T));
+            return FS_ENOMEM;
+        }
+        c->dev_bytes += n * sizeof(T);
+        return FS_OK;
+    }
     if (cudaMalloc(reinterpret_cast<void **>(p), n * sizeof(T)) != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
@@ -255,7 +279,7 @@ fs_status far_field(fs_ctx *c, int sum_prec, bool hilo, const std::vector<int> *
     a.shape_override = c->opt.tile_override;
     std::vector<int4> groups;
     double pairs = 0.0;
-    if (c->S > 1 && act) {
+    if ((c->S > 1 || c->worklist) && act) {
         for (int s : *act) {
             const int lo = static_cast<int>(c->sys_node_ptr[s]), hi = static_cast<int>(c->sys_node_ptr[s + 1]);
             groups.push_back(make_int4(lo, hi, lo, hi));
@@ -648,7 +672,7 @@ fs_status context_init(fs_ctx *c, int S, const int32_t *fps, int M, const int32_
     c->sys_conv.assign(c->S, 0);
     FS_TRY(dalloc(c, &c->d_status, 1));
     FS_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
-    FS_CUDA(cudaMallocHost(&c->h_pinned, 4096 * sizeof(double)));
+    FS_TRY(pinned_alloc(c, &c->h_pinned, 4096));
     if (M == 0 && !c->body.on) return FS_OK;
     if (M > 0) FS_TRY(fiber_arrays(c, M, ppf, kp, zp));
     if (c->body.on) {
@@ -783,9 +807,9 @@ fs_status krylov_arrays(fs_ctx *c)
     FS_TRY(dalloc(c, &c->d_ich, static_cast<size_t>(c->chunk_cap)));
     FS_TRY(dalloc(c, &c->d_isch, static_cast<size_t>(c->S)));
     FS_TRY(dalloc(c, &c->d_ikk, static_cast<size_t>(c->S)));
-    FS_CUDA(cudaFreeHost(c->h_pinned));
+    if (!c->pool) FS_CUDA(cudaFreeHost(c->h_pinned));
     c->h_pinned = nullptr;
-    FS_CUDA(cudaMallocHost(&c->h_pinned, c->S * SHi * sizeof(double)));
+    FS_TRY(pinned_alloc(c, &c->h_pinned, c->S * SHi));
     if (c->opt.prec == FS_MIXED) {
         c->okdim = 17;   // outer (flexible) restart length 16
         const size_t SHo = 4 * size_t(c->okdim) + 8;
@@ -798,7 +822,7 @@ fs_status krylov_arrays(fs_ctx *c)
         FS_TRY(dalloc(c, &c->d_och, static_cast<size_t>(c->chunk_cap)));
         FS_TRY(dalloc(c, &c->d_osch, static_cast<size_t>(c->S)));
         FS_TRY(dalloc(c, &c->d_okk, static_cast<size_t>(c->S)));
-        FS_CUDA(cudaMallocHost(&c->oh_pinned, c->S * SHo * sizeof(double)));
+        FS_TRY(pinned_alloc(c, &c->oh_pinned, c->S * SHo));
     }
     return FS_OK;
 }
@@ -927,10 +951,13 @@ void context_free(fs_ctx *c)
                     c->d_x, c->d_r, c->d_w, c->d_e, c->d_pb, c->d_obasis, c->d_oz, c->d_oh, c->d_opart, c->d_ow, c->d_or, c->d_work, c->d_ich, c->d_isch, c->d_ikk, c->d_och, c->d_osch, c->d_okk, c->d_h, c->d_part, c->surf.y, c->surf.nrm,
                     c->surf.w, c->surf.diag, c->d_usurf, c->surf.A, c->surf.tmp, c->surf.flux, c->surf.excl,
                     c->body.rb, c->body.attach, c->body.att_list};
-    for (void *p : ptrs)
-        if (p) cudaFree(p);
-    if (c->h_pinned) cudaFreeHost(c->h_pinned);
-    if (c->oh_pinned) cudaFreeHost(c->oh_pinned);
+    // buffers carved from a preallocated region go back with the region
+    if (!c->pool) {
+        for (void *p : ptrs)
+            if (p) cudaFree(p);
+        if (c->h_pinned) cudaFreeHost(c->h_pinned);
+        if (c->oh_pinned) cudaFreeHost(c->oh_pinned);
+    }
     c->oh_pinned = nullptr;
     c->prof.release_all();
     for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
@@ -1152,7 +1179,9 @@ fs_status fs_step(fs_ctx *c, fs_step_info *info)
         info->resid = rel;
         info->pairs = c->pairs_last;
     }
-    if (!converged) {
+    // a serving batch updates every system and reports convergence per
+    // system (fs_batch_info); the others are not held back by one that failed
+    if (!converged && !c->partial_ok) {
         if (info) {
             tms[4] = ms_since(t0);
             std::memcpy(info->t_ms, tms, sizeof(tms));
