@@ -315,13 +315,17 @@ def run_workload(args, ws, rank, local, fs, torch):
         else:
             systems = wl.batched(256, seed=rank)
         res = {}
-        for name, prec in (("mixed", fs.FS_MIXED), ("fp64", fs.FS_FP64)):
-            if args.workload == "batched" and name == "fp64":
-                continue
+        legs = (("mixed", fs.FS_MIXED, 0), ("fp64", fs.FS_FP64, 0))
+        if args.workload == "batched":
+            # the host-driven cycles (kernel timings) and the graph cycles
+            # (one graph launch per restart cycle; event records off)
+            legs = (("mixed", fs.FS_MIXED, 0), ("mixed_graph", fs.FS_MIXED, 1))
+        for name, prec, graph in legs:
             opt = fs.fs_options_default()
             opt.prec = prec
             opt.tol = 1e-8
-            opt.profile = 1
+            opt.profile = 0 if graph else 1
+            opt.use_graph = graph
             if args.workload == "confined":
                 h = fs.fs_create(s.n_per_fiber, s.mu, s.eps, s.E, s.dt, boundary=s.boundary, options=opt,
                                  stream=stream)
@@ -346,6 +350,7 @@ def run_workload(args, ws, rank, local, fs, torch):
             out["surface_nodes"] = int(s.boundary.nodes.shape[0])
         else:
             out["systems_per_s"] = len(systems) * res["mixed"]["steps_per_s"]
+            out["systems_per_s_graph"] = len(systems) * res["mixed_graph"]["steps_per_s"]
             out["fibers"] = [int(min(x.n_fibers for x in systems)), int(max(x.n_fibers for x in systems))]
     elif args.workload == "sediment":
         # Sec. 4.3: the four clouds (1,024 fibers x 16 points, L/R0 = 0.15,

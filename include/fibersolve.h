@@ -115,7 +115,15 @@ typedef struct {
                                solves of the flexible GMRES) (default 1e-6) */
     double delta_over_L;    /* regularisation delta of K_delta as a fraction of L (default 0.01) */
     int32_t lsb;            /* 1 = local slender-body theory: drop K_delta (default 0) */
-    int32_t use_graph;      /* reserved, must be 0: CUDA graph capture is not implemented */
+    int32_t use_graph;      /* 1 = every restart cycle of the (inner) GMRES runs as ONE CUDA
+                               graph launch: a conditional WHILE node whose body is one
+                               iteration (operator, CGS2, norm, the Givens rotations of every
+                               system on the device, which also set the loop condition), so
+                               the host synchronises once per cycle instead of once per
+                               iteration; graphs are instantiated once per launch shape and
+                               reused.  Applies with the direct far field and profile = 0;
+                               the flexible outer GMRES (relax = 0) keeps the host path.
+                               Same arithmetic as 0 (default 0) */
     int32_t tile_override;  /* direct-sum launch shape: 0 = the shape measured fastest on
                                GB300 for each precision (targets per thread: FP32 8,
                                float-float 4, FP64 2; grid from the occupancy
@@ -199,7 +207,7 @@ fs_status fs_options_default(fs_options *opt);
  * out of range or a field of opt is outside its documented values (prec not
  * FS_FP64/FS_MIXED, tol or inner_tol outside (0, 1), max_iter or max_refine
  * < 1, restart outside 1..250, delta_over_L negative, lsb/relax/profile not
- * 0 or 1, use_graph not 0, tile_override outside 0..3, bad tree options). */
+ * 0 or 1, use_graph not 0 or 1, tile_override outside 0..3, bad tree options). */
 fs_status fs_create(fs_ctx **out, int32_t n_fibers, const int32_t *points_per_fiber,
                     double mu, double eps, double E, double dt,
                     const fs_boundary *boundary, const fs_options *opt, void *cuda_stream);

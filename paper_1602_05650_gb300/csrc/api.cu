@@ -97,8 +97,8 @@ fs_status check_options(const fs_options &o, const char *who, int n_systems)
         set_error("%s: lsb, relax, profile and growth_implicit are 0 or 1", who);
         return FS_EINVAL;
     }
-    if (o.use_graph != 0) {
-        set_error("%s: use_graph is reserved and must be 0", who);
+    if (o.use_graph != 0 && o.use_graph != 1) {
+        set_error("%s: use_graph is 0 or 1", who);
         return FS_EINVAL;
     }
     if (o.tile_override < 0 || o.tile_override > 3) {

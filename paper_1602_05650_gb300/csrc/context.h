@@ -111,6 +111,17 @@ enum : int {
     kRbSize = 24
 };
 
+// An instantiated GMRES cycle graph (opt.use_graph) and its launch shape.
+struct CycleGraph {
+    int prec = 0;
+    bool hilo = false;
+    int nch = 0, nsch = 0, max_iter = 0;
+    int64_t items = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t body_launches = 0;   // kernels of one loop iteration
+};
+
 struct Body {
     bool on = false;
     int n = 0;                    // surface nodes (inside Surface, after the periphery)
@@ -185,6 +196,19 @@ struct fs_ctx {
     fs::Profiler prof;            // CUDA-event records (opt.profile)
     int64_t pairs_last = 0;
     size_t dev_bytes = 0;         // device memory allocated by the context (without scratch)
+    // GMRES cycles as CUDA graphs (opt.use_graph): device Givens state of the
+    // inner Krylov space ([S][R][R+1], [S][R] x 2, [S][R+1], [S][4] x 2),
+    // the iteration index, per-system start values, the current basis vector,
+    // host mirrors, and the instantiated graphs
+    double *d_gH = nullptr, *d_gcs = nullptr, *d_gsn = nullptr, *d_gg = nullptr, *d_gsc = nullptr,
+           *d_ginit = nullptr, *d_vcur = nullptr;
+    int *d_gst = nullptr, *d_gj = nullptr;
+    double *h_ginit = nullptr, *h_gsc = nullptr;
+    int *h_gst = nullptr, *h_gj = nullptr;
+    double *h_gbuf = nullptr;     // pinned block behind the host mirrors
+    bool capturing = false;       // kernels are being captured into a graph
+    cudaStream_t cap_stream = nullptr;   // the stream graphs are captured on
+    std::vector<fs::CycleGraph> graphs;
     fs::Pool *pool = nullptr;     // preallocated region for every buffer (serving), or nullptr
     bool worklist = false;        // far fields always per system (work-list mode), also for one system
     bool partial_ok = false;      // batch step: update every system, report convergence per system

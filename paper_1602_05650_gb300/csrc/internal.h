@@ -134,6 +134,7 @@ struct PairSumArgs {
     int64_t work_cap = 0;
     Profiler *prof = nullptr;          // record the main kernel with CUDA events
     double pairs = 0.0;                // pairs evaluated (for the profiler)
+    bool work_uploaded = false;        // the work list is on the device already (graph capture)
 };
 
 // slots > 0: CTAs one wave may hold (an upper bound will do); 0: ask the
@@ -145,6 +146,11 @@ size_t pairsum_scratch_bytes(int kind, int64_t n_src, int64_t n_tgt, int sum_pre
 // Enqueue the sum on `st`; scratch must hold pairsum_scratch_bytes(...) bytes.
 fs_status pairsum(const PairSumArgs &a, void *scratch, size_t scratch_bytes, int *d_status,
                   cudaStream_t st);
+
+// The work list of a.groups uploaded to a.work_dev (*items = its length;
+// 0 without groups): what pairsum does before its launch, done ahead of a
+// graph capture.
+fs_status pairsum_work_list(const PairSumArgs &a, cudaStream_t st, int64_t *items);
 
 // Exclusion ranges from non-decreasing source fiber ids (binary search per target).
 fs_status exclusion_from_ids(const int32_t *src_fiber, int64_t n_src, const int32_t *tgt_fiber,

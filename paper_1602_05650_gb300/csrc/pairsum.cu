@@ -1355,6 +1355,41 @@ fs_status exclusion_from_ids(const int32_t *src_fiber, int64_t n_src, const int3
     return FS_OK;
 }
 
+namespace {
+
+// One work item per block of tb targets of a group, sources of that group
+// only; largest source ranges first (the order schedules, the sums of an item
+// do not depend on it).
+std::vector<int4> work_items(const PairSumArgs &a, int tb)
+{
+    std::vector<int4> items;
+    for (const int4 &g : *a.groups)
+        for (int t0 = g.x; t0 < g.y; t0 += tb) items.push_back(make_int4(t0, std::min(tb, g.y - t0), g.z, g.w));
+    std::stable_sort(items.begin(), items.end(),
+                     [](const int4 &u, const int4 &v) { return (u.w - u.z) > (v.w - v.z); });
+    return items;
+}
+
+}  // namespace
+
+fs_status pairsum_work_list(const PairSumArgs &a, cudaStream_t st, int64_t *n_items)
+{
+    *n_items = 0;
+    if (!a.groups) return FS_OK;
+    const bool f32 = a.sum_prec == FS_SUM_FP32;
+    const SumPlan p = plan_pairsum(a.kind, a.n_src, a.n_tgt, a.sum_prec, f32 && a.hilo, a.shape_override, 0);
+    const std::vector<int4> items = work_items(a, p.tb);
+    if (items.empty()) return FS_OK;
+    if (static_cast<int64_t>(items.size()) > a.work_cap) {
+        set_error("pairsum: %zu work items exceed the capacity %lld", items.size(),
+                  static_cast<long long>(a.work_cap));
+        return FS_EINVAL;
+    }
+    FS_CUDA(cudaMemcpyAsync(a.work_dev, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+    *n_items = static_cast<int64_t>(items.size());
+    return FS_OK;
+}
+
 fs_status pairsum(const PairSumArgs &a, void *scratch, size_t scratch_bytes, int *d_status,
                   cudaStream_t st)
 {
@@ -1381,25 +1416,14 @@ fs_status pairsum(const PairSumArgs &a, void *scratch, size_t scratch_bytes, int
     unsigned grid = static_cast<unsigned>(p.grid);
     double *part = nullptr;
     if (a.groups) {
-        // one work item per block of tpt x threads targets of a group, sources of
-        // that group only; largest source ranges first
-        std::vector<int4> items;
-        const int chunk = p.tb;
-        for (const int4 &g : *a.groups)
-            for (int t0 = g.x; t0 < g.y; t0 += chunk)
-                items.push_back(make_int4(t0, std::min(chunk, g.y - t0), g.z, g.w));
-        std::stable_sort(items.begin(), items.end(),
-                         [](const int4 &u, const int4 &v) { return (u.w - u.z) > (v.w - v.z); });
-        if (items.empty()) return FS_OK;
-        if (static_cast<int64_t>(items.size()) > a.work_cap) {
-            set_error("pairsum: %zu work items exceed the capacity %lld", items.size(),
-                      static_cast<long long>(a.work_cap));
-            return FS_EINVAL;
-        }
-        FS_CUDA(cudaMemcpyAsync(a.work_dev, items.data(), items.size() * sizeof(int4),
-                                cudaMemcpyHostToDevice, st));
+        int64_t n_items = 0;
+        if (a.work_uploaded)
+            n_items = static_cast<int64_t>(work_items(a, p.tb).size());
+        else
+            FS_TRY(pairsum_work_list(a, st, &n_items));
+        if (n_items == 0) return FS_OK;
         work = a.work_dev;
-        grid = static_cast<unsigned>(items.size());
+        grid = static_cast<unsigned>(n_items);
     } else {
         part = cv.take<double>(static_cast<size_t>(p.grid + p.nb) * p.tb * 3);
     }

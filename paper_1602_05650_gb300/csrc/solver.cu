@@ -166,6 +166,205 @@ __global__ void k_seg_set(double *__restrict__ out, const double *__restrict__ a
     }
 }
 
+// ------------------------------------------------ GMRES cycle as a CUDA graph
+// With fs_options.use_graph = 1 a restart cycle of the (non-flexible) GMRES
+// runs as ONE graph launch: a conditional WHILE node whose body is one
+// iteration -- operator, CGS2, norm, scaling, and the Givens rotation of
+// every system on the device, which also sets the loop condition (some
+// system still running and the cycle not full).  The iteration index lives
+// in device memory, so the body is the same graph for every iteration; the
+// host synchronises once per cycle, not once per iteration.
+
+// out = V_j on the active chunks, j = *jd
+__global__ void k_copy_col_j(const double *__restrict__ V, int64_t ld, const int *__restrict__ jd,
+                             double *__restrict__ out, const int4 *__restrict__ ch)
+{
+    const int4 q = ch[blockIdx.x];
+    const double *v = V + static_cast<int64_t>(*jd) * ld;
+    for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < q.y; e += gridDim.y * blockDim.x)
+        out[q.x + e] = v[q.x + e];
+}
+
+// k_seg_dot for rows i <= *jd (the grid covers the cycle's largest row count)
+__global__ void k_seg_dot_j(const double *__restrict__ V, int64_t ld, const double *__restrict__ w,
+                            const int4 *__restrict__ ch, int nch, double *__restrict__ part,
+                            const int *__restrict__ jd)
+{
+    const int c = blockIdx.x, i = blockIdx.y;
+    if (i > *jd) return;
+    __shared__ double red[8];
+    const int4 q = ch[c];
+    const double *v = V + i * ld;
+    double s = 0.0;
+    for (int e = threadIdx.x; e < q.y; e += blockDim.x) s += v[q.x + e] * w[q.x + e];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int wv = 0; wv < static_cast<int>(blockDim.x >> 5); ++wv) t += red[wv];
+        part[static_cast<int64_t>(i) * nch + c] = t;
+    }
+}
+
+// k_seg_finish for rows i <= *jd
+__global__ void k_seg_finish_j(const double *__restrict__ part, int nch, const int4 *__restrict__ sch,
+                               double *__restrict__ h, int SH, int off, const int *__restrict__ jd)
+{
+    const int4 q = sch[blockIdx.x];
+    const int k = *jd + 1;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        double s = 0.0;
+        for (int c = q.y; c < q.z; ++c) s += part[static_cast<int64_t>(i) * nch + c];
+        h[static_cast<int64_t>(q.x) * SH + off + i] = s;
+    }
+}
+
+// w -= sum_{i <= *jd} h[s SH + off + i] V_i
+__global__ void k_seg_axpy_j(double *__restrict__ w, const double *__restrict__ V, int64_t ld,
+                             const double *__restrict__ h, int SH, int off, const int4 *__restrict__ ch,
+                             const int *__restrict__ jd)
+{
+    const int4 q = ch[blockIdx.x];
+    const double *hs = h + static_cast<int64_t>(q.z) * SH + off;
+    const int k = *jd + 1;
+    for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < q.y; e += gridDim.y * blockDim.x) {
+        const int64_t g = q.x + e;
+        double s = 0.0;
+        for (int i = 0; i < k; ++i) s += hs[i] * V[i * ld + g];
+        w[g] -= s;
+    }
+}
+
+// V_{j+1} = in / h[s SH + off] (0 if the norm is 0), j = *jd
+__global__ void k_seg_scale_col_j(const double *__restrict__ in, const double *__restrict__ h, int SH, int off,
+                                  double *__restrict__ V, int64_t ld, const int *__restrict__ jd,
+                                  const int4 *__restrict__ ch)
+{
+    const int4 q = ch[blockIdx.x];
+    const double d = h[static_cast<int64_t>(q.z) * SH + off];
+    double *out = V + static_cast<int64_t>(*jd + 1) * ld;
+    for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < q.y; e += gridDim.y * blockDim.x)
+        out[q.x + e] = d > 0.0 ? in[q.x + e] / d : 0.0;
+}
+
+// Per-system Givens state of the device cycle.
+struct GivensState {
+    double *H;       // [S][R][R+1] rotated Hessenberg columns
+    double *cs, *sn; // [S][R]
+    double *g;       // [S][R+1]
+    double *sc;      // [S][4]: beta, lim, res, rel
+    int *st;         // [S][4]: its, kk, conv, done (done < 0: non-finite Arnoldi vector)
+    int *jd;         // [1] iteration index of the cycle
+    int R, max_iter;
+};
+
+// Cycle start for the systems of sch: g = (beta, 0, ...), kk = 0, running;
+// beta from h[s SH + off_beta]; lim and its from the host (init[s] = lim, its).
+__global__ void k_givens_init(GivensState G, const int4 *__restrict__ sch, int nsch,
+                              const double *__restrict__ h, int SH, int off_beta, const double *__restrict__ init)
+{
+    for (int b = threadIdx.x; b < nsch; b += blockDim.x) {
+        const int s = sch[b].x;
+        double *g = G.g + static_cast<int64_t>(s) * (G.R + 1);
+        for (int i = 0; i <= G.R; ++i) g[i] = 0.0;
+        const double beta = h[static_cast<int64_t>(s) * SH + off_beta];
+        g[0] = beta;
+        G.sc[4 * s + 0] = beta;
+        G.sc[4 * s + 1] = init[2 * s];
+        G.sc[4 * s + 2] = beta;
+        G.st[4 * s + 0] = static_cast<int>(init[2 * s + 1]);
+        G.st[4 * s + 1] = 0;
+        G.st[4 * s + 2] = 0;
+        G.st[4 * s + 3] = 0;
+    }
+    if (threadIdx.x == 0) *G.jd = 0;
+}
+
+// Column j = *jd of every running system: the CGS2 coefficients (two passes)
+// and the new norm, the earlier rotations, a new rotation, the residual
+// estimate |g_{j+1}| and the convergence test; a system that converges, breaks
+// down or reaches max_iter keeps its state from then on.  One block; sets the
+// WHILE condition and advances *jd.
+__global__ void __launch_bounds__(256) k_givens_step(GivensState G, const int4 *__restrict__ sch, int nsch,
+                                                     const double *__restrict__ h, int SH, int hs,
+                                                     cudaGraphConditionalHandle cond)
+{
+    const int j = *G.jd;
+    int alive = 0;
+    for (int b = threadIdx.x; b < nsch; b += blockDim.x) {
+        const int s = sch[b].x;
+        int *st = G.st + 4 * s;
+        if (st[3]) continue;
+        const double *hp = h + static_cast<int64_t>(s) * SH;
+        double *hc = G.H + (static_cast<int64_t>(s) * G.R + j) * (G.R + 1);
+        double *cs = G.cs + static_cast<int64_t>(s) * G.R, *sn = G.sn + static_cast<int64_t>(s) * G.R;
+        double *g = G.g + static_cast<int64_t>(s) * (G.R + 1);
+        for (int i = 0; i <= j; ++i) hc[i] = hp[i] + hp[hs + i];
+        const double hn = hp[2 * hs];
+        hc[j + 1] = hn;
+        if (!isfinite(hn)) {
+            st[3] = -1;
+            continue;
+        }
+        for (int i = 0; i < j; ++i) {
+            const double t = cs[i] * hc[i] + sn[i] * hc[i + 1];
+            hc[i + 1] = -sn[i] * hc[i] + cs[i] * hc[i + 1];
+            hc[i] = t;
+        }
+        const double d = hypot(hc[j], hc[j + 1]);
+        cs[j] = d > 0.0 ? hc[j] / d : 1.0;
+        sn[j] = d > 0.0 ? hc[j + 1] / d : 0.0;
+        hc[j] = d;
+        hc[j + 1] = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        st[0] += 1;
+        st[1] = j + 1;
+        const double res = fabs(g[j + 1]);
+        G.sc[4 * s + 2] = res;
+        if (res <= G.sc[4 * s + 1]) {
+            st[2] = 1;
+            st[3] = 1;
+        } else if (hn == 0.0 || st[0] >= G.max_iter) {
+            st[3] = 1;
+        } else {
+            ++alive;
+        }
+    }
+    __shared__ int red[8];
+    for (int o = 16; o > 0; o >>= 1) alive += __shfl_xor_sync(0xffffffffu, alive, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = alive;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) tot += red[w];
+        *G.jd = j + 1;
+        cudaGraphSetConditional(cond, (tot > 0 && j + 1 < G.R) ? 1u : 0u);
+    }
+}
+
+// y = H^-1 g (upper triangular, kk columns) per system of sch, into
+// h[s SH + off_y + i]; kk[s] for the update x += V y.
+__global__ void k_givens_backsub(GivensState G, const int4 *__restrict__ sch, int nsch, double *__restrict__ h,
+                                 int SH, int off_y, int *__restrict__ kk)
+{
+    for (int b = threadIdx.x; b < nsch; b += blockDim.x) {
+        const int s = sch[b].x;
+        const int k = G.st[4 * s + 1];
+        const double *H = G.H + static_cast<int64_t>(s) * G.R * (G.R + 1);
+        const double *g = G.g + static_cast<int64_t>(s) * (G.R + 1);
+        double *y = h + static_cast<int64_t>(s) * SH + off_y;
+        for (int i = k - 1; i >= 0; --i) {
+            double sum = g[i];
+            for (int l = i + 1; l < k; ++l) sum -= H[static_cast<int64_t>(l) * (G.R + 1) + i] * y[l];
+            const double dii = H[static_cast<int64_t>(i) * (G.R + 1) + i];
+            y[i] = dii != 0.0 ? sum / dii : 0.0;
+        }
+        kk[s] = k;
+    }
+}
+
 // ------------------------------------------------------ segmented GMRES (host)
 struct SysState {
     double beta0 = 0.0, beta = 0.0, rel = 0.0, res = 0.0, lim = 0.0;
@@ -256,14 +455,11 @@ fs_status fetch_h(fs_ctx *c, const Space &sp)
 
 // Far field at the fiber nodes for the active systems (each target block sums
 // its own system's sources only): ubar = (1/8 pi mu) sum_{other fibers} G0 W f
-fs_status far_field(fs_ctx *c, int sum_prec, bool hilo, const std::vector<int> *act)
+// Direct-sum arguments of the fiber far field (groups: the per-system work
+// list's groups when the systems are summed separately).
+PairSumArgs far_field_args(fs_ctx *c, int sum_prec, bool hilo, const std::vector<int> *act,
+                           std::vector<int4> &groups)
 {
-    if (c->opt.tree_order > 0) {
-        // fast summation: the treecode at the chosen order, whatever the precision
-        c->pairs_last += c->n_tot * c->n_tot;
-        return tree_sum(c, c->d_X, c->d_wf, c->n_tot, nullptr, c->d_X, nullptr, c->n_tot, c->d_ubar,
-                        c->opt.tree_order, c->opt.tree_theta, c->d_excl);
-    }
     PairSumArgs a;
     a.kind = PAIR_STOKESLET;
     a.src_xyz = c->d_X;
@@ -277,8 +473,8 @@ fs_status far_field(fs_ctx *c, int sum_prec, bool hilo, const std::vector<int> *
     a.sum_prec = sum_prec;
     a.hilo = hilo;
     a.shape_override = c->opt.tile_override;
-    std::vector<int4> groups;
     double pairs = 0.0;
+    groups.clear();
     if ((c->S > 1 || c->worklist) && act) {
         for (int s : *act) {
             const int lo = static_cast<int>(c->sys_node_ptr[s]), hi = static_cast<int>(c->sys_node_ptr[s + 1]);
@@ -294,12 +490,42 @@ fs_status far_field(fs_ctx *c, int sum_prec, bool hilo, const std::vector<int> *
                                                 c->sys_self_pairs[s];
     }
     a.pairs = pairs;
-    a.prof = c->opt.profile ? &c->prof : nullptr;
+    // event records cannot sit in a graph's loop body
+    a.prof = (c->opt.profile && !c->capturing) ? &c->prof : nullptr;
+    a.work_uploaded = c->capturing;
+    return a;
+}
+
+// Far field at the fiber nodes for the active systems (each target block sums
+// its own system's sources only): ubar = (1/8 pi mu) sum_{other fibers} G0 W f
+fs_status far_field(fs_ctx *c, int sum_prec, bool hilo, const std::vector<int> *act)
+{
+    if (c->opt.tree_order > 0) {
+        // fast summation: the treecode at the chosen order, whatever the precision
+        c->pairs_last += c->n_tot * c->n_tot;
+        return tree_sum(c, c->d_X, c->d_wf, c->n_tot, nullptr, c->d_X, nullptr, c->n_tot, c->d_ubar,
+                        c->opt.tree_order, c->opt.tree_theta, c->d_excl);
+    }
+    std::vector<int4> groups;
+    PairSumArgs a = far_field_args(c, sum_prec, hilo, act, groups);
     FS_TRY(c->scratch.reserve(pairsum_scratch_bytes(a.kind, a.n_src, a.n_tgt, sum_prec, a.shape_override),
                               c->stream));
     FS_TRY(pairsum(a, c->scratch.ptr, c->scratch.bytes, c->d_status, c->stream));
-    c->pairs_last += static_cast<int64_t>(pairs);
+    c->pairs_last += static_cast<int64_t>(a.pairs);
     return FS_OK;
+}
+
+// Before a graph capture: the far field's scratch reserved and its work list
+// (if any) uploaded, so that the captured sums neither allocate nor copy from
+// the host; *items = the work list's length (0: one stream-K sum).
+fs_status prepare_far_field(fs_ctx *c, int sum_prec, bool hilo, const std::vector<int> *act, int64_t *items)
+{
+    std::vector<int4> groups;
+    PairSumArgs a = far_field_args(c, sum_prec, hilo, act, groups);
+    a.work_uploaded = false;
+    FS_TRY(c->scratch.reserve(pairsum_scratch_bytes(a.kind, a.n_src, a.n_tgt, sum_prec, a.shape_override),
+                              c->stream));
+    return pairsum_work_list(a, c->stream, items);
 }
 
 // Preconditioned operator of Eq. prec, out = P^-1 A v, evaluated as
@@ -408,6 +634,168 @@ fs_status true_residual(fs_ctx *c, const double *x, double *r, int sum_prec)
     return FS_OK;
 }
 
+GivensState givens_state(fs_ctx *c)
+{
+    GivensState G;
+    G.H = c->d_gH;
+    G.cs = c->d_gcs;
+    G.sn = c->d_gsn;
+    G.g = c->d_gg;
+    G.sc = c->d_gsc;
+    G.st = c->d_gst;
+    G.jd = c->d_gj;
+    G.R = c->kdim - 1;
+    G.max_iter = c->opt.max_iter;
+    return G;
+}
+
+// One iteration of the cycle's body (the WHILE node), enqueued on the
+// capturing stream: V_j -> operator -> CGS2 -> norm -> V_{j+1} -> Givens.
+fs_status cycle_body(fs_ctx *c, Space &sp, const std::vector<int> &act, int sum_prec, bool hilo,
+                     cudaGraphConditionalHandle cond)
+{
+    const int64_t n = c->n_unk;
+    const int R = sp.R, hs = R + 1, SH = SHof(sp);
+    const int *jd = c->d_gj;
+    k_copy_col_j<<<seg_grid(sp), 256, 0, c->stream>>>(sp.V, n, jd, c->d_vcur, sp.d_ch);
+    FS_LAUNCH_CHECK();
+    FS_TRY(apply_pa(c, c->d_vcur, sp.w, sum_prec, &act, hilo));
+    for (int pass = 0; pass < 2; ++pass) {   // CGS2
+        const int off = pass ? hs : 0;
+        k_seg_dot_j<<<dim3(sp.nch, R + 1), 256, 0, c->stream>>>(sp.V, n, sp.w, sp.d_ch, sp.nch, sp.part, jd);
+        FS_LAUNCH_CHECK();
+        k_seg_finish_j<<<sp.nsch, 128, 0, c->stream>>>(sp.part, sp.nch, sp.d_sch, sp.h, SH, off, jd);
+        FS_LAUNCH_CHECK();
+        k_seg_axpy_j<<<seg_grid(sp), 256, 0, c->stream>>>(sp.w, sp.V, n, sp.h, SH, off, sp.d_ch, jd);
+        FS_LAUNCH_CHECK();
+    }
+    FS_TRY(seg_dots(c, sp, sp.w, 0, 1, sp.w, 2 * hs, true));
+    k_seg_scale_col_j<<<seg_grid(sp), 256, 0, c->stream>>>(sp.w, sp.h, SH, 2 * hs, sp.V, n, jd, sp.d_ch);
+    FS_LAUNCH_CHECK();
+    k_givens_step<<<1, 256, 0, c->stream>>>(givens_state(c), sp.d_sch, sp.nsch, sp.h, SH, hs, cond);
+    FS_LAUNCH_CHECK();
+    return FS_OK;
+}
+
+// One restart cycle of the inner GMRES as a CUDA graph (the chunk lists of
+// `act` are on the device and V_0 is set): per-system start values, ONE
+// launch of the graph whose WHILE node iterates until every system of the
+// cycle has converged, stopped or filled the cycle, the back substitution
+// y = H^-1 g per system, and one read of the systems' states.  Graphs are
+// cached per launch shape (precision, chunk and work-list counts); the lists'
+// contents are read at run time, so one graph serves every cycle of a shape.
+fs_status cycle_graph(fs_ctx *c, Space &sp, const std::vector<int> &act, int sum_prec, bool hilo, int max_iter,
+                      std::vector<SysState> &st)
+{
+    const int R = sp.R, hs = R + 1, SH = SHof(sp);
+    // start values: lim and its per system
+    for (int s : act) {
+        c->h_ginit[2 * s] = st[s].lim;
+        c->h_ginit[2 * s + 1] = st[s].its;
+    }
+    FS_CUDA(cudaMemcpyAsync(c->d_ginit, c->h_ginit, 2 * static_cast<size_t>(c->S) * sizeof(double),
+                            cudaMemcpyHostToDevice, c->stream));
+    GivensState G = givens_state(c);
+    G.max_iter = max_iter;
+    k_givens_init<<<1, 256, 0, c->stream>>>(G, sp.d_sch, sp.nsch, sp.h, SH, 2 * hs + 2, c->d_ginit);
+    FS_LAUNCH_CHECK();
+    // the far field's work list and scratch are set up before capture
+    int64_t items = 0;
+    FS_TRY(prepare_far_field(c, sum_prec, hilo, &act, &items));
+    CycleGraph *cg = nullptr;
+    for (CycleGraph &g : c->graphs)
+        if (g.prec == sum_prec && g.hilo == hilo && g.nch == sp.nch && g.nsch == sp.nsch && g.items == items &&
+            g.max_iter == max_iter)
+            cg = &g;
+    if (!cg) {
+        CycleGraph g;
+        g.prec = sum_prec;
+        g.hilo = hilo;
+        g.nch = sp.nch;
+        g.nsch = sp.nsch;
+        g.items = items;
+        g.max_iter = max_iter;
+        FS_CUDA(cudaGraphCreate(&g.graph, 0));
+        cudaGraphConditionalHandle cond;
+        FS_CUDA(cudaGraphConditionalHandleCreate(&cond, g.graph, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams np{};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = cond;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        FS_CUDA(cudaGraphAddNode(&node, g.graph, nullptr, nullptr, 0, &np));
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        // body kernels (G.max_iter is a kernel argument: part of the key)
+        const int saved_iter = c->opt.max_iter;
+        c->opt.max_iter = max_iter;
+        const uint64_t l0 = g_launches;
+        // capture on a stream of its own (the context's stream may be the
+        // legacy default stream, which cannot capture); the graph itself is
+        // launched on the context's stream
+        if (!c->cap_stream) FS_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        FS_CUDA(cudaStreamSynchronize(c->stream));
+        cudaStream_t own = c->stream;
+        c->stream = c->cap_stream;
+        const cudaError_t be =
+            cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+        fs_status bs = FS_ECUDA;
+        cudaGraph_t got = nullptr;
+        cudaError_t ce = be;
+        if (be == cudaSuccess) {
+            c->capturing = true;
+            bs = cycle_body(c, sp, act, sum_prec, hilo, cond);
+            c->capturing = false;
+            ce = cudaStreamEndCapture(c->stream, &got);
+        } else {
+            set_error("gmres: cannot begin a graph capture: %s", cudaGetErrorString(be));
+        }
+        c->stream = own;
+        c->opt.max_iter = saved_iter;
+        if (bs != FS_OK) {
+            cudaGraphDestroy(g.graph);
+            return bs;
+        }
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphDestroy(g.graph);
+            set_error("gmres: graph capture failed: %s", cudaGetErrorString(ce));
+            return FS_ECUDA;
+        }
+        g.body_launches = g_launches - l0;
+        __atomic_sub_fetch(&g_launches, g.body_launches, __ATOMIC_RELAXED);   // counted per iteration below
+        FS_CUDA(cudaGraphInstantiate(&g.exec, g.graph, 0));
+        c->graphs.push_back(g);
+        cg = &c->graphs.back();
+    }
+    FS_CUDA(cudaGraphLaunch(cg->exec, c->stream));
+    k_givens_backsub<<<1, 256, 0, c->stream>>>(G, sp.d_sch, sp.nsch, sp.h, SH, 3 * hs + 4, sp.d_kk);
+    FS_LAUNCH_CHECK();
+    // the systems' states (and the iterations the loop ran) back to the host
+    FS_CUDA(cudaMemcpyAsync(c->h_gst, c->d_gst, 4 * static_cast<size_t>(c->S) * sizeof(int), cudaMemcpyDeviceToHost,
+                            c->stream));
+    FS_CUDA(cudaMemcpyAsync(c->h_gsc, c->d_gsc, 4 * static_cast<size_t>(c->S) * sizeof(double),
+                            cudaMemcpyDeviceToHost, c->stream));
+    FS_CUDA(cudaMemcpyAsync(c->h_gj, c->d_gj, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    FS_CUDA(cudaStreamSynchronize(c->stream));
+    __atomic_add_fetch(&g_launches, cg->body_launches * static_cast<uint64_t>(*c->h_gj), __ATOMIC_RELAXED);
+    for (int s : act) {
+        SysState &q = st[s];
+        const int *gs = c->h_gst + 4 * s;
+        if (gs[3] < 0) {
+            set_error("gmres: non-finite Arnoldi vector (system %d)", s);
+            return FS_ENUMERIC;
+        }
+        q.its = gs[0];
+        q.kk = gs[1];
+        q.conv = gs[2] != 0;
+        q.done = gs[3] != 0 || q.its >= max_iter;
+        q.res = c->h_gsc[4 * s + 2];
+        q.rel = q.beta0 > 0.0 ? q.res / q.beta0 : 0.0;
+    }
+    return FS_OK;
+}
+
 // Restarted GMRES for (P^-1 A) x = pb, x0 = 0, on each system in `want`
 // independently (lockstep: one operator application per iteration for all
 // running systems), CGS2 and Givens rotations per system; x overwritten on
@@ -421,6 +809,10 @@ fs_status gmres_seg(fs_ctx *c, Space &sp, const double *pb, double *x, double to
     const int64_t n = c->n_unk;
     const int R = sp.R, hs = R + 1, SH = SHof(sp);
     const bool flexible = inner_prec >= 0;
+    // device cycles: the inner Krylov space, direct far fields, no event
+    // records (a graph's body holds kernels, copies and memsets only)
+    const bool graph = c->opt.use_graph && !flexible && sp.V == c->d_basis && c->d_gH && !c->opt.profile &&
+                       c->opt.tree_order == 0 && partial_rel == 0.0;
     double *V = sp.V;
     st.assign(c->S, SysState());
     std::vector<int> act = want;
@@ -462,6 +854,10 @@ fs_status gmres_seg(fs_ctx *c, Space &sp, const double *pb, double *x, double to
         FS_TRY(seg_build(c, sp, act));
         k_seg_scale<<<seg_grid(sp), 256, 0, c->stream>>>(sp.r, sp.h, SH, 2 * hs + 2, V, sp.d_ch);
         FS_LAUNCH_CHECK();
+        if (graph) {
+            // the whole cycle on the device: one graph launch, one synchronisation
+            FS_TRY(cycle_graph(c, sp, act, sum_prec, hilo, max_iter, st));
+        } else {
         for (int s : act) {
             SysState &q = st[s];
             std::fill(q.g.begin(), q.g.end(), 0.0);
@@ -554,6 +950,11 @@ fs_status gmres_seg(fs_ctx *c, Space &sp, const double *pb, double *x, double to
                                                            sp.d_kk, sp.d_ch);
         FS_LAUNCH_CHECK();
         FS_CUDA(cudaStreamSynchronize(c->stream));   // hpin and kk are reused below
+        }
+        if (graph) {
+            k_seg_lincomb<<<seg_grid(sp), 256, 0, c->stream>>>(x, V, n, sp.h, SH, 3 * hs + 4, sp.d_kk, sp.d_ch);
+            FS_LAUNCH_CHECK();
+        }
         std::vector<int> again;
         for (int s : act)
             if (!st[s].done) again.push_back(s);
@@ -810,6 +1211,24 @@ fs_status krylov_arrays(fs_ctx *c)
     if (!c->pool) FS_CUDA(cudaFreeHost(c->h_pinned));
     c->h_pinned = nullptr;
     FS_TRY(pinned_alloc(c, &c->h_pinned, c->S * SHi));
+    if (c->opt.use_graph) {
+        const size_t S = c->S, R = c->kdim - 1;
+        FS_TRY(dalloc(c, &c->d_gH, S * R * (R + 1)));
+        FS_TRY(dalloc(c, &c->d_gcs, S * R));
+        FS_TRY(dalloc(c, &c->d_gsn, S * R));
+        FS_TRY(dalloc(c, &c->d_gg, S * (R + 1)));
+        FS_TRY(dalloc(c, &c->d_gsc, 4 * S));
+        FS_TRY(dalloc(c, &c->d_ginit, 2 * S));
+        FS_TRY(dalloc(c, &c->d_gst, 4 * S));
+        FS_TRY(dalloc(c, &c->d_gj, 1));
+        FS_TRY(dalloc(c, &c->d_vcur, static_cast<size_t>(n)));
+        // host mirrors: ginit [2S], gsc [4S] doubles, gst [4S] + gj ints
+        FS_TRY(pinned_alloc(c, &c->h_gbuf, 6 * S + 2 * S + 2));
+        c->h_ginit = c->h_gbuf;
+        c->h_gsc = c->h_gbuf + 2 * S;
+        c->h_gst = reinterpret_cast<int *>(c->h_gbuf + 6 * S);
+        c->h_gj = c->h_gst + 4 * S;
+    }
     if (c->opt.prec == FS_MIXED) {
         c->okdim = 17;   // outer (flexible) restart length 16
         const size_t SHo = 4 * size_t(c->okdim) + 8;
@@ -908,6 +1327,11 @@ size_t estimate_bytes(int M, const int32_t *ppf, int n_surf, const fs_options &o
     add(chunk_cap * sizeof(int4));
     add(sizeof(int4));
     add(sizeof(int));
+    if (opt.use_graph) {   // device Givens state of one system, the current basis vector
+        for (int64_t k : {kdim * (kdim - 1) + 4 * kdim, int64_t(4), int64_t(2), n}) add(k * d);
+        add(4 * sizeof(int));
+        add(sizeof(int));
+    }
     if (opt.prec == FS_MIXED) {
         const int64_t ok = 17;
         add(ok * n * d);
@@ -951,8 +1375,19 @@ void context_free(fs_ctx *c)
                     c->d_x, c->d_r, c->d_w, c->d_e, c->d_pb, c->d_obasis, c->d_oz, c->d_oh, c->d_opart, c->d_ow, c->d_or, c->d_work, c->d_ich, c->d_isch, c->d_ikk, c->d_och, c->d_osch, c->d_okk, c->d_h, c->d_part, c->surf.y, c->surf.nrm,
                     c->surf.w, c->surf.diag, c->d_usurf, c->surf.A, c->surf.tmp, c->surf.flux, c->surf.excl,
                     c->body.rb, c->body.attach, c->body.att_list};
+    for (fs::CycleGraph &g : c->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.graph) cudaGraphDestroy(g.graph);
+    }
+    c->graphs.clear();
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    c->cap_stream = nullptr;
+    void *gptrs[] = {c->d_gH, c->d_gcs, c->d_gsn, c->d_gg, c->d_gsc, c->d_ginit, c->d_vcur, c->d_gst, c->d_gj};
     // buffers carved from a preallocated region go back with the region
     if (!c->pool) {
+        for (void *p : gptrs)
+            if (p) cudaFree(p);
+        if (c->h_gbuf) cudaFreeHost(c->h_gbuf);
         for (void *p : ptrs)
             if (p) cudaFree(p);
         if (c->h_pinned) cudaFreeHost(c->h_pinned);

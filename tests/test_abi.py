@@ -104,7 +104,7 @@ def test_step_options_are_validated_without_gpu(lib):
     bad = [("prec", 2), ("prec", -1), ("tol", 0.0), ("tol", 1.0), ("tol", float("nan")),
            ("inner_tol", 0.0), ("max_iter", 0), ("restart", 0), ("restart", 251),
            ("max_refine", 0), ("delta_over_L", -0.01), ("delta_over_L", float("inf")),
-           ("lsb", 2), ("relax", -1), ("profile", 3), ("use_graph", 1),
+           ("lsb", 2), ("relax", -1), ("profile", 3), ("use_graph", 2),
            ("tile_override", 4), ("tile_override", -1)]
     for field, value in bad:
         o = _native.fs_options()
