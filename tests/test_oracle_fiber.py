@@ -273,3 +273,27 @@ def test_multistep_growth_of_a_curved_end_fiber_at_64_points():
     T64, T32 = run(64), run(32)
     assert T64[-1] > 100.0 * T64[0]
     assert max(T32) < 1.1 * min(T32)
+
+
+def test_block_sensitivity_by_points_per_fiber():
+    """The conditioning gate of the discretisation (rectangular collocation in
+    the integrated basis): the relative change of a single fiber's velocities
+    when every entry of its block is perturbed by a relative 1e-16 (four
+    random sign patterns, the largest change).  Recorded: 3.1e-13, 3.7e-12,
+    7.4e-10, 2.1e-6 at N = 16, 32, 64, 128 (block condition numbers 7e6,
+    1e9, 6e11, 9e14); a discretisation change that worsens them by 5x fails."""
+    rng = np.random.default_rng(0)
+    recorded = {16: 3.1e-13, 32: 3.7e-12, 64: 7.4e-10, 128: 2.1e-6}
+    for N, rec in recorded.items():
+        s = wl.free_space(1, N, 5.0, seed=3, curved_amp=0.05, L_range=(2.0, 2.0))
+        s.f_ext = np.tile([0.3, -0.2, -1.0], (N, 1))
+        S = system.from_suspension(s)
+        fb = S.fibers[0]
+        b = S.rhs()
+        V0 = fb.velocity_nodes(np.linalg.solve(fb.B, b))
+        worst = 0.0
+        for _ in range(4):
+            Bp = fb.B * (1.0 + 1e-16 * rng.choice([-1.0, 1.0], size=fb.B.shape))
+            V = fb.velocity_nodes(np.linalg.solve(Bp, b))
+            worst = max(worst, np.linalg.norm(V - V0) / np.linalg.norm(V0))
+        assert worst <= 5.0 * rec, (N, worst)
