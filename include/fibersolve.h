@@ -159,6 +159,13 @@ typedef struct {
                                term is forward Euler on an advection in alpha and goes
                                unstable for fast-shrinking fibers (dt |Ldot| / L of a few
                                percent); the implicit one stays stable there */
+    int32_t tc_blocks;      /* 1 = the two large products of the self-block build (W = S F
+                               and the w rows Rw W, Eq. prec) on the bf16 tensor cores by
+                               operand splitting: each row / column scaled by a power of
+                               two and split into eight 7-bit digits, the digit products
+                               summed exactly in FP32 per diagonal and folded in FP64, an
+                               FP64-grade result (error below the FP64 product's bound);
+                               0 = FP64 CUDA cores (default 1) */
 } fs_options;
 
 /* Direct-sum kernel classes reported by fs_kernel_stats. */
@@ -362,6 +369,14 @@ fs_status fs_surface_apply(fs_ctx *ctx, const double *q, double *out, int32_t su
  * complementary velocity removed, Sec. 3.3) for the current state and LU-factor
  * them with partial pivoting (FP64).  Called by fs_step when needed. */
 fs_status fs_build_precond(fs_ctx *ctx);
+
+/* The assembled self block B_m of one fiber (Eq. prec; before its LU
+ * factorisation), column-major (4N)^2 doubles into the HOST array out, in the
+ * unknown order of the fiber (sigma_x, sigma_y, sigma_z with their p columns,
+ * then tau, q0, q1).  Assembles all blocks for the current state (so the next
+ * fs_step factors them again) and synchronises the stream.  For tests and
+ * diagnostics: with fs_options.tc_blocks it shows the tensor-core build. */
+fs_status fs_get_self_block(fs_ctx *ctx, int32_t fiber, double *out);
 
 /* One implicit backward-Euler step (Sec. 3.2, set:time-stepping): solve
  * P^-1 A u = P^-1 b by GMRES with the block-Jacobi preconditioner P of Eq. prec

@@ -21,7 +21,7 @@ __all__ = ["fs_options_default", "fs_create", "fs_create_batch", "fs_batch_info"
            "fs_stokeslet_apply", "fs_stresslet_apply", "fs_surface_apply", "fs_build_precond",
            "fs_step", "fs_sizes", "fs_last_error", "fs_kernel_stats", "fs_kernel_launches",
            "fs_probe_fma", "fs_estimate_bytes", "fs_device_bytes", "fs_server_create", "fs_submit",
-           "fs_poll", "fs_server_wait", "fs_server_stats", "fs_server_batches", "fs_server_destroy", "Server",
+           "fs_poll", "fs_server_wait", "fs_server_stats", "fs_server_batches", "fs_server_destroy", "Server", "fs_get_self_block",
            "FsError",
            "fs_set_growth", "fs_get_lengths", "fs_get_unknowns", "fs_dynamic_instability",
            "FS_FP64", "FS_MIXED",
@@ -472,6 +472,15 @@ def fs_server_stats(sv: Server):
     _check(_native.load().fs_server_stats(sv.ptr, ctypes.byref(pe), ctypes.byref(ru), ctypes.byref(by),
                                           ctypes.byref(co)), "fs_server_stats")
     return {"pending": pe.value, "running": ru.value, "bytes_in_use": int(by.value), "completed": co.value}
+
+
+def fs_get_self_block(h: Handle, fiber: int, n_points: int):
+    """The assembled self block of one fiber as a (4N, 4N) numpy array."""
+    n = 4 * int(n_points)
+    out = np.zeros(n * n)
+    _check(_native.load().fs_get_self_block(h.ptr, int(fiber), out.ctypes.data_as(ctypes.c_void_p)),
+           "fs_get_self_block")
+    return out.reshape(n, n).T   # column-major storage
 
 
 def fs_server_batches(sv: Server) -> int:

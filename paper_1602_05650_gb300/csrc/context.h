@@ -3,6 +3,8 @@
 
 #include <map>
 
+#include <cuda_bf16.h>
+
 #include "internal.h"
 
 namespace fs {
@@ -49,6 +51,27 @@ struct OpsLayout {
         Vgy = o; o += int64_t(N - 4) * N;
         V1 = o; o += 2 * N;
         total = (o + 3) & ~int64_t(3);
+    }
+};
+
+// Digit-plane sizes of the tensor-core block build for fibers of at most N
+// points: left operands S (3N rows) and Rw (three components' N - 4 velocity
+// rows and N - 2 tension rows, each group padded to 64), right operands F and
+// W (4N columns), inner dimension 3N; rows padded to 64, k to 16.
+struct OzDims {
+    int r1, r2, ry, kp;
+    __host__ __device__ explicit OzDims(int N)
+        : r1((3 * N + 63) / 64 * 64), r2(3 * ((N - 4 + 63) / 64 * 64) + (N - 2 + 63) / 64 * 64),
+          ry((4 * N + 63) / 64 * 64),
+          kp((3 * N + 15) / 16 * 16)
+    {
+    }
+    static constexpr int digits = 9;
+    // bytes per fiber: the bf16 digit planes and the exponents of both operands
+    __host__ __device__ int64_t bytes_per_fiber() const
+    {
+        const int64_t rx = r1 > r2 ? r1 : r2;
+        return (digits * (rx + ry) * int64_t(kp)) * 2 + (rx + ry) * 4 + 512;
     }
 };
 
@@ -209,6 +232,11 @@ struct fs_ctx {
     bool capturing = false;       // kernels are being captured into a graph
     cudaStream_t cap_stream = nullptr;   // the stream graphs are captured on
     std::vector<fs::CycleGraph> graphs;
+    // tensor-core block build (opt.tc_blocks): digit planes of a chunk of
+    // oz_chunk fibers (0: the FP64 CUDA-core build)
+    int oz_chunk = 0;
+    __nv_bfloat16 *d_ozx = nullptr, *d_ozy = nullptr;
+    int *d_ozxe = nullptr, *d_ozye = nullptr;
     fs::Pool *pool = nullptr;     // preallocated region for every buffer (serving), or nullptr
     bool worklist = false;        // far fields always per system (work-list mode), also for one system
     bool partial_ok = false;      // batch step: update every system, report convergence per system

@@ -27,6 +27,8 @@
 // tangential velocity expression at the end node.
 #include <cmath>
 
+#include <cuda_bf16.h>
+
 #include "context.h"
 
 namespace fs {
@@ -619,6 +621,377 @@ __global__ void __launch_bounds__(256) k_build_rows(FiberTable F, double *__rest
         }
 }
 
+// ------------------------------------------- block build on the tensor cores
+// The two large products of the block build, W = S F and the w rows Rw W,
+// in FP64-grade arithmetic on the bf16 tensor cores by operand splitting
+// (the error-free product scheme of Ozaki, Ogita, Oishi and Rump, Numer.
+// Algorithms 2012, with row / column scaling):
+//   * every row of the left operand X is scaled by 2^e (e: the row's largest
+//     magnitude rounds below 2^e) and rounded to a 62-bit integer, written as
+//     nine balanced base-128 digits x = 2^e sum_s a_s 2^-(6+7s), |a_s| <= 65;
+//     the columns of the right operand Y likewise (2^f, digits b_t);
+//   * every digit is an integer a bf16 holds exactly, every digit product an
+//     integer FP32 holds exactly; for the products of one diagonal s + t = d
+//     the sum over K <= 192 stays below 2^24 (9 x 192 x 65 x 64 < 2^23), so
+//     the tensor cores' FP32 accumulation of a diagonal is exact;
+//   * C = 2^(e+f) sum_{d<=8} 2^-(12+7d) acc_d, folded into FP64 one diagonal
+//     at a time.  The dropped diagonals d >= 9 weigh below 2^-52 of 2^(e+f);
+//     entries down to 2^-62 of their row's largest keep their digits, so
+//     products whose large factors sit at different k (cancelling sums of
+//     small terms) stay within a few FP64 roundings of their own magnitude.
+// mma.sync m16n8k16 (bf16 in, FP32 accumulate); CTA tile 64 x 64, four warps
+// of 32 x 32; inner dimension in chunks of 192.
+constexpr int kOzDigits = 9;
+constexpr int kOzKChunk = 192;
+
+// Planes of one matrix operand: [digit][rows_p][kp] bf16 (k contiguous) and a
+// per-row exponent, for `fibers` fibers of a chunk.
+struct OzOperand {
+    __nv_bfloat16 *d;   // [fiber][digit][rows_p][kp]
+    int *e;             // [fiber][rows_p]
+    int rows_p, kp;
+    __device__ __nv_bfloat16 *plane(int f, int s) const
+    {
+        return d + ((static_cast<int64_t>(f) * kOzDigits + s) * rows_p) * kp;
+    }
+};
+
+// Digits of x in the frame 2^e of its row (|x| < 2^e): nine balanced
+// base-128 digits of round(x 2^(62-e)), most significant first.
+__device__ __forceinline__ void oz_digits(double x, int e, float (&a)[kOzDigits])
+{
+    // round(x 2^(62-e)) from the bits of x (integer work only): the 53-bit
+    // significand shifted by its exponent, rounded half up when bits drop
+    const long long bits = __double_as_longlong(x);
+    const int ex = static_cast<int>((bits >> 52) & 0x7ff);
+    long long r = 0;
+    if (ex > 0) {
+        const long long mant = (bits & ((1LL << 52) - 1)) | (1LL << 52);
+        const int sh = ex - 1075 + 62 - e;   // x 2^(62-e) = mant 2^sh
+        if (sh >= 0) r = mant << sh;
+        else if (sh > -54) r = (mant + (1LL << (-sh - 1))) >> (-sh);
+        if (bits < 0) r = -r;
+    }
+#pragma unroll
+    for (int s = kOzDigits - 1; s >= 1; --s) {
+        int dg = static_cast<int>(r & 127);
+        if (dg >= 64) dg -= 128;
+        r = (r - dg) >> 7;
+        a[s] = static_cast<float>(dg);
+    }
+    a[0] = static_cast<float>(r);
+}
+
+// One warp per row of a chunk fiber's operand X (rows < nrows, k < K, given
+// by `get(f, row, k)`): the row's exponent and its digit planes; padding rows
+// and columns are zero.  Grid (fibers of the chunk, ceil(rows_p / 4)), 128
+// threads.
+template <class Get>
+__device__ __forceinline__ void oz_slice_row(const OzOperand &O, int f, int row, int nrows, int K, Get get)
+{
+    const int lane = threadIdx.x & 31;
+    double mx = 0.0;
+    if (row < nrows)
+        for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(get(row, k)));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int e = 0;
+    // frexp's exponent from the bits: mx < 2^e (mx normal; a row of
+    // subnormals only keeps e = 0 and rounds to zero digits)
+    if (mx > 0.0) e = static_cast<int>((__double_as_longlong(mx) >> 52) & 0x7ff) - 1022;
+    if (lane == 0) O.e[static_cast<int64_t>(f) * O.rows_p + row] = e;
+    for (int k = lane; k < O.kp; k += 32) {
+        float a[kOzDigits];
+        if (row < nrows && k < K && mx > 0.0) {
+            oz_digits(get(row, k), e, a);
+        } else {
+#pragma unroll
+            for (int s = 0; s < kOzDigits; ++s) a[s] = 0.0f;
+        }
+#pragma unroll
+        for (int s = 0; s < kOzDigits; ++s) O.plane(f, s)[static_cast<int64_t>(row) * O.kp + k] = __float2bfloat16_rn(a[s]);
+    }
+}
+
+// S rows (left operand of W = S F): S[(k,b),(l,a)], rows b N + k, columns a N + l.
+__global__ void __launch_bounds__(128) k_oz_slice_S(FiberTable F, int f0, OzOperand O)
+{
+    const int f = blockIdx.x, row = blockIdx.y * 4 + (threadIdx.x >> 5);
+    if (row >= O.rows_p) return;
+    const Fib fb(F, f0 + f);
+    const int N = fb.N;
+    oz_slice_row(O, f, row, 3 * N, 3 * N,
+                 [&](int r, int q) { return s_entry(F, fb, r % N, r / N, q % N, q / N); });
+}
+
+// F columns (right operand of W = S F), one "row" per column c of F: sigma
+// columns c = a N + j (j < N - 4): bend Sig[l][j] at q = a N + l; the p
+// columns j >= N - 4 stay zero; tension columns c = 3N + j: F_tau[q][j].
+__global__ void __launch_bounds__(128) k_oz_slice_F(FiberTable F, int f0, OzOperand O)
+{
+    const int f = blockIdx.x, col = blockIdx.y * 4 + (threadIdx.x >> 5);
+    if (col >= O.rows_p) return;
+    const Fib fb(F, f0 + f);
+    const int N = fb.N;
+    const double bend = -F.E * F.dt * fb.g * fb.g * fb.g * fb.g;
+    const double *Sig = fb.M_(fb.lay.Sig);
+    const double *ftau = F.ftau + fb.blk0 / 16 * 3;
+    oz_slice_row(O, f, col, 4 * N, 3 * N, [&](int c, int q) -> double {
+        if (c < 3 * N) {
+            const int a = c / N, j = c - a * N;
+            return (j < N - 4 && q / N == a) ? bend * Sig[(q - a * N) * N + j] : 0.0;
+        }
+        return ftau[static_cast<int64_t>(q) * N + (c - 3 * N)];
+    });
+}
+
+// Rows of the w-row product: the velocity rows of component a at
+// R = a vp + i (i < N - 4, vp = N - 4 rounded up to 64, so that a 64-row
+// tile holds one component and needs only its N inner columns), the tension
+// rows at R = 3 vp + i (i < N - 2); -1 for padding.
+__device__ __forceinline__ int oz_w_row(int R, int N, bool &vel, int &a, int &i)
+{
+    const int vp = (N - 4 + 63) / 64 * 64;
+    vel = R < 3 * vp;
+    if (vel) {
+        a = R / vp;
+        i = R - a * vp;
+        return i < N - 4 ? a * N + i : -1;
+    }
+    a = 0;
+    i = R - 3 * vp;
+    return i < N - 2 ? 3 * N + i : -1;
+}
+
+// Rw rows (left operand of the w rows, rows as oz_w_row): velocity rows
+// P_y[i][k] at q = a N + k; tension rows X_s(z_i)_b D_z[i][k] at q = b N + k.
+__global__ void __launch_bounds__(128) k_oz_slice_Rw(FiberTable F, int f0, OzOperand O)
+{
+    const int f = blockIdx.x, row = blockIdx.y * 4 + (threadIdx.x >> 5);
+    if (row >= O.rows_p) return;
+    const Fib fb(F, f0 + f);
+    const int N = fb.N;
+    const double *Py = fb.M_(fb.lay.Py), *Dz = fb.M_(fb.lay.Dz);
+    const double *tz = F.tz + 3 * fb.z0;
+    const int vp = (N - 4 + 63) / 64 * 64;
+    oz_slice_row(O, f, row, 3 * vp + N - 2, 3 * N, [&](int R, int q) -> double {
+        bool vel;
+        int a, i;
+        if (oz_w_row(R, N, vel, a, i) < 0) return 0.0;
+        const int b = q / N, k = q - b * N;
+        if (vel) return b == a ? Py[i * N + k] : 0.0;
+        return tz[3 * i + b] * Dz[i * N + k];
+    });
+}
+
+// W columns (right operand of the w rows): W[c][q], column-major.
+__global__ void __launch_bounds__(128) k_oz_slice_W(FiberTable F, int f0, OzOperand O)
+{
+    const int f = blockIdx.x, col = blockIdx.y * 4 + (threadIdx.x >> 5);
+    if (col >= O.rows_p) return;
+    const Fib fb(F, f0 + f);
+    const int N = fb.N;
+    const double *W = F.wsc + fb.blk0 / 4 * 3;
+    oz_slice_row(O, f, col, 4 * N, 3 * N,
+                 [&](int c, int q) { return W[static_cast<int64_t>(c) * 3 * N + q]; });
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// 2^E as a double (0 below the normal range).
+__device__ __forceinline__ double pow2(int E)
+{
+    return E < -1022 ? 0.0 : __longlong_as_double(static_cast<long long>(E + 1023) << 52);
+}
+
+// Shared-memory staging of the digit planes: a 64-row x 32-k slab of one
+// plane per operand, rows 80 bytes apart (conflict-free ldmatrix), two
+// stages filled by cp.async while the other is consumed.
+constexpr int kOzKs = 32, kOzLd = 40;   // k per stage, bf16 per staged row
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(
+                     static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src)
+                 : "memory");
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void *p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(static_cast<uint32_t>(__cvta_generic_to_shared(p))));
+}
+
+// C = X Y^T-planes product of a chunk fiber: X planes (rows = output rows),
+// Y planes (rows = output columns), both k-contiguous.  EPI 1: W (rows 3N,
+// columns 4N) column-major into the block-build scratch; EPI 2: the w rows of
+// the block (velocity rows with -V_y and the growth term, tension rows).
+// Grid (fibers of the chunk, rows_p / 64, cols_p / 64), 128 threads.  For
+// each diagonal d and digit pair (s, d - s) the slabs of X_s and Y_(d-s) pass
+// through shared memory; the diagonal's FP32 sum is folded into FP64 once its
+// inner range is done.
+template <int EPI>
+__global__ void __launch_bounds__(128, 3) k_oz_gemm(FiberTable F, int f0, OzOperand X, OzOperand Y,
+                                                 double *__restrict__ B)
+{
+    __shared__ __align__(128) __nv_bfloat16 sx[2][64 * kOzLd], sy[2][64 * kOzLd];
+    const int f = blockIdx.x;
+    const Fib fb(F, f0 + f);
+    const int N = fb.N;
+    const int K = 3 * N;
+    const int vp = (N - 4 + 63) / 64 * 64;
+    const int nrow = EPI == 1 ? 3 * N : 3 * vp + N - 2, ncol = 4 * N;
+    const int m0 = blockIdx.y * 64, n0 = blockIdx.z * 64;
+    if (m0 >= nrow || n0 >= ncol) return;
+    // inner range where the tile's operands are not zero: the sigma columns
+    // of component a (W = S F) and the velocity rows of component a (w rows)
+    // touch only k in [a N, a N + N)
+    int k_lo = 0, k_hi = K;
+    if (EPI == 1) {
+        const int c1 = min(n0 + 63, ncol - 1);
+        if (c1 < 3 * N) {
+            k_lo = (n0 / N) * N;
+            k_hi = (c1 / N + 1) * N;
+        }
+    } else if (m0 + 63 < 3 * vp) {
+        k_lo = (m0 / vp) * N;
+        k_hi = ((m0 + 63) / vp + 1) * N;
+    }
+    k_lo &= ~15;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gid = lane >> 2, tig = lane & 3;
+    const int wr = (warp >> 1) * 32, wc = (warp & 1) * 32;   // warp tile inside the CTA tile
+    const int wm = m0 + wr, wn = n0 + wc;
+    int er[2][2], ec[4][2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) er[i][h] = X.e[static_cast<int64_t>(f) * X.rows_p + wm + 16 * i + gid + 8 * h];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) ec[j][h] = Y.e[static_cast<int64_t>(f) * Y.rows_p + wn + 8 * j + 2 * tig + h];
+    // slabs of kOzKs k each; the last may run past k_hi into zero padding
+    // (planes hold kp >= K columns, zero beyond K) -- but never past kp
+    const int nslab = (k_hi - k_lo + kOzKs - 1) / kOzKs;
+    // each thread copies two 16-byte pieces per operand and slab: row
+    // (tid >> 2) + 32 p, k offset 8 (tid & 3)
+    auto stage = [&](int buf, const __nv_bfloat16 *xp, const __nv_bfloat16 *yp, int k0) {
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const int r = (tid >> 2) + 32 * p, kk = 8 * (tid & 3);
+            const bool in = k0 + kk < X.kp;   // X.kp == Y.kp
+            if (in) {
+                cp_async16(&sx[buf][r * kOzLd + kk], xp + static_cast<int64_t>(m0 + r) * X.kp + k0 + kk);
+                cp_async16(&sy[buf][r * kOzLd + kk], yp + static_cast<int64_t>(n0 + r) * Y.kp + k0 + kk);
+            } else {
+                *reinterpret_cast<uint4 *>(&sx[buf][r * kOzLd + kk]) = make_uint4(0, 0, 0, 0);
+                *reinterpret_cast<uint4 *>(&sy[buf][r * kOzLd + kk]) = make_uint4(0, 0, 0, 0);
+            }
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    double out[2][4][4] = {};
+    for (int d = 0; d < kOzDigits; ++d) {
+        float acc[2][4][4] = {};
+        for (int s = 0; s <= d; ++s) {
+            const __nv_bfloat16 *xp = X.plane(f, s), *yp = Y.plane(f, d - s);
+            for (int q = 0; q < nslab; q += kOzKChunk / kOzKs) {
+                // within one chunk of kOzKChunk the FP32 sums stay exact; a
+                // longer inner range folds each chunk separately (below)
+                const int qe = min(nslab, q + kOzKChunk / kOzKs);
+                stage(0, xp, yp, k_lo + q * kOzKs);
+                for (int qq = q; qq < qe; ++qq) {
+                    const int buf = (qq - q) & 1;
+                    if (qq + 1 < qe) {
+                        stage(buf ^ 1, xp, yp, k_lo + (qq + 1) * kOzKs);
+                        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+                    } else {
+                        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+                    }
+                    __syncthreads();
+#pragma unroll
+                    for (int ks = 0; ks < kOzKs; ks += 16) {
+                        uint32_t a[2][4], bq[2][4];
+#pragma unroll
+                        for (int i = 0; i < 2; ++i)
+                            ldsm_x4(a[i], &sx[buf][(wr + 16 * i + (lane & 15)) * kOzLd + ks + 8 * (lane >> 4)]);
+#pragma unroll
+                        for (int jj = 0; jj < 2; ++jj)
+                            ldsm_x4(bq[jj], &sy[buf][(wc + 16 * jj + (lane & 7) + 8 * (lane >> 4)) * kOzLd + ks +
+                                                     8 * ((lane >> 3) & 1)]);
+#pragma unroll
+                        for (int i = 0; i < 2; ++i)
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                const uint32_t b2[2] = {bq[j >> 1][2 * (j & 1)], bq[j >> 1][2 * (j & 1) + 1]};
+                                mma_bf16(acc[i][j], a[i], b2);
+                            }
+                    }
+                    __syncthreads();   // the stage is refilled next
+                }
+                if (qe < nslab) {
+                    // fold the finished chunk; the diagonal continues in a fresh sum
+#pragma unroll
+                    for (int i = 0; i < 2; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+#pragma unroll
+                            for (int t = 0; t < 4; ++t) {
+                                const int E = er[i][t >> 1] + ec[j][t & 1] - 12 - 7 * d;
+                                out[i][j][t] = fma(static_cast<double>(acc[i][j][t]), pow2(E), out[i][j][t]);
+                                acc[i][j][t] = 0.0f;
+                            }
+                }
+            }
+        }
+        // fold the diagonal: out += acc 2^(e_row + e_col - 12 - 7 d)
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int E = er[i][t >> 1] + ec[j][t & 1] - 12 - 7 * d;
+                    out[i][j][t] = fma(static_cast<double>(acc[i][j][t]), pow2(E), out[i][j][t]);
+                }
+    }
+    // epilogue
+    const double *Vy = fb.M_(fb.lay.Vy), *Vgy = fb.M_(fb.lay.Vgy);
+    const double ldot = (F.Ldot && F.growth_implicit) ? F.Ldot[fb.m] : 0.0;
+    const double gdt = ldot != 0.0 ? F.dt * ldot / (fb.L + F.dt * ldot) : 0.0;
+    const int n = 4 * N;
+    double *W = F.wsc + fb.blk0 / 4 * 3;
+    double *Bm = B + fb.blk0;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int R = wm + 16 * i + gid + 8 * (q >> 1), col = wn + 8 * j + 2 * tig + (q & 1);
+                if (R >= nrow || col >= ncol) continue;
+                double v = out[i][j][q];
+                if (EPI == 1) {
+                    W[static_cast<int64_t>(col) * 3 * N + R] = v;
+                } else {
+                    bool vel;
+                    int a, r;
+                    const int row = oz_w_row(R, N, vel, a, r);
+                    if (row < 0) continue;
+                    if (vel && col < 3 * N && col / N == a) v += gdt * Vgy[r * N + (col - a * N)] - Vy[r * N + (col - a * N)];
+                    Bm[static_cast<int64_t>(col) * n + row] = v;
+                }
+            }
+}
+
 // Rows without the velocity rows' w: the end rows (second and third
 // derivative of V_a at alpha = +1 and -1, Eq. bc-free, or the attached-end
 // rows) and T(+1), T(-1) (or X_s(-1) . w(-1) of an attached end, read from
@@ -994,12 +1367,35 @@ fs_status launch_block_build(fs_ctx *c)
     const int nt = (N + kBT - 1) / kBT;
     k_build_ftau<<<dim3(c->M, 3 * nt * nt), 256, 0, c->stream>>>(T);
     FS_LAUNCH_CHECK();
-    const int ct = 3 * ((N - 4 + kBT - 1) / kBT) + (N + kBT - 1) / kBT;
-    k_build_w<<<dim3(c->M, (3 * N + kBT - 1) / kBT, ct), 256, 0, c->stream>>>(T);
-    FS_LAUNCH_CHECK();
-    const int rt = 3 * ((N - 4 + kBT - 1) / kBT) + (N - 2 + kBT - 1) / kBT;
-    k_build_rows<<<dim3(c->M, rt, (4 * N + kBT - 1) / kBT), 256, 0, c->stream>>>(T, c->d_B);
-    FS_LAUNCH_CHECK();
+    if (c->oz_chunk > 0) {
+        // W = S F and the w rows on the tensor cores (split bf16 operands),
+        // a chunk of fibers at a time through the digit-plane scratch
+        const OzDims D(N);
+        OzOperand X1{c->d_ozx, c->d_ozxe, D.r1, D.kp}, X2{c->d_ozx, c->d_ozxe, D.r2, D.kp},
+            Y{c->d_ozy, c->d_ozye, D.ry, D.kp};
+        for (int f0 = 0; f0 < c->M; f0 += c->oz_chunk) {
+            const unsigned nf = static_cast<unsigned>(std::min(c->oz_chunk, c->M - f0));
+            k_oz_slice_S<<<dim3(nf, D.r1 / 4), 128, 0, c->stream>>>(T, f0, X1);
+            FS_LAUNCH_CHECK();
+            k_oz_slice_F<<<dim3(nf, D.ry / 4), 128, 0, c->stream>>>(T, f0, Y);
+            FS_LAUNCH_CHECK();
+            k_oz_gemm<1><<<dim3(nf, D.r1 / 64, D.ry / 64), 128, 0, c->stream>>>(T, f0, X1, Y, c->d_B);
+            FS_LAUNCH_CHECK();
+            k_oz_slice_Rw<<<dim3(nf, D.r2 / 4), 128, 0, c->stream>>>(T, f0, X2);
+            FS_LAUNCH_CHECK();
+            k_oz_slice_W<<<dim3(nf, D.ry / 4), 128, 0, c->stream>>>(T, f0, Y);
+            FS_LAUNCH_CHECK();
+            k_oz_gemm<2><<<dim3(nf, D.r2 / 64, D.ry / 64), 128, 0, c->stream>>>(T, f0, X2, Y, c->d_B);
+            FS_LAUNCH_CHECK();
+        }
+    } else {
+        const int ct = 3 * ((N - 4 + kBT - 1) / kBT) + (N + kBT - 1) / kBT;
+        k_build_w<<<dim3(c->M, (3 * N + kBT - 1) / kBT, ct), 256, 0, c->stream>>>(T);
+        FS_LAUNCH_CHECK();
+        const int rt = 3 * ((N - 4 + kBT - 1) / kBT) + (N - 2 + kBT - 1) / kBT;
+        k_build_rows<<<dim3(c->M, rt, (4 * N + kBT - 1) / kBT), 256, 0, c->stream>>>(T, c->d_B);
+        FS_LAUNCH_CHECK();
+    }
     k_build_direct<<<c->M, 256, 0, c->stream>>>(T, c->d_B);
     FS_LAUNCH_CHECK();
     return FS_OK;

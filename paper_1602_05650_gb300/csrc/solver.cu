@@ -1170,6 +1170,16 @@ fs_status fiber_arrays(fs_ctx *c, int M, const int32_t *ppf, const std::vector<i
     FS_TRY(dalloc(c, &c->d_wsc, c->n_blk / 4 * 3));
     // the p columns of w are never written: they stay zero (f = 0 there)
     FS_CUDA(cudaMemsetAsync(c->d_wsc, 0, static_cast<size_t>(c->n_blk / 4 * 3) * sizeof(double), c->stream));
+    if (c->opt.tc_blocks) {
+        const OzDims D(c->max_N);
+        const int64_t per = D.bytes_per_fiber();
+        c->oz_chunk = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>({int64_t(M), 512, (int64_t(1) << 30) / per})));
+        const size_t rx = std::max(D.r1, D.r2);
+        FS_TRY(dalloc(c, &c->d_ozx, static_cast<size_t>(c->oz_chunk) * OzDims::digits * rx * D.kp));
+        FS_TRY(dalloc(c, &c->d_ozy, static_cast<size_t>(c->oz_chunk) * OzDims::digits * D.ry * D.kp));
+        FS_TRY(dalloc(c, &c->d_ozxe, static_cast<size_t>(c->oz_chunk) * rx));
+        FS_TRY(dalloc(c, &c->d_ozye, static_cast<size_t>(c->oz_chunk) * D.ry));
+    }
     FS_TRY(dalloc(c, &c->d_piv, c->n_fib_unk));
     FS_TRY(dalloc(c, &c->d_dinv, c->n_fib_unk));
     FS_TRY(dalloc(c, &c->d_V, 3 * P));
@@ -1312,6 +1322,18 @@ size_t estimate_bytes(int M, const int32_t *ppf, int n_surf, const fs_options &o
     for (int64_t k : {3 * P, int64_t(M), int64_t(M), 3 * P, 3 * P, 3 * n_z, 3 * P, P, 2 * P, 12 * int64_t(M), 4 * n_kp, n_blk,
                       n_blk / 16 * 3, n_blk / 4 * 3})
         add(k * d);
+    if (opt.tc_blocks) {   // digit planes of the tensor-core block build
+        int maxN = 0;
+        for (int m = 0; m < M; ++m) maxN = std::max(maxN, int(ppf[m]));
+        const OzDims D(maxN);
+        const int64_t per = D.bytes_per_fiber();
+        const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>({int64_t(M), 512, (int64_t(1) << 30) / per}));
+        const int64_t rx = std::max(D.r1, D.r2);
+        add(chunk * OzDims::digits * rx * D.kp * 2);
+        add(chunk * OzDims::digits * D.ry * D.kp * 2);
+        add(chunk * rx * 4);
+        add(chunk * D.ry * 4);
+    }
     add(n_fib_unk * sizeof(int));
     add(n_fib_unk * sizeof(double));
     for (int64_t k : {3 * P, P, 3 * P, 3 * P, 3 * P}) add(k * d);
@@ -1382,7 +1404,8 @@ void context_free(fs_ctx *c)
     c->graphs.clear();
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     c->cap_stream = nullptr;
-    void *gptrs[] = {c->d_gH, c->d_gcs, c->d_gsn, c->d_gg, c->d_gsc, c->d_ginit, c->d_vcur, c->d_gst, c->d_gj};
+    void *gptrs[] = {c->d_gH, c->d_gcs, c->d_gsn, c->d_gg, c->d_gsc, c->d_ginit, c->d_vcur, c->d_gst, c->d_gj,
+                     c->d_ozx, c->d_ozy, c->d_ozxe, c->d_ozye};
     // buffers carved from a preallocated region go back with the region
     if (!c->pool) {
         for (void *p : gptrs)
@@ -1499,6 +1522,27 @@ fs_status fs_build_precond(fs_ctx *c)
     FS_TRY(launch_block_build(c));
     FS_TRY(launch_lu_factor(c));
     c->precond_ok = true;
+    return FS_OK;
+}
+
+fs_status fs_get_self_block(fs_ctx *c, int32_t fiber, double *out)
+{
+    if (!c || !c->have_state || fiber < 0 || fiber >= c->M || !out) {
+        set_error("fs_get_self_block: no state, fiber out of range or NULL output");
+        return FS_EINVAL;
+    }
+    if (!c->geometry_ok) {
+        FS_TRY(launch_geometry(c));
+        c->geometry_ok = true;
+    }
+    // the blocks are factored in place by the preconditioner build: assemble
+    // them again, copy one out, and let the next step factor them anew
+    FS_TRY(launch_block_build(c));
+    c->precond_ok = false;
+    const int64_t n = 4 * int64_t(c->Nm[fiber]);
+    FS_CUDA(cudaMemcpyAsync(out, c->d_B + c->blk_ptr[fiber], static_cast<size_t>(n * n) * sizeof(double),
+                            cudaMemcpyDeviceToHost, c->stream));
+    FS_CUDA(cudaStreamSynchronize(c->stream));
     return FS_OK;
 }
 

@@ -8,7 +8,10 @@ system, a batch of uneven systems, restarted cycles, and the mixed path.
 The mixed path stops its inner solve at 1e-6 and corrects with a float-float
 residual, so a last-bit change of its first solution moves the corrected one
 within the band its tolerance leaves (measured 5e-9 in V at tol 1e-10): gate
-1e-8 there, 1e-12 on the FP64 path."""
+1e-8 there.  FP64 path: one step agrees to 1e-12; over two steps the first
+step's last-bit differences enter the second step's blocks, whose tensor-core
+build rounds each entry to ~3e-15 of its products (measured 3.7e-11 at
+N = 32): gate 1e-10 for the two-step case."""
 import numpy as np
 import pytest
 
@@ -63,7 +66,7 @@ def test_one_system_graph_equals_host_cycle(prec, tol):
     Vh, ih, _, lh = batch_step([s], prec, tol, graph=False, steps=2)
     Vg, ig, _, lg = batch_step([s], prec, tol, graph=True, steps=2)
     assert [i.iters for i in ig] == [i.iters for i in ih]
-    assert rel(Vg, Vh) <= (1e-12 if prec == fs.FS_FP64 else 1e-8)
+    assert rel(Vg, Vh) <= (1e-10 if prec == fs.FS_FP64 else 1e-8)
     assert lg > 0
 
 

@@ -196,16 +196,19 @@ def test_not_converged_reports_and_keeps_state():
     fs.fs_destroy(h)
 
 
-@pytest.mark.parametrize("prec,tol,gate_v,gate_x", [(fs.FS_FP64, 1e-12, 5e-8, 3e-11),
-                                                     (fs.FS_MIXED, 1e-10, 3e-7, 1.5e-10)])
+@pytest.mark.parametrize("prec,tol,gate_v,gate_x", [(fs.FS_FP64, 1e-12, 5e-7, 3e-10),
+                                                     (fs.FS_MIXED, 1e-10, 1e-6, 5e-10)])
 def test_trajectory_of_five_steps(prec, tol, gate_v, gate_x):
     """Five consecutive steps, each side advancing its own state (the library
     from its X+, the oracle from its X+): 24 curved fibers, 32 points, a
     smooth load.  The two trajectories separate step by step: a difference
     dX of the positions enters the next step's free-end rows as ~N^6 dX / dt
-    (measured gaps, FP64 path: V 4e-11, 1e-9, 6e-9, 8e-9, 2e-8 with X at
-    4e-14 .. 1e-11; mixed path: V up to 1e-7, X up to 5e-11).  Gates, held
-    at every step: FP64 V 5e-8, X 3e-11; mixed V 3e-7, X 1.5e-10."""
+    and a rounding-level difference in the blocks grows from step to step
+    (measured gaps, FP64 path with the FP64 block build: V 4e-11, 1e-9, 6e-9,
+    8e-9, 2e-8 with X at 4e-14 .. 1e-11; with the tensor-core build, whose
+    blocks differ from the FP64 build's by 3e-15 of their products: V 4e-11,
+    1e-9, 5e-9, 2e-8, 2e-7 with X up to 1e-10; mixed path: V up to 1e-7).
+    Gates, held at every step: FP64 V 5e-7, X 3e-10; mixed V 1e-6, X 5e-10."""
     import copy
     from tests.gpu_helpers import dev, make_ctx
     s = gravity(wl.free_space(24, 32, 6.0, seed=8, curved_amp=0.05), (0.2, -0.1, -1.0))
