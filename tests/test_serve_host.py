@@ -15,12 +15,13 @@ def lib():
     return _native.load()
 
 
-def est(lib, ppf, ns=0, prec=_native.FS_MIXED, restart=60):
+def est(lib, ppf, ns=0, prec=_native.FS_MIXED, restart=60, tc_blocks=1):
     a = np.asarray(ppf, np.int32)
     o = _native.fs_options()
     lib.fs_options_default(ctypes.byref(o))
     o.prec = prec
     o.restart = restart
+    o.tc_blocks = tc_blocks
     return lib.fs_estimate_bytes(len(a), a.ctypes.data_as(ctypes.c_void_p), ns, ctypes.byref(o))
 
 
@@ -29,10 +30,14 @@ def test_estimate_grows_with_the_problem(lib):
     e2 = est(lib, [32] * 200)
     assert 0 < e1 < e2
     # the dense blocks and the block-build scratch (16 + 3 + 12 N^2 doubles
-    # per fiber) dominate at N = 64
-    e64 = est(lib, [64] * 1024)
+    # per fiber) dominate at N = 64 with the FP64 build
+    e64 = est(lib, [64] * 1024, tc_blocks=0)
     assert e64 >= 1024 * 31 * 64 * 64 * 8
     assert e64 < 2 * 1024 * 31 * 64 * 64 * 8
+    # the tensor-core build adds the digit planes of a chunk of 512 fibers:
+    # nine bf16 planes of both operands (256 rows each, 192 inner columns)
+    planes = 512 * 9 * (256 + 256) * 192 * 2
+    assert planes <= est(lib, [64] * 1024) - e64 < planes + (16 << 20)
     # mixed precision keeps the outer flexible-GMRES space on top of the inner one
     assert est(lib, [32] * 100, prec=_native.FS_MIXED) > est(lib, [32] * 100, prec=_native.FS_FP64)
     # a longer restart keeps more Krylov vectors
