@@ -1564,10 +1564,13 @@ fs_status fs_step(fs_ctx *c, fs_step_info *info)
         FS_CUDA(cudaStreamSynchronize(c->stream));
         tms[1] = ms_since(t0);
     }
-    // mixed precision: solve with an FP32 hi/lo right-hand side, then one
-    // float-float true residual and a plain FP32 correction
+    // mixed precision: solve with an FP32 right-hand side, then one
+    // float-float true residual and a plain FP32 correction.  The right-hand
+    // side's Stokeslet sum runs in the packed kernel (per-thread frames: the
+    // hi/lo accuracy on fiber nodes); with a boundary the stresslets keep
+    // hi/lo coordinates
     const bool split = c->opt.prec == FS_MIXED && c->opt.relax;
-    if (split) FS_TRY(rhs(c, c->d_b, c->d_pb, FS_SUM_FP32, true));
+    if (split) FS_TRY(rhs(c, c->d_b, c->d_pb, FS_SUM_FP32, c->surf.n > 0));
     else FS_TRY(rhs(c, c->d_b, c->d_pb));
     FS_TRY(check_status(c));
     if (info) tms[0] = ms_since(t0) - tms[1];
