@@ -634,13 +634,15 @@ __global__ void __launch_bounds__(256) k_build_rows(FiberTable F, double *__rest
 //     integer FP32 holds exactly; for the products of one diagonal s + t = d
 //     the sum over K <= 192 stays below 2^24 (9 x 192 x 65 x 64 < 2^23), so
 //     the tensor cores' FP32 accumulation of a diagonal is exact;
-//   * C = 2^(e+f) sum_{d<=8} 2^-(12+7d) acc_d, folded into FP64 one diagonal
-//     at a time.  The dropped diagonals d >= 9 weigh below 2^-52 of 2^(e+f);
+//   * C = 2^(e+f) sum_{d<=8} 2^-(12+7d) acc_d: each exact acc_d is added as
+//     an integer into one of two 64-bit sums (d <= 3 and d >= 4, each at its
+//     relative power of 128), and the two become one FP64 value with a single
+//     rounding.  The dropped diagonals d >= 9 weigh below 2^-52 of 2^(e+f);
 //     entries down to 2^-62 of their row's largest keep their digits, so
 //     products whose large factors sit at different k (cancelling sums of
 //     small terms) stay within a few FP64 roundings of their own magnitude.
-// mma.sync m16n8k16 (bf16 in, FP32 accumulate); CTA tile 64 x 64, four warps
-// of 32 x 32; inner dimension in chunks of 192.
+// mma.sync m16n8k16 (bf16 in, FP32 accumulate); CTA tile 64 x 64, eight warps
+// of 32 x 16; inner dimension in chunks of 192.
 constexpr int kOzDigits = 9;
 constexpr int kOzKChunk = 192;
 
@@ -834,13 +836,16 @@ __device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void *p)
 // Y planes (rows = output columns), both k-contiguous.  EPI 1: W (rows 3N,
 // columns 4N) column-major into the block-build scratch; EPI 2: the w rows of
 // the block (velocity rows with -V_y and the growth term, tension rows).
-// Grid (fibers of the chunk, rows_p / 64, cols_p / 64), 128 threads.  For
-// each diagonal d and digit pair (s, d - s) the slabs of X_s and Y_(d-s) pass
-// through shared memory; the diagonal's FP32 sum is folded into FP64 once its
-// inner range is done.
+// Grid (fibers of the chunk, rows_p / 64, cols_p / 64), 256 threads: eight
+// warps of 32 x 16.  For each diagonal d and digit pair (s, d - s) the slabs
+// of X_s and Y_(d-s) pass through shared memory.  A diagonal's exact FP32
+// sum is added, as an integer, into two 64-bit accumulators (diagonals 0..3
+// and 4..8 at their relative powers of 128), which become FP64 once at the
+// end: the FP64 pipe converts and scales twice per entry instead of folding
+// every diagonal.
 template <int EPI>
-__global__ void __launch_bounds__(128, 3) k_oz_gemm(FiberTable F, int f0, OzOperand X, OzOperand Y,
-                                                 double *__restrict__ B)
+__global__ void __launch_bounds__(256, 2) k_oz_gemm(FiberTable F, int f0, OzOperand X, OzOperand Y,
+                                                    double *__restrict__ B)
 {
     __shared__ __align__(128) __nv_bfloat16 sx[2][64 * kOzLd], sy[2][64 * kOzLd];
     const int f = blockIdx.x;
@@ -867,45 +872,32 @@ __global__ void __launch_bounds__(128, 3) k_oz_gemm(FiberTable F, int f0, OzOper
     }
     k_lo &= ~15;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gid = lane >> 2, tig = lane & 3;
-    const int wr = (warp >> 1) * 32, wc = (warp & 1) * 32;   // warp tile inside the CTA tile
+    const int wr = (warp >> 2) * 32, wc = (warp & 3) * 16;   // warp tile inside the CTA tile
     const int wm = m0 + wr, wn = n0 + wc;
-    int er[2][2], ec[4][2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) er[i][h] = X.e[static_cast<int64_t>(f) * X.rows_p + wm + 16 * i + gid + 8 * h];
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) ec[j][h] = Y.e[static_cast<int64_t>(f) * Y.rows_p + wn + 8 * j + 2 * tig + h];
     // slabs of kOzKs k each; the last may run past k_hi into zero padding
     // (planes hold kp >= K columns, zero beyond K) -- but never past kp
     const int nslab = (k_hi - k_lo + kOzKs - 1) / kOzKs;
-    // each thread copies two 16-byte pieces per operand and slab: row
-    // (tid >> 2) + 32 p, k offset 8 (tid & 3)
+    // each thread copies one 16-byte piece per operand and slab: row
+    // tid >> 2, k offset 8 (tid & 3)
     auto stage = [&](int buf, const __nv_bfloat16 *xp, const __nv_bfloat16 *yp, int k0) {
-#pragma unroll
-        for (int p = 0; p < 2; ++p) {
-            const int r = (tid >> 2) + 32 * p, kk = 8 * (tid & 3);
-            const bool in = k0 + kk < X.kp;   // X.kp == Y.kp
-            if (in) {
-                cp_async16(&sx[buf][r * kOzLd + kk], xp + static_cast<int64_t>(m0 + r) * X.kp + k0 + kk);
-                cp_async16(&sy[buf][r * kOzLd + kk], yp + static_cast<int64_t>(n0 + r) * Y.kp + k0 + kk);
-            } else {
-                *reinterpret_cast<uint4 *>(&sx[buf][r * kOzLd + kk]) = make_uint4(0, 0, 0, 0);
-                *reinterpret_cast<uint4 *>(&sy[buf][r * kOzLd + kk]) = make_uint4(0, 0, 0, 0);
-            }
+        const int r = tid >> 2, kk = 8 * (tid & 3);
+        if (k0 + kk < X.kp) {   // X.kp == Y.kp
+            cp_async16(&sx[buf][r * kOzLd + kk], xp + static_cast<int64_t>(m0 + r) * X.kp + k0 + kk);
+            cp_async16(&sy[buf][r * kOzLd + kk], yp + static_cast<int64_t>(n0 + r) * Y.kp + k0 + kk);
+        } else {
+            *reinterpret_cast<uint4 *>(&sx[buf][r * kOzLd + kk]) = make_uint4(0, 0, 0, 0);
+            *reinterpret_cast<uint4 *>(&sy[buf][r * kOzLd + kk]) = make_uint4(0, 0, 0, 0);
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
-    double out[2][4][4] = {};
+    long long hi[2][2][4] = {}, lo[2][2][4] = {};
     for (int d = 0; d < kOzDigits; ++d) {
-        float acc[2][4][4] = {};
+        float acc[2][2][4] = {};
         for (int s = 0; s <= d; ++s) {
             const __nv_bfloat16 *xp = X.plane(f, s), *yp = Y.plane(f, d - s);
             for (int q = 0; q < nslab; q += kOzKChunk / kOzKs) {
                 // within one chunk of kOzKChunk the FP32 sums stay exact; a
-                // longer inner range folds each chunk separately (below)
+                // longer inner range adds each chunk to the integers (below)
                 const int qe = min(nslab, q + kOzKChunk / kOzKs);
                 stage(0, xp, yp, k_lo + q * kOzKs);
                 for (int qq = q; qq < qe; ++qq) {
@@ -919,50 +911,52 @@ __global__ void __launch_bounds__(128, 3) k_oz_gemm(FiberTable F, int f0, OzOper
                     __syncthreads();
 #pragma unroll
                     for (int ks = 0; ks < kOzKs; ks += 16) {
-                        uint32_t a[2][4], bq[2][4];
+                        uint32_t a[2][4], bq[4];
 #pragma unroll
                         for (int i = 0; i < 2; ++i)
                             ldsm_x4(a[i], &sx[buf][(wr + 16 * i + (lane & 15)) * kOzLd + ks + 8 * (lane >> 4)]);
-#pragma unroll
-                        for (int jj = 0; jj < 2; ++jj)
-                            ldsm_x4(bq[jj], &sy[buf][(wc + 16 * jj + (lane & 7) + 8 * (lane >> 4)) * kOzLd + ks +
-                                                     8 * ((lane >> 3) & 1)]);
+                        ldsm_x4(bq, &sy[buf][(wc + (lane & 7) + 8 * (lane >> 4)) * kOzLd + ks + 8 * ((lane >> 3) & 1)]);
 #pragma unroll
                         for (int i = 0; i < 2; ++i)
 #pragma unroll
-                            for (int j = 0; j < 4; ++j) {
-                                const uint32_t b2[2] = {bq[j >> 1][2 * (j & 1)], bq[j >> 1][2 * (j & 1) + 1]};
+                            for (int j = 0; j < 2; ++j) {
+                                const uint32_t b2[2] = {bq[2 * j], bq[2 * j + 1]};
                                 mma_bf16(acc[i][j], a[i], b2);
                             }
                     }
                     __syncthreads();   // the stage is refilled next
                 }
-                if (qe < nslab) {
-                    // fold the finished chunk; the diagonal continues in a fresh sum
+                if (qe < nslab || s == d) {
+                    // the chunk's (or the diagonal's) exact sum into the integers
 #pragma unroll
                     for (int i = 0; i < 2; ++i)
 #pragma unroll
-                        for (int j = 0; j < 4; ++j)
+                        for (int j = 0; j < 2; ++j)
 #pragma unroll
                             for (int t = 0; t < 4; ++t) {
-                                const int E = er[i][t >> 1] + ec[j][t & 1] - 12 - 7 * d;
-                                out[i][j][t] = fma(static_cast<double>(acc[i][j][t]), pow2(E), out[i][j][t]);
+                                const long long v = __float2int_rn(acc[i][j][t]);
+                                if (d < 4) hi[i][j][t] += v << (7 * (3 - d));
+                                else lo[i][j][t] += v << (7 * (8 - d));
                                 acc[i][j][t] = 0.0f;
                             }
                 }
             }
         }
-        // fold the diagonal: out += acc 2^(e_row + e_col - 12 - 7 d)
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int E = er[i][t >> 1] + ec[j][t & 1] - 12 - 7 * d;
-                    out[i][j][t] = fma(static_cast<double>(acc[i][j][t]), pow2(E), out[i][j][t]);
-                }
     }
+    // out = 2^(e_row + e_col - 12) (hi 2^-21 + lo 2^-56)
+    double out[2][2][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int er = X.e[static_cast<int64_t>(f) * X.rows_p + wm + 16 * i + gid + 8 * (t >> 1)];
+                const int ec = Y.e[static_cast<int64_t>(f) * Y.rows_p + wn + 8 * j + 2 * tig + (t & 1)];
+                const int E = er + ec - 12;
+                out[i][j][t] = fma(static_cast<double>(hi[i][j][t]), pow2(E - 21),
+                                   static_cast<double>(lo[i][j][t]) * pow2(E - 56));
+            }
     // epilogue
     const double *Vy = fb.M_(fb.lay.Vy), *Vgy = fb.M_(fb.lay.Vgy);
     const double ldot = (F.Ldot && F.growth_implicit) ? F.Ldot[fb.m] : 0.0;
@@ -973,7 +967,7 @@ __global__ void __launch_bounds__(128, 3) k_oz_gemm(FiberTable F, int f0, OzOper
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < 2; ++j)
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int R = wm + 16 * i + gid + 8 * (q >> 1), col = wn + 8 * j + 2 * tig + (q & 1);
@@ -1379,13 +1373,13 @@ fs_status launch_block_build(fs_ctx *c)
             FS_LAUNCH_CHECK();
             k_oz_slice_F<<<dim3(nf, D.ry / 4), 128, 0, c->stream>>>(T, f0, Y);
             FS_LAUNCH_CHECK();
-            k_oz_gemm<1><<<dim3(nf, D.r1 / 64, D.ry / 64), 128, 0, c->stream>>>(T, f0, X1, Y, c->d_B);
+            k_oz_gemm<1><<<dim3(nf, D.r1 / 64, D.ry / 64), 256, 0, c->stream>>>(T, f0, X1, Y, c->d_B);
             FS_LAUNCH_CHECK();
             k_oz_slice_Rw<<<dim3(nf, D.r2 / 4), 128, 0, c->stream>>>(T, f0, X2);
             FS_LAUNCH_CHECK();
             k_oz_slice_W<<<dim3(nf, D.ry / 4), 128, 0, c->stream>>>(T, f0, Y);
             FS_LAUNCH_CHECK();
-            k_oz_gemm<2><<<dim3(nf, D.r2 / 64, D.ry / 64), 128, 0, c->stream>>>(T, f0, X2, Y, c->d_B);
+            k_oz_gemm<2><<<dim3(nf, D.r2 / 64, D.ry / 64), 256, 0, c->stream>>>(T, f0, X2, Y, c->d_B);
             FS_LAUNCH_CHECK();
         }
     } else {
