@@ -304,10 +304,43 @@ def run_workload(args, ws, rank, local, fs, torch):
               31 points clamped to a sphere inside a sphere six radii out,
               force on the sphere, GMRES 1e-5): steps/s and GMRES iterations
               per step, FP64 (up to 512 fibers) and mixed, advanced --steps
-              steps after --warmup steps."""
+              steps after --warmup steps;
+    precond   the preconditioner build (fs_build_precond: self blocks and
+              their LU) of curved free-space clouds at N = 16, 32, 64 (4,096,
+              2,048, 1,024 fibers): FP64 build and LU, tensor-core build with
+              the FP64 LU, tensor-core build and LU; ms per build, CUDA events
+              over --steps builds after --warmup."""
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     out = {"workload": args.workload, "data": "synthetic"}
+    if args.workload == "precond":
+        res = {}
+        for N, M in ((16, 4096), (32, 2048), (64, 1024)):
+            s = wl.free_space(M, N, 40.0 * (M / 1024) ** (1 / 3), seed=rank, curved_amp=0.05)
+            X = torch.tensor(s.X, dtype=torch.float64, device=dev)
+            L = torch.tensor(s.L, dtype=torch.float64, device=dev)
+            F = torch.tensor(s.f_ext, dtype=torch.float64, device=dev)
+            for name, tcb, tcl in (("fp64", 0, 0), ("tc_build", 1, 0), ("tc_build_lu", 1, 1)):
+                opt = fs.fs_options_default()
+                opt.tc_blocks, opt.tc_lu = tcb, tcl
+                h = fs.fs_create(s.n_per_fiber, s.mu, s.eps, s.E, s.dt, options=opt, stream=stream)
+                fs.fs_set_state(h, X, L, F)
+                for _ in range(args.warmup):
+                    fs.fs_build_precond(h)
+                stream.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(args.steps):
+                    fs.fs_build_precond(h)
+                e1.record(stream)
+                e1.synchronize()
+                res["N%d_%s" % (N, name)] = round(e0.elapsed_time(e1) / max(args.steps, 1), 3)
+                fs.fs_destroy(h)
+        out.update({"ms_per_build": res, "fibers": {"16": 4096, "32": 2048, "64": 1024}})
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        return
     if args.workload in ("confined", "batched"):
         if args.workload == "confined":
             s = wl.cfg_confined(seed=rank)
@@ -709,7 +742,7 @@ def main():
                     help="far-field launch shape id (0 = default; 1..3 = targets per thread FP32 2/4/8, "
                          "float-float 1/2/4)")
     ap.add_argument("--workload", choices=["confined", "batched", "large", "sediment", "kinetics", "aster",
-                                           "tree-step", "tree-case"],
+                                           "tree-step", "tree-case", "precond"],
                     default=None,
                     help="a secondary workload instead of the headline step benchmark")
     ap.add_argument("--tree-order", type=int, default=8, help="--workload tree-case: expansion order")

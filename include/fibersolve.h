@@ -162,10 +162,16 @@ typedef struct {
     int32_t tc_blocks;      /* 1 = the two large products of the self-block build (W = S F
                                and the w rows Rw W, Eq. prec) on the bf16 tensor cores by
                                operand splitting: each row / column scaled by a power of
-                               two and split into eight 7-bit digits, the digit products
-                               summed exactly in FP32 per diagonal and folded in FP64, an
-                               FP64-grade result (error below the FP64 product's bound);
-                               0 = FP64 CUDA cores (default 1) */
+                               two and rounded to a 62-bit integer split into nine 7-bit
+                               digits, the digit products summed exactly in FP32 per
+                               diagonal, the diagonals summed as integers and rounded once
+                               to FP64, an FP64-grade result (error below the FP64
+                               product's bound); 0 = FP64 CUDA cores (default 1) */
+    int32_t tc_lu;          /* 1 = the block LU's trailing updates A22 -= L21 U12 (panels
+                               of 32 columns) on the bf16 tensor cores by the same split,
+                               the panels (pivoting) on the FP64 pipe; used while a
+                               fiber's 4N x 32 panel fits in shared memory (N <= 200),
+                               else the FP64 LU; 0 = FP64 LU (default 1) */
 } fs_options;
 
 /* Direct-sum kernel classes reported by fs_kernel_stats. */
@@ -367,7 +373,9 @@ fs_status fs_surface_apply(fs_ctx *ctx, const double *q, double *out, int32_t su
 
 /* Assemble the per-fiber self blocks (Eq. prec: fiber rows with the
  * complementary velocity removed, Sec. 3.3) for the current state and LU-factor
- * them with partial pivoting (FP64).  Called by fs_step when needed. */
+ * them with partial pivoting: FP64 panels, and the trailing updates on the
+ * tensor cores by split operands (FP64-grade) with fs_options.tc_lu, else on
+ * the FP64 pipe.  Called by fs_step when needed. */
 fs_status fs_build_precond(fs_ctx *ctx);
 
 /* The assembled self block B_m of one fiber (Eq. prec; before its LU
@@ -377,6 +385,15 @@ fs_status fs_build_precond(fs_ctx *ctx);
  * fs_step factors them again) and synchronises the stream.  For tests and
  * diagnostics: with fs_options.tc_blocks it shows the tensor-core build. */
 fs_status fs_get_self_block(fs_ctx *ctx, int32_t fiber, double *out);
+
+/* The LU factors of one fiber's self block (Eq. prec, factored with partial
+ * pivoting by fs_build_precond, which this calls first when the factors are
+ * not current): lu receives the column-major (4N)^2 doubles of L (unit lower,
+ * below the diagonal) and U (upper) in one array, piv the 4N row indices
+ * with P B = L U, row i of P B being row piv[i] of B; both HOST arrays.
+ * Synchronises the stream.  For tests and diagnostics: with fs_options.tc_lu
+ * it shows the LU with tensor-core trailing updates. */
+fs_status fs_get_block_lu(fs_ctx *ctx, int32_t fiber, double *lu, int32_t *piv);
 
 /* One implicit backward-Euler step (Sec. 3.2, set:time-stepping): solve
  * P^-1 A u = P^-1 b by GMRES with the block-Jacobi preconditioner P of Eq. prec

@@ -21,7 +21,7 @@ __all__ = ["fs_options_default", "fs_create", "fs_create_batch", "fs_batch_info"
            "fs_stokeslet_apply", "fs_stresslet_apply", "fs_surface_apply", "fs_build_precond",
            "fs_step", "fs_sizes", "fs_last_error", "fs_kernel_stats", "fs_kernel_launches",
            "fs_probe_fma", "fs_estimate_bytes", "fs_device_bytes", "fs_server_create", "fs_submit",
-           "fs_poll", "fs_server_wait", "fs_server_stats", "fs_server_batches", "fs_server_destroy", "Server", "fs_get_self_block",
+           "fs_poll", "fs_server_wait", "fs_server_stats", "fs_server_batches", "fs_server_destroy", "Server", "fs_get_self_block", "fs_get_block_lu",
            "FsError",
            "fs_set_growth", "fs_get_lengths", "fs_get_unknowns", "fs_dynamic_instability",
            "FS_FP64", "FS_MIXED",
@@ -481,6 +481,18 @@ def fs_get_self_block(h: Handle, fiber: int, n_points: int):
     _check(_native.load().fs_get_self_block(h.ptr, int(fiber), out.ctypes.data_as(ctypes.c_void_p)),
            "fs_get_self_block")
     return out.reshape(n, n).T   # column-major storage
+
+
+def fs_get_block_lu(h: Handle, fiber: int, n_points: int):
+    """The LU factors of one fiber's self block: (LU, piv) with LU the (4N, 4N)
+    array holding L below the diagonal (unit diagonal implied) and U on and
+    above it, and P B = L U where row i of P B is row piv[i] of B."""
+    n = 4 * int(n_points)
+    lu = np.zeros(n * n)
+    piv = np.zeros(n, dtype=np.int32)
+    _check(_native.load().fs_get_block_lu(h.ptr, int(fiber), lu.ctypes.data_as(ctypes.c_void_p),
+                                          piv.ctypes.data_as(ctypes.c_void_p)), "fs_get_block_lu")
+    return lu.reshape(n, n).T, piv
 
 
 def fs_server_batches(sv: Server) -> int:

@@ -93,8 +93,8 @@ fs_status check_options(const fs_options &o, const char *who, int n_systems)
         set_error("%s: delta_over_L must be finite and >= 0", who);
         return FS_EINVAL;
     }
-    if ((o.lsb | o.relax | o.profile | o.growth_implicit | o.tc_blocks) & ~1) {
-        set_error("%s: lsb, relax, profile, growth_implicit and tc_blocks are 0 or 1", who);
+    if ((o.lsb | o.relax | o.profile | o.growth_implicit | o.tc_blocks | o.tc_lu) & ~1) {
+        set_error("%s: lsb, relax, profile, growth_implicit, tc_blocks and tc_lu are 0 or 1", who);
         return FS_EINVAL;
     }
     if (o.use_graph != 0 && o.use_graph != 1) {
@@ -168,6 +168,7 @@ fs_status fs_options_default(fs_options *o)
     o->tree_theta = 0.5;
     o->growth_implicit = 0;
     o->tc_blocks = 1;
+    o->tc_lu = 1;
     return FS_OK;
 }
 

@@ -75,6 +75,23 @@ struct OzDims {
     }
 };
 
+// Digit planes of the LU's tensor-core trailing updates for fibers of at most
+// N points: per fiber and operand, nine planes of rows (4 N padded to 64) x 32
+// bf16 and one exponent per row; the LU runs on the tensor cores while one
+// CTA holds a fiber's panel rows one per thread (4 N <= 512).
+struct LuTcDims {
+    int rows, kp = 32;
+    __host__ __device__ explicit LuTcDims(int N) : rows((4 * N + 63) / 64 * 64) {}
+    __host__ __device__ static bool fits(int N) { return 4 * N <= 512; }
+    __host__ __device__ int64_t plane_elems() const { return int64_t(9) * rows * kp; }
+};
+
+struct OzPlan {
+    int oz_chunk = 0, lu_chunk = 0;
+    int64_t x = 0, y = 0, xe = 0, ye = 0;
+};
+OzPlan oz_plan(int M, int maxN, const fs_options &o);
+
 // Host construction of one op set (FP64): returns `total` doubles.
 std::vector<double> build_ops(int N);
 
@@ -235,6 +252,9 @@ struct fs_ctx {
     // tensor-core block build (opt.tc_blocks): digit planes of a chunk of
     // oz_chunk fibers (0: the FP64 CUDA-core build)
     int oz_chunk = 0;
+    // fibers per chunk of the LU with tensor-core trailing updates (0: k_lu);
+    // its digit planes live in d_ozx / d_ozy, its exponents in d_ozxe / d_ozye
+    int lu_chunk = 0;
     __nv_bfloat16 *d_ozx = nullptr, *d_ozy = nullptr;
     int *d_ozxe = nullptr, *d_ozye = nullptr;
     fs::Pool *pool = nullptr;     // preallocated region for every buffer (serving), or nullptr

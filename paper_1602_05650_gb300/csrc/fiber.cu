@@ -692,18 +692,20 @@ template <class Get>
 __device__ __forceinline__ void oz_slice_row(const OzOperand &O, int f, int row, int nrows, int K, Get get)
 {
     const int lane = threadIdx.x & 31;
-    double mx = 0.0;
+    // the row's largest magnitude through bit patterns (monotone for
+    // non-negative doubles; integer work, not the FP64 pipe)
+    long long mb = 0;
     if (row < nrows)
-        for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(get(row, k)));
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        for (int k = lane; k < K; k += 32) mb = max(mb, __double_as_longlong(get(row, k)) & 0x7fffffffffffffffLL);
+    for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
     int e = 0;
-    // frexp's exponent from the bits: mx < 2^e (mx normal; a row of
+    // frexp's exponent from the bits: max < 2^e (normal; a row of
     // subnormals only keeps e = 0 and rounds to zero digits)
-    if (mx > 0.0) e = static_cast<int>((__double_as_longlong(mx) >> 52) & 0x7ff) - 1022;
+    if (mb > 0) e = static_cast<int>(mb >> 52) - 1022;
     if (lane == 0) O.e[static_cast<int64_t>(f) * O.rows_p + row] = e;
     for (int k = lane; k < O.kp; k += 32) {
         float a[kOzDigits];
-        if (row < nrows && k < K && mx > 0.0) {
+        if (row < nrows && k < K && mb > 0) {
             oz_digits(get(row, k), e, a);
         } else {
 #pragma unroll
@@ -810,6 +812,14 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
 __device__ __forceinline__ double pow2(int E)
 {
     return E < -1022 ? 0.0 : __longlong_as_double(static_cast<long long>(E + 1023) << 52);
+}
+
+// The split product's value 2^E (hi 2^-21 + lo 2^-56) from the two integer
+// sums of its diagonals (hi: 0..3, lo: 4..8): hi converts exactly (|hi| <
+// 2^53), lo rounds only beyond 2^53, and the FMA rounds once more.
+__device__ __forceinline__ double oz_fold(long long hi, long long lo, int E)
+{
+    return fma(static_cast<double>(hi), pow2(E - 21), static_cast<double>(lo) * pow2(E - 56));
 }
 
 // Shared-memory staging of the digit planes: a 64-row x 32-k slab of one
@@ -953,9 +963,7 @@ __global__ void __launch_bounds__(256, 2) k_oz_gemm(FiberTable F, int f0, OzOper
             for (int t = 0; t < 4; ++t) {
                 const int er = X.e[static_cast<int64_t>(f) * X.rows_p + wm + 16 * i + gid + 8 * (t >> 1)];
                 const int ec = Y.e[static_cast<int64_t>(f) * Y.rows_p + wn + 8 * j + 2 * tig + (t & 1)];
-                const int E = er + ec - 12;
-                out[i][j][t] = fma(static_cast<double>(hi[i][j][t]), pow2(E - 21),
-                                   static_cast<double>(lo[i][j][t]) * pow2(E - 56));
+                out[i][j][t] = oz_fold(hi[i][j][t], lo[i][j][t], er + ec - 12);
             }
     // epilogue
     const double *Vy = fb.M_(fb.lay.Vy), *Vgy = fb.M_(fb.lay.Vgy);
@@ -1208,6 +1216,347 @@ __global__ void __launch_bounds__(256) k_lu(FiberTable F, double *__restrict__ B
     }
 }
 
+// ------------------------------------------- LU with tensor-core updates
+// The same factorisation (partial pivoting, right-looking, panels of
+// kLuTcBW = 32 columns) as one launch per panel over a chunk of fibers:
+//   k_lu_panel: the panel (pivot search, swaps, scaling, rank-1 updates) on
+//     the FP64 pipe, the panel's swaps on the other columns, U12 = L11^-1 A12,
+//     and the digit planes of L21 (one plane row per trailing row) and of U12
+//     (one plane row per trailing column), 32 digits of k each;
+//   k_lu_trail: A22 -= L21 U12 on the bf16 tensor cores by the split of the
+//     block build (nine balanced base-128 digits of each row / column scaled
+//     by its power of two, exact FP32 sums per diagonal for K = 32: at most
+//     9 x 32 x 65 x 65 < 2^24), rounded once to FP64 and subtracted.
+// The product's error is a few units of 2^-62 of (row max of L21) x (column
+// max of U12), below the rounding of the FP64 update it replaces.  The pivots
+// are chosen by the same rule as k_lu from the same column values up to that
+// rounding; piv and dinv as k_lu.
+constexpr int kLuTcBW = 32;
+
+// Rows of one operand's digit planes: trailing rows (or columns) of a panel,
+// at most 4 N - 32, padded to 64.
+__host__ __device__ inline int lu_tc_rows(int max_N) { return (4 * max_N + 63) / 64 * 64; }
+
+// One plane row from one value per lane (k = lane): the row's exponent from
+// the warp's largest magnitude, then the nine digits of the lane's value.
+__device__ __forceinline__ void oz_slice_lane(const OzOperand &O, int f, int row, double v)
+{
+    const int lane = threadIdx.x & 31;
+    // the largest magnitude through bit patterns (integer work)
+    long long mb = __double_as_longlong(v) & 0x7fffffffffffffffLL;
+    for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    const int e = mb > 0 ? static_cast<int>(mb >> 52) - 1022 : 0;
+    if (lane == 0) O.e[static_cast<int64_t>(f) * O.rows_p + row] = e;
+    float a[kOzDigits];
+    oz_digits(mb > 0 ? v : 0.0, e, a);
+#pragma unroll
+    for (int s = 0; s < kOzDigits; ++s) O.plane(f, s)[static_cast<int64_t>(row) * O.kp + lane] = __float2bfloat16_rn(a[s]);
+}
+
+// Panel k0 of every fiber of the chunk: one CTA of NT >= 4 N - k0 threads
+// per fiber (64 to 512, the smallest that holds the step's largest panel),
+// thread r holding row r of the panel (rows k0.. of its 32 columns) in
+// registers.  Per column j: the pivot (largest |a_rj| over r >= j, lowest r
+// on ties, as k_lu) by a block-wide argmax; rows j and p exchanged through
+// shared memory, which also broadcasts the pivot row and its reciprocal; each
+// row below scales its multiplier and updates its own entries -- two
+// barriers per column, the rank-1 update in registers.  Then the panel's
+// swaps on the other columns, U12, and the digit planes.  Fibers with
+// 4 N <= k0 are done; a fiber's last panel writes dinv.
+template <int NT>
+__global__ void __launch_bounds__(NT, NT >= 256 ? 512 / NT : 4) k_lu_panel(FiberTable F, int f0, int k0, double *__restrict__ B,
+                                                           int *__restrict__ piv, double *__restrict__ dinv,
+                                                           int *__restrict__ status, OzOperand X, OzOperand Y)
+{
+    constexpr int BW = kLuTcBW, NW = NT / 32;
+    __shared__ double rowp[BW + 1], rowj[BW];
+    __shared__ double L11[BW][BW + 1];
+    __shared__ long long s_rv[NW];
+    __shared__ int s_ri[NW];
+    __shared__ int s_perm[NT], s_src[NT], s_touch[2 * BW], s_nt;
+    const int f = blockIdx.x;
+    const Fib fb(F, f0 + f);
+    const int n = 4 * fb.N;
+    if (k0 >= n) return;
+    double *A = B + fb.blk0;
+    int *pv = piv + fb.u0;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int kb = min(BW, n - k0), m = n - k0;
+    const int r = tid;
+    const bool own = r < m;
+    double a[BW];
+#pragma unroll
+    for (int c = 0; c < BW; ++c) a[c] = (own && c < kb) ? A[static_cast<int64_t>(k0 + c) * n + k0 + r] : 0.0;
+    if (own) {
+        s_perm[r] = k0 == 0 ? r : pv[k0 + r];
+        s_src[r] = r;
+    }
+#pragma unroll
+    for (int j = 0; j < BW; ++j) {
+        if (j >= kb) break;
+        // |a_rj| compared through its bit pattern (monotone for non-negative
+        // doubles): integer work, not the FP64 pipe
+        long long v = (own && r >= j) ? (__double_as_longlong(a[j]) & 0x7fffffffffffffffLL) : -1LL;
+        int bi = r;
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long ov = __shfl_xor_sync(0xffffffffu, v, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > v || (ov == v && oi < bi)) {
+                v = ov;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            s_rv[wid] = v;
+            s_ri[wid] = bi;
+        }
+        __syncthreads();
+        long long best = s_rv[0];
+        int p = s_ri[0];
+#pragma unroll
+        for (int w = 1; w < NW; ++w)
+            if (s_rv[w] > best || (s_rv[w] == best && s_ri[w] < p)) {
+                best = s_rv[w];
+                p = s_ri[w];
+            }
+        if (r == p) {
+#pragma unroll
+            for (int c = 0; c < BW; ++c) rowp[c] = a[c];
+            rowp[BW] = a[j] != 0.0 ? 1.0 / a[j] : 0.0;
+        }
+        if (r == j && p != j) {
+#pragma unroll
+            for (int c = 0; c < BW; ++c) rowj[c] = a[c];
+        }
+        if (tid == 0) {
+            if (best <= 0 || best >= 0x7ff0000000000000LL) atomicOr(status, DEV_ERR_NUMERIC);
+            int t = s_perm[j];
+            s_perm[j] = s_perm[p];
+            s_perm[p] = t;
+            t = s_src[j];
+            s_src[j] = s_src[p];
+            s_src[p] = t;
+        }
+        __syncthreads();
+        if (r == j) {
+#pragma unroll
+            for (int c = 0; c < BW; ++c) a[c] = rowp[c];
+        } else if (r == p) {
+#pragma unroll
+            for (int c = 0; c < BW; ++c) a[c] = rowj[c];
+        }
+        if (own && r > j) {
+            const double l = a[j] * rowp[BW];
+            a[j] = l;
+#pragma unroll
+            for (int c = j + 1; c < BW; ++c) a[c] = fma(-l, rowp[c], a[c]);
+        }
+    }
+    __syncthreads();
+    if (own) {
+#pragma unroll
+        for (int c = 0; c < BW; ++c)
+            if (c < kb) A[static_cast<int64_t>(k0 + c) * n + k0 + r] = a[c];
+        pv[k0 + r] = s_perm[r];
+    }
+    if (r < BW) {
+#pragma unroll
+        for (int c = 0; c < BW; ++c) L11[r][c] = a[c];
+    }
+    // the panel's swaps on the columns left and right of it, as one gather
+    // per column: row i of the panel's rows takes row src[i] (the composed
+    // swaps), for the at most 2 kb rows that move; whole columns per round so
+    // that every read precedes the writes of its column
+    if (wid == 0) {
+        int cnt = 0;
+        for (int base = 0; base < m; base += 32) {
+            const int i = base + lane;
+            const bool moved = i < m && s_src[i] != i;
+            const unsigned bal = __ballot_sync(0xffffffffu, moved);
+            if (moved) s_touch[cnt + __popc(bal & ((1u << lane) - 1u))] = i;
+            cnt += __popc(bal);
+        }
+        if (lane == 0) s_nt = cnt;
+    }
+    __syncthreads();
+    const int nt = s_nt, ncol = n - kb;
+    if (nt > 0) {
+        constexpr int Q = 4;
+        const int cpr = max(1, NT * Q / nt);   // whole columns per round
+        for (int c0 = 0; c0 < ncol; c0 += cpr) {
+            const int items = min(cpr, ncol - c0) * nt;
+            double v[Q];
+            int at[Q];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int id = q * NT + tid;
+                at[q] = -1;
+                if (id < items) {
+                    const int ci = c0 + id / nt, i = s_touch[id % nt];
+                    const int col = ci < k0 ? ci : ci + kb;
+                    at[q] = col * n + k0 + i;
+                    v[q] = A[static_cast<int64_t>(col) * n + k0 + s_src[i]];
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
+                if (at[q] >= 0) A[at[q]] = v[q];
+            __syncthreads();
+        }
+    }
+    const int nr = m - kb;
+    if (nr <= 0) {
+        // the fiber's last panel: reciprocals of U's diagonal for the solve
+        for (int i = tid; i < n; i += NT) {
+            const double d = A[static_cast<int64_t>(i) * n + i];
+            dinv[fb.u0 + i] = d != 0.0 ? 1.0 / d : 0.0;
+        }
+        return;
+    }
+    // digit planes of L21: thread r >= BW slices its own row i = r - BW
+    if (own && r >= BW) {
+        const int i = r - BW;
+        long long mb = 0;   // bits of the row's largest magnitude
+#pragma unroll
+        for (int c = 0; c < BW; ++c) mb = max(mb, __double_as_longlong(a[c]) & 0x7fffffffffffffffLL);
+        const bool nz = mb > 0;
+        const int e = nz ? static_cast<int>(mb >> 52) - 1022 : 0;
+        X.e[static_cast<int64_t>(f) * X.rows_p + i] = e;
+#pragma unroll
+        for (int g = 0; g < BW; g += 8) {
+            uint32_t w[kOzDigits][4];
+#pragma unroll
+            for (int h = 0; h < 8; h += 2) {
+                float d0[kOzDigits], d1[kOzDigits];
+                oz_digits(nz ? a[g + h] : 0.0, e, d0);
+                oz_digits(nz ? a[g + h + 1] : 0.0, e, d1);
+#pragma unroll
+                for (int s2 = 0; s2 < kOzDigits; ++s2) {
+                    const __nv_bfloat162 pr = __floats2bfloat162_rn(d0[s2], d1[s2]);
+                    w[s2][h / 2] = *reinterpret_cast<const uint32_t *>(&pr);
+                }
+            }
+#pragma unroll
+            for (int s2 = 0; s2 < kOzDigits; ++s2)
+                *reinterpret_cast<uint4 *>(X.plane(f, s2) + static_cast<int64_t>(i) * X.kp + g) =
+                    make_uint4(w[s2][0], w[s2][1], w[s2][2], w[s2][3]);
+        }
+    }
+    const int rows = (nr + 63) / 64 * 64;   // the rows the trailing tiles read
+    for (int i = nr + tid; i < rows; i += NT) {
+        X.e[static_cast<int64_t>(f) * X.rows_p + i] = 0;
+#pragma unroll
+        for (int s2 = 0; s2 < kOzDigits; ++s2)
+#pragma unroll
+            for (int g = 0; g < BW; g += 8)
+                *reinterpret_cast<uint4 *>(X.plane(f, s2) + static_cast<int64_t>(i) * X.kp + g) = make_uint4(0, 0, 0, 0);
+    }
+    // U12 = L11^-1 A12 (kb == BW == 32 here): one column per thread in
+    // registers, forward substitution with the unit lower triangle of L11
+    // (shared memory, the same entry for all threads: broadcast)
+    // (read through a volatile view: one shared load per use, not 496
+    // loop-invariant registers)
+    const volatile double(*Lv)[BW + 1] = L11;
+    for (int col = k0 + BW + tid; col < n; col += NT) {
+        double *Ac = A + static_cast<int64_t>(col) * n + k0;
+        double u[BW];
+#pragma unroll
+        for (int q = 0; q < BW; q += 2) {
+            const double2 t = *reinterpret_cast<const double2 *>(Ac + q);
+            u[q] = t.x;
+            u[q + 1] = t.y;
+        }
+#pragma unroll
+        for (int c = 0; c + 1 < BW; ++c)
+#pragma unroll
+            for (int r2 = c + 1; r2 < BW; ++r2) u[r2] = fma(-Lv[r2][c], u[c], u[r2]);
+#pragma unroll
+        for (int q = 0; q < BW; q += 2) *reinterpret_cast<double2 *>(Ac + q) = make_double2(u[q], u[q + 1]);
+    }
+    __syncthreads();   // U12 complete
+    // digit planes of U12: one warp per trailing column (lane = k); padding zero
+    for (int col = wid; col < rows; col += NW)
+        oz_slice_lane(Y, f, col, col < nr ? A[static_cast<int64_t>(k0 + BW + col) * n + k0 + lane] : 0.0);
+}
+
+// A22 -= L21 U12 for panel k0: grid (fibers of the chunk, tiles, tiles) of
+// 64 x 64 trailing tiles, 256 threads (eight warps of 32 x 16), all nine
+// digit slabs of both operands in shared memory (2 x 9 x 64 x 40 bf16).
+constexpr size_t kLuTrailSmem = size_t(2) * kOzDigits * 64 * kOzLd * sizeof(__nv_bfloat16);
+
+__global__ void __launch_bounds__(256, 2) k_lu_trail(FiberTable F, int f0, int k0, double *__restrict__ B,
+                                                     OzOperand X, OzOperand Y)
+{
+    extern __shared__ __align__(128) unsigned char lts_raw[];
+    __nv_bfloat16 *sx = reinterpret_cast<__nv_bfloat16 *>(lts_raw);
+    __nv_bfloat16 *sy = sx + kOzDigits * 64 * kOzLd;
+    const int f = blockIdx.x;
+    const Fib fb(F, f0 + f);
+    const int n = 4 * fb.N;
+    const int nr = n - k0 - kLuTcBW;
+    const int m0 = blockIdx.y * 64, n0 = blockIdx.z * 64;
+    if (nr <= 0 || m0 >= nr || n0 >= nr) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gid = lane >> 2, tig = lane & 3;
+    {
+        // one 16-byte piece per thread and plane: row tid >> 2, k offset 8 (tid & 3)
+        const int r = tid >> 2, kk = 8 * (tid & 3);
+#pragma unroll
+        for (int s = 0; s < kOzDigits; ++s) {
+            cp_async16(&sx[(s * 64 + r) * kOzLd + kk], X.plane(f, s) + static_cast<int64_t>(m0 + r) * X.kp + kk);
+            cp_async16(&sy[(s * 64 + r) * kOzLd + kk], Y.plane(f, s) + static_cast<int64_t>(n0 + r) * Y.kp + kk);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        __syncthreads();
+    }
+    const int wr = (warp >> 2) * 32, wc = (warp & 3) * 16;
+    long long hi[2][2][4] = {}, lo[2][2][4] = {};
+    for (int d = 0; d < kOzDigits; ++d) {
+        float acc[2][2][4] = {};
+        for (int s = 0; s <= d; ++s) {
+            const __nv_bfloat16 *xs = sx + s * 64 * kOzLd, *ys = sy + (d - s) * 64 * kOzLd;
+#pragma unroll
+            for (int ks = 0; ks < kLuTcBW; ks += 16) {
+                uint32_t a[2][4], bq[4];
+#pragma unroll
+                for (int i = 0; i < 2; ++i)
+                    ldsm_x4(a[i], &xs[(wr + 16 * i + (lane & 15)) * kOzLd + ks + 8 * (lane >> 4)]);
+                ldsm_x4(bq, &ys[(wc + (lane & 7) + 8 * (lane >> 4)) * kOzLd + ks + 8 * ((lane >> 3) & 1)]);
+#pragma unroll
+                for (int i = 0; i < 2; ++i)
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const uint32_t b2[2] = {bq[2 * j], bq[2 * j + 1]};
+                        mma_bf16(acc[i][j], a[i], b2);
+                    }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const long long v = __float2int_rn(acc[i][j][t]);
+                    if (d < 4) hi[i][j][t] += v << (7 * (3 - d));
+                    else lo[i][j][t] += v << (7 * (8 - d));
+                }
+    }
+    double *A22 = B + fb.blk0 + static_cast<int64_t>(k0 + kLuTcBW) * n + k0 + kLuTcBW;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int R = m0 + wr + 16 * i + gid + 8 * (t >> 1), C = n0 + wc + 8 * j + 2 * tig + (t & 1);
+                if (R >= nr || C >= nr) continue;
+                const int E = X.e[static_cast<int64_t>(f) * X.rows_p + R] + Y.e[static_cast<int64_t>(f) * Y.rows_p + C] - 12;
+                A22[static_cast<int64_t>(C) * n + R] -= oz_fold(hi[i][j][t], lo[i][j][t], E);
+            }
+}
+
 // x = P^-1 in with the factors of k_lu, one CTA per fiber: row permutation, then
 // blocked forward (unit L) and backward (U) substitution -- one warp solves
 // each BW x BW diagonal block from shared memory, all threads update the
@@ -1402,6 +1751,39 @@ int lu_panel(int n) { return n <= 128 ? 32 : 16; }
 fs_status launch_lu_factor(fs_ctx *c)
 {
     if (c->M == 0) return FS_OK;
+    if (c->lu_chunk > 0) {
+        // trailing updates on the tensor cores, a chunk of fibers at a time
+        // through the digit-plane scratch of the block build
+        const int maxn = 4 * c->max_N, rp = lu_tc_rows(c->max_N);
+        const FiberTable T = c->table();
+        OzOperand X{c->d_ozx, c->d_ozxe, rp, kLuTcBW}, Y{c->d_ozy, c->d_ozye, rp, kLuTcBW};
+        FS_CUDA(cudaFuncSetAttribute(k_lu_trail, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(kLuTrailSmem)));
+        for (int f0 = 0; f0 < c->M; f0 += c->lu_chunk) {
+            const unsigned nf = static_cast<unsigned>(std::min(c->lu_chunk, c->M - f0));
+            for (int k0 = 0; k0 < maxn; k0 += kLuTcBW) {
+                // one thread per panel row: the smallest CTA that holds the
+                // largest panel of this step
+                const int mrows = maxn - k0;
+                if (mrows <= 64)
+                    k_lu_panel<64><<<nf, 64, 0, c->stream>>>(T, f0, k0, c->d_B, c->d_piv, c->d_dinv, c->d_status, X, Y);
+                else if (mrows <= 128)
+                    k_lu_panel<128><<<nf, 128, 0, c->stream>>>(T, f0, k0, c->d_B, c->d_piv, c->d_dinv, c->d_status, X, Y);
+                else if (mrows <= 256)
+                    k_lu_panel<256><<<nf, 256, 0, c->stream>>>(T, f0, k0, c->d_B, c->d_piv, c->d_dinv, c->d_status, X, Y);
+                else
+                    k_lu_panel<512><<<nf, 512, 0, c->stream>>>(T, f0, k0, c->d_B, c->d_piv, c->d_dinv, c->d_status, X, Y);
+                FS_LAUNCH_CHECK();
+                const int nr = maxn - k0 - kLuTcBW;
+                if (nr > 0) {
+                    const unsigned tiles = static_cast<unsigned>((nr + 63) / 64);
+                    k_lu_trail<<<dim3(nf, tiles, tiles), 256, kLuTrailSmem, c->stream>>>(T, f0, k0, c->d_B, X, Y);
+                    FS_LAUNCH_CHECK();
+                }
+            }
+        }
+        return FS_OK;
+    }
     const int n = 4 * c->max_N, bw = lu_panel(n);
     const size_t sm = (static_cast<size_t>(n) * bw + static_cast<size_t>(bw) * (kLuTC + 1)) * sizeof(double) +
                       static_cast<size_t>(n) * sizeof(int);

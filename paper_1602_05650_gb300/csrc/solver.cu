@@ -1170,15 +1170,16 @@ fs_status fiber_arrays(fs_ctx *c, int M, const int32_t *ppf, const std::vector<i
     FS_TRY(dalloc(c, &c->d_wsc, c->n_blk / 4 * 3));
     // the p columns of w are never written: they stay zero (f = 0 there)
     FS_CUDA(cudaMemsetAsync(c->d_wsc, 0, static_cast<size_t>(c->n_blk / 4 * 3) * sizeof(double), c->stream));
-    if (c->opt.tc_blocks) {
-        const OzDims D(c->max_N);
-        const int64_t per = D.bytes_per_fiber();
-        c->oz_chunk = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>({int64_t(M), 512, (int64_t(1) << 30) / per})));
-        const size_t rx = std::max(D.r1, D.r2);
-        FS_TRY(dalloc(c, &c->d_ozx, static_cast<size_t>(c->oz_chunk) * OzDims::digits * rx * D.kp));
-        FS_TRY(dalloc(c, &c->d_ozy, static_cast<size_t>(c->oz_chunk) * OzDims::digits * D.ry * D.kp));
-        FS_TRY(dalloc(c, &c->d_ozxe, static_cast<size_t>(c->oz_chunk) * rx));
-        FS_TRY(dalloc(c, &c->d_ozye, static_cast<size_t>(c->oz_chunk) * D.ry));
+    {
+        const OzPlan q = oz_plan(M, c->max_N, c->opt);
+        c->oz_chunk = q.oz_chunk;
+        c->lu_chunk = q.lu_chunk;
+        if (q.x > 0) {
+            FS_TRY(dalloc(c, &c->d_ozx, static_cast<size_t>(q.x)));
+            FS_TRY(dalloc(c, &c->d_ozy, static_cast<size_t>(q.y)));
+            FS_TRY(dalloc(c, &c->d_ozxe, static_cast<size_t>(q.xe)));
+            FS_TRY(dalloc(c, &c->d_ozye, static_cast<size_t>(q.ye)));
+        }
     }
     FS_TRY(dalloc(c, &c->d_piv, c->n_fib_unk));
     FS_TRY(dalloc(c, &c->d_dinv, c->n_fib_unk));
@@ -1290,6 +1291,36 @@ fs_status surface_arrays(fs_ctx *c, const fs_boundary *bd, const fs_body *body)
 // CTAs per SM); lets the estimate run without asking a device.
 constexpr int kSlotsBound = 8192;
 
+// Digit-plane scratch of the tensor-core block build (tc_blocks) and LU
+// (tc_lu): chunk sizes and element counts of the planes (bf16) and exponents
+// (int); the LU reuses the build's planes, which it outgrows only when the
+// build is off.  Shared by the allocation and the memory estimate.
+OzPlan oz_plan(int M, int maxN, const fs_options &o)
+{
+    OzPlan q;
+    if (M <= 0) return q;
+    if (o.tc_blocks) {
+        const OzDims D(maxN);
+        const int64_t per = D.bytes_per_fiber();
+        q.oz_chunk = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>({int64_t(M), 512, (int64_t(1) << 30) / per})));
+        const int64_t rx = std::max(D.r1, D.r2);
+        q.x = int64_t(q.oz_chunk) * OzDims::digits * rx * D.kp;
+        q.y = int64_t(q.oz_chunk) * OzDims::digits * D.ry * D.kp;
+        q.xe = int64_t(q.oz_chunk) * rx;
+        q.ye = int64_t(q.oz_chunk) * D.ry;
+    }
+    if (o.tc_lu && LuTcDims::fits(maxN)) {
+        const LuTcDims L(maxN);
+        const int64_t per = 2 * (L.plane_elems() * 2 + int64_t(L.rows) * 4);
+        q.lu_chunk = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(int64_t(M), (int64_t(1) << 30) / per)));
+        q.x = std::max(q.x, int64_t(q.lu_chunk) * L.plane_elems());
+        q.y = std::max(q.y, int64_t(q.lu_chunk) * L.plane_elems());
+        q.xe = std::max(q.xe, int64_t(q.lu_chunk) * L.rows);
+        q.ye = std::max(q.ye, int64_t(q.lu_chunk) * L.rows);
+    }
+    return q;
+}
+
 // Device bytes context_init allocates for this problem, plus the largest
 // direct-sum scratch a step reserves.  Each allocation is rounded up to the
 // allocator's 512-byte granule; the result bounds what fs_device_bytes reports.
@@ -1322,17 +1353,14 @@ size_t estimate_bytes(int M, const int32_t *ppf, int n_surf, const fs_options &o
     for (int64_t k : {3 * P, int64_t(M), int64_t(M), 3 * P, 3 * P, 3 * n_z, 3 * P, P, 2 * P, 12 * int64_t(M), 4 * n_kp, n_blk,
                       n_blk / 16 * 3, n_blk / 4 * 3})
         add(k * d);
-    if (opt.tc_blocks) {   // digit planes of the tensor-core block build
+    {   // digit planes of the tensor-core block build and LU
         int maxN = 0;
         for (int m = 0; m < M; ++m) maxN = std::max(maxN, int(ppf[m]));
-        const OzDims D(maxN);
-        const int64_t per = D.bytes_per_fiber();
-        const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>({int64_t(M), 512, (int64_t(1) << 30) / per}));
-        const int64_t rx = std::max(D.r1, D.r2);
-        add(chunk * OzDims::digits * rx * D.kp * 2);
-        add(chunk * OzDims::digits * D.ry * D.kp * 2);
-        add(chunk * rx * 4);
-        add(chunk * D.ry * 4);
+        const OzPlan q = oz_plan(M, maxN, opt);
+        add(q.x * 2);
+        add(q.y * 2);
+        add(q.xe * 4);
+        add(q.ye * 4);
     }
     add(n_fib_unk * sizeof(int));
     add(n_fib_unk * sizeof(double));
@@ -1541,6 +1569,22 @@ fs_status fs_get_self_block(fs_ctx *c, int32_t fiber, double *out)
     c->precond_ok = false;
     const int64_t n = 4 * int64_t(c->Nm[fiber]);
     FS_CUDA(cudaMemcpyAsync(out, c->d_B + c->blk_ptr[fiber], static_cast<size_t>(n * n) * sizeof(double),
+                            cudaMemcpyDeviceToHost, c->stream));
+    FS_CUDA(cudaStreamSynchronize(c->stream));
+    return FS_OK;
+}
+
+fs_status fs_get_block_lu(fs_ctx *c, int32_t fiber, double *lu, int32_t *piv)
+{
+    if (!c || !c->have_state || fiber < 0 || fiber >= c->M || !lu || !piv) {
+        set_error("fs_get_block_lu: no state, fiber out of range or NULL output");
+        return FS_EINVAL;
+    }
+    if (!c->precond_ok) FS_TRY(fs_build_precond(c));
+    const int64_t n = 4 * int64_t(c->Nm[fiber]);
+    FS_CUDA(cudaMemcpyAsync(lu, c->d_B + c->blk_ptr[fiber], static_cast<size_t>(n * n) * sizeof(double),
+                            cudaMemcpyDeviceToHost, c->stream));
+    FS_CUDA(cudaMemcpyAsync(piv, c->d_piv + c->unk_ptr[fiber], static_cast<size_t>(n) * sizeof(int32_t),
                             cudaMemcpyDeviceToHost, c->stream));
     FS_CUDA(cudaStreamSynchronize(c->stream));
     return FS_OK;

@@ -15,13 +15,14 @@ def lib():
     return _native.load()
 
 
-def est(lib, ppf, ns=0, prec=_native.FS_MIXED, restart=60, tc_blocks=1):
+def est(lib, ppf, ns=0, prec=_native.FS_MIXED, restart=60, tc_blocks=1, tc_lu=1):
     a = np.asarray(ppf, np.int32)
     o = _native.fs_options()
     lib.fs_options_default(ctypes.byref(o))
     o.prec = prec
     o.restart = restart
     o.tc_blocks = tc_blocks
+    o.tc_lu = tc_lu
     return lib.fs_estimate_bytes(len(a), a.ctypes.data_as(ctypes.c_void_p), ns, ctypes.byref(o))
 
 
@@ -30,14 +31,19 @@ def test_estimate_grows_with_the_problem(lib):
     e2 = est(lib, [32] * 200)
     assert 0 < e1 < e2
     # the dense blocks and the block-build scratch (16 + 3 + 12 N^2 doubles
-    # per fiber) dominate at N = 64 with the FP64 build
-    e64 = est(lib, [64] * 1024, tc_blocks=0)
+    # per fiber) dominate at N = 64 with the FP64 build and LU
+    e64 = est(lib, [64] * 1024, tc_blocks=0, tc_lu=0)
     assert e64 >= 1024 * 31 * 64 * 64 * 8
     assert e64 < 2 * 1024 * 31 * 64 * 64 * 8
     # the tensor-core build adds the digit planes of a chunk of 512 fibers:
     # nine bf16 planes of both operands (256 rows each, 192 inner columns)
     planes = 512 * 9 * (256 + 256) * 192 * 2
+    # (the LU's planes fit in them)
     assert planes <= est(lib, [64] * 1024) - e64 < planes + (16 << 20)
+    # the tensor-core LU alone: planes for all 1,024 fibers, nine bf16 planes
+    # of both operands (256 rows, 32 inner columns) and an exponent per row
+    lu = 1024 * 2 * (9 * 256 * 32 * 2 + 256 * 4)
+    assert lu <= est(lib, [64] * 1024, tc_blocks=0) - e64 < lu + (16 << 20)
     # mixed precision keeps the outer flexible-GMRES space on top of the inner one
     assert est(lib, [32] * 100, prec=_native.FS_MIXED) > est(lib, [32] * 100, prec=_native.FS_FP64)
     # a longer restart keeps more Krylov vectors
