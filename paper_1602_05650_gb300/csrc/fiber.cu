@@ -641,8 +641,9 @@ __global__ void __launch_bounds__(256) k_build_rows(FiberTable F, double *__rest
 //     entries down to 2^-62 of their row's largest keep their digits, so
 //     products whose large factors sit at different k (cancelling sums of
 //     small terms) stay within a few FP64 roundings of their own magnitude.
-// mma.sync m16n8k16 (bf16 in, FP32 accumulate); CTA tile 64 x 64, eight warps
-// of 32 x 16; inner dimension in chunks of 192.
+// mma.sync m16n8k16 (bf16 in, FP32 accumulate); CTA tile 64 x 32, eight warps
+// of 16 x 16, every A fragment multiplied into all the diagonals it enters;
+// inner dimension in chunks of 192.
 constexpr int kOzDigits = 9;
 constexpr int kOzKChunk = 192;
 
@@ -846,32 +847,38 @@ __device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void *p)
 // Y planes (rows = output columns), both k-contiguous.  EPI 1: W (rows 3N,
 // columns 4N) column-major into the block-build scratch; EPI 2: the w rows of
 // the block (velocity rows with -V_y and the growth term, tension rows).
-// Grid (fibers of the chunk, rows_p / 64, cols_p / 64), 256 threads: eight
-// warps of 32 x 16.  For each diagonal d and digit pair (s, d - s) the slabs
-// of X_s and Y_(d-s) pass through shared memory.  A diagonal's exact FP32
-// sum is added, as an integer, into two 64-bit accumulators (diagonals 0..3
-// and 4..8 at their relative powers of 128), which become FP64 once at the
-// end: the FP64 pipe converts and scales twice per entry instead of folding
-// every diagonal.
+// Grid (fibers of the chunk, rows_p / 64, cols_p / 32), 256 threads: eight
+// warps of 16 x 16.  Per k-slab of 32, all nine digit slabs of both
+// operands pass through shared memory once (cp.async, two stages); per k-step
+// of 16 a warp loads the nine B fragments, then each A fragment once and
+// multiplies it into every diagonal it enters (9 + 9 ldmatrix for 90 mma).
+// The nine diagonals accumulate in FP32, exactly, over at most kOzKChunk of
+// k; each chunk's sums are added, as integers, into two 64-bit accumulators
+// (diagonals 0..3 and 4..8 at their relative powers of 128), which become
+// FP64 once at the end.
+constexpr size_t kOzGemmSmem = size_t(2) * kOzDigits * (64 + 32) * kOzLd * sizeof(__nv_bfloat16);
+
 template <int EPI>
-__global__ void __launch_bounds__(256, 2) k_oz_gemm(FiberTable F, int f0, OzOperand X, OzOperand Y,
+__global__ void __launch_bounds__(256, 1) k_oz_gemm(FiberTable F, int f0, OzOperand X, OzOperand Y,
                                                     double *__restrict__ B)
 {
-    __shared__ __align__(128) __nv_bfloat16 sx[2][64 * kOzLd], sy[2][64 * kOzLd];
+    extern __shared__ __align__(128) unsigned char ozg_raw[];
+    __nv_bfloat16 *sx = reinterpret_cast<__nv_bfloat16 *>(ozg_raw);   // [stage][digit][64][kOzLd]
+    __nv_bfloat16 *sy = sx + 2 * kOzDigits * 64 * kOzLd;               // [stage][digit][32][kOzLd]
     const int f = blockIdx.x;
     const Fib fb(F, f0 + f);
     const int N = fb.N;
     const int K = 3 * N;
     const int vp = (N - 4 + 63) / 64 * 64;
     const int nrow = EPI == 1 ? 3 * N : 3 * vp + N - 2, ncol = 4 * N;
-    const int m0 = blockIdx.y * 64, n0 = blockIdx.z * 64;
+    const int m0 = blockIdx.y * 64, n0 = blockIdx.z * 32;
     if (m0 >= nrow || n0 >= ncol) return;
     // inner range where the tile's operands are not zero: the sigma columns
     // of component a (W = S F) and the velocity rows of component a (w rows)
     // touch only k in [a N, a N + N)
     int k_lo = 0, k_hi = K;
     if (EPI == 1) {
-        const int c1 = min(n0 + 63, ncol - 1);
+        const int c1 = min(n0 + 31, ncol - 1);
         if (c1 < 3 * N) {
             k_lo = (n0 / N) * N;
             k_hi = (c1 / N + 1) * N;
@@ -882,89 +889,94 @@ __global__ void __launch_bounds__(256, 2) k_oz_gemm(FiberTable F, int f0, OzOper
     }
     k_lo &= ~15;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gid = lane >> 2, tig = lane & 3;
-    const int wr = (warp >> 2) * 32, wc = (warp & 3) * 16;   // warp tile inside the CTA tile
+    const int wr = (warp >> 1) * 16, wc = (warp & 1) * 16;   // warp tile inside the CTA tile
     const int wm = m0 + wr, wn = n0 + wc;
     // slabs of kOzKs k each; the last may run past k_hi into zero padding
     // (planes hold kp >= K columns, zero beyond K) -- but never past kp
     const int nslab = (k_hi - k_lo + kOzKs - 1) / kOzKs;
-    // each thread copies one 16-byte piece per operand and slab: row
-    // tid >> 2, k offset 8 (tid & 3)
-    auto stage = [&](int buf, const __nv_bfloat16 *xp, const __nv_bfloat16 *yp, int k0) {
-        const int r = tid >> 2, kk = 8 * (tid & 3);
-        if (k0 + kk < X.kp) {   // X.kp == Y.kp
-            cp_async16(&sx[buf][r * kOzLd + kk], xp + static_cast<int64_t>(m0 + r) * X.kp + k0 + kk);
-            cp_async16(&sy[buf][r * kOzLd + kk], yp + static_cast<int64_t>(n0 + r) * Y.kp + k0 + kk);
-        } else {
-            *reinterpret_cast<uint4 *>(&sx[buf][r * kOzLd + kk]) = make_uint4(0, 0, 0, 0);
-            *reinterpret_cast<uint4 *>(&sy[buf][r * kOzLd + kk]) = make_uint4(0, 0, 0, 0);
+    // 16-byte pieces: X 9 x 64 rows x 4, Y 9 x 32 rows x 4
+    auto stage = [&](int buf, int k0) {
+        for (int pc = tid; pc < kOzDigits * 64 * 4; pc += 256) {
+            const int sd = pc >> 8, r = (pc >> 2) & 63, kk = 8 * (pc & 3);
+            __nv_bfloat16 *dst = &sx[((buf * kOzDigits + sd) * 64 + r) * kOzLd + kk];
+            if (k0 + kk < X.kp)
+                cp_async16(dst, X.plane(f, sd) + static_cast<int64_t>(m0 + r) * X.kp + k0 + kk);
+            else
+                *reinterpret_cast<uint4 *>(dst) = make_uint4(0, 0, 0, 0);
+        }
+        for (int pc = tid; pc < kOzDigits * 32 * 4; pc += 256) {
+            const int sd = pc >> 7, r = (pc >> 2) & 31, kk = 8 * (pc & 3);
+            __nv_bfloat16 *dst = &sy[((buf * kOzDigits + sd) * 32 + r) * kOzLd + kk];
+            if (k0 + kk < Y.kp)
+                cp_async16(dst, Y.plane(f, sd) + static_cast<int64_t>(n0 + r) * Y.kp + k0 + kk);
+            else
+                *reinterpret_cast<uint4 *>(dst) = make_uint4(0, 0, 0, 0);
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
-    long long hi[2][2][4] = {}, lo[2][2][4] = {};
-    for (int d = 0; d < kOzDigits; ++d) {
-        float acc[2][2][4] = {};
-        for (int s = 0; s <= d; ++s) {
-            const __nv_bfloat16 *xp = X.plane(f, s), *yp = Y.plane(f, d - s);
-            for (int q = 0; q < nslab; q += kOzKChunk / kOzKs) {
-                // within one chunk of kOzKChunk the FP32 sums stay exact; a
-                // longer inner range adds each chunk to the integers (below)
-                const int qe = min(nslab, q + kOzKChunk / kOzKs);
-                stage(0, xp, yp, k_lo + q * kOzKs);
-                for (int qq = q; qq < qe; ++qq) {
-                    const int buf = (qq - q) & 1;
-                    if (qq + 1 < qe) {
-                        stage(buf ^ 1, xp, yp, k_lo + (qq + 1) * kOzKs);
-                        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-                    } else {
-                        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-                    }
-                    __syncthreads();
+    float acc[kOzDigits][2][4];
 #pragma unroll
-                    for (int ks = 0; ks < kOzKs; ks += 16) {
-                        uint32_t a[2][4], bq[4];
-#pragma unroll
-                        for (int i = 0; i < 2; ++i)
-                            ldsm_x4(a[i], &sx[buf][(wr + 16 * i + (lane & 15)) * kOzLd + ks + 8 * (lane >> 4)]);
-                        ldsm_x4(bq, &sy[buf][(wc + (lane & 7) + 8 * (lane >> 4)) * kOzLd + ks + 8 * ((lane >> 3) & 1)]);
-#pragma unroll
-                        for (int i = 0; i < 2; ++i)
-#pragma unroll
-                            for (int j = 0; j < 2; ++j) {
-                                const uint32_t b2[2] = {bq[2 * j], bq[2 * j + 1]};
-                                mma_bf16(acc[i][j], a[i], b2);
-                            }
-                    }
-                    __syncthreads();   // the stage is refilled next
-                }
-                if (qe < nslab || s == d) {
-                    // the chunk's (or the diagonal's) exact sum into the integers
-#pragma unroll
-                    for (int i = 0; i < 2; ++i)
-#pragma unroll
-                        for (int j = 0; j < 2; ++j)
-#pragma unroll
-                            for (int t = 0; t < 4; ++t) {
-                                const long long v = __float2int_rn(acc[i][j][t]);
-                                if (d < 4) hi[i][j][t] += v << (7 * (3 - d));
-                                else lo[i][j][t] += v << (7 * (8 - d));
-                                acc[i][j][t] = 0.0f;
-                            }
-                }
-            }
-        }
-    }
-    // out = 2^(e_row + e_col - 12) (hi 2^-21 + lo 2^-56)
-    double out[2][2][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
+    for (int d = 0; d < kOzDigits; ++d)
 #pragma unroll
         for (int j = 0; j < 2; ++j)
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int er = X.e[static_cast<int64_t>(f) * X.rows_p + wm + 16 * i + gid + 8 * (t >> 1)];
-                const int ec = Y.e[static_cast<int64_t>(f) * Y.rows_p + wn + 8 * j + 2 * tig + (t & 1)];
-                out[i][j][t] = oz_fold(hi[i][j][t], lo[i][j][t], er + ec - 12);
+            for (int t = 0; t < 4; ++t) acc[d][j][t] = 0.0f;
+    long long hi[2][4] = {}, lo[2][4] = {};
+    stage(0, k_lo);
+    for (int q = 0; q < nslab; ++q) {
+        const int buf = q & 1;
+        if (q + 1 < nslab) {
+            stage(buf ^ 1, k_lo + (q + 1) * kOzKs);
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        }
+        __syncthreads();
+        const __nv_bfloat16 *xs = sx + buf * kOzDigits * 64 * kOzLd, *ys = sy + buf * kOzDigits * 32 * kOzLd;
+#pragma unroll
+        for (int ks = 0; ks < kOzKs; ks += 16) {
+            uint32_t bq[kOzDigits][4];
+#pragma unroll
+            for (int t = 0; t < kOzDigits; ++t)
+                ldsm_x4(bq[t], &ys[(t * 32 + wc + (lane & 7) + 8 * (lane >> 4)) * kOzLd + ks + 8 * ((lane >> 3) & 1)]);
+#pragma unroll
+            for (int sd = 0; sd < kOzDigits; ++sd) {
+                uint32_t a[4];
+                ldsm_x4(a, &xs[(sd * 64 + wr + (lane & 15)) * kOzLd + ks + 8 * (lane >> 4)]);
+#pragma unroll
+                for (int t = 0; t + sd < kOzDigits; ++t) {
+                    const uint32_t b0[2] = {bq[t][0], bq[t][1]}, b1[2] = {bq[t][2], bq[t][3]};
+                    mma_bf16(acc[sd + t][0], a, b0);
+                    mma_bf16(acc[sd + t][1], a, b1);
+                }
             }
+        }
+        __syncthreads();   // the stage is refilled next
+        if ((q + 1) % (kOzKChunk / kOzKs) == 0 || q + 1 == nslab) {
+            // the chunk's exact diagonal sums into the integers
+#pragma unroll
+            for (int d = 0; d < kOzDigits; ++d)
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const long long v = __float2int_rn(acc[d][j][t]);
+                        if (d < 4) hi[j][t] += v << (7 * (3 - d));
+                        else lo[j][t] += v << (7 * (8 - d));
+                        acc[d][j][t] = 0.0f;
+                    }
+        }
+    }
+    // out = 2^(e_row + e_col - 12) (hi 2^-21 + lo 2^-56)
+    double out[2][4];
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int er = X.e[static_cast<int64_t>(f) * X.rows_p + wm + gid + 8 * (t >> 1)];
+            const int ec = Y.e[static_cast<int64_t>(f) * Y.rows_p + wn + 8 * j + 2 * tig + (t & 1)];
+            out[j][t] = oz_fold(hi[j][t], lo[j][t], er + ec - 12);
+        }
     // epilogue
     const double *Vy = fb.M_(fb.lay.Vy), *Vgy = fb.M_(fb.lay.Vgy);
     const double ldot = (F.Ldot && F.growth_implicit) ? F.Ldot[fb.m] : 0.0;
@@ -973,14 +985,13 @@ __global__ void __launch_bounds__(256, 2) k_oz_gemm(FiberTable F, int f0, OzOper
     double *W = F.wsc + fb.blk0 / 4 * 3;
     double *Bm = B + fb.blk0;
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j)
 #pragma unroll
-        for (int j = 0; j < 2; ++j)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int R = wm + 16 * i + gid + 8 * (q >> 1), col = wn + 8 * j + 2 * tig + (q & 1);
+        for (int q = 0; q < 4; ++q) {
+            {
+                const int R = wm + gid + 8 * (q >> 1), col = wn + 8 * j + 2 * tig + (q & 1);
                 if (R >= nrow || col >= ncol) continue;
-                double v = out[i][j][q];
+                double v = out[j][q];
                 if (EPI == 1) {
                     W[static_cast<int64_t>(col) * 3 * N + R] = v;
                 } else {
@@ -992,6 +1003,7 @@ __global__ void __launch_bounds__(256, 2) k_oz_gemm(FiberTable F, int f0, OzOper
                     Bm[static_cast<int64_t>(col) * n + row] = v;
                 }
             }
+        }
 }
 
 // Rows without the velocity rows' w: the end rows (second and third
@@ -1716,19 +1728,23 @@ fs_status launch_block_build(fs_ctx *c)
         const OzDims D(N);
         OzOperand X1{c->d_ozx, c->d_ozxe, D.r1, D.kp}, X2{c->d_ozx, c->d_ozxe, D.r2, D.kp},
             Y{c->d_ozy, c->d_ozye, D.ry, D.kp};
+        FS_CUDA(cudaFuncSetAttribute(k_oz_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(kOzGemmSmem)));
+        FS_CUDA(cudaFuncSetAttribute(k_oz_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(kOzGemmSmem)));
         for (int f0 = 0; f0 < c->M; f0 += c->oz_chunk) {
             const unsigned nf = static_cast<unsigned>(std::min(c->oz_chunk, c->M - f0));
             k_oz_slice_S<<<dim3(nf, D.r1 / 4), 128, 0, c->stream>>>(T, f0, X1);
             FS_LAUNCH_CHECK();
             k_oz_slice_F<<<dim3(nf, D.ry / 4), 128, 0, c->stream>>>(T, f0, Y);
             FS_LAUNCH_CHECK();
-            k_oz_gemm<1><<<dim3(nf, D.r1 / 64, D.ry / 64), 256, 0, c->stream>>>(T, f0, X1, Y, c->d_B);
+            k_oz_gemm<1><<<dim3(nf, D.r1 / 64, D.ry / 32), 256, kOzGemmSmem, c->stream>>>(T, f0, X1, Y, c->d_B);
             FS_LAUNCH_CHECK();
             k_oz_slice_Rw<<<dim3(nf, D.r2 / 4), 128, 0, c->stream>>>(T, f0, X2);
             FS_LAUNCH_CHECK();
             k_oz_slice_W<<<dim3(nf, D.ry / 4), 128, 0, c->stream>>>(T, f0, Y);
             FS_LAUNCH_CHECK();
-            k_oz_gemm<2><<<dim3(nf, D.r2 / 64, D.ry / 64), 256, 0, c->stream>>>(T, f0, X2, Y, c->d_B);
+            k_oz_gemm<2><<<dim3(nf, D.r2 / 64, D.ry / 32), 256, kOzGemmSmem, c->stream>>>(T, f0, X2, Y, c->d_B);
             FS_LAUNCH_CHECK();
         }
     } else {
