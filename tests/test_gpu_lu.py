@@ -15,9 +15,11 @@ scale, and the entry-wise ratio can exceed n u (printed, not gated).  So:
   breaks it by orders of magnitude);
   (measured 0.06 to 0.09 of that bound, the tensor-core updates no larger
   than FP64's);
-* both pick the same pivots.  Their factors differ by the forward error of
-  two backward-stable factorisations of blocks with condition numbers near
-  1e9 (measured 5e-7 of the same scale): printed, not gated."""
+* pivots and factors are printed, not gated: the two roundings may order
+  near-ties differently (at 4N = 512 a few late pivots swap), and where the
+  pivots agree the factors differ by the forward error of two
+  backward-stable factorisations of blocks with condition numbers near 1e9
+  (measured 5e-7 of the same scale)."""
 import numpy as np
 import pytest
 
@@ -54,6 +56,8 @@ CASES = {
     # n = 4N: 36 and 72 end in a partial panel, 256 spans four trailing tiles
     "ragged": lambda: wl.free_space(7, np.array([16, 9, 24, 18, 32, 20, 64]), 5.0, seed=4, curved_amp=0.05),
     "cloud_48": lambda: wl.free_space(96, 48, 12.0, seed=5, curved_amp=0.05),
+    # 4N up to 512: the first panels take 512-thread CTAs
+    "wide": lambda: wl.free_space(3, np.array([96, 128, 40]), 6.0, seed=6, curved_amp=0.05),
 }
 
 
@@ -78,10 +82,12 @@ def test_lu_backward_error(name):
         print("%s tc_lu=%d: max |P B - L U| / n u: %.3f of max|L_i.| max|U_.j|, %.3f of (|L||U|)_ij"
               % (name, tc, w_rc, w_ent))
         res[tc], worst[tc] = fac, w_rc
-    diff = 0.0
+    diff, moved = 0.0, 0
     for (LUa, pa), (LUb, pb) in zip(res[1], res[0]):
-        assert np.array_equal(pa, pb)
-        L, U = split(LUb)
-        diff = max(diff, float((np.abs(LUa - LUb) / np.maximum(rowcol_scale(L, U), 1e-300)).max()))
-    print("%s: tensor-core vs FP64 factors, max difference / (max|L_i.| max|U_.j|) = %.2e" % (name, diff))
+        moved += int((pa != pb).sum())
+        if np.array_equal(pa, pb):
+            L, U = split(LUb)
+            diff = max(diff, float((np.abs(LUa - LUb) / np.maximum(rowcol_scale(L, U), 1e-300)).max()))
+    print("%s: tensor-core vs FP64: %d pivot positions differ; factors with equal pivots, max difference / "
+          "(max|L_i.| max|U_.j|) = %.2e" % (name, moved, diff))
     assert max(worst.values()) <= 0.5
