@@ -1265,6 +1265,49 @@ __device__ __forceinline__ void oz_slice_lane(const OzOperand &O, int f, int row
     for (int s = 0; s < kOzDigits; ++s) O.plane(f, s)[static_cast<int64_t>(row) * O.kp + lane] = __float2bfloat16_rn(a[s]);
 }
 
+// One plane row from a thread's own 32 values (k = 0..31): the row's
+// exponent from the largest magnitude (bit patterns, integer work), then the
+// nine digits of each value, written 8 bf16 (16 bytes) at a time.
+__device__ __forceinline__ void oz_slice_regs(const OzOperand &O, int f, int row, const double (&v)[kLuTcBW])
+{
+    long long mb = 0;
+#pragma unroll
+    for (int c = 0; c < kLuTcBW; ++c) mb = max(mb, __double_as_longlong(v[c]) & 0x7fffffffffffffffLL);
+    const bool nz = mb > 0;
+    const int e = nz ? static_cast<int>(mb >> 52) - 1022 : 0;
+    O.e[static_cast<int64_t>(f) * O.rows_p + row] = e;
+#pragma unroll
+    for (int g = 0; g < kLuTcBW; g += 8) {
+        uint32_t w[kOzDigits][4];
+#pragma unroll
+        for (int h = 0; h < 8; h += 2) {
+            float d0[kOzDigits], d1[kOzDigits];
+            oz_digits(nz ? v[g + h] : 0.0, e, d0);
+            oz_digits(nz ? v[g + h + 1] : 0.0, e, d1);
+#pragma unroll
+            for (int s2 = 0; s2 < kOzDigits; ++s2) {
+                const __nv_bfloat162 pr = __floats2bfloat162_rn(d0[s2], d1[s2]);
+                w[s2][h / 2] = *reinterpret_cast<const uint32_t *>(&pr);
+            }
+        }
+#pragma unroll
+        for (int s2 = 0; s2 < kOzDigits; ++s2)
+            *reinterpret_cast<uint4 *>(O.plane(f, s2) + static_cast<int64_t>(row) * O.kp + g) =
+                make_uint4(w[s2][0], w[s2][1], w[s2][2], w[s2][3]);
+    }
+}
+
+// Zero plane row (padding of the trailing tiles).
+__device__ __forceinline__ void oz_zero_row(const OzOperand &O, int f, int row)
+{
+    O.e[static_cast<int64_t>(f) * O.rows_p + row] = 0;
+#pragma unroll
+    for (int s2 = 0; s2 < kOzDigits; ++s2)
+#pragma unroll
+        for (int g = 0; g < kLuTcBW; g += 8)
+            *reinterpret_cast<uint4 *>(O.plane(f, s2) + static_cast<int64_t>(row) * O.kp + g) = make_uint4(0, 0, 0, 0);
+}
+
 // Panel k0 of every fiber of the chunk: one CTA of NT >= 4 N - k0 threads
 // per fiber (64 to 512, the smallest that holds the step's largest panel),
 // thread r holding row r of the panel (rows k0.. of its 32 columns) in
@@ -1393,7 +1436,7 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? 512 / NT : 4) k_lu_panel(Fiber
     __syncthreads();
     const int nt = s_nt, ncol = n - kb;
     if (nt > 0) {
-        constexpr int Q = 4;
+        constexpr int Q = NT <= 64 ? 16 : (NT <= 128 ? 8 : 4);   // loads in flight per thread
         const int cpr = max(1, NT * Q / nt);   // whole columns per round
         for (int c0 = 0; c0 < ncol; c0 += cpr) {
             const int items = min(cpr, ncol - c0) * nt;
@@ -1426,49 +1469,20 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? 512 / NT : 4) k_lu_panel(Fiber
         }
         return;
     }
-    // digit planes of L21: thread r >= BW slices its own row i = r - BW
-    if (own && r >= BW) {
-        const int i = r - BW;
-        long long mb = 0;   // bits of the row's largest magnitude
-#pragma unroll
-        for (int c = 0; c < BW; ++c) mb = max(mb, __double_as_longlong(a[c]) & 0x7fffffffffffffffLL);
-        const bool nz = mb > 0;
-        const int e = nz ? static_cast<int>(mb >> 52) - 1022 : 0;
-        X.e[static_cast<int64_t>(f) * X.rows_p + i] = e;
-#pragma unroll
-        for (int g = 0; g < BW; g += 8) {
-            uint32_t w[kOzDigits][4];
-#pragma unroll
-            for (int h = 0; h < 8; h += 2) {
-                float d0[kOzDigits], d1[kOzDigits];
-                oz_digits(nz ? a[g + h] : 0.0, e, d0);
-                oz_digits(nz ? a[g + h + 1] : 0.0, e, d1);
-#pragma unroll
-                for (int s2 = 0; s2 < kOzDigits; ++s2) {
-                    const __nv_bfloat162 pr = __floats2bfloat162_rn(d0[s2], d1[s2]);
-                    w[s2][h / 2] = *reinterpret_cast<const uint32_t *>(&pr);
-                }
-            }
-#pragma unroll
-            for (int s2 = 0; s2 < kOzDigits; ++s2)
-                *reinterpret_cast<uint4 *>(X.plane(f, s2) + static_cast<int64_t>(i) * X.kp + g) =
-                    make_uint4(w[s2][0], w[s2][1], w[s2][2], w[s2][3]);
-        }
-    }
+    // digit planes of L21: thread r >= BW slices its own row i = r - BW;
+    // padding rows up to the tiles' 64 are zero (both operands)
+    if (own && r >= BW) oz_slice_regs(X, f, r - BW, a);
     const int rows = (nr + 63) / 64 * 64;   // the rows the trailing tiles read
     for (int i = nr + tid; i < rows; i += NT) {
-        X.e[static_cast<int64_t>(f) * X.rows_p + i] = 0;
-#pragma unroll
-        for (int s2 = 0; s2 < kOzDigits; ++s2)
-#pragma unroll
-            for (int g = 0; g < BW; g += 8)
-                *reinterpret_cast<uint4 *>(X.plane(f, s2) + static_cast<int64_t>(i) * X.kp + g) = make_uint4(0, 0, 0, 0);
+        oz_zero_row(X, f, i);
+        oz_zero_row(Y, f, i);
     }
     // U12 = L11^-1 A12 (kb == BW == 32 here): one column per thread in
     // registers, forward substitution with the unit lower triangle of L11
-    // (shared memory, the same entry for all threads: broadcast)
-    // (read through a volatile view: one shared load per use, not 496
-    // loop-invariant registers)
+    // (shared memory, the same entry for all threads: broadcast; read
+    // through a volatile view: one shared load per use, not 496
+    // loop-invariant registers); the thread then slices its column into
+    // U12's digit planes
     const volatile double(*Lv)[BW + 1] = L11;
     for (int col = k0 + BW + tid; col < n; col += NT) {
         double *Ac = A + static_cast<int64_t>(col) * n + k0;
@@ -1485,11 +1499,8 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? 512 / NT : 4) k_lu_panel(Fiber
             for (int r2 = c + 1; r2 < BW; ++r2) u[r2] = fma(-Lv[r2][c], u[c], u[r2]);
 #pragma unroll
         for (int q = 0; q < BW; q += 2) *reinterpret_cast<double2 *>(Ac + q) = make_double2(u[q], u[q + 1]);
+        oz_slice_regs(Y, f, col - k0 - BW, u);
     }
-    __syncthreads();   // U12 complete
-    // digit planes of U12: one warp per trailing column (lane = k); padding zero
-    for (int col = wid; col < rows; col += NW)
-        oz_slice_lane(Y, f, col, col < nr ? A[static_cast<int64_t>(k0 + BW + col) * n + k0 + lane] : 0.0);
 }
 
 // A22 -= L21 U12 for panel k0: grid (fibers of the chunk, tiles, tiles) of
