@@ -181,12 +181,14 @@ def oracle_baseline(s, gpu_fp64_iters: int, budget_fibers: int = 512, budget_tar
             "kind": "oracle", "sample": sample, "seconds_per_step_extrapolated": t_step}
 
 
-def traffic_for(kernel_class: str):
-    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
-    the committed ncu summary profiles/traffic.txt, if it was taken on the
-    current source of the direct-sum kernels (else None).  Lines:
-    <kernel class> <bytes per launch> <sha1 of csrc/pairsum.cu>."""
-    p = os.path.join(ROOT, "profiles", "traffic.txt")
+def traffic_for(kernel_class: str, name: str = "traffic.txt"):
+    """A per-launch ncu figure of a direct-sum kernel class from a committed
+    summary under profiles/ (DRAM bytes per launch, dram__bytes_read.sum +
+    dram__bytes_write.sum, in traffic.txt; the FMA-pipe active fraction in
+    pipe_util.txt), if it was taken on the current source of the direct-sum
+    kernels (else None).  Lines: <kernel class> <value> <sha1 of
+    csrc/pairsum.cu>."""
+    p = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(p):
         return None
     try:
@@ -895,7 +897,13 @@ def main():
                                 "%d SMs (queried) x 128 FP32 lanes x 2 x max SM clock" % n_sm),
                 "launch_ms_avg": total_ms / launches_d if launches_d else None,
                 "measured_fp32_fma_tflops": fp32_peak / 1e12,
-                "measured_fp64_fma_tflops": fp64_peak / 1e12}
+                "measured_fp64_fma_tflops": fp64_peak / 1e12,
+                "frac_of_measured_fma_loop": (ach * 1e12 / (fp64_peak if is64 else fp32_peak)
+                                              if (fp64_peak if is64 else fp32_peak) else None),
+                "fma_pipe_active_ncu": traffic_for(KS_NAMES[dom], "pipe_util.txt"),
+                "fma_pipe_active_source": "ncu sm__pipe_fma_cycles_active of the dominant kernel, from "
+                                          "profiles/pipe_util.txt, used only when it was captured on the "
+                                          "current source of csrc/pairsum.cu (sha1 match), else null"}
     # the Stokeslet pair rate of the step's FP32 sum (the dominant kernel)
     st32 = per_class["stokeslet_fp32_plain"]
     pairs_per_s = st32["pairs"] / (st32["ms"] * 1e-3) if st32["ms"] > 0 else None
