@@ -5,8 +5,8 @@ makes the fiber coefficients large (|u| ~ 1e5..1e8 for velocities of O(10))
 and V a cancellation of them, so no FP64 evaluation of the same discrete
 system can place V closer to the exact solution than the system's
 sensitivity to one rounding of its entries.  oracle.exact.perturbation_floor
-measures that floor; each gate below is the benchmark spec's tolerance or, where
-the measured floor is above it, a small multiple of the floor (both stated
+measures that floor; each gate below is the stated parity tolerance (1e-10
+FP64, 1e-8 mixed) or, where the measured floor is above it, a small multiple of the floor (both stated
 per case, and the floor re-measured in the test)."""
 import numpy as np
 import pytest
@@ -25,7 +25,7 @@ import paper_1602_05650_gb300 as fs  # noqa: E402
 # by one rounding; the library assembles its entries by other FP64 sums
 # (GEMMs over N terms, double-double geometry), each carrying a few roundings,
 # and lands at 3-10x the floor (measured: 6.7e-9, 4.5e-8, 3.7e-6 for the FP64
-# path).  Gate: max(spec tolerance, 20 x floor), the tolerance being
+# path).  Gate: max(parity tolerance, 20 x floor), the tolerance being
 # 1e-10 for the FP64 path and 1e-8 for the mixed path.
 CASES = {
     "cfg1_16x32_straight": (lambda: wl.cfg_small_fp64(0), 8.8e-10),
