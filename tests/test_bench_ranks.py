@@ -48,7 +48,7 @@ def test_single_process_is_unchanged():
 
 
 def test_reference_arm_under_torchrun_prints_one_line():
-    """`bench.py --impl reference` launched as the driver launches it for
+    """`bench.py --impl reference` launched the way a multi-GPU run launches it for
     N = 2 (torchrun, two ranks, gloo): rank 0 alone runs the oracle and prints
     one JSON line, the other rank exits 0 without work."""
     import json
