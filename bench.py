@@ -285,7 +285,8 @@ def run_workload(args, ws, rank, local, fs, torch):
     confined  2,000 x 32 fibers in a radius-20 sphere with 12,288 surface nodes,
               mixed and FP64 steps/s;
     batched   256 independent systems (fibers log-uniform in [8, 512], N in
-              {16, 32, 64}) in one context, mixed steps/s and systems/s;
+              {16, 32, 64}) in one context, mixed steps/s and systems/s:
+              host-driven cycles, graph cycles, and autotuned launch shapes;
     large     the 1,048,576-point Stokeslet sum (8,192 x 128 fibers in
               [0,80]^3, own-fiber exclusion): direct in FP32 hi/lo, FP32 plain
               and float-float over all targets, FP64 over 16,384 sampled
@@ -350,17 +351,20 @@ def run_workload(args, ws, rank, local, fs, torch):
         else:
             systems = wl.batched(256, seed=rank)
         res = {}
-        legs = (("mixed", fs.FS_MIXED, 0), ("fp64", fs.FS_FP64, 0))
+        legs = (("mixed", fs.FS_MIXED, 0, 0), ("fp64", fs.FS_FP64, 0, 0))
         if args.workload == "batched":
-            # the host-driven cycles (kernel timings) and the graph cycles
-            # (one graph launch per restart cycle; event records off)
-            legs = (("mixed", fs.FS_MIXED, 0), ("mixed_graph", fs.FS_MIXED, 1))
-        for name, prec, graph in legs:
+            # the host-driven cycles (kernel timings), the graph cycles (one
+            # graph launch per restart cycle; event records off) and the
+            # autotuned launch shapes (tuned in the warm-up steps)
+            legs = (("mixed", fs.FS_MIXED, 0, 0), ("mixed_graph", fs.FS_MIXED, 1, 0),
+                    ("mixed_autotune", fs.FS_MIXED, 0, 1))
+        for name, prec, graph, tune in legs:
             opt = fs.fs_options_default()
             opt.prec = prec
             opt.tol = 1e-8
             opt.profile = 0 if graph else 1
             opt.use_graph = graph
+            opt.autotune = tune
             if args.workload == "confined":
                 h = fs.fs_create(s.n_per_fiber, s.mu, s.eps, s.E, s.dt, boundary=s.boundary, options=opt,
                                  stream=stream)
@@ -374,11 +378,14 @@ def run_workload(args, ws, rank, local, fs, torch):
             steps = 1 if name == "fp64" else args.steps
             ms, infos = _timed_steps(fs, torch, h, stream, X, L, F, steps, 1 if name == "fp64" else args.warmup)
             ks = fs.fs_kernel_stats(h)
+            tuned = fs.fs_get_tuned_shapes(h)
             fs.fs_destroy(h)
             res[name] = {"ms_per_step": ms, "steps_per_s": 1e3 / ms, "iters": [i.iters for i in infos],
                          "resid": [i.resid for i in infos],
                          "t_ms_rhs_build_solve": [round(x, 2) for x in infos[0].t_ms[:3]],
                          "kernels": {KS_NAMES[k]: [ks[k][0], round(ks[k][1], 2)] for k in range(7) if ks[k][0]}}
+            if tune:
+                res[name]["tuned_shapes"] = {"prec%d_hilo%d" % k: v for k, v in tuned.items()}
         pts = sum(x.n_points for x in systems)
         out.update({"points": int(pts), "systems": len(systems), "tol": 1e-8, "result": res})
         if args.workload == "confined":
@@ -386,6 +393,7 @@ def run_workload(args, ws, rank, local, fs, torch):
         else:
             out["systems_per_s"] = len(systems) * res["mixed"]["steps_per_s"]
             out["systems_per_s_graph"] = len(systems) * res["mixed_graph"]["steps_per_s"]
+            out["systems_per_s_autotune"] = len(systems) * res["mixed_autotune"]["steps_per_s"]
             out["fibers"] = [int(min(x.n_fibers for x in systems)), int(max(x.n_fibers for x in systems))]
     elif args.workload == "sediment":
         # Sec. 4.3: the four clouds (1,024 fibers x 16 points, L/R0 = 0.15,

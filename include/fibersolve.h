@@ -169,9 +169,20 @@ typedef struct {
                                product's bound); 0 = FP64 CUDA cores (default 1) */
     int32_t tc_lu;          /* 1 = the block LU's trailing updates A22 -= L21 U12 (panels
                                of 32 columns) on the bf16 tensor cores by the same split,
-                               the panels (pivoting) on the FP64 pipe; used while a
-                               fiber's 4N x 32 panel fits in shared memory (N <= 200),
-                               else the FP64 LU; 0 = FP64 LU (default 1) */
+                               the panels (pivoting) on the FP64 pipe; used while one CTA
+                               holds a fiber's panel rows one per thread (4N <= 512, i.e.
+                               N <= 128), else the FP64 LU; 0 = FP64 LU (default 1) */
+    int32_t autotune;       /* 1 = the fiber far field's launch shape (targets per thread,
+                               tile_override's ids 1..3) chosen per precision class by
+                               timing: the first sum of each class (outside a graph
+                               capture) runs every shape once untimed and once timed on
+                               the context's stream and keeps the fastest for the
+                               context's life (fs_get_tuned_shapes).  Results then depend
+                               on that choice through the summation order, so contexts
+                               tuned differently agree to the sums' accuracy, not bit for
+                               bit; ignored when tile_override > 0; refused with
+                               use_graph (a captured cycle keeps its capture's shapes).
+                               0 = the measured default shapes (default 0) */
 } fs_options;
 
 /* Direct-sum kernel classes reported by fs_kernel_stats. */
@@ -394,6 +405,12 @@ fs_status fs_get_self_block(fs_ctx *ctx, int32_t fiber, double *out);
  * Synchronises the stream.  For tests and diagnostics: with fs_options.tc_lu
  * it shows the LU with tensor-core trailing updates. */
 fs_status fs_get_block_lu(fs_ctx *ctx, int32_t fiber, double *lu, int32_t *piv);
+
+/* The fiber far field's launch shapes chosen by fs_options.autotune: out[2 p
+ * + h] for sum precision p (fs_sum_precision) with (h = 1) or without (h = 0)
+ * hi/lo coordinates, a tile_override id 1..3, or 0 where that class has not
+ * been tuned (yet, or autotune is off).  out: HOST array of 8 int32. */
+fs_status fs_get_tuned_shapes(const fs_ctx *ctx, int32_t *out);
 
 /* One implicit backward-Euler step (Sec. 3.2, set:time-stepping): solve
  * P^-1 A u = P^-1 b by GMRES with the block-Jacobi preconditioner P of Eq. prec

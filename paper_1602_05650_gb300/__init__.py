@@ -21,7 +21,7 @@ __all__ = ["fs_options_default", "fs_create", "fs_create_batch", "fs_batch_info"
            "fs_stokeslet_apply", "fs_stresslet_apply", "fs_surface_apply", "fs_build_precond",
            "fs_step", "fs_sizes", "fs_last_error", "fs_kernel_stats", "fs_kernel_launches",
            "fs_probe_fma", "fs_estimate_bytes", "fs_device_bytes", "fs_server_create", "fs_submit",
-           "fs_poll", "fs_server_wait", "fs_server_stats", "fs_server_batches", "fs_server_destroy", "Server", "fs_get_self_block", "fs_get_block_lu",
+           "fs_poll", "fs_server_wait", "fs_server_stats", "fs_server_batches", "fs_server_destroy", "Server", "fs_get_self_block", "fs_get_block_lu", "fs_get_tuned_shapes",
            "FsError",
            "fs_set_growth", "fs_get_lengths", "fs_get_unknowns", "fs_dynamic_instability",
            "FS_FP64", "FS_MIXED",
@@ -493,6 +493,15 @@ def fs_get_block_lu(h: Handle, fiber: int, n_points: int):
     _check(_native.load().fs_get_block_lu(h.ptr, int(fiber), lu.ctypes.data_as(ctypes.c_void_p),
                                           piv.ctypes.data_as(ctypes.c_void_p)), "fs_get_block_lu")
     return lu.reshape(n, n).T, piv
+
+
+def fs_get_tuned_shapes(h: Handle):
+    """The far field's autotuned launch shapes: {(sum precision, hi/lo): shape
+    id 1..3} for the classes tuned so far (fs_options.autotune)."""
+    out = np.zeros(8, dtype=np.int32)
+    _check(_native.load().fs_get_tuned_shapes(h.ptr, out.ctypes.data_as(ctypes.c_void_p)),
+           "fs_get_tuned_shapes")
+    return {(p, hl): int(out[2 * p + hl]) for p in range(4) for hl in range(2) if out[2 * p + hl]}
 
 
 def fs_server_batches(sv: Server) -> int:

@@ -37,7 +37,8 @@ class fs_options(ctypes.Structure):
                 ("max_refine", c_int32), ("inner_tol", c_double), ("delta_over_L", c_double),
                 ("lsb", c_int32), ("use_graph", c_int32), ("tile_override", c_int32),
                 ("profile", c_int32), ("relax", c_int32), ("tree_order", c_int32), ("tree_theta", c_double),
-                ("growth_implicit", c_int32), ("tc_blocks", c_int32), ("tc_lu", c_int32)]
+                ("growth_implicit", c_int32), ("tc_blocks", c_int32), ("tc_lu", c_int32),
+                ("autotune", c_int32)]
 
 
 class fs_kernel_stat(ctypes.Structure):
@@ -106,6 +107,7 @@ SIGNATURES = {
     "fs_server_batches": (c_int32, [P, ctypes.POINTER(c_int64)]),
     "fs_get_self_block": (c_int32, [P, c_int32, P]),
     "fs_get_block_lu": (c_int32, [P, c_int32, P, P]),
+    "fs_get_tuned_shapes": (c_int32, [P, P]),
     "fs_last_error": (ctypes.c_char_p, []),
     "fs_status_str": (ctypes.c_char_p, [c_int32]),
 }

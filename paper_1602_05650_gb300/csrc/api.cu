@@ -93,12 +93,17 @@ fs_status check_options(const fs_options &o, const char *who, int n_systems)
         set_error("%s: delta_over_L must be finite and >= 0", who);
         return FS_EINVAL;
     }
-    if ((o.lsb | o.relax | o.profile | o.growth_implicit | o.tc_blocks | o.tc_lu) & ~1) {
-        set_error("%s: lsb, relax, profile, growth_implicit, tc_blocks and tc_lu are 0 or 1", who);
+    if ((o.lsb | o.relax | o.profile | o.growth_implicit | o.tc_blocks | o.tc_lu | o.autotune) & ~1) {
+        set_error("%s: lsb, relax, profile, growth_implicit, tc_blocks, tc_lu and autotune are 0 or 1", who);
         return FS_EINVAL;
     }
     if (o.use_graph != 0 && o.use_graph != 1) {
         set_error("%s: use_graph is 0 or 1", who);
+        return FS_EINVAL;
+    }
+    if (o.autotune && o.use_graph) {
+        // a captured cycle keeps the shapes (and work lists) of its capture
+        set_error("%s: autotune and use_graph exclude each other", who);
         return FS_EINVAL;
     }
     if (o.tile_override < 0 || o.tile_override > 3) {
@@ -169,6 +174,7 @@ fs_status fs_options_default(fs_options *o)
     o->growth_implicit = 0;
     o->tc_blocks = 1;
     o->tc_lu = 1;
+    o->autotune = 0;
     return FS_OK;
 }
 

@@ -247,6 +247,8 @@ struct fs_ctx {
     int *h_gst = nullptr, *h_gj = nullptr;
     double *h_gbuf = nullptr;     // pinned block behind the host mirrors
     bool capturing = false;       // kernels are being captured into a graph
+    // autotuned far-field shapes, [2 sum precision + hi/lo] (0: not tuned)
+    int tuned[8] = {};
     cudaStream_t cap_stream = nullptr;   // the stream graphs are captured on
     std::vector<fs::CycleGraph> graphs;
     // tensor-core block build (opt.tc_blocks): digit planes of a chunk of

@@ -473,6 +473,7 @@ PairSumArgs far_field_args(fs_ctx *c, int sum_prec, bool hilo, const std::vector
     a.sum_prec = sum_prec;
     a.hilo = hilo;
     a.shape_override = c->opt.tile_override;
+    if (a.shape_override == 0 && c->opt.autotune) a.shape_override = c->tuned[2 * sum_prec + (hilo ? 1 : 0)];
     double pairs = 0.0;
     groups.clear();
     if ((c->S > 1 || c->worklist) && act) {
@@ -496,6 +497,50 @@ PairSumArgs far_field_args(fs_ctx *c, int sum_prec, bool hilo, const std::vector
     return a;
 }
 
+// The autotuner: the far field of `a` once untimed and once timed (CUDA
+// events on the context's stream) in every launch shape 1..3; *shape = the
+// fastest.  Each run overwrites a.out (the caller's sum then writes the
+// result), and none is recorded in the kernel profile.  Synchronises the
+// stream once per shape.
+fs_status tune_far_field(fs_ctx *c, PairSumArgs a, int *shape)
+{
+    a.prof = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    FS_CUDA(cudaEventCreate(&e0));
+    const cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        FS_CUDA(ce);
+    }
+    float best = 0.0f;
+    fs_status st = FS_OK;
+    for (int s = 1; s <= 3 && st == FS_OK; ++s) {
+        a.shape_override = s;
+        st = c->scratch.reserve(pairsum_scratch_bytes(a.kind, a.n_src, a.n_tgt, a.sum_prec, s), c->stream);
+        if (st == FS_OK) st = pairsum(a, c->scratch.ptr, c->scratch.bytes, c->d_status, c->stream);
+        if (st != FS_OK) break;
+        float ms = 0.0f;
+        if (cudaEventRecord(e0, c->stream) != cudaSuccess ||
+            (st = pairsum(a, c->scratch.ptr, c->scratch.bytes, c->d_status, c->stream)) != FS_OK ||
+            cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            if (st == FS_OK) {
+                set_error("autotune: event timing failed: %s", cudaGetErrorString(cudaGetLastError()));
+                st = FS_ECUDA;
+            }
+            break;
+        }
+        if (*shape == 0 || ms < best) {
+            best = ms;
+            *shape = s;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != FS_OK) *shape = 0;
+    return st;
+}
+
 // Far field at the fiber nodes for the active systems (each target block sums
 // its own system's sources only): ubar = (1/8 pi mu) sum_{other fibers} G0 W f
 fs_status far_field(fs_ctx *c, int sum_prec, bool hilo, const std::vector<int> *act)
@@ -508,6 +553,12 @@ fs_status far_field(fs_ctx *c, int sum_prec, bool hilo, const std::vector<int> *
     }
     std::vector<int4> groups;
     PairSumArgs a = far_field_args(c, sum_prec, hilo, act, groups);
+    if (a.shape_override == 0 && c->opt.autotune && !c->capturing) {
+        // this class's first sum: time the shapes, keep the fastest
+        int &shape = c->tuned[2 * sum_prec + (hilo ? 1 : 0)];
+        FS_TRY(tune_far_field(c, a, &shape));
+        a.shape_override = shape;
+    }
     FS_TRY(c->scratch.reserve(pairsum_scratch_bytes(a.kind, a.n_src, a.n_tgt, sum_prec, a.shape_override),
                               c->stream));
     FS_TRY(pairsum(a, c->scratch.ptr, c->scratch.bytes, c->d_status, c->stream));
@@ -1571,6 +1622,16 @@ fs_status fs_get_self_block(fs_ctx *c, int32_t fiber, double *out)
     FS_CUDA(cudaMemcpyAsync(out, c->d_B + c->blk_ptr[fiber], static_cast<size_t>(n * n) * sizeof(double),
                             cudaMemcpyDeviceToHost, c->stream));
     FS_CUDA(cudaStreamSynchronize(c->stream));
+    return FS_OK;
+}
+
+fs_status fs_get_tuned_shapes(const fs_ctx *c, int32_t *out)
+{
+    if (!c || !out) {
+        set_error("fs_get_tuned_shapes: NULL context or output");
+        return FS_EINVAL;
+    }
+    for (int i = 0; i < 8; ++i) out[i] = c->tuned[i];
     return FS_OK;
 }
 

@@ -105,7 +105,7 @@ def test_step_options_are_validated_without_gpu(lib):
            ("inner_tol", 0.0), ("max_iter", 0), ("restart", 0), ("restart", 251),
            ("max_refine", 0), ("delta_over_L", -0.01), ("delta_over_L", float("inf")),
            ("lsb", 2), ("relax", -1), ("profile", 3), ("use_graph", 2),
-           ("tile_override", 4), ("tile_override", -1)]
+           ("tile_override", 4), ("tile_override", -1), ("tc_lu", 2), ("autotune", 2)]
     for field, value in bad:
         o = _native.fs_options()
         lib.fs_options_default(ctypes.byref(o))
@@ -115,6 +115,13 @@ def test_step_options_are_validated_without_gpu(lib):
         assert not out.value
         msg = lib.fs_last_error()
         assert msg.startswith(b"fs_create:") and field.split("_")[0].encode() in msg, (field, msg)
+    # the autotuner and graph cycles exclude each other
+    o = _native.fs_options()
+    lib.fs_options_default(ctypes.byref(o))
+    o.autotune, o.use_graph = 1, 1
+    assert lib.fs_create(ctypes.byref(out), 1, ppf, 1.0, 1e-3, 1.0, 1e-3, None, ctypes.byref(o),
+                         None) == _native.FS_EINVAL
+    assert b"autotune" in lib.fs_last_error()
     # the same checks guard the batch constructor
     o = _native.fs_options()
     lib.fs_options_default(ctypes.byref(o))
