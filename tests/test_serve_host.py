@@ -44,6 +44,9 @@ def test_estimate_grows_with_the_problem(lib):
     # of both operands (256 rows, 32 inner columns) and an exponent per row
     lu = 1024 * 2 * (9 * 256 * 32 * 2 + 256 * 4)
     assert lu <= est(lib, [64] * 1024, tc_blocks=0) - e64 < lu + (16 << 20)
+    # beyond 4N = 512 the LU stays on the FP64 pipe and allocates no planes
+    assert est(lib, [160] * 8, tc_blocks=0) == est(lib, [160] * 8, tc_blocks=0, tc_lu=0)
+    assert est(lib, [128] * 8, tc_blocks=0) > est(lib, [128] * 8, tc_blocks=0, tc_lu=0)
     # mixed precision keeps the outer flexible-GMRES space on top of the inner one
     assert est(lib, [32] * 100, prec=_native.FS_MIXED) > est(lib, [32] * 100, prec=_native.FS_FP64)
     # a longer restart keeps more Krylov vectors
