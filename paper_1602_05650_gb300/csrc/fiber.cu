@@ -1238,32 +1238,19 @@ __global__ void __launch_bounds__(256) k_lu(FiberTable F, double *__restrict__ B
 //   k_lu_trail: A22 -= L21 U12 on the bf16 tensor cores by the split of the
 //     block build (nine balanced base-128 digits of each row / column scaled
 //     by its power of two, exact FP32 sums per diagonal for K = 32: at most
-//     9 x 32 x 65 x 65 < 2^24), rounded once to FP64 and subtracted.
+//     9 x 32 x 65 x 65 < 2^24), the diagonals summed as integers and folded
+//     into FP64, then subtracted.
 // The product's error is a few units of 2^-62 of (row max of L21) x (column
-// max of U12), below the rounding of the FP64 update it replaces.  The pivots
-// are chosen by the same rule as k_lu from the same column values up to that
-// rounding; piv and dinv as k_lu.
+// max of U12): on that row-and-column scale no larger than the rounding of
+// the FP64 update it replaces (entry by entry it can be, where an entry's
+// large l and large u sit at different k).  The pivots are chosen by the same
+// rule as k_lu from the same column values up to that rounding; piv and dinv
+// as k_lu.
 constexpr int kLuTcBW = 32;
 
 // Rows of one operand's digit planes: trailing rows (or columns) of a panel,
 // at most 4 N - 32, padded to 64.
 __host__ __device__ inline int lu_tc_rows(int max_N) { return (4 * max_N + 63) / 64 * 64; }
-
-// One plane row from one value per lane (k = lane): the row's exponent from
-// the warp's largest magnitude, then the nine digits of the lane's value.
-__device__ __forceinline__ void oz_slice_lane(const OzOperand &O, int f, int row, double v)
-{
-    const int lane = threadIdx.x & 31;
-    // the largest magnitude through bit patterns (integer work)
-    long long mb = __double_as_longlong(v) & 0x7fffffffffffffffLL;
-    for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
-    const int e = mb > 0 ? static_cast<int>(mb >> 52) - 1022 : 0;
-    if (lane == 0) O.e[static_cast<int64_t>(f) * O.rows_p + row] = e;
-    float a[kOzDigits];
-    oz_digits(mb > 0 ? v : 0.0, e, a);
-#pragma unroll
-    for (int s = 0; s < kOzDigits; ++s) O.plane(f, s)[static_cast<int64_t>(row) * O.kp + lane] = __float2bfloat16_rn(a[s]);
-}
 
 // One plane row from a thread's own 32 values (k = 0..31): the row's
 // exponent from the largest magnitude (bit patterns, integer work), then the
